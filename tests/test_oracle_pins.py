@@ -1,0 +1,283 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+The oracle evaluates u(x) = (1/2pi) sum_B int_B log|x-y| f_B(y) dy, which is
+v_bulk = -int Phi f of the paper (Sec. 3.2, eq. (vbulk); Phi from Sec. 2), so
+that Laplace(u) = f.  Each test below checks it against something other than
+itself:
+  * closed forms: constant density on a rectangle, centre of a square,
+    radially symmetric Gaussian (exponential integral);
+  * an independent library quadrature (scipy dblquad) on one leaf;
+  * the PDE itself: Laplace(u) = f by spectral differentiation;
+  * exact invariants: scaling law, dihedral symmetry, linearity, additivity.
+A dropped term, a wrong sign or a transposed index in the oracle fails at
+least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from numpy.polynomial import chebyshev as C
+
+pytestmark = []
+
+
+def _F(a, b):
+    """int_0^a int_0^b (1/2) log(x^2 + y^2) dy dx, signed a, b (closed form)."""
+    if a == 0.0 or b == 0.0:
+        return 0.0
+    s = math.copysign(1.0, a) * math.copysign(1.0, b)
+    a, b = abs(a), abs(b)
+    return s * 0.5 * (a * b * (math.log(a * a + b * b) - 3.0)
+                      + a * a * math.atan(b / a) + b * b * math.atan(a / b))
+
+
+def rect_potential(x, y, x0, x1, y0, y1):
+    """(1/2pi) int_R log|x-y| dy for the constant density 1 on R (closed form)."""
+    return (_F(x1 - x, y1 - y) - _F(x0 - x, y1 - y) - _F(x1 - x, y0 - y)
+            + _F(x0 - x, y0 - y)) / (2.0 * math.pi)
+
+
+def uniform_leaves(level):
+    n = 2 ** level
+    ix, iy = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    return [level] * (n * n), ix.ravel().tolist(), iy.ravel().tolist()
+
+
+def refine_leaves(pred, max_level):
+    """Dyadic leaves of [-1,1]^2 obtained by splitting every box where pred(cx,cy,r) holds."""
+    out = ([], [], [])
+    stack = [(0, 0, 0)]
+    while stack:
+        lv, i, j = stack.pop()
+        r = 1.0 / 2 ** lv
+        cx, cy = -1.0 + (2 * i + 1) * r, -1.0 + (2 * j + 1) * r
+        if lv < max_level and pred(cx, cy, r):
+            for di in (0, 1):
+                for dj in (0, 1):
+                    stack.append((lv + 1, 2 * i + di, 2 * j + dj))
+        else:
+            out[0].append(lv)
+            out[1].append(i)
+            out[2].append(j)
+    return out
+
+
+def test_s_rule_moments(oracle_mod):
+    """The Duffy-ray product rule integrates s^(k+1) log s exactly: -1/(k+2)^2."""
+    for ns in (16, 24, 32):
+        s, wr, wl = oracle_mod.s_rule(ns)
+        for k in range(ns):
+            assert abs(np.dot(wl, s ** k) + 1.0 / (k + 2) ** 2) < 1e-15
+            assert abs(np.dot(wr, s ** k) - 1.0 / (k + 2)) < 1e-15
+
+
+def test_nodes_are_first_kind_chebyshev(oracle_mod):
+    for p in (8, 12, 16):
+        x = oracle_mod.cheb_nodes(p)
+        assert np.all(np.diff(x) > 0)
+        # first-kind points are the roots of T_p
+        Tp = C.chebval(x, [0] * p + [1])
+        assert np.abs(Tp).max() < 1e-13
+
+
+def test_interpolant_reproduces_polynomials(oracle_mod):
+    """f_B is the tensor interpolant: exact for degree <= p-1 in each variable."""
+    rng = np.random.default_rng(5)
+    for p in (8, 16):
+        c = rng.standard_normal((p, p)) / (1 + np.add.outer(np.arange(p), np.arange(p))) ** 1.5
+        x = oracle_mod.cheb_nodes(p)
+        X, Y = np.meshgrid(x, x, indexing="xy")   # [jy][jx]
+        fv = C.chebval2d(X, Y, c.T)               # c[a][b]: a in x, b in y
+        pts = rng.uniform(-1, 1, (50, 2))
+        got = oracle_mod.interp(p, fv, pts)
+        want = C.chebval2d(pts[:, 0], pts[:, 1], c.T)
+        assert np.abs(got - want).max() < 1e-13
+
+
+def test_centre_of_square(oracle_mod):
+    """int_{[-1,1]^2} log|y| dy = 2 ln 2 + pi - 6."""
+    for p in (8, 16):
+        geom = oracle_mod.leaf_geometry([0], [0], [0])
+        u = oracle_mod.potential(p, geom, np.ones((1, p, p)), np.array([[0.0, 0.0]]))
+        assert abs(u[0] * 2 * math.pi - (2 * math.log(2) + math.pi - 6)) < 2e-15
+
+
+def test_constant_density_closed_form(oracle_mod):
+    """f = 1 on an adaptive cover of [-1,1]^2: u equals the rectangle formula at
+    every node and at off-grid points near edges, corners and outside."""
+    p = 12
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: abs(cx - 0.3) + abs(cy + 0.2) < 3 * r, 4)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    f = np.ones((len(lv), p, p))
+    nodes = oracle_mod.leaf_nodes(geom, p).reshape(-1, 2)
+    rng = np.random.default_rng(0)
+    pick = nodes[rng.choice(nodes.shape[0], 400, replace=False)]
+    extra = np.array([[1.0 + 1e-3, 0.3], [-1.2, -1.0000001], [3.0, 4.0], [0.9999, 0.5],
+                      [0.5, 0.5], [0.0, 0.0], [-1.0, -1.0], [0.25, -0.5]])
+    pts = np.vstack([pick, extra])
+    u = oracle_mod.potential(p, geom, f, pts)
+    ex = np.array([rect_potential(x, y, -1, 1, -1, 1) for x, y in pts])
+    assert np.abs(u - ex).max() < 1e-14 * np.abs(ex).max()
+
+
+def _dblquad_leaf(fun, xi, eta):
+    """int_{[-1,1]^2} log|x - y| fun(y) dy by scipy dblquad, split at x so that
+    the log singularity sits on rectangle corners."""
+    import warnings
+
+    from scipy import integrate
+    xs = sorted(set([-1.0, 1.0] + ([xi] if -1 < xi < 1 else [])))
+    ys = sorted(set([-1.0, 1.0] + ([eta] if -1 < eta < 1 else [])))
+    tot = 0.0
+    with warnings.catch_warnings():
+        warnings.simplefilter("ignore")
+        for a0, a1 in zip(xs[:-1], xs[1:]):
+            for b0, b1 in zip(ys[:-1], ys[1:]):
+                v, _ = integrate.dblquad(
+                    lambda y, x: 0.5 * np.log((x - xi) ** 2 + (y - eta) ** 2) * fun(x, y),
+                    a0, a1, b0, b1, epsabs=1e-15, epsrel=1e-13)
+                tot += v
+    return tot
+
+
+def test_one_leaf_against_scipy(oracle_mod):
+    """Independent library quadrature on a single leaf with a random polynomial
+    density: targets inside (node, near an edge, near a corner), just outside,
+    and far away."""
+    pytest.importorskip("scipy")
+    p = 8
+    rng = np.random.default_rng(11)
+    c = rng.standard_normal((p, p)) / (1 + np.add.outer(np.arange(p), np.arange(p)))
+    x = oracle_mod.cheb_nodes(p)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    fv = C.chebval2d(X, Y, c.T)[None]
+    geom = oracle_mod.leaf_geometry([0], [0], [0])
+    fun = lambda a, b: C.chebval2d(a, b, c.T)
+    pts = np.array([[x[2], x[5]], [-0.998, 0.997], [1.003, -0.4], [2.5, -3.0]])
+    u = oracle_mod.potential(p, geom, fv, pts)
+    ref = np.array([_dblquad_leaf(fun, a, b) for a, b in pts]) / (2 * math.pi)
+    assert np.abs(u - ref).max() < 5e-14 * max(1.0, np.abs(ref).max())
+
+
+def test_gaussian_closed_form(oracle_mod):
+    """Radial Gaussian a exp(-r^2/(2 s^2)) far from the root edges (tail < 1e-17):
+    u(r) = a s^2 [ln r + E1(r^2/(2 s^2))/2], u(0) = a s^2 [ln(s sqrt 2) - gamma/2]."""
+    special = pytest.importorskip("scipy.special")
+    p = 16
+    a, s, c0 = 1.7, 0.04, np.array([0.1, -0.2])
+    lv, ix, iy = refine_leaves(
+        lambda cx, cy, r: (math.hypot(cx - c0[0], cy - c0[1]) < 10 * s + 1.5 * r) and r > 0.6 * s, 9)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    nodes = oracle_mod.leaf_nodes(geom, p)
+    fvals = a * np.exp(-((nodes[..., 0] - c0[0]) ** 2 + (nodes[..., 1] - c0[1]) ** 2) / (2 * s * s))
+    # the interpolant must itself resolve f (checked on random points of each leaf)
+    rng = np.random.default_rng(1)
+    worst = 0.0
+    for b in rng.choice(len(lv), 12, replace=False):
+        q = rng.uniform(-1, 1, (20, 2))
+        fi = oracle_mod.interp(p, fvals[b], q)
+        phys = geom[b, :2] + geom[b, 2] * q
+        fe = a * np.exp(-((phys[:, 0] - c0[0]) ** 2 + (phys[:, 1] - c0[1]) ** 2) / (2 * s * s))
+        worst = max(worst, np.abs(fi - fe).max())
+    assert worst < 1e-12 * a
+    pts = np.array([c0, c0 + [0.013, 0.0], c0 + [0.05, -0.07], c0 + [0.3, 0.41], [0.9, 0.9]])
+    u = oracle_mod.potential(p, geom, fvals.reshape(len(lv), p, p), pts)
+    r = np.hypot(pts[:, 0] - c0[0], pts[:, 1] - c0[1])
+    ref = np.empty_like(r)
+    ref[0] = a * s * s * (math.log(s * math.sqrt(2.0)) - 0.5772156649015329 / 2)
+    ref[1:] = a * s * s * (np.log(r[1:]) + 0.5 * special.exp1(r[1:] ** 2 / (2 * s * s)))
+    assert np.abs(u - ref).max() < 5e-13 * np.abs(ref).max()
+
+
+def test_laplacian_of_potential_is_density(oracle_mod):
+    """Laplace(u) = +f on a leaf (sign convention of the paper): spectral second
+    derivatives of u at the leaf nodes reproduce f."""
+    p = 16
+    lv, ix, iy = uniform_leaves(2)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    nodes = oracle_mod.leaf_nodes(geom, p)
+    fv = np.exp(-2.0 * ((nodes[..., 0] - 0.2) ** 2 + (nodes[..., 1] + 0.1) ** 2)) * (1 + nodes[..., 0])
+    leaf = 5
+    u = oracle_mod.potential(p, geom, fv, nodes[leaf]).reshape(p, p)  # [jy][jx]
+    x = oracle_mod.cheb_nodes(p)
+    V = C.chebvander2d(np.tile(x, p), np.repeat(x, p), [p - 1, p - 1])   # columns (i,j): T_i(x)T_j(y)
+    coef = np.linalg.solve(V, u.ravel()).reshape(p, p)               # coef[i][j]
+    r = geom[leaf, 2]
+    uxx = C.chebder(coef, 2, axis=0) / r ** 2
+    uyy = C.chebder(coef, 2, axis=1) / r ** 2
+    lap = (C.chebval2d(np.tile(x, p), np.repeat(x, p), np.pad(uxx, ((0, 2), (0, 0))))
+           + C.chebval2d(np.tile(x, p), np.repeat(x, p), np.pad(uyy, ((0, 0), (0, 2)))))
+    err = np.abs(lap - fv[leaf].ravel()).max() / np.abs(fv).max()
+    assert err < 1e-8, err
+
+
+def test_scaling_law(oracle_mod):
+    """Scaling the tree and the density support by s: u_s(s x) = s^2 u(x) + s^2 ln(s) M/(2pi)."""
+    p = 8
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: cx + cy > -0.5 and r > 0.3, 3)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal((len(lv), p, p))
+    g1 = oracle_mod.leaf_geometry(lv, ix, iy)
+    sc = 0.37
+    g2 = oracle_mod.leaf_geometry(lv, ix, iy, x0=-sc, y0=-sc, L=2 * sc)
+    pts = rng.uniform(-1.2, 1.2, (30, 2))
+    u1 = oracle_mod.potential(p, g1, f, pts)
+    u2 = oracle_mod.potential(p, g2, f, sc * pts)
+    # M = int f over the unscaled domain, by the leaf quadrature of the oracle's own interpolant
+    w1 = oracle_mod.potential(p, g1, f, np.array([[1e6, 0.0]]))
+    M = w1[0] * 2 * math.pi / math.log(1e6)   # far field: u -> M log|x| / 2pi (+ O(1/|x|))
+    M_exact = sum(np.sum(f[b] * _fejer_tensor(p)) * g1[b, 2] ** 2 for b in range(len(lv)))
+    assert abs(M - M_exact) < 1e-5 * abs(M_exact) + 1e-5
+    want = sc * sc * u1 + sc * sc * math.log(sc) * M_exact / (2 * math.pi)
+    assert np.abs(u2 - want).max() < 1e-14 * np.abs(want).max()
+
+
+def _fejer_tensor(p):
+    """Fejer first-rule weights (exact for degree <= p-1 on first-kind nodes)."""
+    th = (2 * np.arange(p) + 1) * math.pi / (2 * p)
+    w = np.array([2.0 / p * (1 - 2 * sum(math.cos(2 * k * t) / (4 * k * k - 1) for k in range(1, p // 2 + 1)))
+                  for t in th])[::-1]
+    return np.outer(w, w)
+
+
+def test_dihedral_symmetry(oracle_mod):
+    """Rotating the tree and the density by 90 degrees rotates the potential."""
+    p = 8
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: cx > 0.1 and cy < 0.3 and r > 0.2, 3)
+    rng = np.random.default_rng(7)
+    f = rng.standard_normal((len(lv), p, p))
+    g = oracle_mod.leaf_geometry(lv, ix, iy)
+    # rotation (x, y) -> (-y, x): leaf (l, i, j) -> (l, 2^l - 1 - j, i); node (jx, jy) -> (p-1-jy, jx)
+    lv2 = lv
+    ix2 = [2 ** l - 1 - j for l, j in zip(lv, iy)]
+    iy2 = list(ix)
+    f2 = np.empty_like(f)
+    for jy in range(p):
+        for jx in range(p):
+            f2[:, jx, p - 1 - jy] = f[:, jy, jx]
+    g2 = oracle_mod.leaf_geometry(lv2, ix2, iy2)
+    pts = rng.uniform(-1.1, 1.1, (25, 2))
+    u1 = oracle_mod.potential(p, g, f, pts)
+    u2 = oracle_mod.potential(p, g2, f2, np.stack([-pts[:, 1], pts[:, 0]], axis=1))
+    assert np.abs(u1 - u2).max() < 1e-14 * np.abs(u1).max()
+
+
+def test_linearity_and_source_split(oracle_mod):
+    """u is linear in f, and restricting sources to complementary sets adds up."""
+    p = 8
+    lv, ix, iy = uniform_leaves(2)
+    g = oracle_mod.leaf_geometry(lv, ix, iy)
+    rng = np.random.default_rng(9)
+    f1 = rng.standard_normal((16, p, p))
+    f2 = rng.standard_normal((16, p, p))
+    pts = rng.uniform(-1, 1, (20, 2))
+    u1 = oracle_mod.potential(p, g, f1, pts)
+    u2 = oracle_mod.potential(p, g, f2, pts)
+    u12 = oracle_mod.potential(p, g, 2.0 * f1 - 0.5 * f2, pts)
+    assert np.abs(u12 - (2 * u1 - 0.5 * u2)).max() < 1e-14 * np.abs(u12).max()
+    A = np.arange(0, 16, 2)
+    B = np.arange(1, 16, 2)
+    n = pts.shape[0]
+    uA = oracle_mod.potential(p, g, f1, pts, sources=(np.arange(n + 1) * len(A), np.tile(A, n)))
+    uB = oracle_mod.potential(p, g, f1, pts, sources=(np.arange(n + 1) * len(B), np.tile(B, n)))
+    assert np.abs(uA + uB - u1).max() < 1e-14 * np.abs(u1).max()
