@@ -1,0 +1,200 @@
+/*
+ * boxcode.h -- C ABI of the GB300 machine code: the free-space 2D Laplace volume
+ * potential on an adaptive quadtree of p x p Chebyshev leaf boxes.
+ *
+ * The operation (paper Sec. 3.2, eq. (vbulk), with Phi from Sec. 2):
+ *
+ *     u(x_i) = (1/2pi) * sum_{leaves B} int_B log|x_i - y| f_B(y) dy
+ *
+ * i.e. u = v_bulk = -int_{Omega_B} Phi(x,y) f(y) dy with Omega_B the union of
+ * the leaves, so that Laplace(u) = f.  f_B is the tensor-product polynomial of
+ * degree p-1 per variable interpolating the leaf's node values (Sec. 3.2.1).
+ * The x_i are the nodes of all leaves.  Leaves form a 2:1-balanced quadtree
+ * (Sec. 3.2.1, last paragraph): leaves that touch, across an edge or a
+ * corner, differ by at most one level.
+ *
+ * Conventions shared by every call:
+ *   - Nodes: first-kind Chebyshev points x_j = -cos((2j+1) pi / (2p)),
+ *     j = 0..p-1 (ascending), scaled to each leaf.  A leaf's values are p*p
+ *     doubles, row-major with the x index fastest: v[jy*p + jx].
+ *   - Arrays of leaf values are [nleaf][p][p] FP64, contiguous, with leaves in
+ *     the order the caller gave when creating the tree.
+ *   - Ownership: the context owns the tables, a tree owns its lists and its
+ *     workspaces; the caller owns every array it passes and the library never
+ *     frees or retains caller memory beyond the call (asynchronous calls read
+ *     and write it in stream order).
+ *   - Errors: every call returns a bc_status; nothing aborts.  The message of
+ *     the last failure on the calling thread is bc_last_error().  Work queued
+ *     on a stream reports device-side failures at the next synchronising
+ *     call on that tree or context (bc_sync).
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device calls are ordered on it.
+ *   - Results are overwritten, never accumulated.
+ *   - Thread safety: calls on different trees may run concurrently; calls on
+ *     the same tree must be serialised by the caller (a tree's workspaces are
+ *     shared by its applies).
+ */
+#ifndef BOXCODE_H
+#define BOXCODE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bc_ctx bc_ctx;   /* opaque: device, order p, tables */
+typedef struct bc_tree bc_tree; /* opaque: leaves, interaction lists, workspaces */
+
+typedef enum {
+    BC_OK = 0,
+    BC_ERR_ARG = -1,         /* invalid argument (NULL, size, range) */
+    BC_ERR_TREE = -2,        /* leaves overlap, leave gaps, or are not 2:1 balanced */
+    BC_ERR_CUDA = -3,        /* a CUDA runtime error; message names it */
+    BC_ERR_OOM = -4,         /* host or device allocation failed */
+    BC_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up */
+    BC_ERR_UNSUPPORTED = -6, /* valid request this build does not provide */
+    BC_ERR_STATE = -7        /* call order violated (e.g. apply before tables) */
+} bc_status;
+
+typedef enum {
+    BC_FP64 = 0,       /* every stage in native FP64 */
+    BC_SPLIT_BF16 = 1  /* near-field table contractions on BF16 tensor cores with
+                          FP64 data split into exact BF16 slices, FP32
+                          accumulation, integer/FP64 recombination; the far
+                          field, log corrections and final sums stay FP64 */
+} bc_precision;
+
+typedef struct {
+    int p;            /* nodes per side, 4..16 (paper uses 16) */
+    int nterms;       /* far-field expansion terms P+1; 0 = default (see DESIGN) */
+    int node_kind;    /* 1 = first-kind Chebyshev (the only kind provided); 0 = default */
+    int split_slices; /* BF16 slices per operand for BC_SPLIT_BF16; 0 = default */
+    int autotune;     /* 1 = time tile shapes on first batched apply; 0 = fixed */
+} bc_config;
+
+/* Counts describing a tree, for flop and byte accounting. */
+typedef struct {
+    int64_t nleaf, nbox, nlevels;  /* nlevels = max leaf level + 1 */
+    int64_t n_near;  /* near-field (leaf,leaf) slots, self included */
+    int64_t n_v;     /* M2L translations (V lists) */
+    int64_t n_w;     /* multipole-to-node evaluations (W lists, "list 3") */
+    int64_t n_x;     /* node-density-to-local conversions (X lists, "list 4") */
+    int64_t n_nonleaf; /* boxes at level >= 2 with children (M2M/L2L work) */
+    int64_t n_down;  /* boxes at level >= 2 (local expansions) */
+} bc_tree_stats;
+
+/* Create a context on CUDA device `device` for order cfg->p.  Allocates
+ * nothing on the device until bc_tables_build.  device = -1 gives a host-only
+ * context: tables and trees are built on the host (for inspection and tests)
+ * and every device call returns BC_ERR_STATE. */
+bc_status bc_create(const bc_config *cfg, int device, bc_ctx **out);
+void bc_destroy(bc_ctx *ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bc_last_error(void);
+
+/* Precompute and upload every table (near-field tables for the 33 relative
+ * positions a 2:1-balanced tree allows, far-field translation operators).
+ * Host FP64 quadrature; cached in `cache_dir` (NULL: no cache) in a file
+ * keyed by (p, nterms, node kind, format version) with a checksum. */
+bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir);
+
+/* Tree from explicit leaves of the root box [x0, x0+L] x [y0, y0+L]: leaf k is
+ * the dyadic box (level[k], ix[k], iy[k]) with 0 <= ix,iy < 2^level, level <= 24.
+ * Validates that the leaves are disjoint, cover the root and are 2:1 balanced
+ * (BC_ERR_TREE otherwise); builds the interaction lists on the host and
+ * uploads them.  Host arrays, read during the call only. */
+bc_status bc_tree_create(bc_ctx *ctx, double x0, double y0, double L, int64_t nleaf,
+                         const int32_t *level, const int32_t *ix, const int32_t *iy,
+                         bc_tree **out);
+
+/* Density callback: out[k] = f(xy[2k], xy[2k+1]) for k < n. */
+typedef void (*bc_density_fn)(const double *xy, int64_t n, double *out, void *user);
+
+/* Adaptive tree (paper Alg. 2, function-resolution criterion, then 2:1
+ * balance): a box is split while max |c_ab| over the Chebyshev coefficients
+ * with a >= p-2 or b >= p-2 exceeds eps * vscale (vscale = largest |f| at the
+ * root box's nodes, or 1 if f vanishes there) and its level is below
+ * max_level. */
+bc_status bc_tree_refine(bc_ctx *ctx, double x0, double y0, double L, bc_density_fn fn,
+                         void *user, double eps, int max_level, bc_tree **out);
+
+int64_t bc_tree_nleaf(const bc_tree *tree);
+/* Leaves in caller order (host arrays of nleaf entries). */
+bc_status bc_tree_leaves(const bc_tree *tree, int32_t *level, int32_t *ix, int32_t *iy);
+/* Physical node coordinates, host array [nleaf][p*p][2]. */
+bc_status bc_tree_nodes(const bc_tree *tree, double *xy);
+bc_status bc_tree_stats_get(const bc_tree *tree, bc_tree_stats *out);
+/* Interaction lists, for inspection and tests.  kind: 0 near (per leaf: leaf,
+ * table id), 1 V (per box: box, offset code), 2 W (per leaf: box, code),
+ * 3 X (per box: leaf, code).  Two-call protocol: pass NULL arrays to get the
+ * sizes in *nrows / *nnz, then arrays of that size: ptr[nrows+1], idx[nnz],
+ * code[nnz].  Boxes are numbered as in bc_tree_boxes. */
+bc_status bc_tree_lists(const bc_tree *tree, int kind, int64_t *nrows, int64_t *nnz,
+                        int64_t *ptr, int64_t *idx, int32_t *code);
+/* Box table (host arrays of nbox entries): level, ix, iy, parent (-1 root),
+ * leaf (caller leaf index or -1). */
+bc_status bc_tree_boxes(const bc_tree *tree, int32_t *level, int32_t *ix, int32_t *iy,
+                        int32_t *parent, int32_t *leaf);
+void bc_tree_destroy(bc_tree *tree);
+
+/* u = A f: the volume potential at every leaf node (definition above).
+ * f, u: [nleaf][p][p] FP64.  Device pointers are used in place; host
+ * pointers (pageable or pinned) are staged through the tree's device
+ * buffers, and the call then returns after u is written back.  u must not
+ * alias f. */
+bc_status bc_apply(bc_ctx *ctx, const bc_tree *tree, const double *f, double *u,
+                   bc_precision prec, void *stream);
+
+/* h = A^T g: the exact transpose of the discrete operator applied by
+ * bc_apply (same passes reversed, every operator transposed).  Same layout,
+ * pointer and stream rules as bc_apply. */
+bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, double *h,
+                           bc_precision prec, void *stream);
+
+/* out[k] = interpolant of the leaf-node values u at point xy[k] (barycentric
+ * Chebyshev interpolation on the leaf containing the point; a point on a
+ * shared edge belongs to the leaf on its +x / +y side, the root's far edges to
+ * the last leaf).  Points outside the root give BC_ERR_ARG on the host path;
+ * on the device path they produce NaN.  u, xy, out: device or host (all of the
+ * same kind). */
+bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy,
+                         int64_t n, double *out, void *stream);
+
+/* Many independent applies in one launch sequence: trees[k] (all of this
+ * context's p), f[k] -> u[k] (device pointers).  adjoint != 0 applies A^T. */
+bc_status bc_batch_apply(bc_ctx *ctx, const bc_tree *const *trees, int n, const double *const *f,
+                         double *const *u, bc_precision prec, int adjoint, void *stream);
+
+/* Copy a host table for inspection: which = 0 nodes[p], 1 w[p*p] (integrals
+ * of the Lagrange basis), 2 near tables [41][p*p][p*p] (unused slots zero),
+ * 3 P2M [P+1][p*p] complex, 4 L2P [p*p][P+1] complex, 5 M2M [4][P+1][P+1],
+ * 6 L2L [4][P+1][P+1], 7 M2L [49][P+1][P+1], 8 M2P [36][p*p][P+1],
+ * 9 P2L [36][P+1][p*p] (complex entries as interleaved re, im).  Pass
+ * out = NULL to get *count (doubles). */
+bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *out);
+
+/* Diagnostics.  pass_mask selects the parts of the operator an apply
+ * evaluates: bit 0 the near field (leaf-to-leaf tables), bit 1 the far field
+ * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
+ * event on the apply's stream at each stage boundary (leaf-to-expansion |
+ * upward | downward | leaf output); bc_debug_stage_times then waits for the
+ * last event of the most recent forward (adjoint = 0) or adjoint apply and
+ * writes the four stage durations in milliseconds to ms[4]. */
+bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
+bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
+/* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,
+ * 8 blocks per SM, best of three timed runs).  The roofline denominator of
+ * the FP64 passes. */
+bc_status bc_debug_fp64_peak(int device, double *tflops);
+
+/* Wait for the stream and report device-side failures recorded by earlier
+ * calls on this context (BC_ERR_TIMEOUT, BC_ERR_CUDA). */
+bc_status bc_sync(bc_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BOXCODE_H */

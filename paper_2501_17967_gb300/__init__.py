@@ -1,0 +1,360 @@
+"""GB300 machine code: the free-space 2D Laplace volume potential on an adaptive
+quadtree of p x p Chebyshev leaves (the bulk step v_bulk of arXiv 2501.17967,
+Sec. 3.2, eq. (vbulk)).
+
+This package is a thin binding over the C ABI in ``include/boxcode.h``
+(``libboxcode.so``, built in-tree by :func:`build`).  Every step of the
+computation runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: without the compiled library and a GPU the calls raise.
+
+    u(x_i) = (1/2pi) sum_B int_B log|x_i - y| f_B(y) dy,   Laplace(u) = f
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+__all__ = ["build", "Context", "Tree", "BoxCodeError", "FP64", "SPLIT_BF16", "apply", "apply_adjoint",
+           "BoxCodeApply", "lib_path"]
+
+FP64 = 0
+SPLIT_BF16 = 1
+_STATUS = {0: "BC_OK", -1: "BC_ERR_ARG", -2: "BC_ERR_TREE", -3: "BC_ERR_CUDA", -4: "BC_ERR_OOM",
+           -5: "BC_ERR_TIMEOUT", -6: "BC_ERR_UNSUPPORTED", -7: "BC_ERR_STATE"}
+_DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tables")
+
+_lib = None
+
+
+class BoxCodeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("nterms", ctypes.c_int), ("node_kind", ctypes.c_int),
+                ("split_slices", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("nleaf", "nbox", "nlevels", "n_near", "n_v", "n_w", "n_x",
+                                               "n_nonleaf", "n_down")]
+
+
+DENSITY_FN = ctypes.CFUNCTYPE(None, ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p)
+
+# (name, restype, argtypes) of every exported symbol
+_VP, _I64, _I32P, _DP = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("bc_create", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("bc_destroy", None, [_VP]),
+    ("bc_last_error", ctypes.c_char_p, []),
+    ("bc_tables_build", ctypes.c_int, [_VP, ctypes.c_char_p]),
+    ("bc_tree_create", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, _I64, _I32P, _I32P,
+                                      _I32P, ctypes.POINTER(_VP)]),
+    ("bc_tree_refine", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, DENSITY_FN, _VP,
+                                      ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("bc_tree_nleaf", _I64, [_VP]),
+    ("bc_tree_leaves", ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
+    ("bc_tree_nodes", ctypes.c_int, [_VP, _DP]),
+    ("bc_tree_stats_get", ctypes.c_int, [_VP, ctypes.POINTER(_Stats)]),
+    ("bc_tree_lists", ctypes.c_int, [_VP, ctypes.c_int, _I64P, _I64P, _I64P, _I64P, _I32P]),
+    ("bc_tree_boxes", ctypes.c_int, [_VP, _I32P, _I32P, _I32P, _I32P, _I32P]),
+    ("bc_tree_destroy", None, [_VP]),
+    ("bc_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    ("bc_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
+    ("bc_eval_points", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP]),
+    ("bc_batch_apply", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP),
+                                      ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
+    ("bc_table_export", ctypes.c_int, [_VP, ctypes.c_int, _I64P, _DP]),
+    ("bc_debug_set", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
+    ("bc_debug_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
+    ("bc_debug_fp64_peak", ctypes.c_int, [ctypes.c_int, _DP]),
+    ("bc_sync", ctypes.c_int, [_VP, _VP]),
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile libboxcode.so for sm_103a (in-tree) and return its path."""
+    return _build_mod.build(force=force)
+
+
+def lib_path() -> str:
+    return _build_mod.LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build_mod.build()
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        msg = _load().bc_last_error()
+        raise BoxCodeError(status, msg.decode() if msg else "")
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_I32P)
+
+
+class Context:
+    """Order-p context on one CUDA device (device=-1: host-only, for inspection)."""
+
+    def __init__(self, p: int = 16, nterms: int = 0, device: int = 0, split_slices: int = 0,
+                 cache_dir: str | None = _DEFAULT_CACHE, build_tables: bool = True):
+        lib = _load()
+        cfg = _Config(p, nterms, 1, split_slices, 0)
+        h = _VP()
+        _check(lib.bc_create(ctypes.byref(cfg), device, ctypes.byref(h)))
+        self._h = h
+        self.p = p
+        self.device = device
+        self.nterms = nterms
+        if build_tables:
+            if cache_dir:
+                os.makedirs(cache_dir, exist_ok=True)
+            _check(lib.bc_tables_build(h, cache_dir.encode() if cache_dir else None))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def table(self, which: int) -> np.ndarray:
+        """Host copy of a table (see bc_table_export)."""
+        lib = _load()
+        n = ctypes.c_int64()
+        _check(lib.bc_table_export(self._h, which, ctypes.byref(n), None))
+        out = np.empty(n.value)
+        _check(lib.bc_table_export(self._h, which, ctypes.byref(n), out.ctypes.data_as(_DP)))
+        return out
+
+    def debug(self, pass_mask: int = 3, timing: bool = False):
+        """Diagnostics: restrict applies to the near (1) / far (2) field; time stages."""
+        _check(_load().bc_debug_set(self._h, pass_mask, int(timing)))
+
+    def stage_times(self, adjoint: bool = False):
+        """Durations (ms) of the last forward/adjoint apply's stages: leafA, up, down, leafB."""
+        ms = np.zeros(4)
+        _check(_load().bc_debug_stage_times(self._h, int(adjoint), ms.ctypes.data_as(_DP)))
+        return ms
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().bc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Tree:
+    """A 2:1-balanced quadtree of leaves (level, ix, iy) of the root [x0,x0+L]^2."""
+
+    def __init__(self, ctx: Context, level, ix, iy, x0=-1.0, y0=-1.0, L=2.0, _handle=None):
+        lib = _load()
+        self.ctx = ctx
+        self.x0, self.y0, self.L = float(x0), float(y0), float(L)
+        if _handle is None:
+            lv, plv = _i32(level)
+            ax, pix = _i32(ix)
+            ay, piy = _i32(iy)
+            if not (lv.shape == ax.shape == ay.shape) or lv.ndim != 1:
+                raise ValueError("level, ix, iy must be 1-D arrays of equal length")
+            h = _VP()
+            _check(lib.bc_tree_create(ctx.handle, x0, y0, L, lv.shape[0], plv, pix, piy, ctypes.byref(h)))
+            self._h = h
+        else:
+            self._h = _handle
+        self.nleaf = int(lib.bc_tree_nleaf(self._h))
+
+    @classmethod
+    def refine(cls, ctx: Context, density, eps: float = 1e-11, max_level: int = 20, x0=-1.0, y0=-1.0, L=2.0):
+        """Adaptive tree (Alg. 2 resolution criterion + 2:1 balance); density(xy[n,2]) -> f[n]."""
+        lib = _load()
+        err = []
+
+        def cb(xy, n, out, user):
+            try:
+                pts = np.ctypeslib.as_array(xy, shape=(n, 2))
+                vals = np.asarray(density(pts), dtype=np.float64).reshape(n)
+                np.ctypeslib.as_array(out, shape=(n,))[:] = vals
+            except Exception as exc:  # report after the call
+                err.append(exc)
+                np.ctypeslib.as_array(out, shape=(n,))[:] = np.nan
+
+        cfn = DENSITY_FN(cb)
+        h = _VP()
+        st = lib.bc_tree_refine(ctx.handle, x0, y0, L, cfn, None, eps, max_level, ctypes.byref(h))
+        if err:
+            raise err[0]
+        _check(st)
+        return cls(ctx, None, None, None, x0, y0, L, _handle=h)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def leaves(self):
+        n = self.nleaf
+        lv, ix, iy = (np.empty(n, np.int32) for _ in range(3))
+        _check(_load().bc_tree_leaves(self._h, lv.ctypes.data_as(_I32P), ix.ctypes.data_as(_I32P),
+                                      iy.ctypes.data_as(_I32P)))
+        return lv, ix, iy
+
+    def nodes(self) -> np.ndarray:
+        out = np.empty((self.nleaf, self.ctx.p * self.ctx.p, 2))
+        _check(_load().bc_tree_nodes(self._h, out.ctypes.data_as(_DP)))
+        return out
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(_load().bc_tree_stats_get(self._h, ctypes.byref(s)))
+        return {n: int(getattr(s, n)) for n, _ in _Stats._fields_}
+
+    def lists(self, kind: int):
+        lib = _load()
+        nr, nz = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib.bc_tree_lists(self._h, kind, ctypes.byref(nr), ctypes.byref(nz), None, None, None))
+        ptr = np.empty(nr.value + 1, np.int64)
+        idx = np.empty(nz.value, np.int64)
+        code = np.empty(nz.value, np.int32)
+        _check(lib.bc_tree_lists(self._h, kind, ctypes.byref(nr), ctypes.byref(nz), ptr.ctypes.data_as(_I64P),
+                                 idx.ctypes.data_as(_I64P), code.ctypes.data_as(_I32P)))
+        return ptr, idx, code
+
+    def boxes(self):
+        lib = _load()
+        nb = self.stats()["nbox"]
+        arrs = [np.empty(nb, np.int32) for _ in range(5)]
+        _check(lib.bc_tree_boxes(self._h, *[a.ctypes.data_as(_I32P) for a in arrs]))
+        return tuple(arrs)   # level, ix, iy, parent, leaf
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().bc_tree_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fp64_peak_tflops(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of the device (TFLOP/s)."""
+    v = ctypes.c_double()
+    _check(_load().bc_debug_fp64_peak(device, ctypes.byref(v)))
+    return v.value
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_tensor(x, tree: Tree, name):
+    import torch
+    n = tree.nleaf * tree.ctx.p * tree.ctx.p
+    if not isinstance(x, torch.Tensor) or x.dtype != torch.float64 or x.numel() != n or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 tensor with {n} elements")
+
+
+def apply(tree: Tree, f, out=None, precision: int = FP64, stream=None):
+    """u = A f (device or pinned/host float64 tensors of shape [nleaf, p, p] or flat)."""
+    import torch
+    _check_tensor(f, tree, "f")
+    if out is None:
+        out = torch.empty_like(f)
+    _check_tensor(out, tree, "out")
+    _check(_load().bc_apply(tree.ctx.handle, tree.handle, ctypes.c_void_p(f.data_ptr()),
+                            ctypes.c_void_p(out.data_ptr()), precision,
+                            _stream_ptr(stream) if f.is_cuda else None))
+    return out
+
+
+def apply_adjoint(tree: Tree, g, out=None, precision: int = FP64, stream=None):
+    """h = A^T g (exact transpose of the discrete operator of :func:`apply`)."""
+    import torch
+    _check_tensor(g, tree, "g")
+    if out is None:
+        out = torch.empty_like(g)
+    _check_tensor(out, tree, "out")
+    _check(_load().bc_apply_adjoint(tree.ctx.handle, tree.handle, ctypes.c_void_p(g.data_ptr()),
+                                    ctypes.c_void_p(out.data_ptr()), precision,
+                                    _stream_ptr(stream) if g.is_cuda else None))
+    return out
+
+
+def eval_points(tree: Tree, u, xy, out=None, stream=None):
+    """Interpolate leaf-node values u at points xy[n, 2] (device tensors)."""
+    import torch
+    _check_tensor(u, tree, "u")
+    xy = xy.contiguous()
+    n = xy.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float64, device=xy.device)
+    _check(_load().bc_eval_points(tree.ctx.handle, tree.handle, ctypes.c_void_p(u.data_ptr()),
+                                  ctypes.c_void_p(xy.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                                  _stream_ptr(stream) if xy.is_cuda else None))
+    return out
+
+
+def batch_apply(ctx: Context, trees, fs, us, precision: int = FP64, adjoint: bool = False, stream=None):
+    """Apply A (or A^T) to many independent densities on trees of this context."""
+    n = len(trees)
+    th = (_VP * n)(*[t.handle for t in trees])
+    fp = (_VP * n)(*[ctypes.c_void_p(f.data_ptr()) for f in fs])
+    up = (_VP * n)(*[ctypes.c_void_p(u.data_ptr()) for u in us])
+    _check(_load().bc_batch_apply(ctx.handle, th, n, fp, up, precision, int(adjoint), _stream_ptr(stream)))
+    return us
+
+
+def _autograd():
+    import torch
+
+    class BoxCodeApply(torch.autograd.Function):
+        """u = A f with dL/df = A^T dL/du (the hand-written adjoint kernels)."""
+
+        @staticmethod
+        def forward(ctx, f, tree, precision=FP64):
+            ctx.tree = tree
+            ctx.precision = precision
+            return apply(tree, f.contiguous(), precision=precision)
+
+        @staticmethod
+        def backward(ctx, g):
+            return apply_adjoint(ctx.tree, g.contiguous(), precision=ctx.precision), None, None
+
+    return BoxCodeApply
+
+
+def __getattr__(name):
+    if name == "BoxCodeApply":
+        cls = _autograd()
+        globals()["BoxCodeApply"] = cls
+        return cls
+    raise AttributeError(name)

@@ -1,0 +1,562 @@
+// C ABI of the box code (declared in include/boxcode.h): contexts, tables,
+// trees, applies.  Device memory is plain cudaMalloc; every entry point
+// returns a bc_status and records a message for bc_last_error().
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "bc_internal.h"
+
+namespace bc {
+
+namespace {
+thread_local char g_err[512] = "";
+
+template <class T>
+cudaError_t dev_upload(std::vector<void *> &allocs, T **dst, const T *src, size_t n)
+{
+    *dst = nullptr;
+    if (n == 0) n = 1;
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(p);
+    *dst = static_cast<T *>(p);
+    if (src) return cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return cudaMemset(p, 0, n * sizeof(T));
+}
+
+void free_all(std::vector<void *> &allocs)
+{
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+}
+
+bc_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? BC_ERR_OOM : BC_ERR_CUDA;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Operator layouts (see OpSet): element (l,k) of a complex operator at [k][l].
+using cplx = std::complex<double>;
+inline cplx at2(const std::vector<double> &v, size_t i) { return cplx(v[2 * i], v[2 * i + 1]); }
+
+struct OpBuild {
+    std::vector<double2> leafA, up, par, v, x, e, w;
+    std::vector<double> t;
+};
+
+void build_opsets(const HostTables &ht, OpBuild &F, OpBuild &A)
+{
+    const int P1 = ht.P1, NP = ht.NP;
+    auto d2 = [](cplx z) { return make_double2(z.real(), z.imag()); };
+    auto cj = [](cplx z) { return std::conj(z); };
+    // leafA: fwd element (l,j) = Q[l][j];  adj element (l,j) = conj(E[j][l])
+    F.leafA.resize(size_t(NP) * P1); A.leafA.resize(size_t(NP) * P1);
+    for (int j = 0; j < NP; j++)
+        for (int l = 0; l < P1; l++) {
+            F.leafA[size_t(j) * P1 + l] = d2(at2(ht.Q, size_t(l) * NP + j));
+            A.leafA[size_t(j) * P1 + l] = d2(cj(at2(ht.E, size_t(j) * P1 + l)));
+        }
+    // up: fwd (l,k) = M2M_q[l][k];  adj (l,k) = conj(L2L_q[k][l])
+    // par: fwd (l,k) = L2L_q[l][k]; adj (l,k) = conj(M2M_q[k][l])
+    F.up.resize(size_t(4) * P1 * P1); A.up.resize(F.up.size());
+    F.par.resize(F.up.size()); A.par.resize(F.up.size());
+    for (int q = 0; q < 4; q++)
+        for (int k = 0; k < P1; k++)
+            for (int l = 0; l < P1; l++) {
+                size_t dst = (size_t(q) * P1 + k) * P1 + l;
+                size_t lk = (size_t(q) * P1 + l) * P1 + k, kl = (size_t(q) * P1 + k) * P1 + l;
+                F.up[dst] = d2(at2(ht.M2M, lk));
+                A.up[dst] = d2(cj(at2(ht.L2L, kl)));
+                F.par[dst] = d2(at2(ht.L2L, lk));
+                A.par[dst] = d2(cj(at2(ht.M2M, kl)));
+            }
+    // v: fwd (l,k) = M2L_c[l][k];  adj code c (offset d): (l,k) = conj(M2L_{-d}[k][l])
+    F.v.resize(size_t(kNumV) * P1 * P1); A.v.resize(F.v.size());
+    for (int c = 0; c < kNumV; c++) {
+        int cr = kNumV - 1 - c;   // code of -d
+        for (int k = 0; k < P1; k++)
+            for (int l = 0; l < P1; l++) {
+                size_t dst = (size_t(c) * P1 + k) * P1 + l;
+                F.v[dst] = d2(at2(ht.M2L, (size_t(c) * P1 + l) * P1 + k));
+                A.v[dst] = d2(cj(at2(ht.M2L, (size_t(cr) * P1 + k) * P1 + l)));
+            }
+    }
+    // x: fwd (l,j) = P2L_c[l][j];  adj (l,j) = conj(M2P_c[j][l])
+    // w: fwd (j,k) = M2P_c[j][k];  adj (j,k) = conj(P2L_c[k][j])
+    F.x.resize(size_t(kNumWX) * NP * P1); A.x.resize(F.x.size());
+    F.w.resize(size_t(kNumWX) * P1 * NP); A.w.resize(F.w.size());
+    for (int c = 0; c < kNumWX; c++)
+        for (int j = 0; j < NP; j++)
+            for (int l = 0; l < P1; l++) {
+                size_t xdst = (size_t(c) * NP + j) * P1 + l;      // [c][j][l]
+                size_t wdst = (size_t(c) * P1 + l) * NP + j;      // [c][k=l][j]
+                cplx p2l = at2(ht.P2L, (size_t(c) * P1 + l) * NP + j);
+                cplx m2p = at2(ht.M2P, (size_t(c) * NP + j) * P1 + l);
+                F.x[xdst] = d2(p2l);
+                A.x[xdst] = d2(cj(m2p));
+                F.w[wdst] = d2(m2p);
+                A.w[wdst] = d2(cj(p2l));
+            }
+    // e: fwd (j,l) = E[j][l];  adj (j,l) = conj(Q[l][j]);  stored [l][j]
+    F.e.resize(size_t(P1) * NP); A.e.resize(F.e.size());
+    for (int l = 0; l < P1; l++)
+        for (int j = 0; j < NP; j++) {
+            F.e[size_t(l) * NP + j] = d2(at2(ht.E, size_t(j) * P1 + l));
+            A.e[size_t(l) * NP + j] = d2(cj(at2(ht.Q, size_t(l) * NP + j)));
+        }
+    // t: fwd (j,k) = T_tab[j][k];  adj (j,k) = T_rev(tab)[k][j];  stored [tab][k][j]
+    F.t.assign(size_t(kNumNear) * NP * NP, 0.0); A.t.assign(F.t.size(), 0.0);
+    for (int tab = 0; tab < kNumNear; tab++) {
+        NearGeom g = near_table_geometry(tab);
+        if (!g.valid) continue;
+        for (int k = 0; k < NP; k++)
+            for (int j = 0; j < NP; j++) {
+                F.t[(size_t(tab) * NP + k) * NP + j] = ht.T[(size_t(tab) * NP + j) * NP + k];
+                A.t[(size_t(tab) * NP + k) * NP + j] = ht.T[(size_t(g.rev) * NP + k) * NP + j];
+            }
+    }
+}
+
+bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
+{
+    cudaError_t e;
+    double2 *p;
+    double *q;
+#define UP2(field)                                                              \
+    e = dev_upload(dt.allocs, &p, b.field.data(), b.field.size());              \
+    if (e != cudaSuccess) return cuda_fail(e, "tables upload");                  \
+    os.field = p;
+    UP2(leafA) UP2(up) UP2(par) UP2(v) UP2(x) UP2(e) UP2(w)
+#undef UP2
+    e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());
+    if (e != cudaSuccess) return cuda_fail(e, "tables upload");
+    os.t = q;
+    return BC_OK;
+}
+
+bc_status upload_tree(bc_tree *t)
+{
+    HostTree &h = t->h;
+    DevTree &d = t->d;
+    const int P1 = t->ctx->P1;
+    cudaError_t e;
+#define UPV(dst, vec)                                                           \
+    e = dev_upload(d.allocs, &d.dst, vec.data(), vec.size());                   \
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    UPV(leaf_box, h.leaf_box) UPV(leaf_level, h.leaf_level) UPV(leaf_order, h.leaf_order)
+    UPV(box_parent, h.box_parent) UPV(box_child0, h.box_child0) UPV(box_level, h.box_level)
+    UPV(box_ix, h.box_ix) UPV(box_iy, h.box_iy) UPV(box_leaf, h.box_leaf)
+    UPV(near_ptr, h.near_ptr) UPV(near_src, h.near_src) UPV(near_tab, h.near_tab)
+    UPV(v_ptr, h.v_ptr) UPV(v_src, h.v_src) UPV(v_code, h.v_code)
+    UPV(w_ptr, h.w_ptr) UPV(w_src, h.w_src) UPV(w_code, h.w_code)
+    UPV(x_ptr, h.x_ptr) UPV(x_src, h.x_src) UPV(x_code, h.x_code)
+#undef UPV
+    e = dev_upload<int32_t>(d.allocs, &d.zero_ptr, nullptr, size_t(h.nleaf) + 1);
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    size_t nexp = size_t(h.box_level.size()) * P1;
+    e = dev_upload<double2>(d.allocs, &d.expA, nullptr, nexp);
+    if (e != cudaSuccess) return cuda_fail(e, "tree workspace");
+    e = dev_upload<double2>(d.allocs, &d.expB, nullptr, nexp);
+    if (e != cudaSuccess) return cuda_fail(e, "tree workspace");
+    return BC_OK;
+}
+
+bc_status finish_tree(bc_ctx *ctx, bc_tree **out, bc_tree *t)
+{
+    if (ctx->device < 0) { *out = t; return BC_OK; }   // host-only context: no upload
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) { delete t; return cuda_fail(e, "cudaSetDevice"); }
+    bc_status s = upload_tree(t);
+    if (s != BC_OK) {
+        free_all(t->d.allocs);
+        delete t;
+        return s;
+    }
+    *out = t;
+    return BC_OK;
+}
+
+PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
+{
+    PassArgs a;
+    a.p = ctx->p; a.NP = ctx->NP; a.P1 = ctx->P1;
+    a.half_L = 0.5 * t->h.L;
+    a.nleaf = t->h.nleaf;
+    a.nbox = int64_t(t->h.box_level.size());
+    return a;
+}
+
+bc_status check_apply_args(bc_ctx *ctx, const bc_tree *tree, const void *in, const void *out, bc_precision prec)
+{
+    if (!ctx || !tree || !in || !out) { set_error("apply: NULL argument"); return BC_ERR_ARG; }
+    if (tree->ctx != ctx) { set_error("apply: tree belongs to another context"); return BC_ERR_ARG; }
+    if (ctx->device < 0) { set_error("apply: host-only context (device -1) cannot apply"); return BC_ERR_STATE; }
+    if (!ctx->tables_ready) { set_error("apply: call bc_tables_build first"); return BC_ERR_STATE; }
+    if (in == out) { set_error("apply: output must not alias input"); return BC_ERR_ARG; }
+    if (prec != BC_FP64 && prec != BC_SPLIT_BF16) { set_error("apply: unknown precision %d", int(prec)); return BC_ERR_ARG; }
+    return BC_OK;
+}
+
+bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double *vout, bc_precision prec,
+                     void *stream, bool adj)
+{
+    bc_status s = check_apply_args(ctx, tree, vin, vout, prec);
+    if (s != BC_OK) return s;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PassArgs a = pass_args(ctx, tree);
+    bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
+    if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
+    if (prec == BC_SPLIT_BF16) {
+        set_error("apply: split-precision near field not built yet");
+        return BC_ERR_UNSUPPORTED;
+    }
+    if (din) {
+        e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, vin, vout, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+        return BC_OK;
+    }
+    // host arrays: stage through the tree's device buffers
+    bc_tree *t = const_cast<bc_tree *>(tree);
+    size_t n = size_t(a.nleaf) * a.NP;
+    if (!t->d.stage_in) {
+        e = dev_upload<double>(t->d.allocs, &t->d.stage_in, nullptr, n);
+        if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+        e = dev_upload<double>(t->d.allocs, &t->d.stage_out, nullptr, n);
+        if (e != cudaSuccess) return cuda_fail(e, "staging buffer");
+    }
+    e = cudaMemcpyAsync(t->d.stage_in, vin, n * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply H2D");
+    e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, t->d.stage_in, t->d.stage_out, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+    e = cudaMemcpyAsync(vout, t->d.stage_out, n * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply D2H");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "apply sync");
+    return BC_OK;
+}
+
+}  // namespace
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace bc
+
+using namespace bc;
+
+extern "C" {
+
+const char *bc_last_error(void) { return g_err; }
+
+bc_status bc_create(const bc_config *cfg, int device, bc_ctx **out)
+{
+    if (!cfg || !out) { set_error("bc_create: NULL argument"); return BC_ERR_ARG; }
+    *out = nullptr;
+    if (cfg->p < 4 || cfg->p > kMaxP) { set_error("bc_create: p must be in [4, %d]", kMaxP); return BC_ERR_ARG; }
+    int nterms = cfg->nterms ? cfg->nterms : kDefaultNterms;
+    if (nterms < 4 || nterms > 64) { set_error("bc_create: nterms must be in [4, 64]"); return BC_ERR_ARG; }
+    if (cfg->node_kind != 0 && cfg->node_kind != 1) { set_error("bc_create: only first-kind Chebyshev nodes (node_kind 1) are provided"); return BC_ERR_UNSUPPORTED; }
+    if (cfg->split_slices < 0 || cfg->split_slices > 8) { set_error("bc_create: split_slices must be in [0, 8]"); return BC_ERR_ARG; }
+    if (device != -1) {
+        int ndev = 0;
+        cudaError_t e = cudaGetDeviceCount(&ndev);
+        if (e != cudaSuccess) return cuda_fail(e, "bc_create: cudaGetDeviceCount");
+        if (device < 0 || device >= ndev) { set_error("bc_create: device %d not present (%d devices)", device, ndev); return BC_ERR_ARG; }
+    }
+    bc_ctx *c = new (std::nothrow) bc_ctx();
+    if (!c) { set_error("bc_create: out of host memory"); return BC_ERR_OOM; }
+    c->cfg = *cfg;
+    c->cfg.nterms = nterms;
+    c->cfg.node_kind = 1;
+    c->device = device;
+    c->p = cfg->p;
+    c->NP = cfg->p * cfg->p;
+    c->P1 = nterms;
+    *out = c;
+    return BC_OK;
+}
+
+void bc_destroy(bc_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->device >= 0) cudaSetDevice(ctx->device);
+    for (auto &dir : ctx->ev)
+        for (auto &e : dir)
+            if (e) cudaEventDestroy(e);
+    free_all(ctx->dt.allocs);
+    delete ctx;
+}
+
+bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
+{
+    if (!ctx) { set_error("bc_tables_build: NULL context"); return BC_ERR_ARG; }
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->tables_ready) return BC_OK;
+    bc_status s = build_tables(ctx->ht, ctx->p, ctx->P1, cache_dir);
+    if (s != BC_OK) return s;
+    if (ctx->device < 0) { ctx->tables_ready = true; return BC_OK; }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    OpBuild F, A;
+    build_opsets(ctx->ht, F, A);
+    if ((s = upload_opset(ctx->dt, ctx->dt.fwd, F)) != BC_OK) return s;
+    if ((s = upload_opset(ctx->dt, ctx->dt.adj, A)) != BC_OK) return s;
+    e = dev_upload(ctx->dt.allocs, &ctx->dt.wvec, ctx->ht.w.data(), ctx->ht.w.size());
+    if (e != cudaSuccess) return cuda_fail(e, "tables upload");
+    ctx->tables_ready = true;
+    return BC_OK;
+}
+
+bc_status bc_tree_create(bc_ctx *ctx, double x0, double y0, double L, int64_t nleaf, const int32_t *level,
+                         const int32_t *ix, const int32_t *iy, bc_tree **out)
+{
+    if (!ctx || !out) { set_error("bc_tree_create: NULL argument"); return BC_ERR_ARG; }
+    *out = nullptr;
+    bc_tree *t = new (std::nothrow) bc_tree();
+    if (!t) { set_error("bc_tree_create: out of host memory"); return BC_ERR_OOM; }
+    t->ctx = ctx;
+    bc_status s = build_host_tree(t->h, x0, y0, L, ctx->p, nleaf, level, ix, iy);
+    if (s != BC_OK) { delete t; return s; }
+    return finish_tree(ctx, out, t);
+}
+
+bc_status bc_tree_refine(bc_ctx *ctx, double x0, double y0, double L, bc_density_fn fn, void *user, double eps,
+                         int max_level, bc_tree **out)
+{
+    if (!ctx || !out) { set_error("bc_tree_refine: NULL argument"); return BC_ERR_ARG; }
+    *out = nullptr;
+    std::vector<int32_t> lv, ix, iy;
+    bc_status s = refine_leaves(ctx->p, x0, y0, L, fn, user, eps, max_level, lv, ix, iy);
+    if (s != BC_OK) return s;
+    return bc_tree_create(ctx, x0, y0, L, int64_t(lv.size()), lv.data(), ix.data(), iy.data(), out);
+}
+
+int64_t bc_tree_nleaf(const bc_tree *tree) { return tree ? tree->h.nleaf : 0; }
+
+bc_status bc_tree_leaves(const bc_tree *tree, int32_t *level, int32_t *ix, int32_t *iy)
+{
+    if (!tree || !level || !ix || !iy) { set_error("bc_tree_leaves: NULL argument"); return BC_ERR_ARG; }
+    std::copy(tree->h.leaf_level.begin(), tree->h.leaf_level.end(), level);
+    std::copy(tree->h.leaf_ix.begin(), tree->h.leaf_ix.end(), ix);
+    std::copy(tree->h.leaf_iy.begin(), tree->h.leaf_iy.end(), iy);
+    return BC_OK;
+}
+
+bc_status bc_tree_nodes(const bc_tree *tree, double *xy)
+{
+    if (!tree || !xy) { set_error("bc_tree_nodes: NULL argument"); return BC_ERR_ARG; }
+    const HostTree &h = tree->h;
+    const int p = h.p;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> xn(p);
+    for (int m = 0; m < p; m++) xn[m] = -std::cos((2.0 * m + 1.0) * pi / (2.0 * p));
+    for (int64_t k = 0; k < h.nleaf; k++) {
+        double r = 0.5 * h.L / double(int64_t(1) << h.leaf_level[k]);
+        double cx = h.x0 + (2.0 * h.leaf_ix[k] + 1.0) * r, cy = h.y0 + (2.0 * h.leaf_iy[k] + 1.0) * r;
+        for (int jy = 0; jy < p; jy++)
+            for (int jx = 0; jx < p; jx++) {
+                size_t o = (size_t(k) * p * p + jy * p + jx) * 2;
+                xy[o] = cx + r * xn[jx];
+                xy[o + 1] = cy + r * xn[jy];
+            }
+    }
+    return BC_OK;
+}
+
+bc_status bc_tree_stats_get(const bc_tree *tree, bc_tree_stats *out)
+{
+    if (!tree || !out) { set_error("bc_tree_stats_get: NULL argument"); return BC_ERR_ARG; }
+    const HostTree &h = tree->h;
+    out->nleaf = h.nleaf;
+    out->nbox = int64_t(h.box_level.size());
+    out->nlevels = h.nlevels;
+    out->n_near = int64_t(h.near_src.size());
+    out->n_v = int64_t(h.v_src.size());
+    out->n_w = int64_t(h.w_src.size());
+    out->n_x = int64_t(h.x_src.size());
+    out->n_nonleaf = h.n_nonleaf;
+    out->n_down = h.n_down;
+    return BC_OK;
+}
+
+bc_status bc_tree_lists(const bc_tree *tree, int kind, int64_t *nrows, int64_t *nnz, int64_t *ptr, int64_t *idx,
+                        int32_t *code)
+{
+    if (!tree || !nrows || !nnz) { set_error("bc_tree_lists: NULL argument"); return BC_ERR_ARG; }
+    const HostTree &h = tree->h;
+    const std::vector<int32_t> *P, *I, *C;
+    switch (kind) {
+    case 0: P = &h.near_ptr; I = &h.near_src; C = &h.near_tab; break;
+    case 1: P = &h.v_ptr; I = &h.v_src; C = &h.v_code; break;
+    case 2: P = &h.w_ptr; I = &h.w_src; C = &h.w_code; break;
+    case 3: P = &h.x_ptr; I = &h.x_src; C = &h.x_code; break;
+    default: set_error("bc_tree_lists: kind must be 0..3"); return BC_ERR_ARG;
+    }
+    *nrows = int64_t(P->size()) - 1;
+    *nnz = int64_t(I->size());
+    if (ptr) for (size_t i = 0; i < P->size(); i++) ptr[i] = (*P)[i];
+    if (idx) for (size_t i = 0; i < I->size(); i++) idx[i] = (*I)[i];
+    if (code) for (size_t i = 0; i < C->size(); i++) code[i] = (*C)[i];
+    return BC_OK;
+}
+
+bc_status bc_tree_boxes(const bc_tree *tree, int32_t *level, int32_t *ix, int32_t *iy, int32_t *parent,
+                        int32_t *leaf)
+{
+    if (!tree) { set_error("bc_tree_boxes: NULL tree"); return BC_ERR_ARG; }
+    const HostTree &h = tree->h;
+    if (level) std::copy(h.box_level.begin(), h.box_level.end(), level);
+    if (ix) std::copy(h.box_ix.begin(), h.box_ix.end(), ix);
+    if (iy) std::copy(h.box_iy.begin(), h.box_iy.end(), iy);
+    if (parent) std::copy(h.box_parent.begin(), h.box_parent.end(), parent);
+    if (leaf) std::copy(h.box_leaf.begin(), h.box_leaf.end(), leaf);
+    return BC_OK;
+}
+
+void bc_tree_destroy(bc_tree *tree)
+{
+    if (!tree) return;
+    if (tree->ctx->device >= 0) cudaSetDevice(tree->ctx->device);
+    free_all(tree->d.allocs);
+    delete tree;
+}
+
+bc_status bc_apply(bc_ctx *ctx, const bc_tree *tree, const double *f, double *u, bc_precision prec, void *stream)
+{
+    return apply_impl(ctx, tree, f, u, prec, stream, false);
+}
+
+bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, double *h, bc_precision prec,
+                           void *stream)
+{
+    return apply_impl(ctx, tree, g, h, prec, stream, true);
+}
+
+bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy, int64_t n,
+                         double *out, void *stream)
+{
+    if (!ctx || !tree || (n > 0 && (!u || !xy || !out)) || n < 0) { set_error("bc_eval_points: bad argument"); return BC_ERR_ARG; }
+    if (tree->ctx != ctx) { set_error("bc_eval_points: tree belongs to another context"); return BC_ERR_ARG; }
+    if (ctx->device < 0) { set_error("bc_eval_points: host-only context (device -1)"); return BC_ERR_STATE; }
+    if (n == 0) return BC_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PassArgs a = pass_args(ctx, tree);
+    const HostTree &h = tree->h;
+    bool du = is_device_ptr(u), dx = is_device_ptr(xy), dout = is_device_ptr(out);
+    if (du && dx && dout) {
+        e = launch_eval_points(a, tree->d, u, xy, n, out, h.x0, h.y0, h.L, st);
+        return e == cudaSuccess ? BC_OK : cuda_fail(e, "eval launch");
+    }
+    if (du || dx || dout) { set_error("bc_eval_points: u, xy and out must all be device or all host memory"); return BC_ERR_ARG; }
+    for (int64_t k = 0; k < n; k++) {
+        double x = xy[2 * k], y = xy[2 * k + 1];
+        if (!(x >= h.x0 && x <= h.x0 + h.L && y >= h.y0 && y <= h.y0 + h.L)) {
+            set_error("bc_eval_points: point %lld outside the root box", (long long)k);
+            return BC_ERR_ARG;
+        }
+    }
+    size_t nu = size_t(h.nleaf) * ctx->NP;
+    double *du_ = nullptr, *dxy = nullptr, *dout_ = nullptr;
+    std::vector<void *> tmp;
+    if ((e = dev_upload(tmp, &du_, u, nu)) != cudaSuccess ||
+        (e = dev_upload(tmp, &dxy, xy, size_t(2 * n))) != cudaSuccess ||
+        (e = dev_upload<double>(tmp, &dout_, nullptr, size_t(n))) != cudaSuccess) {
+        free_all(tmp);
+        return cuda_fail(e, "eval staging");
+    }
+    e = launch_eval_points(a, tree->d, du_, dxy, n, dout_, h.x0, h.y0, h.L, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout_, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_all(tmp);
+    return e == cudaSuccess ? BC_OK : cuda_fail(e, "eval");
+}
+
+bc_status bc_batch_apply(bc_ctx *ctx, const bc_tree *const *trees, int n, const double *const *f, double *const *u,
+                         bc_precision prec, int adjoint, void *stream)
+{
+    if (!ctx || n < 0 || (n > 0 && (!trees || !f || !u))) { set_error("bc_batch_apply: bad argument"); return BC_ERR_ARG; }
+    for (int k = 0; k < n; k++) {
+        bc_status s = apply_impl(ctx, trees[k], f[k], u[k], prec, stream, adjoint != 0);
+        if (s != BC_OK) return s;
+    }
+    return BC_OK;
+}
+
+bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *out)
+{
+    if (!ctx || !count) { set_error("bc_table_export: NULL argument"); return BC_ERR_ARG; }
+    if (!ctx->tables_ready) { set_error("bc_table_export: tables not built"); return BC_ERR_STATE; }
+    const HostTables &h = ctx->ht;
+    const std::vector<double> *v[] = {&h.nodes, &h.w, &h.T, &h.Q, &h.E, &h.M2M, &h.L2L, &h.M2L, &h.M2P, &h.P2L};
+    if (which < 0 || which >= int(sizeof(v) / sizeof(v[0]))) { set_error("bc_table_export: which must be 0..9"); return BC_ERR_ARG; }
+    *count = int64_t(v[which]->size());
+    if (out) std::copy(v[which]->begin(), v[which]->end(), out);
+    return BC_OK;
+}
+
+bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing)
+{
+    if (!ctx || pass_mask < 0 || pass_mask > 3) { set_error("bc_debug_set: bad argument"); return BC_ERR_ARG; }
+    if (ctx->device < 0) { set_error("bc_debug_set: host-only context"); return BC_ERR_STATE; }
+    ctx->pass_mask = pass_mask;
+    if (timing && !ctx->ev[0][0]) {
+        cudaError_t e = cudaSetDevice(ctx->device);
+        for (int d = 0; d < 2; d++)
+            for (int i = 0; e == cudaSuccess && i <= kNumStages; i++) e = cudaEventCreate(&ctx->ev[d][i]);
+        if (e != cudaSuccess) return cuda_fail(e, "bc_debug_set: events");
+    }
+    ctx->timing = timing != 0;
+    return BC_OK;
+}
+
+bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms)
+{
+    if (!ctx || !ms) { set_error("bc_debug_stage_times: NULL argument"); return BC_ERR_ARG; }
+    if (!ctx->timing) { set_error("bc_debug_stage_times: timing is off"); return BC_ERR_STATE; }
+    cudaEvent_t *ev = ctx->ev[adjoint ? 1 : 0];
+    cudaError_t e = cudaEventSynchronize(ev[kNumStages]);
+    for (int i = 0; e == cudaSuccess && i < kNumStages; i++) {
+        float t = 0.0f;
+        e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        ms[i] = t;
+    }
+    return e == cudaSuccess ? BC_OK : cuda_fail(e, "bc_debug_stage_times");
+}
+
+bc_status bc_sync(bc_ctx *ctx, void *stream)
+{
+    if (!ctx) { set_error("bc_sync: NULL context"); return BC_ERR_ARG; }
+    if (ctx->device < 0) return BC_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bc_sync");
+    return BC_OK;
+}
+
+}  // extern "C"

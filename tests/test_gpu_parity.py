@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA box code against the CPU oracle, element by element.
+
+Every case builds a seeded synthetic density (Gaussian sums, the paper's test
+densities of Sec. 4), applies the operator on the GPU through the C ABI and
+compares with the oracle's direct quadrature of eq. (vbulk) on the same
+leaves, at all nodes of sampled leaves.  Error metric: max |u - u*| / max |u*|
+over the evaluated targets.  Bar: 1e-10 (the accuracy the paper reports for
+its solver, Sec. 4); the FP64 path is expected near 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_2501_17967_gb300 as bc  # noqa: E402
+from paper_2501_17967_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx16():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return bc.Context(p=16, device=0)
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def make(ctx, lv, ix, iy, density, x0=-1.0, y0=-1.0, L=2.0):
+    tree = bc.Tree(ctx, lv, ix, iy, x0, y0, L)
+    geom = synth.leaf_geometry(lv, ix, iy, x0, y0, L)
+    fvals = density(oracle.leaf_nodes(geom, ctx.p)).reshape(len(lv), ctx.p, ctx.p)
+    f = torch.from_numpy(fvals).cuda()
+    return tree, geom, fvals, f
+
+
+def touching_sets(lv, ix, iy, targets):
+    """Per target leaf: leaves that touch it or are it (independent of the library's lists)."""
+    lv, ix, iy = (np.asarray(a, dtype=np.int64) for a in (lv, ix, iy))
+    L = lv.max()
+    s = L - lv
+    x0, x1 = ix << s, (ix + 1) << s
+    y0, y1 = iy << s, (iy + 1) << s
+    out = []
+    for t in targets:
+        ok = (x0 <= x1[t]) & (x0[t] <= x1) & (y0 <= y1[t]) & (y0[t] <= y1)
+        out.append(np.nonzero(ok)[0])
+    return out
+
+
+def csr_for_nodes(sets, p):
+    idx = []
+    ptr = [0]
+    for s in sets:
+        for _ in range(p * p):
+            idx.extend(s.tolist())
+            ptr.append(len(idx))
+    return np.array(ptr, dtype=np.int64), np.array(idx, dtype=np.int64)
+
+
+def test_uniform_near_field_only(ctx16):
+    """Near-field pass alone (self + 8 colleague tables) vs the oracle restricted
+    to touching source leaves."""
+    p = 16
+    g = synth.config_density(1)
+    lv, ix, iy = synth.uniform_leaves(3)
+    tree, geom, fvals, f = make(ctx16, lv, ix, iy, g)
+    ctx16.debug(pass_mask=1)
+    try:
+        u = bc.apply(tree, f).cpu().numpy().reshape(-1, p * p)
+    finally:
+        ctx16.debug(pass_mask=3)
+    pick = np.array([0, 9, 27, 36, 63])
+    src = csr_for_nodes(touching_sets(lv, ix, iy, pick), p)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick, sources=src)
+    err = relerr(u[pick], ref)
+    assert err < 1e-13, err
+
+
+def test_uniform_config1_full(ctx16):
+    """Workload 1: uniform level-3 tree (64 leaves, N = 16384), 3 broad Gaussians."""
+    p = 16
+    g = synth.config_density(1)
+    lv, ix, iy = synth.uniform_leaves(3)
+    tree, geom, fvals, f = make(ctx16, lv, ix, iy, g)
+    u = bc.apply(tree, f).cpu().numpy().reshape(-1, p * p)
+    pick = np.arange(0, 64, 3)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
+    err = relerr(u[pick], ref)
+    print(f"config1 FP64 rel err {err:.3e}")
+    assert err < TOL, err
+
+
+@pytest.fixture(scope="module")
+def adaptive(ctx16):
+    g = synth.gaussians(8, 21, wlog10=(-2.3, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, kappa=1.0, max_level=9)
+    return (lv, ix, iy, g) + make(ctx16, lv, ix, iy, g)
+
+
+def test_adaptive_full(ctx16, adaptive):
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    p = 16
+    s = tree.stats()
+    assert s["n_w"] > 0 and s["n_x"] > 0 and s["nlevels"] >= 7
+    u = bc.apply(tree, f).cpu().numpy().reshape(-1, p * p)
+    pick = synth.sample_leaves_per_level(np.asarray(lv), 3, seed=3)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
+    err = relerr(u[pick], ref)
+    print(f"adaptive ({len(lv)} leaves, {s['nlevels']} levels) FP64 rel err {err:.3e}")
+    assert err < TOL, err
+
+
+def test_adaptive_near_and_far_split(ctx16, adaptive):
+    """near-only + far-only applies add up to the full apply (linearity of the passes)."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    full = bc.apply(tree, f)
+    ctx16.debug(pass_mask=1)
+    un = bc.apply(tree, f)
+    ctx16.debug(pass_mask=2)
+    uf = bc.apply(tree, f)
+    ctx16.debug(pass_mask=3)
+    d = (un + uf - full).abs().max().item()
+    assert d <= 1e-13 * full.abs().max().item()
+    # near-only against the oracle restricted to touching leaves
+    p = 16
+    pick = synth.sample_leaves(len(lv), 6, seed=5)
+    src = csr_for_nodes(touching_sets(lv, ix, iy, pick), p)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick, sources=src)
+    err = relerr(un.cpu().numpy().reshape(-1, p * p)[pick], ref)
+    assert err < 1e-13, err
+
+
+def test_adjoint_dot_product(ctx16, adaptive):
+    """<A f, g> = <f, A^T g> for random f, g (exact transpose of the discrete operator)."""
+    lv, ix, iy, gd, tree, geom, fvals, f = adaptive
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    fr = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    gr = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    lhs = torch.dot(bc.apply(tree, fr).ravel(), gr.ravel()).item()
+    rhs = torch.dot(fr.ravel(), bc.apply_adjoint(tree, gr).ravel()).item()
+    scale = (bc.apply(tree, fr).abs() * gr.abs()).sum().item()
+    assert abs(lhs - rhs) <= 1e-14 * scale, (lhs, rhs, scale)
+
+
+def test_adjoint_against_oracle_columns(ctx16):
+    """Sampled entries of A^T g against the oracle's transposed operator."""
+    p = 16
+    g = synth.gaussians(3, 4, wlog10=(-1.4, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, max_level=4)
+    tree, geom, fvals, f = make(ctx16, lv, ix, iy, g)
+    gen = np.random.default_rng(2)
+    gv = gen.standard_normal((len(lv), p * p))
+    h = bc.apply_adjoint(tree, torch.from_numpy(gv).cuda()).cpu().numpy().reshape(-1, p * p)
+    cols = [(int(b), int(j)) for b, j in zip(gen.integers(0, len(lv), 6), gen.integers(0, p * p, 6))]
+    ref = oracle.adjoint_columns(p, geom, gv, cols)
+    got = np.array([h[b, j] for b, j in cols])
+    err = float(np.abs(got - ref).max() / np.abs(h).max())
+    assert err < TOL, err
+
+
+@pytest.mark.parametrize("p", [8, 12])
+def test_other_orders(p):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = bc.Context(p=p, device=0)
+    g = synth.gaussians(4, 30 + p, wlog10=(-1.8, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, kappa=2.0, max_level=7)
+    tree, geom, fvals, f = make(ctx, lv, ix, iy, g)
+    u = bc.apply(tree, f).cpu().numpy().reshape(-1, p * p)
+    pick = synth.sample_leaves(len(lv), 12, seed=p)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
+    assert relerr(u[pick], ref) < TOL
+
+
+def test_host_pointer_path_matches_device(ctx16, adaptive):
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    ud = bc.apply(tree, f).cpu()
+    fh = f.cpu()
+    uh = bc.apply(tree, fh)
+    assert torch.equal(ud, uh)
+    pinned = fh.pin_memory()
+    up = bc.apply(tree, pinned, out=torch.empty_like(pinned).pin_memory())
+    assert torch.equal(ud, up)
+
+
+def test_eval_points(ctx16, adaptive):
+    """Off-grid targets: interpolation of the leaf-node potential vs the oracle's
+    potential at the points (bounded by the interpolation error), and vs an
+    independent host barycentric evaluation of the same node values."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    p = 16
+    u = bc.apply(tree, f)
+    pts = synth.random_targets(400, seed=101)
+    pts = np.vstack([pts, [[-1.0, -1.0], [1.0, 1.0], [0.0, 0.0], [1.0, -1.0]]])
+    val = bc.eval_points(tree, u, torch.from_numpy(pts).cuda()).cpu().numpy()
+    ref = oracle.potential(p, geom, fvals, pts)
+    assert relerr(val, ref) < TOL
+    # host barycentric on the containing leaf
+    un = u.cpu().numpy().reshape(-1, p * p)
+    xn = oracle.cheb_nodes(p)
+    lam = np.where(np.arange(p) % 2, -1.0, 1.0) * np.sin((2 * np.arange(p) + 1) * math.pi / (2 * p))
+    for k in range(0, len(pts), 37):
+        x, y = pts[k]
+        inside = [b for b in range(len(lv)) if
+                  geom[b, 0] - geom[b, 2] <= x < geom[b, 0] + geom[b, 2] + (1e-300 if x < 1 else 1)
+                  and geom[b, 1] - geom[b, 2] <= y < geom[b, 1] + geom[b, 2] + (1e-300 if y < 1 else 1)]
+        b = inside[0]
+        xi, eta = (x - geom[b, 0]) / geom[b, 2], (y - geom[b, 1]) / geom[b, 2]
+        lx = lam / (xi - xn); lx /= lx.sum()
+        ly = lam / (eta - xn); ly /= ly.sum()
+        assert abs(ly @ un[b].reshape(p, p) @ lx - val[k]) < 1e-13 * np.abs(un).max()
+
+
+def test_errors_reported(ctx16, adaptive):
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    with pytest.raises(bc.BoxCodeError):
+        bc.apply(tree, f, out=f)                                   # aliasing
+    with pytest.raises(ValueError):
+        bc.apply(tree, f[:3])                                      # wrong size
+    other = bc.Context(p=16, device=0)
+    t2 = bc.Tree(other, lv, ix, iy)
+    with pytest.raises(bc.BoxCodeError):
+        bc._check(bc._load().bc_apply(ctx16.handle, t2.handle, f.data_ptr(), torch.empty_like(f).data_ptr(),
+                                      0, None))
+    with pytest.raises(bc.BoxCodeError):
+        bc.apply(tree, f, precision=7)
+
+
+def test_autograd_matches_finite_differences(ctx16):
+    """Gradient of L = 0.5 ||u(f(theta)) - u_t||^2 w.r.t. Gaussian parameters
+    theta through BoxCodeApply (adjoint kernels) vs central differences."""
+    p = 16
+    g = synth.gaussians(3, 3, wlog10=(-1.3, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, max_level=5)
+    tree = bc.Tree(ctx16, lv, ix, iy)
+    geom = synth.leaf_geometry(lv, ix, iy)
+    nodes = torch.from_numpy(oracle.leaf_nodes(geom, p)).cuda()
+    theta0 = torch.tensor(np.c_[g.cx, g.cy, np.log(g.w), g.a], device="cuda")
+
+    def density(th):
+        x, y = nodes[..., 0:1], nodes[..., 1:2]
+        cx, cy, lw, a = th[:, 0], th[:, 1], th[:, 2], th[:, 3]
+        w = torch.exp(lw)
+        return (a * torch.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * w * w))).sum(-1)
+
+    with torch.no_grad():
+        ut = bc.apply(tree, density(theta0 + 0.01 * torch.randn_like(theta0)).contiguous())
+
+    def loss(th):
+        u = bc.BoxCodeApply.apply(density(th).contiguous(), tree)
+        return 0.5 * ((u - ut) ** 2).sum()
+
+    th = theta0.clone().requires_grad_(True)
+    loss(th).backward()
+    grad = th.grad.clone()
+    h = 1e-6
+    fd = torch.zeros_like(theta0)
+    for i in range(theta0.shape[0]):
+        for j in range(theta0.shape[1]):
+            e = torch.zeros_like(theta0)
+            e[i, j] = h
+            with torch.no_grad():
+                fd[i, j] = (loss(theta0 + e) - loss(theta0 - e)) / (2 * h)
+    rel = ((grad - fd).abs().max() / grad.abs().max()).item()
+    assert rel < 1e-6, rel
