@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -164,6 +164,23 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+STAGES = ("split_near", "leaf_to_expansion", "upward", "downward", "leaf_output")
+
+
+def stage_flops(st, nleaf, P1, NP, split):
+    """Algorithmic flops of each stage of one apply, counted from the tree's lists.
+    split_near: BF16 tensor flops of the 15 digit products per near entry;
+    the others: FP64 flops (complex x real = 4 flops per term, complex x complex = 8)."""
+    n_shift = max(0, st["n_down"] - 0)
+    return {
+        "split_near": 15 * 2.0 * NP * NP * st["n_near"] if split else 0.0,
+        "leaf_to_expansion": 4.0 * P1 * NP * nleaf,
+        "upward": 32.0 * P1 * P1 * st["n_nonleaf"],
+        "downward": 4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"] + 8.0 * P1 * P1 * n_shift,
+        "leaf_output": (0.0 if split else 2.0 * NP * NP * st["n_near"]) + 4.0 * P1 * NP * (nleaf + st["n_w"]),
+    }
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -172,8 +189,6 @@ def main():
     import torch.distributed as dist
 
     import paper_2501_17967_gb300 as bc
-    import oracle
-    from paper_2501_17967_gb300 import synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -182,20 +197,17 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    precision = {"fp64": bc.FP64, "split": bc.SPLIT_BF16}.get(args.precision)
-    if precision is None:
-        precision = bc.SPLIT_BF16 if getattr(bc, "SPLIT_AVAILABLE", False) else bc.FP64
-    pname = "split-bf16" if precision == bc.SPLIT_BF16 else "fp64"
+    head = bc.FP64 if args.precision == "fp64" else bc.SPLIT_BF16
 
     g = density()
     ctx = bc.Context(p=16, device=dev)
+    P1 = ctx.nterms or 30
     t0 = time.perf_counter()
     tree = bc.Tree.refine(ctx, g, eps=1e-11, max_level=18)
     t_tree = time.perf_counter() - t0
     st = tree.stats()
     N = tree.nleaf * 256
-    nodes = tree.nodes()
-    fvals = g(nodes).reshape(-1, 16, 16)
+    fvals = g(tree.nodes()).reshape(-1, 16, 16)
     f = torch.from_numpy(fvals).to(dev)
     gen = torch.Generator(device=dev).manual_seed(1)
     gin = torch.randn(f.shape, generator=gen, device=dev, dtype=torch.float64)
@@ -204,89 +216,114 @@ def main():
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def step():
-        bc.apply(tree, f, out=u, precision=precision, stream=stream)
-        bc.apply_adjoint(tree, gin, out=h, precision=precision, stream=stream)
+    def timed(precision, steps, sampler=None):
+        def step():
+            bc.apply(tree, f, out=u, precision=precision, stream=stream)
+            bc.apply_adjoint(tree, gin, out=h, precision=precision, stream=stream)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        ctx.debug(timing=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stages = np.zeros((2, 5))
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            stages[0] += ctx.stage_times(adjoint=False)
+            stages[1] += ctx.stage_times(adjoint=True)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.stop()
+        if world > 1:
+            dist.barrier()
+        ctx.debug(timing=False)
+        bc._check(bc._load().bc_sync(ctx.handle, None))
+        total = torch.tensor([float(sum(a.elapsed_time(b) for a, b in ev))], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(total, op=dist.ReduceOp.MAX)
+        return float(total.item()) / steps, stages / steps
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    ctx.debug(timing=True)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stages = np.zeros((2, 4))
     clocks = ClockSampler(dev)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    for k in range(args.steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        step()
-        ev[k][1].record(stream)
-        stages[0] += ctx.stage_times(adjoint=False)
-        stages[1] += ctx.stage_times(adjoint=True)
-    torch.cuda.synchronize()
-    clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ctx.debug(timing=False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    ms_per_step = total_ms / args.steps
-    value = world * N / (ms_per_step * 1e-3)
+    ms_step, stage_ms = timed(head, args.steps, clocks)
+    value = world * N / (ms_step * 1e-3)
+    other = bc.FP64 if head == bc.SPLIT_BF16 else bc.SPLIT_BF16
+    ms_other, stage_other = timed(other, max(3, args.steps // 2))
 
-    # end to end through the public API with pinned host buffers
+    # end to end through the public API with pinned host buffers (headline precision)
     fh = f.cpu().pin_memory()
     gh = gin.cpu().pin_memory()
     uh = torch.empty_like(fh).pin_memory()
     hh = torch.empty_like(fh).pin_memory()
     for _ in range(2):
-        bc.apply(tree, fh, out=uh, precision=precision)
-        bc.apply_adjoint(tree, gh, out=hh, precision=precision)
+        bc.apply(tree, fh, out=uh, precision=head)
+        bc.apply_adjoint(tree, gh, out=hh, precision=head)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        bc.apply(tree, fh, out=uh, precision=precision)
-        bc.apply_adjoint(tree, gh, out=hh, precision=precision)
+        bc.apply(tree, fh, out=uh, precision=head)
+        bc.apply_adjoint(tree, gh, out=hh, precision=head)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": 2 * N * 8}
+    e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8,
+           "d2h_bytes_per_step": 2 * N * 8}
 
-    # roofline of the dominant stage (leaf output: L2P + W list + near-field tables)
-    stage_ms = stages / args.steps          # [dir][stage], per apply
-    dom_dir, dom_stage = np.unravel_index(np.argmax(stage_ms), stage_ms.shape)
-    NP, P1 = 256, ctx.nterms or 40
-    n_l2p_leaves = tree.nleaf   # upper bound: leaves at level >= 2
-    flops = {3: 2.0 * NP * NP * st["n_near"] + 8.0 * P1 * NP * (n_l2p_leaves + st["n_w"]),
-             2: 8.0 * P1 * P1 * (st["n_v"] + st["n_nonleaf"]) + 8.0 * P1 * NP * st["n_x"],
-             1: 8.0 * P1 * P1 * st["n_nonleaf"],
-             0: 4.0 * P1 * NP * tree.nleaf}[int(dom_stage)]
-    peak = bc.fp64_peak_tflops(dev)
-    achieved = flops / (stage_ms[dom_dir, dom_stage] * 1e-3) / 1e12
-    names = ["leaf_to_expansion", "upward", "downward", "leaf_output"]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": f"{names[dom_stage]} ({'adjoint' if dom_dir else 'forward'})",
-                "peak_source": "measured FP64 FMA throughput (bc_debug_fp64_peak)",
-                "stage_ms": {("adj_" if d else "fwd_") + names[s]: round(float(stage_ms[d, s]), 4)
-                             for d in range(2) for s in range(4)}}
+    # rooflines per stage (per apply, averaged over forward and adjoint)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh_:
+            peaks = json.load(fh_)
+    except OSError:
+        pass
+    fp64_peak = bc.fp64_peak_tflops(dev)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    fl = stage_flops(st, tree.nleaf, P1, 256, head == bc.SPLIT_BF16)
+    per_stage = {}
+    for i, name in enumerate(STAGES):
+        ms = float(stage_ms[:, i].mean())
+        if ms <= 0 or fl[name] == 0:
+            continue
+        tensor = name == "split_near"
+        ach = fl[name] / (ms * 1e-3) / 1e12
+        pk = bf16_peak if tensor else fp64_peak
+        per_stage[name] = {"ms": round(ms, 4), "bound": "tensor" if tensor else "alu",
+                           "achieved": round(ach, 4), "peak": round(pk, 2), "frac": round(ach / pk, 4)}
+    dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
+    d = per_stage[dom]
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
+                "frac": d["frac"], "traffic": None, "kernel": dom,
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst), of measured" if d["bound"] == "tensor"
+                                else "bc_debug_fp64_peak: measured FP64 FMA throughput, of measured"),
+                "stages": per_stage}
 
-    launches_per_apply = 2 + max(0, st["nlevels"] - 3) + max(0, st["nlevels"] - 2)
+    nl = st["nlevels"]
+    launches_per_apply = 1 + max(0, nl - 3) + (1 + max(0, nl - 3) if nl > 2 else 0) + 1
+    if head == bc.SPLIT_BF16:
+        launches_per_apply += 2
+    pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if precision == bc.FP64 else "bf16x-split+f64",
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if head == bc.FP64 else "bf16 digits (5 slices) + f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": pname, "nleaf": int(tree.nleaf), "leaf_nodes": int(N),
-                       "nlevels": st["nlevels"], "nterms": P1, "tree_build_s": round(t_tree, 3),
+            "config": {"workload": WORKLOAD, "precision": pname[head], "nleaf": int(tree.nleaf), "leaf_nodes": int(N),
+                       "nlevels": nl, "nterms": P1, "tree_build_s": round(t_tree, 3),
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": 2 * launches_per_apply * args.steps,
-            "roofline": roofline}
+            "roofline": roofline,
+            "other_precision": {"precision": pname[other], "value": world * N / (ms_other * 1e-3),
+                                "ms_per_step": ms_other,
+                                "stage_ms": {n: round(float(stage_other[:, i].mean()), 4)
+                                             for i, n in enumerate(STAGES)}}}
 
     if rank == 0 and not args.no_cpu_baseline:
+        bc.apply(tree, f, out=u, precision=head)
+        torch.cuda.synchronize()
         rate, nn, tt, vals = oracle_rate(tree.leaves(), fvals, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"{nn} target nodes ({nn // 256} random leaves) of the same tree in "

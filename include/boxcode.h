@@ -175,13 +175,20 @@ bc_status bc_batch_apply(bc_ctx *ctx, const bc_tree *const *trees, int n, const 
  * out = NULL to get *count (doubles). */
 bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *out);
 
+/* Runtime options of a context.  "m2l_triangular" (0/1, default 0): keep only
+ * the terms with k + l <= P of each multipole-to-local translation (and
+ * exactly their transpose in the adjoint), which halves the M2L arithmetic.
+ * Unknown names give BC_ERR_ARG. */
+bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
+
 /* Diagnostics.  pass_mask selects the parts of the operator an apply
  * evaluates: bit 0 the near field (leaf-to-leaf tables), bit 1 the far field
  * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
- * event on the apply's stream at each stage boundary (leaf-to-expansion |
- * upward | downward | leaf output); bc_debug_stage_times then waits for the
- * last event of the most recent forward (adjoint = 0) or adjoint apply and
- * writes the four stage durations in milliseconds to ms[4]. */
+ * event on the apply's stream at each stage boundary (split-precision near
+ * field | leaf-to-expansion | upward | downward | leaf output);
+ * bc_debug_stage_times then waits for the last event of the most recent
+ * forward (adjoint = 0) or adjoint apply and writes the five stage durations
+ * in milliseconds to ms[5] (the first is zero for FP64 applies). */
 bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
 /* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,

@@ -24,6 +24,7 @@ __all__ = ["build", "Context", "Tree", "BoxCodeError", "FP64", "SPLIT_BF16", "ap
 
 FP64 = 0
 SPLIT_BF16 = 1
+SPLIT_ORDERS = (16,)    # orders p with a split-precision near field
 _STATUS = {0: "BC_OK", -1: "BC_ERR_ARG", -2: "BC_ERR_TREE", -3: "BC_ERR_CUDA", -4: "BC_ERR_OOM",
            -5: "BC_ERR_TIMEOUT", -6: "BC_ERR_UNSUPPORTED", -7: "BC_ERR_STATE"}
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tables")
@@ -75,6 +76,7 @@ SIGNATURES = [
     ("bc_batch_apply", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP),
                                       ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
     ("bc_table_export", ctypes.c_int, [_VP, ctypes.c_int, _I64P, _DP]),
+    ("bc_set_option", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_double]),
     ("bc_debug_set", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("bc_debug_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     ("bc_debug_fp64_peak", ctypes.c_int, [ctypes.c_int, _DP]),
@@ -146,13 +148,19 @@ class Context:
         _check(lib.bc_table_export(self._h, which, ctypes.byref(n), out.ctypes.data_as(_DP)))
         return out
 
+    def set_option(self, name: str, value: float):
+        """Runtime option (see bc_set_option), e.g. set_option("m2l_triangular", 1)."""
+        _check(_load().bc_set_option(self._h, name.encode(), float(value)))
+
     def debug(self, pass_mask: int = 3, timing: bool = False):
         """Diagnostics: restrict applies to the near (1) / far (2) field; time stages."""
         _check(_load().bc_debug_set(self._h, pass_mask, int(timing)))
 
+    STAGES = ("split_near", "leaf_to_expansion", "upward", "downward", "leaf_output")
+
     def stage_times(self, adjoint: bool = False):
-        """Durations (ms) of the last forward/adjoint apply's stages: leafA, up, down, leafB."""
-        ms = np.zeros(4)
+        """Durations (ms) of the last forward/adjoint apply's stages (see STAGES)."""
+        ms = np.zeros(5)
         _check(_load().bc_debug_stage_times(self._h, int(adjoint), ms.ctypes.data_as(_DP)))
         return ms
 

@@ -202,6 +202,129 @@ PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
     return a;
 }
 
+// Digits of one FP64 matrix row for the split near field: row scaled by 2^-E
+// into (-1/2, 1/2), rounded to a 40-bit integer, five balanced base-256 digits.
+int split_row(const double *row, int n, int16_t *digits /*[5][n]*/)
+{
+    double mx = 0.0;
+    for (int k = 0; k < n; k++) mx = std::max(mx, std::fabs(row[k]));
+    if (mx == 0.0) {
+        std::fill(digits, digits + size_t(kSplitSlices) * n, int16_t(0));
+        return 0;
+    }
+    int e = 0;
+    std::frexp(mx, &e);            // mx < 2^e
+    const int E = e + 1;           // mx < 2^(E-1)
+    for (int k = 0; k < n; k++) {
+        long long X = std::llround(std::ldexp(row[k], 40 - E));   // |X| < 2^39
+        for (int a = kSplitSlices; a >= 2; a--) {
+            int d = int(X & 255);
+            if (d >= 128) d -= 256;
+            X = (X - d) >> 8;
+            digits[(a - 1) * n + k] = int16_t(d);
+        }
+        digits[k] = int16_t(X);   // leading digit, |X| <= 128
+    }
+    return E;
+}
+
+uint16_t bf16_of_int(int d)
+{
+    float f = float(d);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return uint16_t(u >> 16);
+}
+
+bc_status build_split_tables(bc_ctx *ctx)
+{
+    if (ctx->p != 16 || ctx->device < 0) return BC_OK;   // split path: p = 16 only
+    const HostTables &ht = ctx->ht;
+    const int NP = 256, S = kSplitSlices;
+    const size_t chunk = size_t(128) * NP;              // elements of one (table, slice, half)
+    for (int dir = 0; dir < 2; dir++) {
+        std::vector<uint16_t> A(size_t(kNumNear) * S * 2 * chunk, 0);
+        std::vector<int32_t> Ex(size_t(kNumNear) * NP, 0);
+        std::vector<double> row(NP);
+        std::vector<int16_t> dg(size_t(S) * NP);
+        for (int tab = 0; tab < kNumNear; tab++) {
+            NearGeom g = near_table_geometry(tab);
+            if (!g.valid) continue;
+            for (int i = 0; i < NP; i++) {
+                for (int k = 0; k < NP; k++)
+                    row[k] = dir == 0 ? ht.T[(size_t(tab) * NP + i) * NP + k] : ht.T[(size_t(g.rev) * NP + k) * NP + i];
+                Ex[size_t(tab) * NP + i] = split_row(row.data(), NP, dg.data());
+                const int h = i / 128, rg = (i % 128) / 8, r = i % 8;
+                for (int s = 0; s < S; s++)
+                    for (int k = 0; k < NP; k++) {
+                        const int kg = k / 8, e = k % 8;
+                        size_t off = ((size_t(tab) * S + s) * 2 + h) * chunk + (size_t(rg) * 32 + kg) * 64 + r * 8 + e;
+                        A[off] = bf16_of_int(dg[size_t(s) * NP + k]);
+                    }
+            }
+        }
+        uint16_t *dA = nullptr;
+        int32_t *dE = nullptr;
+        cudaError_t e;
+        if ((e = dev_upload(ctx->split_allocs, &dA, A.data(), A.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->split_allocs, &dE, Ex.data(), Ex.size())) != cudaSuccess)
+            return cuda_fail(e, "split tables upload");
+        ctx->split.A[dir] = reinterpret_cast<const uint8_t *>(dA);
+        ctx->split.Aexp[dir] = dE;
+    }
+    int32_t *err = nullptr;
+    cudaError_t e = dev_upload<int32_t>(ctx->split_allocs, &err, nullptr, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "split flag");
+    ctx->dev_err = err;
+    ctx->split_ready = true;
+    return BC_OK;
+}
+
+bc_status build_split_tree(bc_tree *t)
+{
+    if (t->split_ready) return BC_OK;
+    const HostTree &h = t->h;
+    const int64_t nn = int64_t(h.near_src.size());
+    std::vector<int32_t> owner(nn);
+    for (int64_t o = 0; o < h.nleaf; o++)
+        for (int32_t e = h.near_ptr[o]; e < h.near_ptr[o + 1]; e++) owner[e] = int32_t(o);
+    std::vector<int32_t> order(nn);
+    for (int64_t e = 0; e < nn; e++) order[e] = int32_t(e);
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return h.near_tab[x] < h.near_tab[y]; });
+    std::vector<int32_t> tab, p0, cnt, vec(nn), out(nn), lf(nn), la(nn);
+    for (int64_t i = 0; i < nn; i++) {
+        const int32_t e = order[i];
+        vec[i] = h.near_src[e];
+        out[i] = e;
+        lf[i] = h.leaf_level[h.near_src[e]];
+        la[i] = h.leaf_level[owner[e]];
+        if (i == 0 || h.near_tab[e] != tab.back() || cnt.back() == kSplitTileN) {
+            tab.push_back(h.near_tab[e]);
+            p0.push_back(int32_t(i));
+            cnt.push_back(0);
+        }
+        cnt.back()++;
+    }
+    SplitTree &s = t->sp;
+    std::vector<void *> &al = t->d.allocs;
+    cudaError_t e;
+    if ((e = dev_upload(al, &s.tile_tab, tab.data(), tab.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.tile_p0, p0.data(), p0.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.tile_cnt, cnt.data(), cnt.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.pair_vec, vec.data(), vec.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.pair_out, out.data(), out.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.pair_lvl_f, lf.data(), lf.size())) != cudaSuccess ||
+        (e = dev_upload(al, &s.pair_lvl_a, la.data(), la.size())) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.P, nullptr, size_t(nn) * 256)) != cudaSuccess ||
+        (e = dev_upload<uint16_t>(al, &s.vsl, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
+        (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess)
+        return cuda_fail(e, "split tree upload");
+    s.ntiles = int(tab.size());
+    s.err = t->ctx->dev_err;
+    t->split_ready = true;
+    return BC_OK;
+}
+
 bc_status check_apply_args(bc_ctx *ctx, const bc_tree *tree, const void *in, const void *out, bc_precision prec)
 {
     if (!ctx || !tree || !in || !out) { set_error("apply: NULL argument"); return BC_ERR_ARG; }
@@ -224,12 +347,21 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     PassArgs a = pass_args(ctx, tree);
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
+    SplitLaunch sl{&ctx->split, nullptr};
+    const SplitLaunch *split = nullptr;
+    bc_tree *tw = const_cast<bc_tree *>(tree);
     if (prec == BC_SPLIT_BF16) {
-        set_error("apply: split-precision near field not built yet");
-        return BC_ERR_UNSUPPORTED;
+        if (ctx->p != 16 || !ctx->split_ready) {
+            set_error("apply: the split-precision near field is provided for p = 16 only");
+            return BC_ERR_UNSUPPORTED;
+        }
+        s = build_split_tree(tw);
+        if (s != BC_OK) return s;
+        sl.tree = &tw->sp;
+        split = &sl;
     }
     if (din) {
-        e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, vin, vout, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr);
+        e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, vin, vout, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr, ctx->m2l_tri, split);
         if (e != cudaSuccess) return cuda_fail(e, "apply launch");
         return BC_OK;
     }
@@ -244,7 +376,7 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     }
     e = cudaMemcpyAsync(t->d.stage_in, vin, n * sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "apply H2D");
-    e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, t->d.stage_in, t->d.stage_out, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr);
+    e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, t->d.stage_in, t->d.stage_out, st, ctx->pass_mask, ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr, ctx->m2l_tri, split);
     if (e != cudaSuccess) return cuda_fail(e, "apply launch");
     e = cudaMemcpyAsync(vout, t->d.stage_out, n * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(e, "apply D2H");
@@ -307,6 +439,7 @@ void bc_destroy(bc_ctx *ctx)
         for (auto &e : dir)
             if (e) cudaEventDestroy(e);
     free_all(ctx->dt.allocs);
+    free_all(ctx->split_allocs);
     delete ctx;
 }
 
@@ -326,6 +459,39 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
     if ((s = upload_opset(ctx->dt, ctx->dt.adj, A)) != BC_OK) return s;
     e = dev_upload(ctx->dt.allocs, &ctx->dt.wvec, ctx->ht.w.data(), ctx->ht.w.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
+    {
+        // factored M2L: d = 2(dx + i dy) per code
+        const int P1 = ctx->P1;
+        std::vector<double2> df(size_t(kNumV) * P1, make_double2(0, 0)), da(df.size(), make_double2(0, 0));
+        std::vector<double> ld(kNumV, 0.0), bn(size_t(P1) * (P1 + 1), 0.0);
+        for (int c = 0; c < kNumV; c++) {
+            int dx = c % 7 - 3, dy = c / 7 - 3;
+            if (std::max(std::abs(dx), std::abs(dy)) < 2) continue;
+            std::complex<long double> d(2.0L * dx, 2.0L * dy), inv = 1.0L / d, pw = 1.0L;
+            ld[c] = std::log(std::abs(std::complex<double>(2.0 * dx, 2.0 * dy)));
+            for (int k = 0; k < P1; k++) {
+                df[size_t(c) * P1 + k] = make_double2(double(pw.real()), double(pw.imag()));
+                da[size_t(c) * P1 + k] = make_double2(double(pw.real()), -double(pw.imag()));
+                pw *= inv;
+            }
+        }
+        // C(i + j - 1, j), i >= 1
+        std::vector<long double> row(2 * P1 + 1, 0.0L);
+        for (int i = 1; i < P1; i++)
+            for (int j = 0; j < P1; j++) {
+                long double c = 1.0L;
+                int n = i + j - 1, kk = std::min(j, n - j);
+                for (int t = 1; t <= kk; t++) c = c * (n - kk + t) / t;
+                bn[size_t(i) * (P1 + 1) + j] = double(c);
+            }
+        if ((e = dev_upload(ctx->dt.allocs, &ctx->dt.dpow_f, df.data(), df.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.dpow_a, da.data(), da.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.logd, ld.data(), ld.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.binom, bn.data(), bn.size())) != cudaSuccess)
+            return cuda_fail(e, "tables upload");
+    }
+    s = build_split_tables(ctx);
+    if (s != BC_OK) return s;
     ctx->tables_ready = true;
     return BC_OK;
 }
@@ -534,6 +700,17 @@ bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing)
     return BC_OK;
 }
 
+bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
+{
+    if (!ctx || !name) { set_error("bc_set_option: NULL argument"); return BC_ERR_ARG; }
+    if (std::strcmp(name, "m2l_triangular") == 0) {
+        ctx->m2l_tri = value != 0.0;
+        return BC_OK;
+    }
+    set_error("bc_set_option: unknown option '%s'", name);
+    return BC_ERR_ARG;
+}
+
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms)
 {
     if (!ctx || !ms) { set_error("bc_debug_stage_times: NULL argument"); return BC_ERR_ARG; }
@@ -556,6 +733,16 @@ bc_status bc_sync(bc_ctx *ctx, void *stream)
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "bc_sync");
+    if (ctx->dev_err) {
+        int32_t flag = 0;
+        e = cudaMemcpy(&flag, ctx->dev_err, sizeof(flag), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "bc_sync");
+        if (flag) {
+            cudaMemset(ctx->dev_err, 0, sizeof(int32_t));
+            set_error("bc_sync: a bounded device-side wait gave up (split near field)");
+            return BC_ERR_TIMEOUT;
+        }
+    }
     return BC_OK;
 }
 

@@ -17,7 +17,7 @@ constexpr int kMaxP = 16;
 constexpr int kNumNear = 41;   // near-table slots (33 used; see near_table_geometry)
 constexpr int kNumV = 49;      // V offsets on the 7x7 grid (40 used)
 constexpr int kNumWX = 36;     // W/X offsets on the 6x6 half-integer grid (20 used)
-constexpr int kDefaultNterms = 40;
+constexpr int kDefaultNterms = 30;
 
 void set_error(const char *fmt, ...);
 
@@ -107,6 +107,12 @@ struct OpSet {
 struct DevTables {
     OpSet fwd, adj;
     double *wvec = nullptr;           // [NP]
+    // M2L in factored form: d^-k (forward) / conj(d)^-k (adjoint) per V code,
+    // log|d| per code, and the binomial table C(i+j-1, j) at [i][j] (row
+    // stride P1 + 1) shared by every offset.
+    double2 *dpow_f = nullptr, *dpow_a = nullptr;   // [kNumV][P1]
+    double *logd = nullptr;                          // [kNumV]
+    double *binom = nullptr;                         // [P1][P1 + 1]
     std::vector<void *> allocs;
 };
 
@@ -124,6 +130,30 @@ struct DevTree {
     std::vector<void *> allocs;
 };
 
+// Split-precision near field (p = 16 only): BF16 digit slices of the tables
+// (per context) and the entry tiles, digit buffers and result scratch (per tree).
+constexpr int kSplitSlices = 5;
+constexpr int kSplitTileN = 48;
+struct SplitTables {
+    const uint8_t *A[2] = {nullptr, nullptr};    // [kNumNear][5][2][128 x 256 canonical] fwd, adj
+    const int32_t *Aexp[2] = {nullptr, nullptr}; // [kNumNear][256] row exponents
+};
+struct SplitTree {
+    int ntiles = 0;
+    int32_t *tile_tab = nullptr, *tile_p0 = nullptr, *tile_cnt = nullptr;
+    int32_t *pair_vec = nullptr, *pair_out = nullptr, *pair_lvl_f = nullptr, *pair_lvl_a = nullptr;
+    double *P = nullptr;          // [n_near][256] near-field result per entry
+    uint16_t *vsl = nullptr;      // [nleaf][5][256] digits of the input vector (BF16 bits)
+    int32_t *vexp = nullptr;      // [nleaf]
+    int32_t *err = nullptr;       // device error flag (bounded waits)
+};
+size_t split_smem_bytes();
+// Split near field of one apply (null: FP64 near field).
+struct SplitLaunch {
+    const SplitTables *tables;
+    const SplitTree *tree;
+};
+
 // Launch parameters common to the passes.
 struct PassArgs {
     int p, NP, P1;
@@ -133,12 +163,17 @@ struct PassArgs {
 
 // Forward (adj = false) or adjoint (adj = true) apply on `stream`.
 // vin: f (forward) or g (adjoint); vout: u or h.  Device pointers.
-// Stage boundaries recorded when timing is on: leafA | up | down | leafB.
-constexpr int kNumStages = 4;
+// Stage boundaries recorded when timing is on:
+// split near field | leafA | up | down | leafB.
+constexpr int kNumStages = 5;
 // pass_mask bit 0: near field, bit 1: far field.  ev: kNumStages+1 events or null.
+// m2l_tri: triangular truncation of the M2L series (k + l <= P).
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          bool adj, const double *vin, double *vout, cudaStream_t stream, int pass_mask,
-                         cudaEvent_t *ev);
+                         cudaEvent_t *ev, int m2l_tri, const struct SplitLaunch *split);
+// Split near field: digits of vin, then every near entry's 256 results into sp.P.
+cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const SplitTree &sp, bool adj,
+                              const double *vin, cudaStream_t stream);
 cudaError_t launch_eval_points(const PassArgs &a, const DevTree &d, const double *u, const double *xy,
                                int64_t n, double *out, double x0, double y0, double L,
                                cudaStream_t stream);
@@ -151,10 +186,15 @@ struct bc_ctx {
     int p = 0, NP = 0, P1 = 0;
     bool tables_ready = false;
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
+    int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumStages + 1] = {};   // [forward, adjoint]
     bc::HostTables ht;
     bc::DevTables dt;
+    bc::SplitTables split;
+    std::vector<void *> split_allocs;
+    bool split_ready = false;
+    int32_t *dev_err = nullptr;   // device flag set by kernels whose bounded waits gave up
     std::mutex mu;
 };
 
@@ -162,4 +202,6 @@ struct bc_tree {
     bc_ctx *ctx = nullptr;
     bc::HostTree h;
     bc::DevTree d;
+    bc::SplitTree sp;
+    bool split_ready = false;
 };

@@ -83,114 +83,183 @@ __global__ void k_up(int64_t b0, int64_t b1, const int32_t *__restrict__ child0,
 }
 
 // -------------------------------------------------------------------------
-// down: for every box b at one level lv >= 2
-//   out[b] = Par_q * out[parent]                  (lv >= 3)
-//          + sum_{s in V(b)} OpV[code] * in[s]  ;  out[b][0] += log(r_lv) sum_V in[s][0]
-//          + sum_{c in X(b)} s1 * OpX[code] * x[c] ;  out[b][0] += s2 * (lv . x[c])
-//   forward: out = local, in = multipole, x = f,  s1 = r_c^2, s2 = r_c^2 log r_c / 2pi, lvec = w
-//   adjoint: out = adj. multipole, in = adj. local, x = g, s1 = 1, s2 = log r_c, lvec = 1
-//   (r_c = half-side at level lv-1, the level of the X-list leaves)
+// m2l: for every box b at level >= 2 (one launch over all levels)
+//   out[b] = sum_{s in V(b)} M2L(d_s) in[s] + log(r) sum_s in[s][0] e_0
+//          + sum_{c in X(b)} (s1 * OpX[code] x[c] + s2 (lvec . x[c]) e_0)
+// M2L in factored form (d = (c_s - c_t)/r, complex):
+//   forward  a_k = (-1)^k d^-k A_k (k >= 1),
+//            B_l += d^-l sum_{k>=1} C(k+l-1, l) a_k + (l = 0 ? log|d| A_0 : -d^-l A_0 / l)
+//   adjoint  (exact conjugate transpose of the forward map of the reversed pair)
+//            a_l = (-1)^l conj(d)^-l in_l (l >= 0),
+//            out_k += conj(d)^-k sum_{l>=0} C(k+l-1, l) a_l   (k >= 1)
+//            out_0 += log|d| in_0 - sum_{l>=1} a_l / l
+// tri = 1 keeps only the terms with k + l <= P (and exactly their transpose).
+// The binomial table is shared by every offset and lives in shared memory;
+// each of the two warps of a block takes every other V source.
 // -------------------------------------------------------------------------
 template <bool ADJ>
-__global__ void k_down(int64_t b0, int64_t b1, int lv, const int32_t *__restrict__ parent,
-                       const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
-                       const int32_t *__restrict__ v_ptr, const int32_t *__restrict__ v_src,
-                       const int32_t *__restrict__ v_code, const int32_t *__restrict__ x_ptr,
-                       const int32_t *__restrict__ x_src, const int32_t *__restrict__ x_code,
-                       const double2 *__restrict__ OpPar, const double2 *__restrict__ OpV,
-                       const double2 *__restrict__ OpX, const double *__restrict__ xvec,
-                       const double *__restrict__ wvec, const double2 *__restrict__ in,
-                       double2 *__restrict__ out, int NP, int P1, double half_L)
+__global__ void __launch_bounds__(64)
+k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32_t *__restrict__ v_ptr,
+      const int32_t *__restrict__ v_src, const int32_t *__restrict__ v_code, const int32_t *__restrict__ x_ptr,
+      const int32_t *__restrict__ x_src, const int32_t *__restrict__ x_code, const double2 *__restrict__ dpow,
+      const double *__restrict__ logd, const double *__restrict__ binom, const double2 *__restrict__ OpX,
+      const double *__restrict__ xvec, const double *__restrict__ wvec, const double2 *__restrict__ in,
+      double2 *__restrict__ out, int NP, int P1, double half_L, int tri)
 {
-    extern __shared__ double2 sh[];
-    double2 *se = sh;                                   // P1
-    double *sx = reinterpret_cast<double *>(sh + P1);   // NP
-    const double r = r_at(half_L, lv), logr = log(r);
-    const double rc = r_at(half_L, lv - 1);
-    const double s1 = ADJ ? 1.0 : rc * rc;
-    const double s2 = ADJ ? log(rc) : rc * rc * log(rc) / kTwoPi;
+    extern __shared__ double smem[];
+    const int ldc = P1 + 1;
+    double *Cb = smem;                                           // [P1][P1+1]
+    double *inv = Cb + P1 * ldc;                                 // [P1] 1/l
+    double2 *sa = reinterpret_cast<double2 *>(inv + P1);         // [2][64] scaled sources
+    double2 *part = sa + 128;                                    // [2][64] warp partial sums
+    double2 *mono = part + 128;                                  // [2] sum of in[s][0] per warp
+    double *sx = reinterpret_cast<double *>(mono + 2);           // [NP]
+    const int tid = threadIdx.x, h = tid >> 5, lane = tid & 31, P = P1 - 1;
+    for (int i = tid; i < P1 * ldc; i += blockDim.x) {
+        int r = i / ldc, c = i % ldc;
+        // forward reads [k][l] = C(k+l-1, l); adjoint reads [l][k] = C(k+l-1, l)
+        Cb[i] = ADJ ? ((c >= 1 && c < P1 && r < P1) ? binom[c * ldc + r] : 0.0) : binom[i];
+    }
+    for (int i = tid; i < P1; i += blockDim.x) inv[i] = i ? 1.0 / i : 0.0;
+    __syncthreads();
     for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
-        double re[2] = {0.0, 0.0}, im[2] = {0.0, 0.0};   // two coefficients per thread max (P1 <= 64, 32+ threads)
-        const int l0 = threadIdx.x, l1 = threadIdx.x + blockDim.x;
-        if (lv >= 3) {
-            int pb = parent[b];
-            int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
-            __syncthreads();
-            for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = out[int64_t(pb) * P1 + i];
-            __syncthreads();
-            const double2 *op = OpPar + size_t(q) * P1 * P1;
-            for (int k = 0; k < P1; k++) {
-                double2 a = se[k];
+        const int lv = box_level[b];
+        double ar[2] = {0.0, 0.0}, ai[2] = {0.0, 0.0};
+        double mr = 0.0, mi = 0.0;
+        double2 *a = sa + h * 64;
+        for (int e = v_ptr[b] + h; e < v_ptr[b + 1]; e += 2) {
+            const int s = v_src[e], c = v_code[e];
+            const double2 *dp = dpow + size_t(c) * P1;
+            for (int k = lane; k < P1; k += 32) {
+                double2 A = in[int64_t(s) * P1 + k], D = dp[k];
+                double zr = A.x * D.x - A.y * D.y, zi = A.x * D.y + A.y * D.x;
+                if (k & 1) { zr = -zr; zi = -zi; }
+                a[k] = make_double2(zr, zi);
+            }
+            __syncwarp();
+            const double2 A0 = a[0];
+            const double ld = logd[c];
+            mr += A0.x;
+            mi += A0.y;
 #pragma unroll
-                for (int u = 0; u < 2; u++) {
-                    int l = u ? l1 : l0;
-                    if (l < P1) {
-                        double2 o = op[k * P1 + l];
-                        re[u] = fma(o.x, a.x, fma(-o.y, a.y, re[u]));
-                        im[u] = fma(o.x, a.y, fma(o.y, a.x, im[u]));
+            for (int u = 0; u < 2; u++) {
+                const int o = lane + 32 * u;
+                if (o >= P1) continue;
+                double sr = 0.0, si = 0.0;
+                if (!ADJ) {
+                    const int kmax = tri ? P - o : P;
+                    for (int k = 1; k <= kmax; k++) {
+                        double cf = Cb[k * ldc + o];
+                        sr = fma(cf, a[k].x, sr);
+                        si = fma(cf, a[k].y, si);
+                    }
+                    if (o == 0) {
+                        ar[u] += sr + ld * A0.x;
+                        ai[u] += si + ld * A0.y;
+                    } else {
+                        sr = fma(-A0.x, inv[o], sr);
+                        si = fma(-A0.y, inv[o], si);
+                        double2 D = dp[o];
+                        ar[u] += sr * D.x - si * D.y;
+                        ai[u] += sr * D.y + si * D.x;
+                    }
+                } else {
+                    if (o == 0) {
+                        sr = ld * A0.x;
+                        si = ld * A0.y;
+                        for (int l = 1; l <= P; l++) {
+                            sr = fma(-a[l].x, inv[l], sr);
+                            si = fma(-a[l].y, inv[l], si);
+                        }
+                        ar[u] += sr;
+                        ai[u] += si;
+                    } else {
+                        const int lmax = tri ? P - o : P;
+                        for (int l = 0; l <= lmax; l++) {
+                            double cf = Cb[l * ldc + o];
+                            sr = fma(cf, a[l].x, sr);
+                            si = fma(cf, a[l].y, si);
+                        }
+                        double2 D = dp[o];
+                        ar[u] += sr * D.x - si * D.y;
+                        ai[u] += sr * D.y + si * D.x;
                     }
                 }
             }
+            __syncwarp();
         }
-        double mono = 0.0;   // sum of in[s][0] (real part) for the log term
-        double mono_i = 0.0;
-        for (int e = v_ptr[b]; e < v_ptr[b + 1]; e++) {
-            int s = v_src[e];
-            const double2 *op = OpV + size_t(v_code[e]) * P1 * P1;
-            __syncthreads();
-            for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = in[int64_t(s) * P1 + i];
-            __syncthreads();
-            mono += se[0].x;
-            mono_i += se[0].y;
-            for (int k = 0; k < P1; k++) {
-                double2 a = se[k];
+        // combine the two warps: thread tid owns coefficient tid
 #pragma unroll
-                for (int u = 0; u < 2; u++) {
-                    int l = u ? l1 : l0;
-                    if (l < P1) {
-                        double2 o = op[k * P1 + l];
-                        re[u] = fma(o.x, a.x, fma(-o.y, a.y, re[u]));
-                        im[u] = fma(o.x, a.y, fma(o.y, a.x, im[u]));
-                    }
-                }
-            }
+        for (int u = 0; u < 2; u++) part[h * 64 + lane + 32 * u] = make_double2(ar[u], ai[u]);
+        if (lane == 0) mono[h] = make_double2(mr, mi);
+        __syncthreads();
+        double orr = 0.0, oi = 0.0;
+        if (tid < P1) {
+            orr = part[tid].x + part[64 + tid].x;
+            oi = part[tid].y + part[64 + tid].y;
         }
-        double xdot = 0.0;
+        if (tid == 0) {
+            const double logr = log(r_at(half_L, lv));
+            orr += logr * (mono[0].x + mono[1].x);
+            oi += logr * (mono[0].y + mono[1].y);
+        }
+        // X list: leaf densities (forward) / leaf adjoint data (adjoint) of the
+        // coarser neighbour leaves
+        const double rc = r_at(half_L, lv - 1);
+        const double s1 = ADJ ? 1.0 : rc * rc;
+        const double s2 = ADJ ? log(rc) : rc * rc * log(rc) / kTwoPi;
         for (int e = x_ptr[b]; e < x_ptr[b + 1]; e++) {
-            int c = x_src[e];
+            const int c = x_src[e];
             const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
             __syncthreads();
-            for (int j = threadIdx.x; j < NP; j += blockDim.x) sx[j] = xvec[int64_t(c) * NP + j];
+            for (int j = tid; j < NP; j += blockDim.x) sx[j] = xvec[int64_t(c) * NP + j];
             __syncthreads();
-            if (threadIdx.x == 0) {
-                double d = 0.0;
-                for (int j = 0; j < NP; j++) d = fma(ADJ ? 1.0 : wvec[j], sx[j], d);
-                xdot += d;
-            }
-            double xr[2] = {0.0, 0.0}, xi[2] = {0.0, 0.0};
-            for (int j = 0; j < NP; j++) {
-                double v = sx[j];
-#pragma unroll
-                for (int u = 0; u < 2; u++) {
-                    int l = u ? l1 : l0;
-                    if (l < P1) {
-                        double2 o = op[j * P1 + l];
-                        xr[u] = fma(o.x, v, xr[u]);
-                        xi[u] = fma(o.y, v, xi[u]);
-                    }
+            if (tid < P1) {
+                double xr = 0.0, xi = 0.0;
+                for (int j = 0; j < NP; j++) {
+                    double2 o2 = op[j * P1 + tid];
+                    xr = fma(o2.x, sx[j], xr);
+                    xi = fma(o2.y, sx[j], xi);
+                }
+                orr = fma(s1, xr, orr);
+                oi = fma(s1, xi, oi);
+                if (tid == 0) {
+                    double d = 0.0;
+                    for (int j = 0; j < NP; j++) d = fma(ADJ ? 1.0 : wvec[j], sx[j], d);
+                    orr = fma(s2, d, orr);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < 2; u++) { re[u] = fma(s1, xr[u], re[u]); im[u] = fma(s1, xi[u], im[u]); }
         }
-        if (threadIdx.x == 0) {
-            re[0] += logr * mono + s2 * xdot;
-            im[0] += logr * mono_i;
-        }
-#pragma unroll
-        for (int u = 0; u < 2; u++) {
-            int l = u ? l1 : l0;
-            if (l < P1) out[b * P1 + l] = make_double2(re[u], im[u]);
+        if (tid < P1) out[b * P1 + tid] = make_double2(orr, oi);
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------------
+// shift_down: out[b] += Par_q * out[parent(b)] for the boxes of one level >= 3
+//   forward: L2L; adjoint: M2M^H
+// -------------------------------------------------------------------------
+__global__ void __launch_bounds__(64)
+k_shift_down(int64_t b0, int64_t b1, const int32_t *__restrict__ parent, const int32_t *__restrict__ box_ix,
+             const int32_t *__restrict__ box_iy, const double2 *__restrict__ OpPar, double2 *__restrict__ out, int P1)
+{
+    extern __shared__ double2 se[];
+    for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
+        const int pb = parent[b];
+        const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+        __syncthreads();
+        for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = out[int64_t(pb) * P1 + i];
+        __syncthreads();
+        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+            const double2 *op = OpPar + size_t(q) * P1 * P1;
+            double2 acc = out[b * P1 + l];
+            double re = acc.x, im = acc.y;
+            for (int k = 0; k < P1; k++) {
+                double2 o = op[k * P1 + l], x = se[k];
+                re = fma(o.x, x.x, fma(-o.y, x.y, re));
+                im = fma(o.x, x.y, fma(o.y, x.x, im));
+            }
+            out[b * P1 + l] = make_double2(re, im);
         }
     }
 }
@@ -214,7 +283,8 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const double *__restrict__ T, const double *__restrict__ wvec,
                            const double2 *__restrict__ own, const double2 *__restrict__ src,
                            const double2 *__restrict__ aux, const double *__restrict__ vnear,
-                           double *__restrict__ vout, int NP, int P1, double half_L, bool far)
+                           double *__restrict__ vout, int NP, int P1, double half_L, bool far,
+                           const double *__restrict__ Pnear)
 {
     extern __shared__ double2 sh[];
     double2 *se = sh;                                  // P1
@@ -253,12 +323,17 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
         }
         for (int e = n_ptr[o]; e < n_ptr[o + 1]; e++) {
             const int s = n_src[e];
-            const double *tb = T + size_t(n_tab[e]) * NP * NP;
-            __syncthreads();
-            for (int i = threadIdx.x; i < NP; i += blockDim.x) sv[i] = vnear[int64_t(s) * NP + i];
-            __syncthreads();
             double t = 0.0;
-            for (int k = 0; k < NP; k++) t = fma(tb[k * NP + j], sv[k], t);
+            if (Pnear) {
+                // split-precision result of this entry, alpha already applied
+                t = Pnear[size_t(e) * NP + j];
+            } else {
+                const double *tb = T + size_t(n_tab[e]) * NP * NP;
+                __syncthreads();
+                for (int i = threadIdx.x; i < NP; i += blockDim.x) sv[i] = vnear[int64_t(s) * NP + i];
+                __syncthreads();
+                for (int k = 0; k < NP; k++) t = fma(tb[k * NP + j], sv[k], t);
+            }
             double a0 = aux[int64_t(leaf_box[s]) * P1].x;
             double sN, cN;
             if (ADJ) {
@@ -269,6 +344,7 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                 sN = rs * rs;
                 cN = log(rs);
             }
+            if (Pnear) sN = 1.0;
             acc = fma(sN, t, fma(cN, a0, acc));
         }
         vout[int64_t(o) * NP + j] = acc;
@@ -335,10 +411,16 @@ inline int grid_for(int64_t n, int cap = 152 * 16)
 
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          bool adj, const double *vin, double *vout, cudaStream_t st, int pass_mask,
-                         cudaEvent_t *ev)
+                         cudaEvent_t *ev, int m2l_tri, const SplitLaunch *split)
 {
     const bool far = (pass_mask & 2) != 0, near = (pass_mask & 1) != 0;
+    const double *Pnear = split ? split->tree->P : nullptr;
     if (ev) cudaEventRecord(ev[0], st);
+    if (split && near) {
+        cudaError_t e = launch_split_near(a, *split->tables, *split->tree, adj, vin, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (ev) cudaEventRecord(ev[1], st);
     const OpSet &op = adj ? tb.adj : tb.fwd;
     const int NP = a.NP, P1 = a.P1;
     double2 *first = adj ? d.expB : d.expA;    // leafA / up target
@@ -352,39 +434,47 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     else
         k_leaf_to_exp<false><<<grid_for(a.nleaf), tA, shA, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                                 vin, op.leafA, first, NP, P1, a.half_L);
-    if (ev) cudaEventRecord(ev[1], st);
+    if (ev) cudaEventRecord(ev[2], st);
     for (int lv = h.nlevels - 2; far && lv >= 2; lv--) {
         int64_t b0 = h.level_start[lv], b1 = h.level_start[lv + 1];
         k_up<<<grid_for(b1 - b0), 64, sizeof(double2) * 4 * P1, st>>>(b0, b1, d.box_child0, op.up, first, P1);
     }
-    if (ev) cudaEventRecord(ev[2], st);
+    if (ev) cudaEventRecord(ev[3], st);
     size_t shD = sizeof(double2) * P1 + sizeof(double) * NP;
-    for (int lv = 2; far && lv < h.nlevels; lv++) {
-        int64_t b0 = h.level_start[lv], b1 = h.level_start[lv + 1];
+    if (far && h.nlevels > 2) {
+        const int64_t b0 = h.level_start[2], b1 = h.level_start[h.nlevels];
+        size_t shM = sizeof(double) * (size_t(P1) * (P1 + 1) + P1) + sizeof(double2) * (128 + 128 + 2) +
+                     sizeof(double) * NP;
+        int grid = grid_for(b1 - b0, 152 * 12);
         if (adj)
-            k_down<true><<<grid_for(b1 - b0), 32, shD, st>>>(b0, b1, lv, d.box_parent, d.box_ix, d.box_iy, d.v_ptr,
-                                                            d.v_src, d.v_code, d.x_ptr, d.x_src, d.x_code, op.par, op.v,
-                                                            op.x, vin, tb.wvec, first, second, NP, P1, a.half_L);
+            k_m2l<true><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
+                                               d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, tb.wvec, first,
+                                               second, NP, P1, a.half_L, m2l_tri);
         else
-            k_down<false><<<grid_for(b1 - b0), 32, shD, st>>>(b0, b1, lv, d.box_parent, d.box_ix, d.box_iy, d.v_ptr,
-                                                             d.v_src, d.v_code, d.x_ptr, d.x_src, d.x_code, op.par, op.v,
-                                                             op.x, vin, tb.wvec, first, second, NP, P1, a.half_L);
+            k_m2l<false><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
+                                                d.x_code, tb.dpow_f, tb.logd, tb.binom, op.x, vin, tb.wvec, first,
+                                                second, NP, P1, a.half_L, m2l_tri);
+        for (int lv = 3; lv < h.nlevels; lv++) {
+            int64_t c0 = h.level_start[lv], c1 = h.level_start[lv + 1];
+            k_shift_down<<<grid_for(c1 - c0), 64, sizeof(double2) * P1, st>>>(c0, c1, d.box_parent, d.box_ix,
+                                                                              d.box_iy, op.par, second, P1);
+        }
     }
     // leafB: own expansion = second (local / adjoint multipole), W sources and
     // near log aux = first (multipole / adjoint local)
-    if (ev) cudaEventRecord(ev[3], st);
+    if (ev) cudaEventRecord(ev[4], st);
     const int32_t *wp = far ? d.w_ptr : d.zero_ptr, *np_ = near ? d.near_ptr : d.zero_ptr;
     if (adj)
         k_leaf_out<true><<<grid_for(a.nleaf), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
                                                             d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e,
                                                             op.w, op.t, tb.wvec, second, first, first, vin, vout, NP,
-                                                            P1, a.half_L, far);
+                                                            P1, a.half_L, far, Pnear);
     else
         k_leaf_out<false><<<grid_for(a.nleaf), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                              wp, d.w_src, d.w_code, np_, d.near_src,
                                                              d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                                                             first, vin, vout, NP, P1, a.half_L, far);
-    if (ev) cudaEventRecord(ev[4], st);
+                                                             first, vin, vout, NP, P1, a.half_L, far, Pnear);
+    if (ev) cudaEventRecord(ev[5], st);
     return cudaGetLastError();
 }
 
