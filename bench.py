@@ -44,12 +44,22 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", default="adaptive20", choices=list(WORKLOADS),
+                    help="adaptive20: the benchmark workload; adaptive200: 200 Gaussians, widths 1e-4..1e-1")
+    ap.add_argument("--profile-run", action="store_true",
+                    help="only the warm-up and timed steps of the chosen precision (for profiler captures)")
     return ap.parse_args()
 
 
-def density():
+WORKLOADS = {
+    "adaptive20": (2, "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"),
+    "adaptive200": (3, "adaptive 200-Gaussian quadtree (widths 1e-4..1e-1), p=16, eps=1e-11"),
+}
+
+
+def density(workload="adaptive20"):
     from paper_2501_17967_gb300 import synth
-    return synth.config_density(2)
+    return synth.config_density(WORKLOADS[workload][0])
 
 
 # ---------------------------------------------------------------- clocks
@@ -135,7 +145,7 @@ def run_reference(args):
     import paper_2501_17967_gb300 as bc
     import oracle
     from paper_2501_17967_gb300 import synth
-    g = density()
+    g = density(args.workload)
     hctx = bc.Context(p=16, device=-1, cache_dir=None, build_tables=False)
     tree = bc.Tree.refine(hctx, g, eps=1e-11, max_level=18)
     leaves = tree.leaves()
@@ -154,7 +164,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nleaf": int(tree.nleaf), "leaf_nodes": int(tree.nleaf) * 256,
+            "config": {"workload": WORKLOADS[args.workload][1], "nleaf": int(tree.nleaf), "leaf_nodes": int(tree.nleaf) * 256,
                        "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": f"{nodes_tot} target nodes of randomly sampled leaves over {args.steps} steps "
@@ -199,7 +209,8 @@ def main():
     dev = torch.cuda.current_device()
     head = bc.FP64 if args.precision == "fp64" else bc.SPLIT_BF16
 
-    g = density()
+    g = density(args.workload)
+    workload_name = WORKLOADS[args.workload][1]
     ctx = bc.Context(p=16, device=dev)
     P1 = ctx.nterms or 30
     t0 = time.perf_counter()
@@ -252,6 +263,14 @@ def main():
         return float(total.item()) / steps, stages / steps
 
     clocks = ClockSampler(dev)
+    if args.profile_run:
+        ms_step, _ = timed(head, args.steps)
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "workload": workload_name, "nleaf": int(tree.nleaf),
+                              "ms_per_step": ms_step}))
+        if world > 1:
+            dist.destroy_process_group()
+        return
     ms_step, stage_ms = timed(head, args.steps, clocks)
     value = world * N / (ms_step * 1e-3)
     other = bc.FP64 if head == bc.SPLIT_BF16 else bc.SPLIT_BF16
@@ -311,7 +330,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if head == bc.FP64 else "bf16 digits (5 slices) + f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": pname[head], "nleaf": int(tree.nleaf), "leaf_nodes": int(N),
+            "config": {"workload": workload_name, "precision": pname[head], "nleaf": int(tree.nleaf), "leaf_nodes": int(N),
                        "nlevels": nl, "nterms": P1, "tree_build_s": round(t_tree, 3),
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
             "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": 2 * launches_per_apply * args.steps,
