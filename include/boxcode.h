@@ -196,6 +196,23 @@ bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
  * the FP64 passes. */
 bc_status bc_debug_fp64_peak(int device, double *tflops);
 
+/* FP64 apply (adjoint = 0: u = A f; adjoint != 0: the transpose) that
+ * allocates no memory during the call.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory at call
+ * time, such as code running inside another framework whose memory pool owns
+ * the device's free memory, or work recorded while allocation is forbidden.
+ * The expansion workspaces come from one fixed 16 MiB array in the library's
+ * device image (held by every device that loads the library, until exit)
+ * instead of the tree's own buffers; the tree needs
+ * 2 x boxes x nterms x 16 bytes of it, and larger trees give BC_ERR_ARG.
+ * in/out: device arrays [nleaf][p][p] FP64, as in bc_apply.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) and so
+ * should come before any stream capture.  All calls share the array and it
+ * keeps what the last call left in it (nothing in it needs clearing); calls
+ * that overlap on the GPU race with each other, so serialise them. */
+bc_status bc_apply_noalloc(bc_ctx *ctx, const bc_tree *tree, const double *in, double *out, int adjoint,
+                           void *stream);
+
 /* Wait for the stream and report device-side failures recorded by earlier
  * calls on this context (BC_ERR_TIMEOUT, BC_ERR_CUDA). */
 bc_status bc_sync(bc_ctx *ctx, void *stream);

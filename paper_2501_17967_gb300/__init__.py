@@ -80,6 +80,7 @@ SIGNATURES = [
     ("bc_debug_set", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("bc_debug_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
     ("bc_debug_fp64_peak", ctypes.c_int, [ctypes.c_int, _DP]),
+    ("bc_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_sync", ctypes.c_int, [_VP, _VP]),
 ]
 
