@@ -174,7 +174,7 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-STAGES = ("split_near", "leaf_to_expansion", "upward", "downward", "leaf_output")
+STAGES = ("split_near", "clear", "leaf_up", "downward", "leaf_output")
 
 
 def stage_flops(st, nleaf, P1, NP, split):
@@ -184,8 +184,8 @@ def stage_flops(st, nleaf, P1, NP, split):
     n_shift = max(0, st["n_down"] - 0)
     return {
         "split_near": 15 * 2.0 * NP * NP * st["n_near"] if split else 0.0,
-        "leaf_to_expansion": 4.0 * P1 * NP * nleaf,
-        "upward": 32.0 * P1 * P1 * st["n_nonleaf"],
+        "clear": 0.0,
+        "leaf_up": 4.0 * P1 * NP * nleaf + 32.0 * P1 * P1 * st["n_nonleaf"],
         "downward": 4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"] + 8.0 * P1 * P1 * n_shift,
         "leaf_output": (0.0 if split else 2.0 * NP * NP * st["n_near"]) + 4.0 * P1 * NP * (nleaf + st["n_w"]),
     }

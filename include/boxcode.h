@@ -185,7 +185,8 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  * evaluates: bit 0 the near field (leaf-to-leaf tables), bit 1 the far field
  * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
  * event on the apply's stream at each stage boundary (split-precision near
- * field | leaf-to-expansion | upward | downward | leaf output);
+ * field | counter reset | leaf-to-expansion with the upward pass | downward
+ * pass | leaf output);
  * bc_debug_stage_times then waits for the last event of the most recent
  * forward (adjoint = 0) or adjoint apply and writes the five stage durations
  * in milliseconds to ms[5] (the first is zero for FP64 applies). */

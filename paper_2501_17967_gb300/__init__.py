@@ -157,7 +157,7 @@ class Context:
         """Diagnostics: restrict applies to the near (1) / far (2) field; time stages."""
         _check(_load().bc_debug_set(self._h, pass_mask, int(timing)))
 
-    STAGES = ("split_near", "leaf_to_expansion", "upward", "downward", "leaf_output")
+    STAGES = ("split_near", "clear", "leaf_up", "downward", "leaf_output")
 
     def stage_times(self, adjoint: bool = False):
         """Durations (ms) of the last forward/adjoint apply's stages (see STAGES)."""

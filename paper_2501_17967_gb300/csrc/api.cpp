@@ -169,6 +169,8 @@ bc_status upload_tree(bc_tree *t)
 #undef UPV
     e = dev_upload<int32_t>(d.allocs, &d.zero_ptr, nullptr, size_t(h.nleaf) + 1);
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    e = dev_upload<int32_t>(d.allocs, &d.cnt, nullptr, 2 * h.box_level.size());
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     size_t nexp = size_t(h.box_level.size()) * P1;
     e = dev_upload<double2>(d.allocs, &d.expA, nullptr, nexp);
     if (e != cudaSuccess) return cuda_fail(e, "tree workspace");

@@ -126,6 +126,7 @@ struct DevTree {
     int32_t *x_ptr = nullptr, *x_src = nullptr, *x_code = nullptr;
     double2 *expA = nullptr, *expB = nullptr;  // [nbox][P1] workspaces
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
+    int32_t *cnt = nullptr;                    // [2][nbox] arrival counters (upward, downward passes)
     double *stage_in = nullptr, *stage_out = nullptr; // host-pointer staging [nleaf*NP]
     std::vector<void *> allocs;
 };

@@ -27,57 +27,71 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 __device__ __forceinline__ double r_at(double half_L, int lv) { return ldexp(half_L, -lv); }
 
 // -------------------------------------------------------------------------
-// leafA: out[box(leaf)][l] = s * sum_j Op[j][l] v[leaf][j]
-//   forward (P2M): Op = Q^T, s = r^2;  adjoint (L2P^H): Op = E^H, s = 1
+// leaf_up: per leaf, the box expansion from the leaf vector, then the upward
+// pass without per-level launches: a parent's expansion is computed by the
+// block whose child arrives last (arrival counter per box, no waiting).
+//   leaf:   ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
+//           forward (P2M): OpA = Q^T, s = r^2;  adjoint (L2P^H): OpA = E^H, s = 1
+//   parent: ex[p][l] = sum_q sum_k OpUp[q][k][l] ex[child_q(p)][k]    (levels >= 2)
+//           forward: M2M; adjoint: L2L^H
+// cnt[] must be zero on entry (the apply clears it).
 // -------------------------------------------------------------------------
 template <bool ADJ>
-__global__ void k_leaf_to_exp(int64_t nleaf, const int32_t *__restrict__ order,
-                              const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ leaf_level,
-                              const double *__restrict__ vin, const double2 *__restrict__ Op,
-                              double2 *__restrict__ out, int NP, int P1, double half_L)
+__global__ void __launch_bounds__(64)
+k_leaf_up(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
+          const int32_t *__restrict__ leaf_level, const int32_t *__restrict__ box_parent,
+          const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_child0,
+          const double *__restrict__ vin, const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp,
+          double2 *ex, int32_t *cnt, int NP, int P1, double half_L)
 {
-    extern __shared__ double sv[];
+    extern __shared__ double2 shu[];
+    double2 *sc = shu;                                     // 4 * P1
+    double *sv = reinterpret_cast<double *>(shu + 4 * P1); // NP
+    __shared__ int s_go;
     for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
-        int leaf = order[li];
+        const int leaf = order[li];
+        int b = leaf_box[leaf];
         __syncthreads();
         for (int j = threadIdx.x; j < NP; j += blockDim.x) sv[j] = vin[int64_t(leaf) * NP + j];
         __syncthreads();
-        double r = r_at(half_L, leaf_level[leaf]);
-        double s = ADJ ? 1.0 : r * r;
+        const double r = r_at(half_L, leaf_level[leaf]);
+        const double s = ADJ ? 1.0 : r * r;
         for (int l = threadIdx.x; l < P1; l += blockDim.x) {
-            double re = 0.0, im = 0.0;
-            for (int j = 0; j < NP; j++) {
-                double2 o = Op[j * P1 + l];
-                re = fma(o.x, sv[j], re);
-                im = fma(o.y, sv[j], im);
+            double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+            for (int j = 0; j < NP; j += 2) {
+                double2 o0 = OpA[j * P1 + l], o1 = OpA[(j + 1) * P1 + l];
+                re0 = fma(o0.x, sv[j], re0);
+                im0 = fma(o0.y, sv[j], im0);
+                re1 = fma(o1.x, sv[j + 1], re1);
+                im1 = fma(o1.y, sv[j + 1], im1);
             }
-            out[int64_t(leaf_box[leaf]) * P1 + l] = make_double2(s * re, s * im);
+            ex[int64_t(b) * P1 + l] = make_double2(s * (re0 + re1), s * (im0 + im1));
         }
-    }
-}
-
-// -------------------------------------------------------------------------
-// up: exp[b][l] = sum_q sum_k Op[q][k][l] exp[child_q(b)][k]   (non-leaf b)
-// -------------------------------------------------------------------------
-__global__ void k_up(int64_t b0, int64_t b1, const int32_t *__restrict__ child0,
-                     const double2 *__restrict__ Op, double2 *__restrict__ ex, int P1)
-{
-    extern __shared__ double2 se[];
-    for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
-        int c0 = child0[b];
-        if (c0 < 0) continue;   // leaf: uniform across the block
-        __syncthreads();
-        for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) se[i] = ex[int64_t(c0) * P1 + i];
-        __syncthreads();
-        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
-            double re = 0.0, im = 0.0;
-            for (int q = 0; q < 4; q++)
+        for (; cnt;) {
+            const int p = box_parent[b];
+            if (p < 0 || box_level[p] < 2) break;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) s_go = atomicAdd(&cnt[p], 1) == 3;
+            __syncthreads();
+            if (!s_go) break;
+            __threadfence();
+            const int c0 = box_child0[p];
+            for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
+            __syncthreads();
+            for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+                double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
                 for (int k = 0; k < P1; k++) {
-                    double2 o = Op[(q * P1 + k) * P1 + l], a = se[q * P1 + k];
-                    re = fma(o.x, a.x, fma(-o.y, a.y, re));
-                    im = fma(o.x, a.y, fma(o.y, a.x, im));
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        double2 o = OpUp[(q * P1 + k) * P1 + l], a = sc[q * P1 + k];
+                        re[q] = fma(o.x, a.x, fma(-o.y, a.y, re[q]));
+                        im[q] = fma(o.x, a.y, fma(o.y, a.x, im[q]));
+                    }
                 }
-            ex[b * P1 + l] = make_double2(re, im);
+                ex[int64_t(p) * P1 + l] = make_double2((re[0] + re[1]) + (re[2] + re[3]), (im[0] + im[1]) + (im[2] + im[3]));
+            }
+            b = p;
         }
     }
 }
@@ -103,8 +117,8 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
       const int32_t *__restrict__ v_src, const int32_t *__restrict__ v_code, const int32_t *__restrict__ x_ptr,
       const int32_t *__restrict__ x_src, const int32_t *__restrict__ x_code, const double2 *__restrict__ dpow,
       const double *__restrict__ logd, const double *__restrict__ binom, const double2 *__restrict__ OpX,
-      const double *__restrict__ xvec, const double *__restrict__ wvec, const double2 *__restrict__ in,
-      double2 *__restrict__ out, int NP, int P1, double half_L, int tri)
+      const double *__restrict__ xvec, const int32_t *__restrict__ leaf_box, const double2 *__restrict__ in,
+      double2 *out, int NP, int P1, double half_L, int tri)
 {
     extern __shared__ double smem[];
     const int ldc = P1 + 1;
@@ -117,8 +131,12 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
     const int tid = threadIdx.x, h = tid >> 5, lane = tid & 31, P = P1 - 1;
     for (int i = tid; i < P1 * ldc; i += blockDim.x) {
         int r = i / ldc, c = i % ldc;
-        // forward reads [k][l] = C(k+l-1, l); adjoint reads [l][k] = C(k+l-1, l)
-        Cb[i] = ADJ ? ((c >= 1 && c < P1 && r < P1) ? binom[c * ldc + r] : 0.0) : binom[i];
+        // forward reads [k][l] = C(k+l-1, l); adjoint reads [l][k] = C(k+l-1, l),
+        // with column k = 0 holding the coefficients -1/l of out_0 (l >= 1)
+        if (ADJ)
+            Cb[i] = (c >= 1 && c < P1 && r < P1) ? binom[c * ldc + r] : ((c == 0 && r >= 1 && r < P1) ? -1.0 / r : 0.0);
+        else
+            Cb[i] = binom[i];
     }
     for (int i = tid; i < P1; i += blockDim.x) inv[i] = i ? 1.0 / i : 0.0;
     __syncthreads();
@@ -147,44 +165,31 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
                 if (o >= P1) continue;
                 double sr = 0.0, si = 0.0;
                 if (!ADJ) {
+                    // B_o += d^-o (sum_{k>=1} C(k+o-1, o) a_k + c_o A_0), c_0 = log|d| (d^0 = 1), c_o = -1/o
                     const int kmax = tri ? P - o : P;
                     for (int k = 1; k <= kmax; k++) {
                         double cf = Cb[k * ldc + o];
                         sr = fma(cf, a[k].x, sr);
                         si = fma(cf, a[k].y, si);
                     }
-                    if (o == 0) {
-                        ar[u] += sr + ld * A0.x;
-                        ai[u] += si + ld * A0.y;
-                    } else {
-                        sr = fma(-A0.x, inv[o], sr);
-                        si = fma(-A0.y, inv[o], si);
-                        double2 D = dp[o];
-                        ar[u] += sr * D.x - si * D.y;
-                        ai[u] += sr * D.y + si * D.x;
-                    }
+                    const double c0 = o == 0 ? ld : -inv[o];
+                    sr = fma(c0, A0.x, sr);
+                    si = fma(c0, A0.y, si);
                 } else {
-                    if (o == 0) {
-                        sr = ld * A0.x;
-                        si = ld * A0.y;
-                        for (int l = 1; l <= P; l++) {
-                            sr = fma(-a[l].x, inv[l], sr);
-                            si = fma(-a[l].y, inv[l], si);
-                        }
-                        ar[u] += sr;
-                        ai[u] += si;
-                    } else {
-                        const int lmax = tri ? P - o : P;
-                        for (int l = 0; l <= lmax; l++) {
-                            double cf = Cb[l * ldc + o];
-                            sr = fma(cf, a[l].x, sr);
-                            si = fma(cf, a[l].y, si);
-                        }
-                        double2 D = dp[o];
-                        ar[u] += sr * D.x - si * D.y;
-                        ai[u] += sr * D.y + si * D.x;
+                    // out_o += conj(d)^-o sum_{l} Cb[l][o] a_l  (+ log|d| in_0 for o = 0)
+                    const int lmax = (tri && o > 0) ? P - o : P;
+                    for (int l = 0; l <= lmax; l++) {
+                        double cf = Cb[l * ldc + o];
+                        sr = fma(cf, a[l].x, sr);
+                        si = fma(cf, a[l].y, si);
                     }
+                    const double c0 = o == 0 ? ld : 0.0;
+                    sr = fma(c0, A0.x, sr);
+                    si = fma(c0, A0.y, si);
                 }
+                const double2 D = dp[o];
+                ar[u] += sr * D.x - si * D.y;
+                ai[u] += sr * D.y + si * D.x;
             }
             __syncwarp();
         }
@@ -204,10 +209,12 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
             oi += logr * (mono[0].y + mono[1].y);
         }
         // X list: leaf densities (forward) / leaf adjoint data (adjoint) of the
-        // coarser neighbour leaves
+        // coarser neighbour leaves.  The log term uses coefficient 0 of the
+        // leaf's own expansion from the upward pass: forward A_0 = r_c^2 (w.f)/2pi,
+        // adjoint B_0 = sum_j g_j, so the term is log(r_c) * that coefficient.
         const double rc = r_at(half_L, lv - 1);
         const double s1 = ADJ ? 1.0 : rc * rc;
-        const double s2 = ADJ ? log(rc) : rc * rc * log(rc) / kTwoPi;
+        const double logrc = log(rc);
         for (int e = x_ptr[b]; e < x_ptr[b + 1]; e++) {
             const int c = x_src[e];
             const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
@@ -215,19 +222,17 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
             for (int j = tid; j < NP; j += blockDim.x) sx[j] = xvec[int64_t(c) * NP + j];
             __syncthreads();
             if (tid < P1) {
-                double xr = 0.0, xi = 0.0;
-                for (int j = 0; j < NP; j++) {
-                    double2 o2 = op[j * P1 + tid];
-                    xr = fma(o2.x, sx[j], xr);
-                    xi = fma(o2.y, sx[j], xi);
+                double xr0 = 0.0, xi0 = 0.0, xr1 = 0.0, xi1 = 0.0;
+                for (int j = 0; j < NP; j += 2) {
+                    double2 o0 = op[j * P1 + tid], o1 = op[(j + 1) * P1 + tid];
+                    xr0 = fma(o0.x, sx[j], xr0);
+                    xi0 = fma(o0.y, sx[j], xi0);
+                    xr1 = fma(o1.x, sx[j + 1], xr1);
+                    xi1 = fma(o1.y, sx[j + 1], xi1);
                 }
-                orr = fma(s1, xr, orr);
-                oi = fma(s1, xi, oi);
-                if (tid == 0) {
-                    double d = 0.0;
-                    for (int j = 0; j < NP; j++) d = fma(ADJ ? 1.0 : wvec[j], sx[j], d);
-                    orr = fma(s2, d, orr);
-                }
+                orr = fma(s1, xr0 + xr1, orr);
+                oi = fma(s1, xi0 + xi1, oi);
+                if (tid == 0) orr = fma(logrc, in[int64_t(leaf_box[c]) * P1].x, orr);
             }
         }
         if (tid < P1) out[b * P1 + tid] = make_double2(orr, oi);
@@ -237,7 +242,7 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
 
 // -------------------------------------------------------------------------
 // shift_down: out[b] += Par_q * out[parent(b)] for the boxes of one level >= 3
-//   forward: L2L; adjoint: M2M^H
+//   forward: L2L; adjoint: M2M^H.  Two independent FMA chains per thread.
 // -------------------------------------------------------------------------
 __global__ void __launch_bounds__(64)
 k_shift_down(int64_t b0, int64_t b1, const int32_t *__restrict__ parent, const int32_t *__restrict__ box_ix,
@@ -252,14 +257,22 @@ k_shift_down(int64_t b0, int64_t b1, const int32_t *__restrict__ parent, const i
         __syncthreads();
         for (int l = threadIdx.x; l < P1; l += blockDim.x) {
             const double2 *op = OpPar + size_t(q) * P1 * P1;
-            double2 acc = out[b * P1 + l];
-            double re = acc.x, im = acc.y;
-            for (int k = 0; k < P1; k++) {
-                double2 o = op[k * P1 + l], x = se[k];
-                re = fma(o.x, x.x, fma(-o.y, x.y, re));
-                im = fma(o.x, x.y, fma(o.y, x.x, im));
+            const double2 acc = out[b * P1 + l];
+            double re0 = acc.x, im0 = acc.y, re1 = 0.0, im1 = 0.0;
+            int k = 0;
+            for (; k + 1 < P1; k += 2) {
+                double2 o0 = op[k * P1 + l], a0 = se[k], o1 = op[(k + 1) * P1 + l], a1 = se[k + 1];
+                re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
+                im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
+                re1 = fma(o1.x, a1.x, fma(-o1.y, a1.y, re1));
+                im1 = fma(o1.x, a1.y, fma(o1.y, a1.x, im1));
             }
-            out[b * P1 + l] = make_double2(re, im);
+            if (k < P1) {
+                double2 o0 = op[k * P1 + l], a0 = se[k];
+                re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
+                im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
+            }
+            out[b * P1 + l] = make_double2(re0 + re1, im0 + im1);
         }
     }
 }
@@ -425,20 +438,22 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const int NP = a.NP, P1 = a.P1;
     double2 *first = adj ? d.expB : d.expA;    // leafA / up target
     double2 *second = adj ? d.expA : d.expB;   // down target
-    const int tA = 64;
-    size_t shA = sizeof(double) * NP;
-    // leafA always runs: the near-field log term reads coefficient 0 of its output
-    if (adj)
-        k_leaf_to_exp<true><<<grid_for(a.nleaf), tA, shA, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                               vin, op.leafA, first, NP, P1, a.half_L);
-    else
-        k_leaf_to_exp<false><<<grid_for(a.nleaf), tA, shA, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                                vin, op.leafA, first, NP, P1, a.half_L);
+    // arrival counters of the upward pass start at zero
+    cudaError_t ce = cudaMemsetAsync(d.cnt, 0, sizeof(int32_t) * size_t(a.nbox), st);
+    if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[2], st);
-    for (int lv = h.nlevels - 2; far && lv >= 2; lv--) {
-        int64_t b0 = h.level_start[lv], b1 = h.level_start[lv + 1];
-        k_up<<<grid_for(b1 - b0), 64, sizeof(double2) * 4 * P1, st>>>(b0, b1, d.box_child0, op.up, first, P1);
-    }
+    // leafA + upward pass in one launch (leafA always runs: the near-field log
+    // term reads coefficient 0 of its output; without the far field no climb)
+    int32_t *cnt_up = d.cnt;
+    const size_t shU = sizeof(double) * NP + sizeof(double2) * 4 * P1;
+    if (adj)
+        k_leaf_up<true><<<grid_for(a.nleaf), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                                                           d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
+                                                           op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
+    else
+        k_leaf_up<false><<<grid_for(a.nleaf), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                                                            d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
+                                                            op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
     if (ev) cudaEventRecord(ev[3], st);
     size_t shD = sizeof(double2) * P1 + sizeof(double) * NP;
     if (far && h.nlevels > 2) {
@@ -448,11 +463,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         int grid = grid_for(b1 - b0, 152 * 12);
         if (adj)
             k_m2l<true><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
-                                               d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, tb.wvec, first,
+                                               d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
                                                second, NP, P1, a.half_L, m2l_tri);
         else
             k_m2l<false><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
-                                                d.x_code, tb.dpow_f, tb.logd, tb.binom, op.x, vin, tb.wvec, first,
+                                                d.x_code, tb.dpow_f, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
                                                 second, NP, P1, a.half_L, m2l_tri);
         for (int lv = 3; lv < h.nlevels; lv++) {
             int64_t c0 = h.level_start[lv], c1 = h.level_start[lv + 1];

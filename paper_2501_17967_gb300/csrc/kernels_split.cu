@@ -130,17 +130,36 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// S * 2^ex as an FP64 value (round to nearest even) by integer operations on
+// the bit pattern, keeping the conversion off the FP64 pipe.  |S| < 2^62.
+__device__ __forceinline__ double i64_scaled(long long S, int ex)
+{
+    if (S == 0) return 0.0;
+    const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
+    const unsigned long long m = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
+    const int lz = __clzll(m);
+    const unsigned long long t = m << lz;                 // leading one at bit 63
+    unsigned long long mant = t >> 11;                    // 53 bits with the leading one
+    const unsigned long long rem = t & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;
+    const long long be = (long long)(63 - lz + ex) + 1023;   // biased exponent
+    if (be <= 0) return 0.0;                              // below the normal range: negligible here
+    const unsigned long long bits = ((unsigned long long)be << 52) + (mant - (1ull << 52));
+    return __longlong_as_double((long long)(bits | sign));
+}
+
 // ---------------------------------------------------------------------------
-// Digits of the leaf vectors: vsl[leaf][a][k] (BF16 bits), vexp[leaf] = E with
-// max |v| < 2^(E-1).  Integer arithmetic on the FP64 bit patterns only.
+// Digits of the leaf vectors times alpha0: vsl[leaf][a][k] (BF16 bits),
+// vexp[leaf] = E with max |alpha0 v| < 2^(E-1).  One FP64 multiply per value;
+// the rest is integer arithmetic on the FP64 bit patterns.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *__restrict__ v,
+__global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *__restrict__ v, double alpha0,
                                                    uint16_t *__restrict__ vsl, int32_t *__restrict__ vexp)
 {
     __shared__ int wmax[8];
     const int k = threadIdx.x;
     for (int64_t leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
-        const long long bits = __double_as_longlong(v[leaf * kNP + k]);
+        const long long bits = __double_as_longlong(alpha0 * v[leaf * kNP + k]);
         const int e = int((bits >> 52) & 0x7FF);
         int m = e;
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -182,7 +201,7 @@ struct TileArgs {
 __global__ void __launch_bounds__(128, 1)
 k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restrict__ Aexp,
            const uint16_t *__restrict__ vsl, const int32_t *__restrict__ vexp, double *__restrict__ P,
-           double alpha0, int32_t *__restrict__ err)
+           int32_t *__restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *Bs = smem;                                            // kS * kBSlice
@@ -275,7 +294,7 @@ k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restric
                         S += (long long)__float2int_rn(__uint_as_float(d[g][q])) << (8 * (kS - 1 - g));
                     const int pv = T.pair_vec[p0 + c];
                     const int ex = ea + vexp[pv] - 48 - 2 * T.pair_lvl[p0 + c];
-                    P[size_t(T.pair_out[p0 + c]) * kNP + row] = ldexp(double(S), ex) * alpha0;
+                    P[size_t(T.pair_out[p0 + c]) * kNP + row] = i64_scaled(S, ex);
                 }
             }
         }
@@ -295,7 +314,7 @@ cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const Sp
                               const double *vin, cudaStream_t stream)
 {
     const int grid_v = int(std::min<int64_t>(a.nleaf, 152 * 16));
-    k_split_vec<<<grid_v, 256, 0, stream>>>(a.nleaf, vin, sp.vsl, sp.vexp);
+    k_split_vec<<<grid_v, 256, 0, stream>>>(a.nleaf, vin, a.half_L * a.half_L, sp.vsl, sp.vexp);
     if (sp.ntiles == 0) return cudaGetLastError();
     static bool attr_set = false;
     if (!attr_set) {
@@ -310,7 +329,7 @@ cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const Sp
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int grid = std::min(sp.ntiles, sms);
     k_near_mma<<<grid, 128, split_smem_bytes(), stream>>>(T, adj ? st.A[1] : st.A[0], adj ? st.Aexp[1] : st.Aexp[0],
-                                                          sp.vsl, sp.vexp, sp.P, a.half_L * a.half_L, sp.err);
+                                                          sp.vsl, sp.vexp, sp.P, sp.err);
     return cudaGetLastError();
 }
 
