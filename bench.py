@@ -54,6 +54,7 @@ def parse():
 WORKLOADS = {
     "adaptive20": (2, "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"),
     "adaptive200": (3, "adaptive 200-Gaussian quadtree (widths 1e-4..1e-1), p=16, eps=1e-11"),
+    "batch64": (None, "64 adaptive trees (about 2e2..2e4 leaves, log-uniform), p in {8,12,16}, batched"),
 }
 
 
@@ -191,10 +192,75 @@ def stage_flops(st, nleaf, P1, NP, split):
     }
 
 
+def run_batch64(args):
+    """64 independent Gaussian-sum densities on their own adaptive trees, p in
+    {8, 12, 16} round-robin; one batch (union of trees, CUDA graph, autotuned
+    launch shapes) per order.  A step = forward + adjoint of all 64."""
+    import torch
+
+    import paper_2501_17967_gb300 as bc
+    from paper_2501_17967_gb300 import synth
+    dev = torch.cuda.current_device()
+    ctxs = {p: bc.Context(p=p, device=dev) for p in (8, 12, 16)}
+    groups = {8: [], 12: [], 16: []}
+    t0 = time.perf_counter()
+    for k in range(64):
+        g, p, eps = synth.batch_density(k)
+        tree = bc.Tree.refine(ctxs[p], g, eps=eps, max_level=16)
+        groups[p].append((tree, torch.from_numpy(g(tree.nodes())).to(dev)))
+    t_tree = time.perf_counter() - t0
+    batches = {p: bc.Batch(ctxs[p], [t for t, _ in groups[p]]) for p in groups}
+    prec = {p: (bc.SPLIT_BF16 if (p in bc.SPLIT_ORDERS and args.precision == "split") else bc.FP64) for p in groups}
+    outs = {p: [torch.empty_like(f) for _, f in groups[p]] for p in groups}
+    adjs = {p: [torch.empty_like(f) for _, f in groups[p]] for p in groups}
+    for p in groups:
+        batches[p].autotune(prec[p])
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for p in groups:
+            ins = [f for _, f in groups[p]]
+            batches[p].run(ins, outs[p], precision=prec[p], stream=stream)
+            batches[p].run(outs[p], adjs[p], precision=prec[p], adjoint=True, stream=stream)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    nodes = sum(t.nleaf * p * p for p in groups for t, _ in groups[p])
+    leaves = [t.nleaf for p in groups for t, _ in groups[p]]
+    line = {"metric": METRIC + " (batched)", "value": nodes / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64 (p=8,12) / bf16 digits + f64 (p=16)" if args.precision == "split" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch64"][1], "trees": 64, "leaves_min": min(leaves),
+                       "leaves_max": max(leaves), "leaves_total": sum(leaves), "leaf_nodes": nodes,
+                       "tree_build_s": round(t_tree, 2),
+                       "launch_shapes": {str(p): batches[p].shape(prec[p], 0) for p in groups},
+                       "l2": "flushed (256 MB write) between timed steps"},
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch64":
+        return run_batch64(args)
     import torch
     import torch.distributed as dist
 

@@ -162,10 +162,34 @@ bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, do
 bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy,
                          int64_t n, double *out, void *stream);
 
-/* Many independent applies in one launch sequence: trees[k] (all of this
- * context's p), f[k] -> u[k] (device pointers).  adjoint != 0 applies A^T. */
-bc_status bc_batch_apply(bc_ctx *ctx, const bc_tree *const *trees, int n, const double *const *f,
-                         double *const *u, bc_precision prec, int adjoint, void *stream);
+/* Batched applies: many independent densities on different trees (all of
+ * this context's p and root side L) in one launch per pass.  A batch is the
+ * disjoint union of its trees (leaves and boxes renumbered, lists
+ * concatenated), uploaded once; every pass of an apply then covers all trees
+ * in a single kernel launch, and the whole pass sequence is captured once per
+ * (precision, direction) as a CUDA graph and replayed.  The trees must stay
+ * alive while the batch exists.  bc_batch_create allocates the union's lists,
+ * workspaces and input/output buffers. */
+typedef struct bc_batch bc_batch;
+bc_status bc_batch_create(bc_ctx *ctx, const bc_tree *const *trees, int n, bc_batch **out);
+void bc_batch_destroy(bc_batch *batch);
+int64_t bc_batch_nleaf(const bc_batch *batch);   /* total leaves */
+/* in[k] -> out[k] for tree k (device arrays [nleaf_k][p][p]); adjoint != 0
+ * applies A^T.  Ordered on `stream`: gather into the union's buffer, replay of
+ * the captured graph, scatter to out[k].  The first run of a (precision,
+ * direction) captures the graph (with the context's autotune flag set it
+ * first runs bc_batch_autotune). */
+bc_status bc_batch_run(bc_ctx *ctx, bc_batch *batch, const double *const *in, double *const *out,
+                       bc_precision prec, int adjoint, void *stream);
+/* Times a few launch shapes (resident blocks per SM of the leaf kernels and
+ * of the M2L kernel) for both directions on `stream`, keeps the fastest graph
+ * and records the choice in the context, keyed by precision, direction and
+ * log2 of the batch's leaf count, for later batches of that size.  The batch
+ * buffers' contents are overwritten. */
+bc_status bc_batch_autotune(bc_ctx *ctx, bc_batch *batch, bc_precision prec, void *stream);
+/* The launch shape in use for (precision, adjoint): 0 before the first run. */
+bc_status bc_batch_shape(const bc_batch *batch, int precision, int adjoint, int *leaf_blocks_per_sm,
+                         int *m2l_blocks_per_sm);
 
 /* Copy a host table for inspection: which = 0 nodes[p], 1 w[p*p] (integrals
  * of the Lagrange basis), 2 near tables [41][p*p][p*p] (unused slots zero),

@@ -19,8 +19,8 @@ import numpy as np
 
 from . import build as _build_mod
 
-__all__ = ["build", "Context", "Tree", "BoxCodeError", "FP64", "SPLIT_BF16", "apply", "apply_adjoint",
-           "BoxCodeApply", "lib_path"]
+__all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "apply", "apply_adjoint",
+           "eval_points", "BoxCodeApply", "lib_path"]
 
 FP64 = 0
 SPLIT_BF16 = 1
@@ -73,8 +73,14 @@ SIGNATURES = [
     ("bc_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_eval_points", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP]),
-    ("bc_batch_apply", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP),
-                                      ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int, _VP]),
+    ("bc_batch_create", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("bc_batch_destroy", None, [_VP]),
+    ("bc_batch_nleaf", _I64, [_VP]),
+    ("bc_batch_run", ctypes.c_int, [_VP, _VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.c_int, ctypes.c_int,
+                                    _VP]),
+    ("bc_batch_autotune", ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    ("bc_batch_shape", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
     ("bc_table_export", ctypes.c_int, [_VP, ctypes.c_int, _I64P, _DP]),
     ("bc_set_option", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_double]),
     ("bc_debug_set", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
@@ -122,9 +128,9 @@ class Context:
     """Order-p context on one CUDA device (device=-1: host-only, for inspection)."""
 
     def __init__(self, p: int = 16, nterms: int = 0, device: int = 0, split_slices: int = 0,
-                 cache_dir: str | None = _DEFAULT_CACHE, build_tables: bool = True):
+                 cache_dir: str | None = _DEFAULT_CACHE, build_tables: bool = True, autotune: bool = False):
         lib = _load()
-        cfg = _Config(p, nterms, 1, split_slices, 0)
+        cfg = _Config(p, nterms, 1, split_slices, int(autotune))
         h = _VP()
         _check(lib.bc_create(ctypes.byref(cfg), device, ctypes.byref(h)))
         self._h = h
@@ -332,14 +338,50 @@ def eval_points(tree: Tree, u, xy, out=None, stream=None):
     return out
 
 
-def batch_apply(ctx: Context, trees, fs, us, precision: int = FP64, adjoint: bool = False, stream=None):
-    """Apply A (or A^T) to many independent densities on trees of this context."""
-    n = len(trees)
-    th = (_VP * n)(*[t.handle for t in trees])
-    fp = (_VP * n)(*[ctypes.c_void_p(f.data_ptr()) for f in fs])
-    up = (_VP * n)(*[ctypes.c_void_p(u.data_ptr()) for u in us])
-    _check(_load().bc_batch_apply(ctx.handle, th, n, fp, up, precision, int(adjoint), _stream_ptr(stream)))
-    return us
+class Batch:
+    """Many trees of one context applied together (one launch per pass, CUDA graph)."""
+
+    def __init__(self, ctx: Context, trees):
+        self.ctx = ctx
+        self.trees = list(trees)   # kept alive while the batch exists
+        arr = (_VP * len(self.trees))(*[t.handle for t in self.trees])
+        h = _VP()
+        _check(_load().bc_batch_create(ctx.handle, arr, len(self.trees), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def nleaf(self) -> int:
+        return int(_load().bc_batch_nleaf(self._h))
+
+    def run(self, ins, outs, precision: int = FP64, adjoint: bool = False, stream=None):
+        n = len(self.trees)
+        for t, x, y in zip(self.trees, ins, outs):
+            _check_tensor(x, t, "input")
+            _check_tensor(y, t, "output")
+        ip = (_VP * n)(*[ctypes.c_void_p(x.data_ptr()) for x in ins])
+        op = (_VP * n)(*[ctypes.c_void_p(y.data_ptr()) for y in outs])
+        _check(_load().bc_batch_run(self.ctx.handle, self._h, ip, op, precision, int(adjoint), _stream_ptr(stream)))
+        return outs
+
+    def autotune(self, precision: int = FP64, stream=None):
+        _check(_load().bc_batch_autotune(self.ctx.handle, self._h, precision, _stream_ptr(stream)))
+        return {d: self.shape(precision, d) for d in (0, 1)}
+
+    def shape(self, precision: int = FP64, adjoint: int = 0):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        _check(_load().bc_batch_shape(self._h, precision, adjoint, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().bc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd():

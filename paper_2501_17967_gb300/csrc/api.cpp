@@ -277,6 +277,8 @@ bc_status build_split_tables(bc_ctx *ctx)
     int32_t *err = nullptr;
     cudaError_t e = dev_upload<int32_t>(ctx->split_allocs, &err, nullptr, 1);
     if (e != cudaSuccess) return cuda_fail(e, "split flag");
+    e = split_prepare();
+    if (e != cudaSuccess) return cuda_fail(e, "split kernel attributes");
     ctx->dev_err = err;
     ctx->split_ready = true;
     return BC_OK;
@@ -397,6 +399,74 @@ void set_error(const char *fmt, ...)
     va_end(ap);
 }
 
+}  // namespace bc
+
+struct bc_batch {
+    bc_ctx *ctx = nullptr;
+    std::vector<const bc_tree *> trees;
+    std::vector<int64_t> leaf_offset;
+    bc_tree *u = nullptr;
+    double *in_buf = nullptr, *out_buf = nullptr;
+    cudaStream_t cap = nullptr;
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        int leaf_bps = 0, m2l_bps = 0;
+    } g[2][2];   // [precision][adjoint]
+    std::vector<void *> allocs;
+};
+
+namespace bc {
+namespace {
+
+int tune_key(int prec, int adj, int64_t nleaf)
+{
+    int lg = 0;
+    while ((int64_t(1) << (lg + 1)) <= nleaf) lg++;
+    return prec * 1024 + adj * 512 + lg;
+}
+
+bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bps, cudaGraphExec_t *out)
+{
+    bc_ctx *ctx = b->ctx;
+    PassArgs a = pass_args(ctx, b->u);
+    a.leaf_bps = leaf_bps;
+    a.m2l_bps = m2l_bps;
+    SplitLaunch sl{&ctx->split, &b->u->sp};
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
+    cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,
+                                  ctx->m2l_tri, prec == BC_SPLIT_BF16 ? &sl : nullptr);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(b->cap, &graph);
+    if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(le, "batch: capture launch");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch: end capture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e == cudaSuccess ? BC_OK : cuda_fail(e, "batch: instantiate");
+}
+
+bc_status batch_copy(bc_batch *b, const double *const *in, double *const *out, bool gather, cudaStream_t st)
+{
+    const int n = int(b->trees.size());
+    for (int k0 = 0; k0 < n; k0 += kBatchChunk) {
+        BatchPtrs bp{};
+        bp.n = std::min(kBatchChunk, n - k0);
+        for (int i = 0; i < bp.n; i++) {
+            bp.in[i] = gather ? in[k0 + i] : nullptr;
+            bp.out[i] = gather ? nullptr : out[k0 + i];
+            bp.off[i] = b->leaf_offset[k0 + i];
+        }
+        bp.off[bp.n] = b->leaf_offset[k0 + bp.n];
+        cudaError_t e = launch_batch_copy(bp, gather, gather ? b->in_buf : b->out_buf, b->ctx->NP, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch: copy launch");
+    }
+    return BC_OK;
+}
+
+}  // namespace
 }  // namespace bc
 
 using namespace bc;
@@ -664,14 +734,158 @@ bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, cons
     return e == cudaSuccess ? BC_OK : cuda_fail(e, "eval");
 }
 
-bc_status bc_batch_apply(bc_ctx *ctx, const bc_tree *const *trees, int n, const double *const *f, double *const *u,
-                         bc_precision prec, int adjoint, void *stream)
+bc_status bc_batch_create(bc_ctx *ctx, const bc_tree *const *trees, int n, bc_batch **out)
 {
-    if (!ctx || n < 0 || (n > 0 && (!trees || !f || !u))) { set_error("bc_batch_apply: bad argument"); return BC_ERR_ARG; }
+    if (!ctx || !trees || n <= 0 || !out) { set_error("bc_batch_create: bad argument"); return BC_ERR_ARG; }
+    *out = nullptr;
+    if (ctx->device < 0) { set_error("bc_batch_create: host-only context"); return BC_ERR_STATE; }
+    if (!ctx->tables_ready) { set_error("bc_batch_create: call bc_tables_build first"); return BC_ERR_STATE; }
+    std::vector<const HostTree *> hs;
     for (int k = 0; k < n; k++) {
-        bc_status s = apply_impl(ctx, trees[k], f[k], u[k], prec, stream, adjoint != 0);
-        if (s != BC_OK) return s;
+        if (!trees[k] || trees[k]->ctx != ctx) { set_error("bc_batch_create: tree %d missing or from another context", k); return BC_ERR_ARG; }
+        hs.push_back(&trees[k]->h);
     }
+    bc_batch *b = new (std::nothrow) bc_batch();
+    if (!b) { set_error("bc_batch_create: out of host memory"); return BC_ERR_OOM; }
+    b->ctx = ctx;
+    b->trees.assign(trees, trees + n);
+    b->u = new (std::nothrow) bc_tree();
+    if (!b->u) { delete b; set_error("bc_batch_create: out of host memory"); return BC_ERR_OOM; }
+    b->u->ctx = ctx;
+    b->u->is_union = true;
+    bc_status s = merge_host_trees(hs, b->u->h, b->leaf_offset);
+    cudaError_t e = cudaSuccess;
+    if (s == BC_OK) {
+        e = cudaSetDevice(ctx->device);
+        if (e != cudaSuccess) s = cuda_fail(e, "cudaSetDevice");
+    }
+    if (s == BC_OK) s = upload_tree(b->u);
+    const size_t nv = size_t(b->u->h.nleaf) * ctx->NP;
+    if (s == BC_OK && ((e = dev_upload<double>(b->allocs, &b->in_buf, nullptr, nv)) != cudaSuccess ||
+                       (e = dev_upload<double>(b->allocs, &b->out_buf, nullptr, nv)) != cudaSuccess))
+        s = cuda_fail(e, "batch buffers");
+    if (s == BC_OK && ctx->split_ready) s = build_split_tree(b->u);
+    if (s == BC_OK && (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        s = cuda_fail(e, "batch stream");
+    if (s != BC_OK) {
+        bc_batch_destroy(b);
+        return s;
+    }
+    *out = b;
+    return BC_OK;
+}
+
+void bc_batch_destroy(bc_batch *b)
+{
+    if (!b) return;
+    if (b->ctx && b->ctx->device >= 0) cudaSetDevice(b->ctx->device);
+    for (auto &row : b->g)
+        for (auto &gr : row)
+            if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->u) {
+        free_all(b->u->d.allocs);
+        delete b->u;
+    }
+    free_all(b->allocs);
+    delete b;
+}
+
+bc_status bc_batch_autotune(bc_ctx *ctx, bc_batch *b, bc_precision prec, void *stream)
+{
+    if (!ctx || !b || b->ctx != ctx) { set_error("bc_batch_autotune: bad argument"); return BC_ERR_ARG; }
+    if (prec == BC_SPLIT_BF16 && !ctx->split_ready) { set_error("bc_batch_autotune: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    static const int cand[][2] = {{16, 12}, {8, 8}, {4, 4}, {16, 16}, {8, 12}, {32, 12}, {16, 6}};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int adj = 0; adj < 2; adj++) {
+        float best = 1e30f;
+        cudaGraphExec_t best_exec = nullptr;
+        int bl = 0, bm = 0;
+        for (const auto &c : cand) {
+            cudaGraphExec_t ex = nullptr;
+            bc_status s = batch_capture(b, int(prec), adj, c[0], c[1], &ex);
+            if (s != BC_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            float ms = 1e30f;
+            for (int rep = 0; rep < 4; rep++) {
+                cudaEventRecord(e0, st);
+                cudaGraphLaunch(ex, st);
+                cudaEventRecord(e1, st);
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) { cudaGraphExecDestroy(ex); cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(e, "bc_batch_autotune"); }
+                float t = 0.0f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (rep > 0) ms = std::min(ms, t);
+            }
+            if (ms < best) {
+                if (best_exec) cudaGraphExecDestroy(best_exec);
+                best = ms; best_exec = ex; bl = c[0]; bm = c[1];
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
+        }
+        auto &g = b->g[int(prec)][adj];
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = best_exec; g.leaf_bps = bl; g.m2l_bps = bm;
+        const int key = tune_key(int(prec), adj, b->u->h.nleaf);
+        bool found = false;
+        for (auto &kv : ctx->tuned)
+            if (kv.first == key) { kv.second = {bl, bm}; found = true; }
+        if (!found) ctx->tuned.push_back({key, {bl, bm}});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return BC_OK;
+}
+
+bc_status bc_batch_run(bc_ctx *ctx, bc_batch *b, const double *const *in, double *const *out, bc_precision prec,
+                       int adjoint, void *stream)
+{
+    if (!ctx || !b || b->ctx != ctx || !in || !out) { set_error("bc_batch_run: bad argument"); return BC_ERR_ARG; }
+    if (prec != BC_FP64 && prec != BC_SPLIT_BF16) { set_error("bc_batch_run: unknown precision"); return BC_ERR_ARG; }
+    if (prec == BC_SPLIT_BF16 && !ctx->split_ready) { set_error("bc_batch_run: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    const int n = int(b->trees.size());
+    for (int k = 0; k < n; k++)
+        if (!in[k] || !out[k] || !is_device_ptr(in[k]) || !is_device_ptr(out[k]) || in[k] == out[k]) {
+            set_error("bc_batch_run: array %d must be distinct device memory", k);
+            return BC_ERR_ARG;
+        }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int adj = adjoint != 0;
+    auto &g = b->g[int(prec)][adj];
+    if (!g.exec) {
+        if (ctx->cfg.autotune) {
+            bc_status s = bc_batch_autotune(ctx, b, prec, stream);
+            if (s != BC_OK) return s;
+        } else {
+            int lb = 0, mb = 0;
+            const int key = tune_key(int(prec), adj, b->u->h.nleaf);
+            for (auto &kv : ctx->tuned)
+                if (kv.first == key) { lb = kv.second.first; mb = kv.second.second; }
+            bc_status s = batch_capture(b, int(prec), adj, lb, mb, &g.exec);
+            if (s != BC_OK) return s;
+            g.leaf_bps = lb; g.m2l_bps = mb;
+        }
+    }
+    bc_status s = batch_copy(b, in, nullptr, true, st);
+    if (s != BC_OK) return s;
+    e = cudaGraphLaunch(g.exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "bc_batch_run: graph launch");
+    return batch_copy(b, nullptr, out, false, st);
+}
+
+int64_t bc_batch_nleaf(const bc_batch *b) { return b ? b->u->h.nleaf : 0; }
+
+bc_status bc_batch_shape(const bc_batch *b, int precision, int adjoint, int *leaf_blocks_per_sm, int *m2l_blocks_per_sm)
+{
+    if (!b || precision < 0 || precision > 1 || !leaf_blocks_per_sm || !m2l_blocks_per_sm) { set_error("bc_batch_shape: bad argument"); return BC_ERR_ARG; }
+    const auto &g = b->g[precision][adjoint != 0];
+    *leaf_blocks_per_sm = g.leaf_bps;
+    *m2l_blocks_per_sm = g.m2l_bps;
     return BC_OK;
 }
 

@@ -149,18 +149,27 @@ struct SplitTree {
     int32_t *err = nullptr;       // device error flag (bounded waits)
 };
 size_t split_smem_bytes();
+cudaError_t split_prepare();   // kernel attributes of the split path (before any capture)
 // Split near field of one apply (null: FP64 near field).
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
 };
 
-// Launch parameters common to the passes.
+// Launch parameters common to the passes.  leaf_bps / m2l_bps: resident
+// blocks per SM used to size the grids of the leaf kernels and of the M2L
+// kernel (tunable; 0 = default).
 struct PassArgs {
     int p, NP, P1;
     double half_L;        // r at level 0
     int64_t nleaf, nbox;
+    int leaf_bps = 0, m2l_bps = 0;
 };
+
+// Disjoint union of trees (batched applies): leaves and boxes renumbered,
+// boxes sorted by (level, tree, Morton order), lists concatenated.
+bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree &out,
+                           std::vector<int64_t> &leaf_offset);
 
 // Forward (adj = false) or adjoint (adj = true) apply on `stream`.
 // vin: f (forward) or g (adjoint); vout: u or h.  Device pointers.
@@ -175,6 +184,15 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 // Split near field: digits of vin, then every near entry's 256 results into sp.P.
 cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const SplitTree &sp, bool adj,
                               const double *vin, cudaStream_t stream);
+// Batched applies: copy the per-tree arrays into / out of the union's vectors.
+constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
+struct BatchPtrs {
+    const double *in[kBatchChunk];
+    double *out[kBatchChunk];
+    int64_t off[kBatchChunk + 1];   // first union leaf of each tree in this chunk (+ end)
+    int n;
+};
+cudaError_t launch_batch_copy(const BatchPtrs &bp, bool gather, double *union_buf, int NP, cudaStream_t st);
 cudaError_t launch_eval_points(const PassArgs &a, const DevTree &d, const double *u, const double *xy,
                                int64_t n, double *out, double x0, double y0, double L,
                                cudaStream_t stream);
@@ -196,11 +214,14 @@ struct bc_ctx {
     std::vector<void *> split_allocs;
     bool split_ready = false;
     int32_t *dev_err = nullptr;   // device flag set by kernels whose bounded waits gave up
+    // launch shapes chosen by the autotuner: key = precision*1024 + adjoint*512 + log2(nleaf)
+    std::vector<std::pair<int, std::pair<int, int>>> tuned;
     std::mutex mu;
 };
 
 struct bc_tree {
     bc_ctx *ctx = nullptr;
+    bool is_union = false;   // the union tree of a batch
     bc::HostTree h;
     bc::DevTree d;
     bc::SplitTree sp;

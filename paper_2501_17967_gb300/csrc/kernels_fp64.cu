@@ -420,6 +420,23 @@ inline int grid_for(int64_t n, int cap = 152 * 16)
     return int(n < cap ? (n > 0 ? n : 1) : cap);
 }
 
+// Per-tree arrays <-> the union's vectors for batched applies.
+__global__ void k_batch_copy(BatchPtrs bp, bool gather, double *__restrict__ ubuf, int NP)
+{
+    const int64_t base = bp.off[0], total = (bp.off[bp.n] - base) * NP;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < total; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t leaf = base + i / NP;
+        int lo = 0, hi = bp.n - 1;   // tree of this leaf: last k with off[k] <= leaf
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (bp.off[mid] <= leaf) lo = mid; else hi = mid - 1;
+        }
+        const int64_t local = (leaf - bp.off[lo]) * NP + i % NP;
+        if (gather) ubuf[base * NP + i] = bp.in[lo][local];
+        else bp.out[lo][local] = ubuf[base * NP + i];
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
@@ -447,11 +464,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     int32_t *cnt_up = d.cnt;
     const size_t shU = sizeof(double) * NP + sizeof(double2) * 4 * P1;
     if (adj)
-        k_leaf_up<true><<<grid_for(a.nleaf), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+        k_leaf_up<true><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                            d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
                                                            op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
     else
-        k_leaf_up<false><<<grid_for(a.nleaf), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+        k_leaf_up<false><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                             d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
                                                             op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
     if (ev) cudaEventRecord(ev[3], st);
@@ -460,7 +477,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         const int64_t b0 = h.level_start[2], b1 = h.level_start[h.nlevels];
         size_t shM = sizeof(double) * (size_t(P1) * (P1 + 1) + P1) + sizeof(double2) * (128 + 128 + 2) +
                      sizeof(double) * NP;
-        int grid = grid_for(b1 - b0, 152 * 12);
+        int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : 12));
         if (adj)
             k_m2l<true><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
                                                d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
@@ -480,16 +497,25 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (ev) cudaEventRecord(ev[4], st);
     const int32_t *wp = far ? d.w_ptr : d.zero_ptr, *np_ = near ? d.near_ptr : d.zero_ptr;
     if (adj)
-        k_leaf_out<true><<<grid_for(a.nleaf), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
+        k_leaf_out<true><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
                                                             d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e,
                                                             op.w, op.t, tb.wvec, second, first, first, vin, vout, NP,
                                                             P1, a.half_L, far, Pnear);
     else
-        k_leaf_out<false><<<grid_for(a.nleaf), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+        k_leaf_out<false><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                              wp, d.w_src, d.w_code, np_, d.near_src,
                                                              d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
                                                              first, vin, vout, NP, P1, a.half_L, far, Pnear);
     if (ev) cudaEventRecord(ev[5], st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_copy(const BatchPtrs &bp, bool gather, double *union_buf, int NP, cudaStream_t st)
+{
+    const int64_t total = (bp.off[bp.n] - bp.off[0]) * NP;
+    if (total <= 0) return cudaSuccess;
+    const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 8));
+    k_batch_copy<<<grid, 256, 0, st>>>(bp, gather, union_buf, NP);
     return cudaGetLastError();
 }
 

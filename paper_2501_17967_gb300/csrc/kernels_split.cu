@@ -310,19 +310,17 @@ k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restric
 
 size_t split_smem_bytes() { return size_t(kS) * kBSlice + kAChunk + 64; }
 
+cudaError_t split_prepare()
+{
+    return cudaFuncSetAttribute(k_near_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(split_smem_bytes()));
+}
+
 cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const SplitTree &sp, bool adj,
                               const double *vin, cudaStream_t stream)
 {
     const int grid_v = int(std::min<int64_t>(a.nleaf, 152 * 16));
     k_split_vec<<<grid_v, 256, 0, stream>>>(a.nleaf, vin, a.half_L * a.half_L, sp.vsl, sp.vexp);
     if (sp.ntiles == 0) return cudaGetLastError();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_near_mma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(split_smem_bytes()));
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
     TileArgs T{sp.tile_tab, sp.tile_p0, sp.tile_cnt, sp.pair_vec, sp.pair_out, adj ? sp.pair_lvl_a : sp.pair_lvl_f,
                sp.ntiles};
     int sms = 152;

@@ -64,18 +64,20 @@ def config_density(cfg: int) -> GaussianSum:
     raise ValueError(cfg)
 
 
-def batch_density(k: int) -> tuple[GaussianSum, int]:
-    """Density k of the 64-tree batch and its order p (p in {8, 12, 16} round-robin).
+def batch_density(k: int) -> tuple[GaussianSum, int, float]:
+    """Density k of the 64-tree batch, its order p (8, 12, 16 round-robin) and
+    the refinement tolerance eps = max(1e-11, 10^-p) (the paper pairs the
+    order with the tolerance, p ~ log10(1/eps), Sec. 4.2).
 
-    Tree size is steered by the number of Gaussians and the smallest width,
-    drawn from the tree's own seed so that leaf counts spread log-uniformly
-    over roughly 2e2..2e4."""
+    A per-tree knob t ~ U[0,1] (drawn first from the tree's seed) sets the
+    number of Gaussians (3..20) and the smallest width; with the per-order
+    width offset the trees span roughly 2e2..2e4 leaves, log-uniformly."""
     rng = np.random.default_rng(1000 + k)
-    t = rng.uniform(0.0, 1.0)                    # log-uniform size knob
-    n = int(round(2 + 18 * t))
-    wmin = -1.3 - 1.7 * t
+    t = rng.uniform(0.0, 1.0)
+    n = int(round(3 + 17 * t))
     p = (8, 12, 16)[k % 3]
-    return gaussians(n, 1000 + k, wlog10=(wmin, -1.0)), p
+    wmin = -1.0 - {8: 0.0, 12: 0.35, 16: 0.75}[p] - 1.6 * t
+    return gaussians(n, 1000 + k, wlog10=(wmin, -0.9)), p, max(1e-11, 10.0 ** (-p))
 
 
 def random_targets(n: int, seed: int = 101) -> np.ndarray:
