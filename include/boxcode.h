@@ -199,9 +199,16 @@ bc_status bc_batch_shape(const bc_batch *batch, int precision, int adjoint, int 
  * out = NULL to get *count (doubles). */
 bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *out);
 
-/* Runtime options of a context.  "m2l_triangular" (0/1, default 0): keep only
- * the terms with k + l <= P of each multipole-to-local translation (and
- * exactly their transpose in the adjoint), which halves the M2L arithmetic.
+/* Runtime options of a context.
+ *   "m2l_triangular" (0/1, default 0): keep only the terms with k + l <= P of
+ *     each multipole-to-local translation (and exactly their transpose in the
+ *     adjoint), which halves the M2L arithmetic but loses accuracy.
+ *   "wait_limit" (default 2^26): polls of each bounded device-side wait of the
+ *     split-precision kernel before it gives up, records the failure (reported
+ *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns.
+ *   "debug_withhold_copy" (0/1, default 0): diagnostics; the split-precision
+ *     kernel never starts its table copy, so its first wait runs out (tests of
+ *     the timeout path).
  * Unknown names give BC_ERR_ARG. */
 bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
 

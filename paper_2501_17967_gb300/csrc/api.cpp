@@ -923,6 +923,15 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
         ctx->m2l_tri = value != 0.0;
         return BC_OK;
     }
+    if (std::strcmp(name, "wait_limit") == 0) {
+        if (!(value >= 1.0 && value <= 1e15)) { set_error("bc_set_option: wait_limit must be in [1, 1e15]"); return BC_ERR_ARG; }
+        ctx->split.wait_limit = (long long)value;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "debug_withhold_copy") == 0) {
+        ctx->split.withhold_copy = value != 0.0;
+        return BC_OK;
+    }
     set_error("bc_set_option: unknown option '%s'", name);
     return BC_ERR_ARG;
 }

@@ -138,6 +138,8 @@ constexpr int kSplitTileN = 48;
 struct SplitTables {
     const uint8_t *A[2] = {nullptr, nullptr};    // [kNumNear][5][2][128 x 256 canonical] fwd, adj
     const int32_t *Aexp[2] = {nullptr, nullptr}; // [kNumNear][256] row exponents
+    long long wait_limit = 1ll << 26;            // polls of a bounded mbarrier wait
+    int withhold_copy = 0;                       // diagnostics: never start the table copy (forces a timeout)
 };
 struct SplitTree {
     int ntiles = 0;

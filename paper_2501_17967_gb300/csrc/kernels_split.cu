@@ -35,7 +35,6 @@ constexpr int kS = kSplitSlices;              // 5 digits
 constexpr int kN = kSplitTileN;               // 48 entries per tile
 constexpr int kBSlice = kN * kNP * 2;         // bytes of one B digit slice (24 KB)
 constexpr int kAChunk = 128 * kNP * 2;        // bytes of one A digit slice, 128 rows (64 KB)
-constexpr long long kSpinLimit = 1ll << 26;   // bounded waits (well over a second)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -73,10 +72,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 }
 
 // Bounded wait on an mbarrier phase; false when the limit ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit)
 {
     const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; it++) {
+    for (long long it = 0; it < limit; it++) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -201,7 +200,7 @@ struct TileArgs {
 __global__ void __launch_bounds__(128, 1)
 k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restrict__ Aexp,
            const uint16_t *__restrict__ vsl, const int32_t *__restrict__ vexp, double *__restrict__ P,
-           int32_t *__restrict__ err)
+           int32_t *__restrict__ err, long long wait_limit, int withhold)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *Bs = smem;                                            // kS * kBSlice
@@ -245,9 +244,12 @@ k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restric
             for (int h = 0; h < 2 && !failed; h++) {
                 if (tid == 0) {
                     const uint8_t *src = Asl + (size_t((tab * kS + (a - 1)) * 2 + h)) * kAChunk;
-                    mbar_expect_tx(&bars[0], kAChunk);
-                    for (int q = 0; q < 4; q++) bulk_g2s(As + q * (kAChunk / 4), src + q * (kAChunk / 4), kAChunk / 4, &bars[0]);
-                    bool ok = mbar_wait(&bars[0], phA);
+                    if (!withhold) {
+                        mbar_expect_tx(&bars[0], kAChunk);
+                        for (int q = 0; q < 4; q++)
+                            bulk_g2s(As + q * (kAChunk / 4), src + q * (kAChunk / 4), kAChunk / 4, &bars[0]);
+                    }
+                    bool ok = mbar_wait(&bars[0], phA, wait_limit);
                     if (ok) {
                         tc_fence_after();
                         for (int b = 1; b + a <= kS + 1; b++) {
@@ -260,7 +262,7 @@ k_near_mma(TileArgs T, const uint8_t *__restrict__ Asl, const int32_t *__restric
                             }
                         }
                         umma_commit(&bars[1]);
-                        ok = mbar_wait(&bars[1], phM);
+                        ok = mbar_wait(&bars[1], phM, wait_limit);
                     }
                     if (!ok) {
                         atomicExch(err, 1);
@@ -327,7 +329,8 @@ cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const Sp
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
     const int grid = std::min(sp.ntiles, sms);
     k_near_mma<<<grid, 128, split_smem_bytes(), stream>>>(T, adj ? st.A[1] : st.A[0], adj ? st.Aexp[1] : st.Aexp[0],
-                                                          sp.vsl, sp.vexp, sp.P, sp.err);
+                                                          sp.vsl, sp.vexp, sp.P, sp.err, st.wait_limit,
+                                                          st.withhold_copy);
     return cudaGetLastError();
 }
 

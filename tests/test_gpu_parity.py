@@ -337,3 +337,24 @@ def test_split_unsupported_order_reports():
     with pytest.raises(bc.BoxCodeError) as e:
         bc.apply(tree, f, precision=bc.SPLIT_BF16)
     assert e.value.status == -6
+
+
+def test_split_wait_timeout_is_reported_and_context_survives(ctx16, adaptive):
+    """A bounded device-side wait that runs out (the table copy is withheld)
+    gives BC_ERR_TIMEOUT at bc_sync; the context keeps working afterwards."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    ctx16.set_option("wait_limit", 2000)
+    ctx16.set_option("debug_withhold_copy", 1)
+    try:
+        bc.apply(tree, f, precision=bc.SPLIT_BF16)
+        st = bc._load().bc_sync(ctx16.handle, None)
+    finally:
+        ctx16.set_option("debug_withhold_copy", 0)
+        ctx16.set_option("wait_limit", 2 ** 26)
+    assert st == -5
+    assert "wait" in bc._load().bc_last_error().decode()
+    bc._check(bc._load().bc_sync(ctx16.handle, None))     # flag cleared
+    u64 = bc.apply(tree, f)
+    us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    bc._check(bc._load().bc_sync(ctx16.handle, None))
+    assert ((us - u64).abs().max() / u64.abs().max()).item() < 1e-11
