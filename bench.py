@@ -175,20 +175,33 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-STAGES = ("split_near", "clear", "leaf_up", "downward", "leaf_output")
+STAGES = ("tensor_v", "clear", "upward", "downward", "tensor_e", "leaf_output")
 
 
-def stage_flops(st, nleaf, P1, NP, split):
-    """Algorithmic flops of each stage of one apply, counted from the tree's lists.
-    split_near: BF16 tensor flops of the 15 digit products per near entry;
-    the others: FP64 flops (complex x real = 4 flops per term, complex x complex = 8)."""
-    n_shift = max(0, st["n_down"] - 0)
+def stage_work(st, nleaf, nleaf_far, P1, NP, split):
+    """Algorithmic work of each stage of one apply, counted from the tree's lists:
+    (amount, kind) with kind "tensor" (BF16 flops of the 15 digit products,
+    rows x K x columns of the real operators), "fp64" (FP64 flops: complex x
+    real = 4 per term, complex x complex = 8) or "bytes" (leaf output of the
+    split path: FP64 partial results read + result written)."""
+    n_shift = st["n_down"]
+    R = 2 * P1
+    if split:
+        return {
+            "tensor_v": (15 * 2.0 * NP * (NP * st["n_near"] + R * (nleaf + st["n_x"])), "tensor"),
+            "clear": (0.0, "fp64"),
+            "upward": (32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
+            "downward": (4.0 * P1 * P1 * st["n_v"] + 8.0 * P1 * P1 * n_shift, "fp64"),
+            "tensor_e": (15 * 2.0 * R * NP * (nleaf_far + st["n_w"]), "tensor"),
+            "leaf_output": (8.0 * NP * (st["n_near"] + st["n_w"] + nleaf_far + nleaf), "bytes"),
+        }
     return {
-        "split_near": 15 * 2.0 * NP * NP * st["n_near"] if split else 0.0,
-        "clear": 0.0,
-        "leaf_up": 4.0 * P1 * NP * nleaf + 32.0 * P1 * P1 * st["n_nonleaf"],
-        "downward": 4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"] + 8.0 * P1 * P1 * n_shift,
-        "leaf_output": (0.0 if split else 2.0 * NP * NP * st["n_near"]) + 4.0 * P1 * NP * (nleaf + st["n_w"]),
+        "tensor_v": (0.0, "tensor"),
+        "clear": (0.0, "fp64"),
+        "upward": (4.0 * P1 * NP * nleaf + 32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
+        "downward": (4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"] + 8.0 * P1 * P1 * n_shift, "fp64"),
+        "tensor_e": (0.0, "tensor"),
+        "leaf_output": (2.0 * NP * NP * st["n_near"] + 4.0 * P1 * NP * (nleaf_far + st["n_w"]), "fp64"),
     }
 
 
@@ -302,7 +315,7 @@ def main():
         torch.cuda.synchronize()
         ctx.debug(timing=True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        stages = np.zeros((2, 5))
+        stages = np.zeros((2, len(STAGES)))
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -368,29 +381,37 @@ def main():
         pass
     fp64_peak = bc.fp64_peak_tflops(dev)
     bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    fl = stage_flops(st, tree.nleaf, P1, 256, head == bc.SPLIT_BF16)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    lv = tree.leaves()[0]
+    wk = stage_work(st, tree.nleaf, int((lv >= 2).sum()), P1, 256, head == bc.SPLIT_BF16)
     per_stage = {}
     for i, name in enumerate(STAGES):
         ms = float(stage_ms[:, i].mean())
-        if ms <= 0 or fl[name] == 0:
+        amount, kind = wk[name]
+        if ms <= 0 or amount == 0:
             continue
-        tensor = name == "split_near"
-        ach = fl[name] / (ms * 1e-3) / 1e12
-        pk = bf16_peak if tensor else fp64_peak
-        per_stage[name] = {"ms": round(ms, 4), "bound": "tensor" if tensor else "alu",
-                           "achieved": round(ach, 4), "peak": round(pk, 2), "frac": round(ach / pk, 4)}
+        if kind == "bytes":
+            ach, pk, bound, unit = amount / (ms * 1e-3) / 1e9, hbm_peak, "hbm", "GB/s"
+        else:
+            ach = amount / (ms * 1e-3) / 1e12
+            pk, bound, unit = (bf16_peak, "tensor", "TFLOP/s") if kind == "tensor" else (fp64_peak, "alu", "TFLOP/s")
+        per_stage[name] = {"ms": round(ms, 4), "bound": bound, "achieved": round(ach, 4), "unit": unit,
+                           "peak": round(pk, 2), "frac": round(ach / pk, 4)}
     dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
     d = per_stage[dom]
-    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
-                "frac": d["frac"], "traffic": None, "kernel": dom,
-                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (burst), of measured" if d["bound"] == "tensor"
-                                else "bc_debug_fp64_peak: measured FP64 FMA throughput, of measured"),
+    src = {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+           "alu": "bc_debug_fp64_peak: measured FP64 FMA throughput, of measured",
+           "hbm": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": None, "kernel": dom, "peak_source": src[d["bound"]],
                 "stages": per_stage}
 
     nl = st["nlevels"]
-    launches_per_apply = 1 + max(0, nl - 3) + (1 + max(0, nl - 3) if nl > 2 else 0) + 1
+    # upward pass, M2L + one shift per level >= 3, leaf output; split: + two
+    # digit kernels and two tensor-core launches
+    launches_per_apply = 1 + (1 + max(0, nl - 3) if nl > 2 else 0) + 1
     if head == bc.SPLIT_BF16:
-        launches_per_apply += 2
+        launches_per_apply += 4
     pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -163,11 +163,11 @@ class Context:
         """Diagnostics: restrict applies to the near (1) / far (2) field; time stages."""
         _check(_load().bc_debug_set(self._h, pass_mask, int(timing)))
 
-    STAGES = ("split_near", "clear", "leaf_up", "downward", "leaf_output")
+    STAGES = ("tensor_v", "clear", "upward", "downward", "tensor_e", "leaf_output")
 
     def stage_times(self, adjoint: bool = False):
         """Durations (ms) of the last forward/adjoint apply's stages (see STAGES)."""
-        ms = np.zeros(5)
+        ms = np.zeros(len(self.STAGES))
         _check(_load().bc_debug_stage_times(self._h, int(adjoint), ms.ctypes.data_as(_DP)))
         return ms
 

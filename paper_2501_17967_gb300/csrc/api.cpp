@@ -169,7 +169,18 @@ bc_status upload_tree(bc_tree *t)
 #undef UPV
     e = dev_upload<int32_t>(d.allocs, &d.zero_ptr, nullptr, size_t(h.nleaf) + 1);
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
-    e = dev_upload<int32_t>(d.allocs, &d.cnt, nullptr, 2 * h.box_level.size());
+    // r^2 and log r per level, r = (L/2) 2^-lv
+    std::vector<double> lt(2 * kLvTab, 0.0);
+    for (int lv = 0; lv < kLvTab; lv++) {
+        const double r = std::ldexp(0.5 * h.L, -lv);
+        lt[lv] = r * r;
+        lt[kLvTab + lv] = double(std::log((long double)(0.5 * h.L)) - (long double)lv * std::log(2.0L));
+    }
+    e = dev_upload(d.allocs, &d.lvtab, lt.data(), lt.size());
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    e = dev_upload(d.allocs, &d.level_start, h.level_start.data(), h.level_start.size());
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    e = dev_upload<uint32_t>(d.allocs, &d.gbar, nullptr, 2);
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     size_t nexp = size_t(h.box_level.size()) * P1;
     e = dev_upload<double2>(d.allocs, &d.expA, nullptr, nexp);
@@ -201,6 +212,10 @@ PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
     a.half_L = 0.5 * t->h.L;
     a.nleaf = t->h.nleaf;
     a.nbox = int64_t(t->h.box_level.size());
+    a.up_blocks = ctx->up_blocks;
+    a.shift_blocks = ctx->shift_blocks;
+    a.wait_limit = ctx->split.wait_limit;
+    a.err = ctx->dev_err;
     return a;
 }
 
@@ -238,92 +253,269 @@ uint16_t bf16_of_int(int d)
     return uint16_t(u >> 16);
 }
 
+// Appends the BF16 digits of a real operator (rows x K, row-major) to `dig`
+// in the chunk layout [digit a][row half h][K chunk kc] x (128 rows x KC) of
+// canonical K-major core matrices, and its row exponents to `ex`.
+SplitOp add_split_op(std::vector<uint16_t> &dig, std::vector<int32_t> &ex, const std::vector<double> &m, int rows,
+                     int K)
+{
+    const int KC = std::min(K, 128), nkc = K / KC, mh = rows > 128 ? 2 : 1;
+    const size_t chunk = size_t(128) * KC;   // elements per chunk
+    SplitOp op;
+    op.a_off = int64_t(dig.size()) * int64_t(sizeof(uint16_t));
+    op.rows = rows;
+    op.exp_off = int32_t(ex.size());
+    const size_t base = dig.size();
+    dig.resize(base + size_t(kSplitSlices) * mh * nkc * chunk, 0);
+    ex.resize(ex.size() + size_t(mh) * 128, 0);
+    std::vector<int16_t> dg(size_t(kSplitSlices) * K);
+    for (int i = 0; i < rows; i++) {
+        ex[size_t(op.exp_off) + i] = split_row(&m[size_t(i) * K], K, dg.data());
+        const int h = i / 128, rg = (i % 128) / 8, r = i % 8;
+        for (int a = 0; a < kSplitSlices; a++)
+            for (int k = 0; k < K; k++) {
+                const int kc = k / KC, kg = (k % KC) / 8, e = k % 8;
+                const size_t off = base + ((size_t(a) * mh + h) * nkc + kc) * chunk +
+                                   (size_t(rg) * (KC / 8) + kg) * 64 + size_t(r) * 8 + e;
+                dig[off] = bf16_of_int(dg[size_t(a) * K + k]);
+            }
+    }
+    return op;
+}
+
+// Real operators of the split path, direction dir (0 forward, 1 adjoint):
+//   group V, K = p^2 = 256: near tables (256 rows), leafA (2 P1 rows: P2M /
+//     L2P^H), X list per code (2 P1 rows: P2L / M2P^H); output rows 2l, 2l+1 =
+//     Re, Im of coefficient l;
+//   group E, K = 64 (coefficient l at columns 2l, 2l+1 = Re, Im): L2P / P2M^H
+//     and the W list per code (M2P / P2L^H), 256 rows, output = real part.
 bc_status build_split_tables(bc_ctx *ctx)
 {
-    if (ctx->p != 16 || ctx->device < 0) return BC_OK;   // split path: p = 16 only
+    if (ctx->p != 16 || ctx->device < 0 || 2 * ctx->P1 > kSplitKE) return BC_OK;   // split path: p = 16, P1 <= 32
     const HostTables &ht = ctx->ht;
-    const int NP = 256, S = kSplitSlices;
-    const size_t chunk = size_t(128) * NP;              // elements of one (table, slice, half)
+    const int NP = 256, P1 = ctx->P1, R = 2 * P1, KE = kSplitKE;
+    SplitTables &T = ctx->split;
     for (int dir = 0; dir < 2; dir++) {
-        std::vector<uint16_t> A(size_t(kNumNear) * S * 2 * chunk, 0);
-        std::vector<int32_t> Ex(size_t(kNumNear) * NP, 0);
-        std::vector<double> row(NP);
-        std::vector<int16_t> dg(size_t(S) * NP);
+        std::vector<uint16_t> dv, de;
+        std::vector<int32_t> xv, xe;
+        std::vector<double> m;
+        // group V
+        T.near_op[dir].assign(kNumNear, SplitOp());
+        m.assign(size_t(NP) * NP, 0.0);
         for (int tab = 0; tab < kNumNear; tab++) {
             NearGeom g = near_table_geometry(tab);
             if (!g.valid) continue;
-            for (int i = 0; i < NP; i++) {
+            for (int i = 0; i < NP; i++)
                 for (int k = 0; k < NP; k++)
-                    row[k] = dir == 0 ? ht.T[(size_t(tab) * NP + i) * NP + k] : ht.T[(size_t(g.rev) * NP + k) * NP + i];
-                Ex[size_t(tab) * NP + i] = split_row(row.data(), NP, dg.data());
-                const int h = i / 128, rg = (i % 128) / 8, r = i % 8;
-                for (int s = 0; s < S; s++)
-                    for (int k = 0; k < NP; k++) {
-                        const int kg = k / 8, e = k % 8;
-                        size_t off = ((size_t(tab) * S + s) * 2 + h) * chunk + (size_t(rg) * 32 + kg) * 64 + r * 8 + e;
-                        A[off] = bf16_of_int(dg[size_t(s) * NP + k]);
-                    }
+                    m[size_t(i) * NP + k] = dir == 0 ? ht.T[(size_t(tab) * NP + i) * NP + k]
+                                                     : ht.T[(size_t(g.rev) * NP + k) * NP + i];
+            T.near_op[dir][tab] = add_split_op(dv, xv, m, NP, NP);
+        }
+        m.assign(size_t(R) * NP, 0.0);
+        for (int l = 0; l < P1; l++)
+            for (int j = 0; j < NP; j++) {
+                cplx z = dir == 0 ? at2(ht.Q, size_t(l) * NP + j) : std::conj(at2(ht.E, size_t(j) * P1 + l));
+                m[size_t(2 * l) * NP + j] = z.real();
+                m[size_t(2 * l + 1) * NP + j] = z.imag();
+            }
+        T.leafA_op[dir] = add_split_op(dv, xv, m, R, NP);
+        T.x_op[dir].assign(kNumWX, SplitOp());
+        for (int c = 0; c < kNumWX; c++) {
+            for (int l = 0; l < P1; l++)
+                for (int j = 0; j < NP; j++) {
+                    cplx z = dir == 0 ? at2(ht.P2L, (size_t(c) * P1 + l) * NP + j)
+                                      : std::conj(at2(ht.M2P, (size_t(c) * NP + j) * P1 + l));
+                    m[size_t(2 * l) * NP + j] = z.real();
+                    m[size_t(2 * l + 1) * NP + j] = z.imag();
+                }
+            T.x_op[dir][c] = add_split_op(dv, xv, m, R, NP);
+        }
+        // group E: out_j = Re(sum_l Op(j,l) b_l) = sum_l Re Op(j,l) Re b_l - Im Op(j,l) Im b_l;
+        // columns rescaled by powers of two (the expansion digits carry the inverse scale)
+        std::vector<double> me(size_t(NP) * KE, 0.0);
+        std::vector<std::vector<double>> mw(kNumWX, std::vector<double>(size_t(NP) * KE, 0.0));
+        for (int j = 0; j < NP; j++)
+            for (int l = 0; l < P1; l++) {
+                cplx z = dir == 0 ? at2(ht.E, size_t(j) * P1 + l) : std::conj(at2(ht.Q, size_t(l) * NP + j));
+                me[size_t(j) * KE + 2 * l] = z.real();
+                me[size_t(j) * KE + 2 * l + 1] = -z.imag();
+                for (int c = 0; c < kNumWX; c++) {
+                    cplx w = dir == 0 ? at2(ht.M2P, (size_t(c) * NP + j) * P1 + l)
+                                      : std::conj(at2(ht.P2L, (size_t(c) * P1 + l) * NP + j));
+                    mw[c][size_t(j) * KE + 2 * l] = w.real();
+                    mw[c][size_t(j) * KE + 2 * l + 1] = -w.imag();
+                }
+            }
+        // Column scales.  The rounding error of output j is about
+        // 2^-40 (max_k |A'_jk| sum_k |x'_k| + max_k |x'_k| sum_k |A'_jk|) with
+        // A' = A / s, x' = s x; it is smallest for s_k = sqrt(alpha_k / beta_k),
+        // alpha_k ~ |A_jk| and beta_k ~ |x_k| the profiles of coefficient k.
+        // Expansion-to-leaf (L2P, P2M^H): the operator grows like (sqrt 2)^l
+        // (nodes up to a corner of the box) and its inputs (local coefficients,
+        // adjoint multipoles) decay at least like 3^-l (sources two box widths
+        // away), so s = 2^l; the W list (M2P, P2L^H): operator ~ 3^-l, inputs
+        // (multipoles, adjoint locals) ~ (sqrt 2)^l, so s = 2^-l.
+        std::vector<double> se(KE), sw(KE);
+        for (int k = 0; k < KE; k++) {
+            se[k] = std::ldexp(1.0, k / 2);
+            sw[k] = std::ldexp(1.0, -(k / 2));
+            for (int j = 0; j < NP; j++) {
+                me[size_t(j) * KE + k] /= se[k];
+                for (int c = 0; c < kNumWX; c++) mw[c][size_t(j) * KE + k] /= sw[k];
             }
         }
-        uint16_t *dA = nullptr;
-        int32_t *dE = nullptr;
+        T.e_op[dir] = add_split_op(de, xe, me, NP, KE);
+        T.w_op[dir].assign(kNumWX, SplitOp());
+        for (int c = 0; c < kNumWX; c++) T.w_op[dir][c] = add_split_op(de, xe, mw[c], NP, KE);
+        // expA is the W source (first) in the forward apply and the P2M^H input
+        // (second) in the adjoint; expB the other way round
+        std::vector<double> scl(2 * KE);
+        for (int k = 0; k < KE; k++) {
+            scl[k] = dir == 0 ? sw[k] : se[k];
+            scl[KE + k] = dir == 0 ? se[k] : sw[k];
+        }
+        double *dsc = nullptr;
+        uint16_t *d0 = nullptr, *d1 = nullptr;
+        int32_t *e0 = nullptr, *e1 = nullptr;
         cudaError_t e;
-        if ((e = dev_upload(ctx->split_allocs, &dA, A.data(), A.size())) != cudaSuccess ||
-            (e = dev_upload(ctx->split_allocs, &dE, Ex.data(), Ex.size())) != cudaSuccess)
+        if ((e = dev_upload(ctx->split_allocs, &d0, dv.data(), dv.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->split_allocs, &e0, xv.data(), xv.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->split_allocs, &d1, de.data(), de.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->split_allocs, &e1, xe.data(), xe.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->split_allocs, &dsc, scl.data(), scl.size())) != cudaSuccess)
             return cuda_fail(e, "split tables upload");
-        ctx->split.A[dir] = reinterpret_cast<const uint8_t *>(dA);
-        ctx->split.Aexp[dir] = dE;
+        T.escale[dir] = dsc;
+        T.ops[0][dir] = reinterpret_cast<const uint8_t *>(d0);
+        T.op_exp[0][dir] = e0;
+        T.ops[1][dir] = reinterpret_cast<const uint8_t *>(d1);
+        T.op_exp[1][dir] = e1;
     }
-    int32_t *err = nullptr;
-    cudaError_t e = dev_upload<int32_t>(ctx->split_allocs, &err, nullptr, 1);
-    if (e != cudaSuccess) return cuda_fail(e, "split flag");
-    e = split_prepare();
+    cudaError_t e = split_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "split kernel attributes");
-    ctx->dev_err = err;
     ctx->split_ready = true;
     return BC_OK;
 }
+
+// Column lists of the split path for one tree.  Tiles hold up to
+// kSplitTileN columns that share one operator; tiles of 256-row operators
+// come first (longest work first).
+struct TileBuilder {
+    std::vector<SplitTile> tiles;
+    std::vector<SplitCol> cols;
+    // one operator, its columns given in order
+    void add(const SplitOp &op, const std::vector<SplitCol> &c)
+    {
+        for (size_t i = 0; i < c.size(); i += kSplitTileN) {
+            SplitTile t;
+            t.a_off = op.a_off;
+            t.rows = op.rows;
+            t.exp_off = op.exp_off;
+            t.p0 = int32_t(cols.size());
+            t.cnt = int32_t(std::min<size_t>(kSplitTileN, c.size() - i));
+            cols.insert(cols.end(), c.begin() + i, c.begin() + i + t.cnt);
+            tiles.push_back(t);
+        }
+    }
+};
+
+inline int32_t col_ctl(int shift, bool inv_alpha) { return int32_t(shift * 2 + (inv_alpha ? 1 : 0)); }
 
 bc_status build_split_tree(bc_tree *t)
 {
     if (t->split_ready) return BC_OK;
     const HostTree &h = t->h;
-    const int64_t nn = int64_t(h.near_src.size());
-    std::vector<int32_t> owner(nn);
-    for (int64_t o = 0; o < h.nleaf; o++)
-        for (int32_t e = h.near_ptr[o]; e < h.near_ptr[o + 1]; e++) owner[e] = int32_t(o);
-    std::vector<int32_t> order(nn);
-    for (int64_t e = 0; e < nn; e++) order[e] = int32_t(e);
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return h.near_tab[x] < h.near_tab[y]; });
-    std::vector<int32_t> tab, p0, cnt, vec(nn), out(nn), lf(nn), la(nn);
-    for (int64_t i = 0; i < nn; i++) {
-        const int32_t e = order[i];
-        vec[i] = h.near_src[e];
-        out[i] = e;
-        lf[i] = h.leaf_level[h.near_src[e]];
-        la[i] = h.leaf_level[owner[e]];
-        if (i == 0 || h.near_tab[e] != tab.back() || cnt.back() == kSplitTileN) {
-            tab.push_back(h.near_tab[e]);
-            p0.push_back(int32_t(i));
-            cnt.push_back(0);
-        }
-        cnt.back()++;
-    }
+    const SplitTables &T = t->ctx->split;
+    const int P1 = t->ctx->P1;
+    const int64_t nn = int64_t(h.near_src.size()), nx = int64_t(h.x_src.size()), nw = int64_t(h.w_src.size());
+    const int64_t nbox = int64_t(h.box_level.size());
     SplitTree &s = t->sp;
     std::vector<void *> &al = t->d.allocs;
     cudaError_t e;
-    if ((e = dev_upload(al, &s.tile_tab, tab.data(), tab.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.tile_p0, p0.data(), p0.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.tile_cnt, cnt.data(), cnt.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.pair_vec, vec.data(), vec.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.pair_out, out.data(), out.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.pair_lvl_f, lf.data(), lf.size())) != cudaSuccess ||
-        (e = dev_upload(al, &s.pair_lvl_a, la.data(), la.size())) != cudaSuccess ||
-        (e = dev_upload<double>(al, &s.P, nullptr, size_t(nn) * 256)) != cudaSuccess ||
-        (e = dev_upload<uint16_t>(al, &s.vsl, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
-        (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess)
+    if ((e = dev_upload<double>(al, &s.Pnear, nullptr, size_t(nn) * 256)) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.PX, nullptr, size_t(nx) * kSplitKE)) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.PE, nullptr, size_t(h.nleaf) * 256)) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.PW, nullptr, size_t(nw) * 256)) != cudaSuccess ||
+        (e = dev_upload<uint16_t>(al, &s.vdig, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
+        (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess ||
+        (e = dev_upload<uint16_t>(al, &s.edig, nullptr, size_t(2 * nbox) * kSplitSlices * kSplitKE)) != cudaSuccess ||
+        (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess)
         return cuda_fail(e, "split tree upload");
-    s.ntiles = int(tab.size());
+    // owners of the near and W entries, box of each X entry
+    std::vector<int32_t> near_owner(nn), w_owner(nw), x_box(nx);
+    for (int64_t o = 0; o < h.nleaf; o++) {
+        for (int32_t k = h.near_ptr[o]; k < h.near_ptr[o + 1]; k++) near_owner[k] = int32_t(o);
+        for (int32_t k = h.w_ptr[o]; k < h.w_ptr[o + 1]; k++) w_owner[k] = int32_t(o);
+    }
+    for (int64_t b = 0; b < nbox; b++)
+        for (int32_t k = h.x_ptr[b]; k < h.x_ptr[b + 1]; k++) x_box[k] = int32_t(b);
+    for (int dir = 0; dir < 2; dir++) {
+        const bool adj = dir == 1;
+        double2 *first = adj ? t->d.expB : t->d.expA;
+        const int first_which = adj ? 1 : 0, second_which = adj ? 0 : 1;   // expA = 0, expB = 1
+        TileBuilder V, E;
+        // near entries, by table
+        std::vector<std::vector<SplitCol>> by_tab(kNumNear);
+        for (int64_t k = 0; k < nn; k++) {
+            const int32_t src = h.near_src[k], own = near_owner[k];
+            SplitCol c;
+            c.vec = src;
+            c.ctl = col_ctl(-2 * (adj ? h.leaf_level[own] : h.leaf_level[src]), false);
+            c.out = s.Pnear + size_t(k) * 256;
+            by_tab[h.near_tab[k]].push_back(c);
+        }
+        for (int tab = 0; tab < kNumNear; tab++)
+            if (!by_tab[tab].empty()) V.add(T.near_op[dir][tab], by_tab[tab]);
+        // leafA of every leaf (Morton order), then the X entries by code
+        std::vector<SplitCol> cl;
+        for (int64_t i = 0; i < h.nleaf; i++) {
+            const int32_t o = h.leaf_order[i];
+            SplitCol c;
+            c.vec = o;
+            c.ctl = adj ? col_ctl(0, true) : col_ctl(-2 * h.leaf_level[o], false);
+            c.out = reinterpret_cast<double *>(first + size_t(h.leaf_box[o]) * P1);
+            cl.push_back(c);
+        }
+        V.add(T.leafA_op[dir], cl);
+        std::vector<std::vector<SplitCol>> by_code(kNumWX);
+        for (int64_t k = 0; k < nx; k++) {
+            SplitCol c;
+            c.vec = h.x_src[k];
+            c.ctl = adj ? col_ctl(0, true) : col_ctl(-2 * (h.box_level[x_box[k]] - 1), false);
+            c.out = s.PX + size_t(k) * kSplitKE;
+            by_code[h.x_code[k]].push_back(c);
+        }
+        for (int c = 0; c < kNumWX; c++)
+            if (!by_code[c].empty()) V.add(T.x_op[dir][c], by_code[c]);
+        // group E: L2P of the leaves at level >= 2, then the W entries by code
+        cl.clear();
+        for (int64_t i = 0; i < h.nleaf; i++) {
+            const int32_t o = h.leaf_order[i];
+            if (h.leaf_level[o] < 2) continue;
+            SplitCol c;
+            c.vec = int32_t(second_which * nbox + h.leaf_box[o]);
+            c.ctl = col_ctl(adj ? -2 * h.leaf_level[o] : 0, false);
+            c.out = s.PE + size_t(o) * 256;
+            cl.push_back(c);
+        }
+        E.add(T.e_op[dir], cl);
+        for (auto &v : by_code) v.clear();
+        for (int64_t k = 0; k < nw; k++) {
+            SplitCol c;
+            c.vec = int32_t(first_which * nbox + h.w_src[k]);
+            c.ctl = col_ctl(adj ? -2 * h.leaf_level[w_owner[k]] : 0, false);
+            c.out = s.PW + size_t(k) * 256;
+            by_code[h.w_code[k]].push_back(c);
+        }
+        for (int c = 0; c < kNumWX; c++)
+            if (!by_code[c].empty()) E.add(T.w_op[dir][c], by_code[c]);
+        if ((e = dev_upload(al, &s.tV[dir], V.tiles.data(), V.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cV[dir], V.cols.data(), V.cols.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.tE[dir], E.tiles.data(), E.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess)
+            return cuda_fail(e, "split tree upload");
+        s.ntV[dir] = int(V.tiles.size());
+        s.ntE[dir] = int(E.tiles.size());
+    }
     s.err = t->ctx->dev_err;
     t->split_ready = true;
     return BC_OK;
@@ -351,12 +543,12 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     PassArgs a = pass_args(ctx, tree);
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
-    SplitLaunch sl{&ctx->split, nullptr};
+    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts};
     const SplitLaunch *split = nullptr;
     bc_tree *tw = const_cast<bc_tree *>(tree);
     if (prec == BC_SPLIT_BF16) {
-        if (ctx->p != 16 || !ctx->split_ready) {
-            set_error("apply: the split-precision near field is provided for p = 16 only");
+        if (!ctx->split_ready) {
+            set_error("apply: split precision is provided for p = 16 with nterms <= 32 only");
             return BC_ERR_UNSUPPORTED;
         }
         s = build_split_tree(tw);
@@ -431,7 +623,7 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     PassArgs a = pass_args(ctx, b->u);
     a.leaf_bps = leaf_bps;
     a.m2l_bps = m2l_bps;
-    SplitLaunch sl{&ctx->split, &b->u->sp};
+    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts};
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
     cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,
@@ -562,6 +754,10 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
             (e = dev_upload(ctx->dt.allocs, &ctx->dt.binom, bn.data(), bn.size())) != cudaSuccess)
             return cuda_fail(e, "tables upload");
     }
+    e = dev_upload<int32_t>(ctx->dt.allocs, &ctx->dev_err, nullptr, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "error flag");
+    e = fp64_prepare(ctx->NP, ctx->P1, 4, &ctx->up_blocks, &ctx->shift_blocks);
+    if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel occupancy");
     s = build_split_tables(ctx);
     if (s != BC_OK) return s;
     ctx->tables_ready = true;
@@ -928,6 +1124,14 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
         ctx->split.wait_limit = (long long)value;
         return BC_OK;
     }
+    if (std::strcmp(name, "debug_split_parts") == 0) {
+        if (!(value >= 0.0 && value <= double(kSplitAllParts)) || value != std::floor(value)) {
+            set_error("bc_set_option: debug_split_parts must be an integer in [0, %d]", kSplitAllParts);
+            return BC_ERR_ARG;
+        }
+        ctx->split_parts = int(value);
+        return BC_OK;
+    }
     if (std::strcmp(name, "debug_withhold_copy") == 0) {
         ctx->split.withhold_copy = value != 0.0;
         return BC_OK;
@@ -964,7 +1168,7 @@ bc_status bc_sync(bc_ctx *ctx, void *stream)
         if (e != cudaSuccess) return cuda_fail(e, "bc_sync");
         if (flag) {
             cudaMemset(ctx->dev_err, 0, sizeof(int32_t));
-            set_error("bc_sync: a bounded device-side wait gave up (split near field)");
+            set_error("bc_sync: a bounded device-side wait gave up (tensor-core operand copy or grid barrier)");
             return BC_ERR_TIMEOUT;
         }
     }

@@ -18,6 +18,7 @@ constexpr int kNumNear = 41;   // near-table slots (33 used; see near_table_geom
 constexpr int kNumV = 49;      // V offsets on the 7x7 grid (40 used)
 constexpr int kNumWX = 36;     // W/X offsets on the 6x6 half-integer grid (20 used)
 constexpr int kDefaultNterms = 30;
+constexpr int kLvTab = 32;     // levels in the per-level constant tables (tree levels <= 24)
 
 void set_error(const char *fmt, ...);
 
@@ -126,37 +127,99 @@ struct DevTree {
     int32_t *x_ptr = nullptr, *x_src = nullptr, *x_code = nullptr;
     double2 *expA = nullptr, *expB = nullptr;  // [nbox][P1] workspaces
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
-    int32_t *cnt = nullptr;                    // [2][nbox] arrival counters (upward, downward passes)
+    double *lvtab = nullptr;                   // [2][kLvTab]: r^2 and log r per level
+    int64_t *level_start = nullptr;            // [nlevels + 1] first box of each level
+    uint32_t *gbar = nullptr;                  // [2] grid barrier of the persistent passes (count, generation)
     double *stage_in = nullptr, *stage_out = nullptr; // host-pointer staging [nleaf*NP]
     std::vector<void *> allocs;
 };
 
-// Split-precision near field (p = 16 only): BF16 digit slices of the tables
-// (per context) and the entry tiles, digit buffers and result scratch (per tree).
+// Split precision (p = 16 only).  Every fixed-operator product of the apply
+// except the multipole-to-local translations runs on the tensor cores as
+// exact BF16 digit products (kernels_split.cu):
+//   group V (K = 256, input = leaf vectors): near tables, P2M (adjoint L2P^H),
+//            X list (adjoint M2P^H)
+//   group E (K = 64, input = expansions, 2*P1 reals padded to 64): L2P
+//            (adjoint P2M^H), W list (adjoint P2L^H)
+// An operator is a real matrix of `rows` <= 256 rows; its BF16 digits are
+// stored as chunks [digit a][row half h][K chunk kc] of 128 rows x KC
+// columns (KC = min(K, 128)) in the canonical K-major core-matrix layout.
 constexpr int kSplitSlices = 5;
 constexpr int kSplitTileN = 48;
+constexpr int kSplitKE = 64;                 // K of group E (expansion reals, padded)
+struct SplitOp {
+    int64_t a_off = 0;     // byte offset of the operator's first chunk
+    int32_t rows = 0;      // valid rows
+    int32_t exp_off = 0;   // index of the operator's first row exponent
+};
 struct SplitTables {
-    const uint8_t *A[2] = {nullptr, nullptr};    // [kNumNear][5][2][128 x 256 canonical] fwd, adj
-    const int32_t *Aexp[2] = {nullptr, nullptr}; // [kNumNear][256] row exponents
+    // [group V, group E][forward, adjoint]
+    const uint8_t *ops[2][2] = {};
+    const int32_t *op_exp[2][2] = {};
+    std::vector<SplitOp> near_op[2], x_op[2], w_op[2];   // [dir][code]
+    SplitOp leafA_op[2], e_op[2];
+    // group E column scales (powers of two) per direction: [expA][64], [expB][64].
+    // Coefficient k of an expansion is multiplied by s_k before its digits are
+    // taken and column k of the operator is divided by s_k (exact rescaling
+    // that balances the fixed-point rounding of operator and input).
+    const double *escale[2] = {nullptr, nullptr};
     long long wait_limit = 1ll << 26;            // polls of a bounded mbarrier wait
-    int withhold_copy = 0;                       // diagnostics: never start the table copy (forces a timeout)
+    int withhold_copy = 0;                       // diagnostics: never start the operator copies (forces a timeout)
+};
+// One tile = one operator times up to kSplitTileN columns.
+struct SplitTile {
+    int64_t a_off;
+    int32_t rows, exp_off;
+    int32_t p0, cnt;       // columns [p0, p0 + cnt)
+};
+// One column = one input vector and where its result rows go.
+struct SplitCol {
+    int32_t vec;           // digit-vector index
+    int32_t ctl;           // (power-of-two exponent shift << 1) | (multiply by 1/alpha0)
+    double *out;           // result row r goes to out[r]
+};
+struct SplitGemm {
+    const SplitTile *tiles = nullptr;
+    const SplitCol *cols = nullptr;
+    int ntiles = 0;
+    const uint8_t *ops = nullptr;
+    const int32_t *op_exp = nullptr;
+    const uint16_t *dig = nullptr;     // [nvec][5][K] BF16 digit bits
+    const int32_t *dexp = nullptr;     // [nvec]
 };
 struct SplitTree {
-    int ntiles = 0;
-    int32_t *tile_tab = nullptr, *tile_p0 = nullptr, *tile_cnt = nullptr;
-    int32_t *pair_vec = nullptr, *pair_out = nullptr, *pair_lvl_f = nullptr, *pair_lvl_a = nullptr;
-    double *P = nullptr;          // [n_near][256] near-field result per entry
-    uint16_t *vsl = nullptr;      // [nleaf][5][256] digits of the input vector (BF16 bits)
+    // [forward, adjoint]
+    SplitTile *tV[2] = {}, *tE[2] = {};
+    SplitCol *cV[2] = {}, *cE[2] = {};
+    int ntV[2] = {}, ntE[2] = {};
+    double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
+    double *PX = nullptr;         // [n_x][64] X-list result per entry
+    double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf
+    double *PW = nullptr;         // [n_w][256] W-list result per entry
+    uint16_t *vdig = nullptr;     // [nleaf][5][256] digits of the leaf vectors
     int32_t *vexp = nullptr;      // [nleaf]
+    uint16_t *edig = nullptr;     // [2 nbox][5][64] digits of expA (first nbox) and expB
+    int32_t *eexp = nullptr;      // [2 nbox]
     int32_t *err = nullptr;       // device error flag (bounded waits)
 };
-size_t split_smem_bytes();
+size_t split_smem_bytes(int kd);
 cudaError_t split_prepare();   // kernel attributes of the split path (before any capture)
-// Split near field of one apply (null: FP64 near field).
+// parts: which products take the tensor-core results (bits: 1 near field,
+// 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list); the others run in FP64.
+constexpr int kSplitAllParts = 31;
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
+    int parts = kSplitAllParts;
 };
+// Digits of the leaf vectors (times scale), of the two expansion arrays
+// (times scale), and the tensor-core operator products of one group.
+cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
+                                    cudaStream_t st);
+cudaError_t launch_split_digits_exp(int64_t nbox, const double2 *ea, const double2 *eb, int P1, double scale,
+                                    const double *escale, uint16_t *dig, int32_t *dexp, cudaStream_t st);
+cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int32_t *err, long long wait_limit,
+                              int withhold, cudaStream_t st);
 
 // Launch parameters common to the passes.  leaf_bps / m2l_bps: resident
 // blocks per SM used to size the grids of the leaf kernels and of the M2L
@@ -166,7 +229,15 @@ struct PassArgs {
     double half_L;        // r at level 0
     int64_t nleaf, nbox;
     int leaf_bps = 0, m2l_bps = 0;
+    // persistent level-synchronous passes: resident blocks of the upward and
+    // shift kernels (all blocks must be resident), bounded barrier waits
+    int up_blocks = 0, shift_blocks = 0;
+    long long wait_limit = 1ll << 26;
+    int32_t *err = nullptr;
 };
+// Largest grids of the persistent FP64 passes whose blocks are all resident
+// (occupancy calculator), capped at `per_sm` blocks per SM.
+cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_blocks);
 
 // Disjoint union of trees (batched applies): leaves and boxes renumbered,
 // boxes sorted by (level, tree, Morton order), lists concatenated.
@@ -176,16 +247,14 @@ bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree 
 // Forward (adj = false) or adjoint (adj = true) apply on `stream`.
 // vin: f (forward) or g (adjoint); vout: u or h.  Device pointers.
 // Stage boundaries recorded when timing is on:
-// split near field | leafA | up | down | leafB.
-constexpr int kNumStages = 5;
+// tensor group V | clear | upward | downward | tensor group E | leaf output.
+// (The FP64 path leaves the two tensor stages empty.)
+constexpr int kNumStages = 6;
 // pass_mask bit 0: near field, bit 1: far field.  ev: kNumStages+1 events or null.
 // m2l_tri: triangular truncation of the M2L series (k + l <= P).
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          bool adj, const double *vin, double *vout, cudaStream_t stream, int pass_mask,
                          cudaEvent_t *ev, int m2l_tri, const struct SplitLaunch *split);
-// Split near field: digits of vin, then every near entry's 256 results into sp.P.
-cudaError_t launch_split_near(const PassArgs &a, const SplitTables &st, const SplitTree &sp, bool adj,
-                              const double *vin, cudaStream_t stream);
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
 struct BatchPtrs {
@@ -208,6 +277,7 @@ struct bc_ctx {
     bool tables_ready = false;
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
+    int split_parts = bc::kSplitAllParts;   // diagnostics: split-precision products in use
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumStages + 1] = {};   // [forward, adjoint]
     bc::HostTables ht;
@@ -216,6 +286,7 @@ struct bc_ctx {
     std::vector<void *> split_allocs;
     bool split_ready = false;
     int32_t *dev_err = nullptr;   // device flag set by kernels whose bounded waits gave up
+    int up_blocks = 0, shift_blocks = 0;   // grids of the persistent passes
     // launch shapes chosen by the autotuner: key = precision*1024 + adjoint*512 + log2(nleaf)
     std::vector<std::pair<int, std::pair<int, int>>> tuned;
     std::mutex mu;

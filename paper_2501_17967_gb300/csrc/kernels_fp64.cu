@@ -22,76 +22,129 @@ namespace bc {
 
 namespace {
 
-constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kInvTwoPi = 0.15915494309189533576888376337251;   // 1 / (2 pi)
 
-__device__ __forceinline__ double r_at(double half_L, int lv) { return ldexp(half_L, -lv); }
+// Per-level constants of the tree (no FP64 log or divide in the kernels):
+// lvtab[lv] = r_lv^2, lvtab[kLvTab + lv] = log r_lv, r_lv = (L/2) 2^-lv.
 
 // -------------------------------------------------------------------------
-// leaf_up: per leaf, the box expansion from the leaf vector, then the upward
-// pass without per-level launches: a parent's expansion is computed by the
-// block whose child arrives last (arrival counter per box, no waiting).
-//   leaf:   ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
+// Grid-wide barrier of the persistent level-synchronous passes.  Their grids
+// are sized so that every block is resident (occupancy calculator), so the
+// wait ends once all blocks arrive; it is bounded all the same: a block whose
+// wait runs out records the failure in *err (reported by bc_sync) and goes on.
+// bar[0] counts arrivals, bar[1] is the generation.  Data written before the
+// barrier is read after it with L2 loads (__ldcg).
+// -------------------------------------------------------------------------
+__device__ void grid_sync(uint32_t *bar, long long limit, int32_t *err)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile uint32_t *vb = bar;
+        const uint32_t gen = vb[1];
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            for (long long it = 0; vb[1] == gen; it++) {
+                if (it >= limit) {
+                    atomicExch(err, 2);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// -------------------------------------------------------------------------
+// upward pass, one persistent launch:
+//   leaves: ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
 //           forward (P2M): OpA = Q^T, s = r^2;  adjoint (L2P^H): OpA = E^H, s = 1
+//           (OpA == nullptr: the leaf expansions are already in ex, split path)
+//   then level by level, deepest first, separated by grid barriers:
 //   parent: ex[p][l] = sum_q sum_k OpUp[q][k][l] ex[child_q(p)][k]    (levels >= 2)
 //           forward: M2M; adjoint: L2L^H
-// cnt[] must be zero on entry (the apply clears it).
+// Four warps per block: in the leaf step warp w sums over the w-th quarter of
+// the nodes, in a parent step warp q applies the operator of child q; the four
+// partial sums meet in shared memory.
 // -------------------------------------------------------------------------
 template <bool ADJ>
-__global__ void __launch_bounds__(64)
-k_leaf_up(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
-          const int32_t *__restrict__ leaf_level, const int32_t *__restrict__ box_parent,
-          const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_child0,
-          const double *__restrict__ vin, const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp,
-          double2 *ex, int32_t *cnt, int NP, int P1, double half_L)
+__global__ void __launch_bounds__(128)
+k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
+            const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
+            const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
+            const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, double2 *ex, int NP, int P1,
+            const double *__restrict__ lvtab, bool climb, uint32_t *gbar, long long limit, int32_t *err)
 {
     extern __shared__ double2 shu[];
-    double2 *sc = shu;                                     // 4 * P1
-    double *sv = reinterpret_cast<double *>(shu + 4 * P1); // NP
-    __shared__ int s_go;
-    for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
+    double2 *sc = shu;                                       // 4 * P1 children
+    double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
+    double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = NP / 4;
+    for (int64_t li = blockIdx.x; OpA && li < nleaf; li += gridDim.x) {
         const int leaf = order[li];
-        int b = leaf_box[leaf];
+        const int b = leaf_box[leaf];
+        const double s = ADJ ? 1.0 : lvtab[leaf_level[leaf]];   // r^2
         __syncthreads();
         for (int j = threadIdx.x; j < NP; j += blockDim.x) sv[j] = vin[int64_t(leaf) * NP + j];
         __syncthreads();
-        const double r = r_at(half_L, leaf_level[leaf]);
-        const double s = ADJ ? 1.0 : r * r;
-        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+        for (int l = lane; l < P1; l += 32) {
             double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-            for (int j = 0; j < NP; j += 2) {
+            for (int j = w * nq; j < (w + 1) * nq; j += 2) {
                 double2 o0 = OpA[j * P1 + l], o1 = OpA[(j + 1) * P1 + l];
                 re0 = fma(o0.x, sv[j], re0);
                 im0 = fma(o0.y, sv[j], im0);
                 re1 = fma(o1.x, sv[j + 1], re1);
                 im1 = fma(o1.y, sv[j + 1], im1);
             }
-            ex[int64_t(b) * P1 + l] = make_double2(s * (re0 + re1), s * (im0 + im1));
+            part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
         }
-        for (; cnt;) {
-            const int p = box_parent[b];
-            if (p < 0 || box_level[p] < 2) break;
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) s_go = atomicAdd(&cnt[p], 1) == 3;
-            __syncthreads();
-            if (!s_go) break;
-            __threadfence();
+        __syncthreads();
+        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+            const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
+            ex[int64_t(b) * P1 + l] =
+                make_double2(s * ((a0.x + a1.x) + (a2.x + a3.x)), s * ((a0.y + a1.y) + (a2.y + a3.y)));
+        }
+    }
+    if (!climb) return;
+    for (int lv = nlevels - 2; lv >= 2; lv--) {
+        grid_sync(gbar, limit, err);   // every box of the levels below is complete
+        for (int64_t p = level_start[lv] + blockIdx.x; p < level_start[lv + 1]; p += gridDim.x) {
             const int c0 = box_child0[p];
+            if (c0 < 0) continue;   // a leaf (uniform over the block)
+            __syncthreads();
             for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
             __syncthreads();
-            for (int l = threadIdx.x; l < P1; l += blockDim.x) {
-                double re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
-                for (int k = 0; k < P1; k++) {
+            const double2 *op = OpUp + size_t(w) * P1 * P1;
+            const double2 *a = sc + w * P1;
+            for (int l = lane; l < P1; l += 32) {
+                double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+                for (int k0 = 0; k0 < P1; k0 += 8) {   // 8 operator loads in flight
+                    double2 o[8];
 #pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        double2 o = OpUp[(q * P1 + k) * P1 + l], a = sc[q * P1 + k];
-                        re[q] = fma(o.x, a.x, fma(-o.y, a.y, re[q]));
-                        im[q] = fma(o.x, a.y, fma(o.y, a.x, im[q]));
+                    for (int u = 0; u < 8; u++)
+                        o[u] = k0 + u < P1 ? __ldg(&op[(k0 + u) * P1 + l]) : make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        if (k0 + u >= P1) break;
+                        const double2 a0 = a[k0 + u], a1 = k0 + u + 1 < P1 ? a[k0 + u + 1] : make_double2(0.0, 0.0);
+                        re0 = fma(o[u].x, a0.x, fma(-o[u].y, a0.y, re0));
+                        im0 = fma(o[u].x, a0.y, fma(o[u].y, a0.x, im0));
+                        re1 = fma(o[u + 1].x, a1.x, fma(-o[u + 1].y, a1.y, re1));
+                        im1 = fma(o[u + 1].x, a1.y, fma(o[u + 1].y, a1.x, im1));
                     }
                 }
-                ex[int64_t(p) * P1 + l] = make_double2((re[0] + re[1]) + (re[2] + re[3]), (im[0] + im[1]) + (im[2] + im[3]));
+                part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
             }
-            b = p;
+            __syncthreads();
+            for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+                const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
+                ex[int64_t(p) * P1 + l] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+            }
         }
     }
 }
@@ -118,7 +171,7 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
       const int32_t *__restrict__ x_src, const int32_t *__restrict__ x_code, const double2 *__restrict__ dpow,
       const double *__restrict__ logd, const double *__restrict__ binom, const double2 *__restrict__ OpX,
       const double *__restrict__ xvec, const int32_t *__restrict__ leaf_box, const double2 *__restrict__ in,
-      double2 *out, int NP, int P1, double half_L, int tri)
+      double2 *out, int NP, int P1, const double *__restrict__ lvtab, int tri, const double *__restrict__ PX)
 {
     extern __shared__ double smem[];
     const int ldc = P1 + 1;
@@ -204,7 +257,7 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
             oi = part[tid].y + part[64 + tid].y;
         }
         if (tid == 0) {
-            const double logr = log(r_at(half_L, lv));
+            const double logr = lvtab[kLvTab + lv];
             orr += logr * (mono[0].x + mono[1].x);
             oi += logr * (mono[0].y + mono[1].y);
         }
@@ -212,10 +265,17 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
         // coarser neighbour leaves.  The log term uses coefficient 0 of the
         // leaf's own expansion from the upward pass: forward A_0 = r_c^2 (w.f)/2pi,
         // adjoint B_0 = sum_j g_j, so the term is log(r_c) * that coefficient.
-        const double rc = r_at(half_L, lv - 1);
-        const double s1 = ADJ ? 1.0 : rc * rc;
-        const double logrc = log(rc);
-        for (int e = x_ptr[b]; e < x_ptr[b + 1]; e++) {
+        const double s1 = ADJ ? 1.0 : lvtab[lv - 1];   // r_c^2
+        const double logrc = lvtab[kLvTab + lv - 1];
+        for (int e = x_ptr[b]; e < x_ptr[b + 1] && PX; e++) {
+            // split path: the scaled product s1 * OpX x[c] comes from the tensor cores
+            if (tid < P1) {
+                orr += PX[size_t(e) * kSplitKE + 2 * tid];
+                oi += PX[size_t(e) * kSplitKE + 2 * tid + 1];
+                if (tid == 0) orr = fma(logrc, in[int64_t(leaf_box[x_src[e]]) * P1].x, orr);
+            }
+        }
+        for (int e = x_ptr[b]; e < x_ptr[b + 1] && !PX; e++) {
             const int c = x_src[e];
             const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
             __syncthreads();
@@ -241,38 +301,44 @@ k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32
 }
 
 // -------------------------------------------------------------------------
-// shift_down: out[b] += Par_q * out[parent(b)] for the boxes of one level >= 3
+// shift_levels: out[b] += Par_q * out[parent(b)] for every box of level >= 3,
+// level by level (one persistent launch, grid barriers between levels)
 //   forward: L2L; adjoint: M2M^H.  Two independent FMA chains per thread.
 // -------------------------------------------------------------------------
 __global__ void __launch_bounds__(64)
-k_shift_down(int64_t b0, int64_t b1, const int32_t *__restrict__ parent, const int32_t *__restrict__ box_ix,
-             const int32_t *__restrict__ box_iy, const double2 *__restrict__ OpPar, double2 *__restrict__ out, int P1)
+k_shift_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_t *__restrict__ parent,
+               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
+               const double2 *__restrict__ OpPar, double2 *out, int P1, uint32_t *gbar, long long limit,
+               int32_t *err)
 {
     extern __shared__ double2 se[];
-    for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
-        const int pb = parent[b];
-        const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
-        __syncthreads();
-        for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = out[int64_t(pb) * P1 + i];
-        __syncthreads();
-        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
-            const double2 *op = OpPar + size_t(q) * P1 * P1;
-            const double2 acc = out[b * P1 + l];
-            double re0 = acc.x, im0 = acc.y, re1 = 0.0, im1 = 0.0;
-            int k = 0;
-            for (; k + 1 < P1; k += 2) {
-                double2 o0 = op[k * P1 + l], a0 = se[k], o1 = op[(k + 1) * P1 + l], a1 = se[k + 1];
-                re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
-                im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
-                re1 = fma(o1.x, a1.x, fma(-o1.y, a1.y, re1));
-                im1 = fma(o1.x, a1.y, fma(o1.y, a1.x, im1));
+    for (int lv = 3; lv < nlevels; lv++) {
+        if (lv > 3) grid_sync(gbar, limit, err);   // the parents' level is complete
+        for (int64_t b = level_start[lv] + blockIdx.x; b < level_start[lv + 1]; b += gridDim.x) {
+            const int pb = parent[b];
+            const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+            __syncthreads();
+            for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
+            __syncthreads();
+            for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+                const double2 *op = OpPar + size_t(q) * P1 * P1;
+                const double2 acc = __ldcg(&out[b * P1 + l]);
+                double re0 = acc.x, im0 = acc.y, re1 = 0.0, im1 = 0.0;
+                int k = 0;
+                for (; k + 1 < P1; k += 2) {
+                    double2 o0 = op[k * P1 + l], a0 = se[k], o1 = op[(k + 1) * P1 + l], a1 = se[k + 1];
+                    re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
+                    im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
+                    re1 = fma(o1.x, a1.x, fma(-o1.y, a1.y, re1));
+                    im1 = fma(o1.x, a1.y, fma(o1.y, a1.x, im1));
+                }
+                if (k < P1) {
+                    double2 o0 = op[k * P1 + l], a0 = se[k];
+                    re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
+                    im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
+                }
+                out[b * P1 + l] = make_double2(re0 + re1, im0 + im1);
             }
-            if (k < P1) {
-                double2 o0 = op[k * P1 + l], a0 = se[k];
-                re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
-                im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
-            }
-            out[b * P1 + l] = make_double2(re0 + re1, im0 + im1);
         }
     }
 }
@@ -296,8 +362,9 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const double *__restrict__ T, const double *__restrict__ wvec,
                            const double2 *__restrict__ own, const double2 *__restrict__ src,
                            const double2 *__restrict__ aux, const double *__restrict__ vnear,
-                           double *__restrict__ vout, int NP, int P1, double half_L, bool far,
-                           const double *__restrict__ Pnear)
+                           double *__restrict__ vout, int NP, int P1, const double *__restrict__ lvtab, bool far,
+                           const double *__restrict__ Pnear, const double *__restrict__ PE,
+                           const double *__restrict__ PW)
 {
     extern __shared__ double2 sh[];
     double2 *se = sh;                                  // P1
@@ -305,11 +372,15 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
     for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int o = order[li];
         const int lvo = leaf_level[o];
-        const double ro = r_at(half_L, lvo);
+        const double r2o = lvtab[lvo], lgo = lvtab[kLvTab + lvo];
         const int j = threadIdx.x;   // blockDim.x == NP
         const double wj = wvec[j];
+        // adjoint log term of a target leaf o: r_o^2 log(r_o) w_j / (2 pi)
+        const double cO = ADJ ? r2o * lgo * wj * kInvTwoPi : lgo;
         double acc = 0.0;
-        if (far && lvo >= 2) {
+        if (far && lvo >= 2 && PE) {
+            acc = PE[int64_t(o) * NP + j];   // split path: scaled L2P from the tensor cores
+        } else if (far && lvo >= 2) {
             __syncthreads();
             for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = own[int64_t(leaf_box[o]) * P1 + i];
             __syncthreads();
@@ -318,11 +389,13 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                 double2 op = OpE[l * NP + j], b = se[l];
                 s = fma(op.x, b.x, fma(-op.y, b.y, s));
             }
-            acc = ADJ ? ro * ro * s : s;
+            acc = ADJ ? r2o * s : s;
         }
-        const double sW = ADJ ? ro * ro : 1.0;
-        const double cW = ADJ ? ro * ro * log(ro) * wj / kTwoPi : log(ro);
-        for (int e = w_ptr[o]; e < w_ptr[o + 1]; e++) {
+        const double sW = ADJ ? r2o : 1.0;
+        const double cW = cO;
+        for (int e = w_ptr[o]; e < w_ptr[o + 1] && PW; e++)
+            acc = PW[size_t(e) * NP + j] + fma(cW, src[int64_t(w_src[e]) * P1].x, acc);
+        for (int e = w_ptr[o]; e < w_ptr[o + 1] && !PW; e++) {
             const double2 *op = OpW + size_t(w_code[e]) * P1 * NP;
             __syncthreads();
             for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = src[int64_t(w_src[e]) * P1 + i];
@@ -350,12 +423,12 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
             double a0 = aux[int64_t(leaf_box[s]) * P1].x;
             double sN, cN;
             if (ADJ) {
-                sN = ro * ro;
-                cN = ro * ro * log(ro) * wj / kTwoPi;
+                sN = r2o;
+                cN = cO;
             } else {
-                double rs = r_at(half_L, leaf_level[s]);
-                sN = rs * rs;
-                cN = log(rs);
+                const int ls = leaf_level[s];
+                sN = lvtab[ls];
+                cN = lvtab[kLvTab + ls];
             }
             if (Pnear) sN = 1.0;
             acc = fma(sN, t, fma(cN, a0, acc));
@@ -444,70 +517,127 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                          cudaEvent_t *ev, int m2l_tri, const SplitLaunch *split)
 {
     const bool far = (pass_mask & 2) != 0, near = (pass_mask & 1) != 0;
-    const double *Pnear = split ? split->tree->P : nullptr;
-    if (ev) cudaEventRecord(ev[0], st);
-    if (split && near) {
-        cudaError_t e = launch_split_near(a, *split->tables, *split->tree, adj, vin, st);
-        if (e != cudaSuccess) return e;
-    }
-    if (ev) cudaEventRecord(ev[1], st);
     const OpSet &op = adj ? tb.adj : tb.fwd;
-    const int NP = a.NP, P1 = a.P1;
+    const int NP = a.NP, P1 = a.P1, dir = adj ? 1 : 0;
     double2 *first = adj ? d.expB : d.expA;    // leafA / up target
     double2 *second = adj ? d.expA : d.expB;   // down target
-    // arrival counters of the upward pass start at zero
-    cudaError_t ce = cudaMemsetAsync(d.cnt, 0, sizeof(int32_t) * size_t(a.nbox), st);
+    const double alpha0 = a.half_L * a.half_L;  // r^2 at level 0
+    const SplitTables *sT = split ? split->tables : nullptr;
+    const SplitTree *sp = split ? split->tree : nullptr;
+    const int parts = split ? split->parts : 0;
+    cudaError_t ce;
+    if (ev) cudaEventRecord(ev[0], st);
+    if (split) {
+        // tensor group V: digits of alpha0 * vin; near field, leafA (P2M / L2P^H)
+        // into `first`, X list into PX
+        ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
+        if (ce != cudaSuccess) return ce;
+        SplitGemm g;
+        g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir];
+        g.ops = sT->ops[0][dir]; g.op_exp = sT->op_exp[0][dir];
+        g.dig = sp->vdig; g.dexp = sp->vexp;
+        ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+        if (ce != cudaSuccess) return ce;
+    }
+    if (ev) cudaEventRecord(ev[1], st);
+    // the grid barrier of the persistent passes starts from zero (a barrier
+    // wait that ran out in an earlier apply cannot leave it out of step)
+    ce = cudaMemsetAsync(d.gbar, 0, 2 * sizeof(uint32_t), st);
     if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[2], st);
-    // leafA + upward pass in one launch (leafA always runs: the near-field log
-    // term reads coefficient 0 of its output; without the far field no climb)
-    int32_t *cnt_up = d.cnt;
-    const size_t shU = sizeof(double) * NP + sizeof(double2) * 4 * P1;
-    if (adj)
-        k_leaf_up<true><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                           d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
-                                                           op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
-    else
-        k_leaf_up<false><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), 64, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                            d.box_parent, d.box_level, d.box_child0, vin, op.leafA,
-                                                            op.up, first, far ? cnt_up : nullptr, NP, P1, a.half_L);
+    // grid-barrier polls go to L2 (about a microsecond each): a sixteenth of
+    // the mbarrier poll limit
+    const long long glimit = std::max(1ll, a.wait_limit / 16);
+    // leafA + upward pass in one persistent launch (leafA always runs: the
+    // near-field log term reads coefficient 0 of its output; without the far
+    // field no climb).  Split path: leafA came from the tensor cores.
+    const size_t shU = sizeof(double) * NP + sizeof(double2) * 8 * P1;
+    const int grid_leaf = grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16));
+    const double2 *opA = (parts & 2) ? nullptr : op.leafA;
+    const bool climb = far && h.nlevels > 3;
+    if (opA || climb) {
+        if (adj)
+            k_up_levels<true><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                                                             d.level_start, h.nlevels, d.box_child0, vin, opA,
+                                                             op.up, first, NP, P1, d.lvtab, climb, d.gbar,
+                                                             glimit, a.err);
+        else
+            k_up_levels<false><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                                                              d.level_start, h.nlevels, d.box_child0, vin, opA,
+                                                              op.up, first, NP, P1, d.lvtab, climb, d.gbar,
+                                                              glimit, a.err);
+    }
     if (ev) cudaEventRecord(ev[3], st);
-    size_t shD = sizeof(double2) * P1 + sizeof(double) * NP;
     if (far && h.nlevels > 2) {
         const int64_t b0 = h.level_start[2], b1 = h.level_start[h.nlevels];
         size_t shM = sizeof(double) * (size_t(P1) * (P1 + 1) + P1) + sizeof(double2) * (128 + 128 + 2) +
                      sizeof(double) * NP;
         int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : 12));
+        const double *PX = (parts & 4) ? sp->PX : nullptr;
         if (adj)
             k_m2l<true><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
                                                d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
-                                               second, NP, P1, a.half_L, m2l_tri);
+                                               second, NP, P1, d.lvtab, m2l_tri, PX);
         else
             k_m2l<false><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
                                                 d.x_code, tb.dpow_f, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
-                                                second, NP, P1, a.half_L, m2l_tri);
-        for (int lv = 3; lv < h.nlevels; lv++) {
-            int64_t c0 = h.level_start[lv], c1 = h.level_start[lv + 1];
-            k_shift_down<<<grid_for(c1 - c0), 64, sizeof(double2) * P1, st>>>(c0, c1, d.box_parent, d.box_ix,
-                                                                              d.box_iy, op.par, second, P1);
-        }
+                                                second, NP, P1, d.lvtab, m2l_tri, PX);
+        if (h.nlevels > 3)
+            k_shift_levels<<<a.shift_blocks, 64, sizeof(double2) * P1, st>>>(d.level_start, h.nlevels, d.box_parent,
+                                                                            d.box_ix, d.box_iy, op.par, second, P1,
+                                                                            d.gbar, glimit, a.err);
     }
+    if (ev) cudaEventRecord(ev[4], st);
+    if (split && far) {
+        // tensor group E: digits of both expansion arrays (times alpha0 in the
+        // adjoint), then L2P (P2M^H) of `second` into PE and the W list of
+        // `first` into PW
+        ce = launch_split_digits_exp(a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0, sT->escale[dir], sp->edig,
+                                     sp->eexp, st);
+        if (ce != cudaSuccess) return ce;
+        SplitGemm g;
+        g.tiles = sp->tE[dir]; g.cols = sp->cE[dir]; g.ntiles = sp->ntE[dir];
+        g.ops = sT->ops[1][dir]; g.op_exp = sT->op_exp[1][dir];
+        g.dig = sp->edig; g.dexp = sp->eexp;
+        ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+        if (ce != cudaSuccess) return ce;
+    }
+    if (ev) cudaEventRecord(ev[5], st);
     // leafB: own expansion = second (local / adjoint multipole), W sources and
     // near log aux = first (multipole / adjoint local)
-    if (ev) cudaEventRecord(ev[4], st);
+    size_t shD = sizeof(double2) * P1 + sizeof(double) * NP;
     const int32_t *wp = far ? d.w_ptr : d.zero_ptr, *np_ = near ? d.near_ptr : d.zero_ptr;
+    const double *Pnear = (parts & 1) ? sp->Pnear : nullptr, *PE = (parts & 8) ? sp->PE : nullptr,
+                 *PW = (parts & 16) ? sp->PW : nullptr;
     if (adj)
-        k_leaf_out<true><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
-                                                            d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e,
-                                                            op.w, op.t, tb.wvec, second, first, first, vin, vout, NP,
-                                                            P1, a.half_L, far, Pnear);
+        k_leaf_out<true><<<grid_leaf, NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp, d.w_src,
+                                                     d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t,
+                                                     tb.wvec, second, first, first, vin, vout, NP, P1, d.lvtab, far,
+                                                     Pnear, PE, PW);
     else
-        k_leaf_out<false><<<grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16)), NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                             wp, d.w_src, d.w_code, np_, d.near_src,
-                                                             d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                                                             first, vin, vout, NP, P1, a.half_L, far, Pnear);
-    if (ev) cudaEventRecord(ev[5], st);
+        k_leaf_out<false><<<grid_leaf, NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
+                                                      d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w,
+                                                      op.t, tb.wvec, second, first, first, vin, vout, NP, P1,
+                                                      d.lvtab, far, Pnear, PE, PW);
+    if (ev) cudaEventRecord(ev[6], st);
     return cudaGetLastError();
+}
+
+cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_blocks)
+{
+    int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t shU = sizeof(double) * NP + sizeof(double2) * 8 * P1;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false>, 128, shU);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true>, 128, shU);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_shift_levels, 64, sizeof(double2) * P1);
+    if (e != cudaSuccess) return e;
+    if (std::min(bu0, bu1) < 1 || bs < 1) return cudaErrorInvalidConfiguration;
+    *up_blocks = sms * std::min(per_sm, std::min(bu0, bu1));
+    *shift_blocks = sms * std::min(per_sm, bs);
+    return cudaSuccess;
 }
 
 cudaError_t launch_batch_copy(const BatchPtrs &bp, bool gather, double *union_buf, int NP, cudaStream_t st)

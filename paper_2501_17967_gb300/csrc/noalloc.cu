@@ -96,6 +96,10 @@ extern "C" bc_status bc_apply_noalloc(bc_ctx *ctx, const bc_tree *tree, const do
     a.half_L = 0.5 * tree->h.L;
     a.nleaf = tree->h.nleaf;
     a.nbox = int64_t(nbox);
+    a.up_blocks = ctx->up_blocks;
+    a.shift_blocks = ctx->shift_blocks;
+    a.wait_limit = ctx->split.wait_limit;
+    a.err = ctx->dev_err;
     e = launch_apply(a, tree->h, d, ctx->dt, adjoint != 0, in, out, static_cast<cudaStream_t>(stream), 3, nullptr,
                      ctx->m2l_tri, nullptr);
     if (e != cudaSuccess) { set_error("bc_apply_noalloc: launch: %s", cudaGetErrorString(e)); return BC_ERR_CUDA; }

@@ -58,6 +58,19 @@ def hctx():
     return bc.Context(p=8, device=-1, cache_dir=None)
 
 
+def test_set_option_validation(hctx):
+    """Options are checked on the host: unknown names and out-of-range values
+    give BC_ERR_ARG; valid values are accepted."""
+    for name, bad in (("debug_split_parts", 32), ("debug_split_parts", -1), ("debug_split_parts", 2.5),
+                      ("wait_limit", 0), ("no_such_option", 1)):
+        with pytest.raises(bc.BoxCodeError) as e:
+            hctx.set_option(name, bad)
+        assert e.value.status == -1, (name, bad)
+    for name, good in (("debug_split_parts", 0), ("debug_split_parts", 31), ("wait_limit", 2 ** 26),
+                       ("m2l_triangular", 0)):
+        hctx.set_option(name, good)
+
+
 def test_tree_validation_errors(hctx):
     lv, ix, iy = synth.uniform_leaves(2)
     with pytest.raises(bc.BoxCodeError) as e:   # gap

@@ -275,8 +275,15 @@ def test_autograd_matches_finite_differences(ctx16):
 
 
 # ---------------------------------------------------------------------------
-# Split precision: near-field tables on BF16 tensor cores (tcgen05), p = 16.
+# Split precision, p = 16: the near-field tables, leaf-to-expansion, X list,
+# expansion-to-leaf and W list on BF16 tensor cores (tcgen05) as exact
+# products of 40-bit fixed-point digits; M2L, shifts, log terms and sums FP64.
+# Each product's rounding is about 2^-40 of its largest term times a small
+# multiple (balanced power-of-two column scales), ~1e-11 of max|u| after the
+# expansion-to-leaf step; the bound checked is the 1e-10 target (TOL).  The
+# near field alone stays at the 1e-12 level (SPLIT_NEAR_TOL).
 # ---------------------------------------------------------------------------
+SPLIT_NEAR_TOL = 1e-11
 def test_split_config1_vs_oracle(ctx16):
     p = 16
     g = synth.config_density(1)
@@ -299,7 +306,7 @@ def test_split_adaptive_vs_fp64_and_oracle(ctx16, adaptive):
     us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
     bc._check(bc._load().bc_sync(ctx16.handle, None))
     d = ((us - u64).abs().max() / u64.abs().max()).item()
-    assert d < 1e-11, d
+    assert d < TOL, d
     pick = synth.sample_leaves_per_level(np.asarray(lv), 2, seed=9)
     ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
     err = relerr(us.cpu().numpy().reshape(-1, p * p)[pick], ref)
@@ -315,13 +322,13 @@ def test_split_near_only_and_adjoint(ctx16, adaptive):
         ns = bc.apply(tree, f, precision=bc.SPLIT_BF16)
     finally:
         ctx16.debug(pass_mask=3)
-    assert ((ns - n64).abs().max() / n64.abs().max()).item() < 1e-11
+    assert ((ns - n64).abs().max() / n64.abs().max()).item() < SPLIT_NEAR_TOL
     gen = torch.Generator(device="cuda").manual_seed(5)
     gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
     h64 = bc.apply_adjoint(tree, gg)
     hs = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
     bc._check(bc._load().bc_sync(ctx16.handle, None))
-    assert ((hs - h64).abs().max() / h64.abs().max()).item() < 1e-11
+    assert ((hs - h64).abs().max() / h64.abs().max()).item() < TOL
     # host-pointer path gives the same split result as the device path
     uh = bc.apply(tree, f.cpu(), precision=bc.SPLIT_BF16)
     assert torch.equal(uh, bc.apply(tree, f, precision=bc.SPLIT_BF16).cpu())
@@ -357,4 +364,29 @@ def test_split_wait_timeout_is_reported_and_context_survives(ctx16, adaptive):
     u64 = bc.apply(tree, f)
     us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
     bc._check(bc._load().bc_sync(ctx16.handle, None))
-    assert ((us - u64).abs().max() / u64.abs().max()).item() < 1e-11
+    assert ((us - u64).abs().max() / u64.abs().max()).item() < TOL
+
+
+def test_split_parts_each_within_tolerance(ctx16, adaptive):
+    """Each tensor-core product alone (the others FP64) stays within the split
+    tolerance in both directions; with none of them the split apply equals
+    the FP64 apply bit for bit."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    u64, h64 = bc.apply(tree, f), bc.apply_adjoint(tree, gg)
+    try:
+        for parts in (0, 1, 2, 4, 8, 16):
+            ctx16.set_option("debug_split_parts", parts)
+            us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+            hs = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
+            bc._check(bc._load().bc_sync(ctx16.handle, None))
+            if parts == 0:
+                assert torch.equal(us, u64) and torch.equal(hs, h64)
+                continue
+            du = ((us - u64).abs().max() / u64.abs().max()).item()
+            dh = ((hs - h64).abs().max() / h64.abs().max()).item()
+            print(f"split part {parts}: fwd {du:.2e} adj {dh:.2e}")
+            assert 0.0 < du < TOL and 0.0 < dh < TOL, (parts, du, dh)
+    finally:
+        ctx16.set_option("debug_split_parts", 31)
