@@ -67,7 +67,7 @@ typedef enum {
 
 typedef struct {
     int p;            /* nodes per side, 4..16 (paper uses 16) */
-    int nterms;       /* far-field expansion terms P+1; 0 = default (see DESIGN) */
+    int nterms;       /* far-field expansion terms P+1, 4..32; 0 = default 30 */
     int node_kind;    /* 1 = first-kind Chebyshev (the only kind provided); 0 = default */
     int split_slices; /* BF16 slices per operand for BC_SPLIT_BF16; 0 = default */
     int autotune;     /* 1 = time tile shapes on first batched apply; 0 = fixed */

@@ -178,6 +178,18 @@ bc_status upload_tree(bc_tree *t)
     }
     e = dev_upload(d.allocs, &d.lvtab, lt.data(), lt.size());
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    {
+        std::vector<int32_t> vb(h.v_src.size()), xb(h.x_src.size());
+        for (size_t b = 0; b + 1 < h.v_ptr.size(); b++)
+            for (int32_t k = h.v_ptr[b]; k < h.v_ptr[b + 1]; k++) vb[k] = int32_t(b);
+        for (size_t b = 0; b + 1 < h.x_ptr.size(); b++)
+            for (int32_t k = h.x_ptr[b]; k < h.x_ptr[b + 1]; k++) xb[k] = int32_t(b);
+        if ((e = dev_upload(d.allocs, &d.v_box, vb.data(), vb.size())) != cudaSuccess ||
+            (e = dev_upload(d.allocs, &d.x_box, xb.data(), xb.size())) != cudaSuccess ||
+            (e = dev_upload<double2>(d.allocs, &d.Pv, nullptr, h.v_src.size() * size_t(P1))) != cudaSuccess ||
+            (e = dev_upload<double2>(d.allocs, &d.PX, nullptr, h.x_src.size() * size_t(P1))) != cudaSuccess)
+            return cuda_fail(e, "tree upload");
+    }
     e = dev_upload(d.allocs, &d.level_start, h.level_start.data(), h.level_start.size());
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     e = dev_upload<uint32_t>(d.allocs, &d.gbar, nullptr, 2);
@@ -673,7 +685,7 @@ bc_status bc_create(const bc_config *cfg, int device, bc_ctx **out)
     *out = nullptr;
     if (cfg->p < 4 || cfg->p > kMaxP) { set_error("bc_create: p must be in [4, %d]", kMaxP); return BC_ERR_ARG; }
     int nterms = cfg->nterms ? cfg->nterms : kDefaultNterms;
-    if (nterms < 4 || nterms > 64) { set_error("bc_create: nterms must be in [4, 64]"); return BC_ERR_ARG; }
+    if (nterms < 4 || nterms > 32) { set_error("bc_create: nterms must be in [4, 32]"); return BC_ERR_ARG; }
     if (cfg->node_kind != 0 && cfg->node_kind != 1) { set_error("bc_create: only first-kind Chebyshev nodes (node_kind 1) are provided"); return BC_ERR_UNSUPPORTED; }
     if (cfg->split_slices < 0 || cfg->split_slices > 8) { set_error("bc_create: split_slices must be in [0, 8]"); return BC_ERR_ARG; }
     if (device != -1) {
@@ -727,31 +739,27 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
         // factored M2L: d = 2(dx + i dy) per code
         const int P1 = ctx->P1;
         std::vector<double2> df(size_t(kNumV) * P1, make_double2(0, 0)), da(df.size(), make_double2(0, 0));
-        std::vector<double> ld(kNumV, 0.0), bn(size_t(P1) * (P1 + 1), 0.0);
+        std::vector<double2> sf(df.size(), make_double2(0, 0)), sa(df.size(), make_double2(0, 0));
+        std::vector<double> ld(kNumV, 0.0);
         for (int c = 0; c < kNumV; c++) {
             int dx = c % 7 - 3, dy = c / 7 - 3;
             if (std::max(std::abs(dx), std::abs(dy)) < 2) continue;
             std::complex<long double> d(2.0L * dx, 2.0L * dy), inv = 1.0L / d, pw = 1.0L;
             ld[c] = std::log(std::abs(std::complex<double>(2.0 * dx, 2.0 * dy)));
             for (int k = 0; k < P1; k++) {
+                const double sg = (k & 1) ? -1.0 : 1.0;
                 df[size_t(c) * P1 + k] = make_double2(double(pw.real()), double(pw.imag()));
                 da[size_t(c) * P1 + k] = make_double2(double(pw.real()), -double(pw.imag()));
+                sf[size_t(c) * P1 + k] = make_double2(sg * double(pw.real()), sg * double(pw.imag()));
+                sa[size_t(c) * P1 + k] = make_double2(sg * double(pw.real()), -sg * double(pw.imag()));
                 pw *= inv;
             }
         }
-        // C(i + j - 1, j), i >= 1
-        std::vector<long double> row(2 * P1 + 1, 0.0L);
-        for (int i = 1; i < P1; i++)
-            for (int j = 0; j < P1; j++) {
-                long double c = 1.0L;
-                int n = i + j - 1, kk = std::min(j, n - j);
-                for (int t = 1; t <= kk; t++) c = c * (n - kk + t) / t;
-                bn[size_t(i) * (P1 + 1) + j] = double(c);
-            }
         if ((e = dev_upload(ctx->dt.allocs, &ctx->dt.dpow_f, df.data(), df.size())) != cudaSuccess ||
             (e = dev_upload(ctx->dt.allocs, &ctx->dt.dpow_a, da.data(), da.size())) != cudaSuccess ||
-            (e = dev_upload(ctx->dt.allocs, &ctx->dt.logd, ld.data(), ld.size())) != cudaSuccess ||
-            (e = dev_upload(ctx->dt.allocs, &ctx->dt.binom, bn.data(), bn.size())) != cudaSuccess)
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.dsig_f, sf.data(), sf.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.dsig_a, sa.data(), sa.size())) != cudaSuccess ||
+            (e = dev_upload(ctx->dt.allocs, &ctx->dt.logd, ld.data(), ld.size())) != cudaSuccess)
             return cuda_fail(e, "tables upload");
     }
     e = dev_upload<int32_t>(ctx->dt.allocs, &ctx->dev_err, nullptr, 1);

@@ -109,11 +109,11 @@ struct DevTables {
     OpSet fwd, adj;
     double *wvec = nullptr;           // [NP]
     // M2L in factored form: d^-k (forward) / conj(d)^-k (adjoint) per V code,
-    // log|d| per code, and the binomial table C(i+j-1, j) at [i][j] (row
-    // stride P1 + 1) shared by every offset.
+    // the same with the sign (-1)^k, and log|d| per code (the binomial table
+    // is a constant-memory table of the kernels).
     double2 *dpow_f = nullptr, *dpow_a = nullptr;   // [kNumV][P1]
+    double2 *dsig_f = nullptr, *dsig_a = nullptr;   // [kNumV][P1]
     double *logd = nullptr;                          // [kNumV]
-    double *binom = nullptr;                         // [P1][P1 + 1]
     std::vector<void *> allocs;
 };
 
@@ -125,6 +125,9 @@ struct DevTree {
     int32_t *v_ptr = nullptr, *v_src = nullptr, *v_code = nullptr;
     int32_t *w_ptr = nullptr, *w_src = nullptr, *w_code = nullptr;
     int32_t *x_ptr = nullptr, *x_src = nullptr, *x_code = nullptr;
+    int32_t *v_box = nullptr, *x_box = nullptr;       // target box of each V / X entry
+    double2 *Pv = nullptr;                             // [n_v][P1] M2L contribution of each V pair
+    double2 *PX = nullptr;                             // [n_x][P1] X-list product of each entry (FP64 path)
     double2 *expA = nullptr, *expB = nullptr;  // [nbox][P1] workspaces
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
     double *lvtab = nullptr;                   // [2][kLvTab]: r^2 and log r per level

@@ -149,195 +149,232 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
     }
 }
 
-// -------------------------------------------------------------------------
-// m2l: for every box b at level >= 2 (one launch over all levels)
-//   out[b] = sum_{s in V(b)} M2L(d_s) in[s] + log(r) sum_s in[s][0] e_0
-//          + sum_{c in X(b)} (s1 * OpX[code] x[c] + s2 (lvec . x[c]) e_0)
-// M2L in factored form (d = (c_s - c_t)/r, complex):
-//   forward  a_k = (-1)^k d^-k A_k (k >= 1),
-//            B_l += d^-l sum_{k>=1} C(k+l-1, l) a_k + (l = 0 ? log|d| A_0 : -d^-l A_0 / l)
-//   adjoint  (exact conjugate transpose of the forward map of the reversed pair)
-//            a_l = (-1)^l conj(d)^-l in_l (l >= 0),
-//            out_k += conj(d)^-k sum_{l>=0} C(k+l-1, l) a_l   (k >= 1)
-//            out_0 += log|d| in_0 - sum_{l>=1} a_l / l
-// tri = 1 keeps only the terms with k + l <= P (and exactly their transpose).
-// The binomial table is shared by every offset and lives in shared memory;
-// each of the two warps of a block takes every other V source.
-// -------------------------------------------------------------------------
-template <bool ADJ>
-__global__ void __launch_bounds__(64)
-k_m2l(int64_t b0, int64_t b1, const int32_t *__restrict__ box_level, const int32_t *__restrict__ v_ptr,
-      const int32_t *__restrict__ v_src, const int32_t *__restrict__ v_code, const int32_t *__restrict__ x_ptr,
-      const int32_t *__restrict__ x_src, const int32_t *__restrict__ x_code, const double2 *__restrict__ dpow,
-      const double *__restrict__ logd, const double *__restrict__ binom, const double2 *__restrict__ OpX,
-      const double *__restrict__ xvec, const int32_t *__restrict__ leaf_box, const double2 *__restrict__ in,
-      double2 *out, int NP, int P1, const double *__restrict__ lvtab, int tri, const double *__restrict__ PX)
+// Level of box b from the level offsets (boxes are sorted by level).
+__device__ __forceinline__ int lv_of(const int64_t *__restrict__ level_start, int nlevels, int64_t b)
 {
-    extern __shared__ double smem[];
-    const int ldc = P1 + 1;
-    double *Cb = smem;                                           // [P1][P1+1]
-    double *inv = Cb + P1 * ldc;                                 // [P1] 1/l
-    double2 *sa = reinterpret_cast<double2 *>(inv + P1);         // [2][64] scaled sources
-    double2 *part = sa + 128;                                    // [2][64] warp partial sums
-    double2 *mono = part + 128;                                  // [2] sum of in[s][0] per warp
-    double *sx = reinterpret_cast<double *>(mono + 2);           // [NP]
-    const int tid = threadIdx.x, h = tid >> 5, lane = tid & 31, P = P1 - 1;
-    for (int i = tid; i < P1 * ldc; i += blockDim.x) {
-        int r = i / ldc, c = i % ldc;
-        // forward reads [k][l] = C(k+l-1, l); adjoint reads [l][k] = C(k+l-1, l),
-        // with column k = 0 holding the coefficients -1/l of out_0 (l >= 1)
-        if (ADJ)
-            Cb[i] = (c >= 1 && c < P1 && r < P1) ? binom[c * ldc + r] : ((c == 0 && r >= 1 && r < P1) ? -1.0 / r : 0.0);
-        else
-            Cb[i] = binom[i];
+    int lo = 0, hi = nlevels - 1;   // last lv with level_start[lv] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (level_start[mid] <= b) lo = mid; else hi = mid - 1;
     }
-    for (int i = tid; i < P1; i += blockDim.x) inv[i] = i ? 1.0 / i : 0.0;
-    __syncthreads();
-    for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
-        const int lv = box_level[b];
-        double ar[2] = {0.0, 0.0}, ai[2] = {0.0, 0.0};
-        double mr = 0.0, mi = 0.0;
-        double2 *a = sa + h * 64;
-        for (int e = v_ptr[b] + h; e < v_ptr[b + 1]; e += 2) {
-            const int s = v_src[e], c = v_code[e];
-            const double2 *dp = dpow + size_t(c) * P1;
-            for (int k = lane; k < P1; k += 32) {
-                double2 A = in[int64_t(s) * P1 + k], D = dp[k];
-                double zr = A.x * D.x - A.y * D.y, zi = A.x * D.y + A.y * D.x;
-                if (k & 1) { zr = -zr; zi = -zi; }
-                a[k] = make_double2(zr, zi);
-            }
-            __syncwarp();
-            const double2 A0 = a[0];
-            const double ld = logd[c];
-            mr += A0.x;
-            mi += A0.y;
+    return lo;
+}
+
+// -------------------------------------------------------------------------
+// Binomial table of the factored M2L, shared by every offset and every
+// expansion order P + 1 <= 32 (entries depend only on the indices):
+//   c_binom[k][o] = C(k + o - 1, o) for k >= 1, c_binom[0][o] = -1/o (o >= 1),
+//   c_binom[0][0] = 0.
+// Constant memory: in the unrolled loops below each entry is a DFMA operand.
+// -------------------------------------------------------------------------
+__constant__ double c_binom[32][32];
+
+// -------------------------------------------------------------------------
+// m2l_pairs: one thread per V-list pair e (target box b, source box s, offset
+// code c, d = (c_s - c_b)/r), writing the pair's contribution Pv[e][0..P]:
+//   forward  a_k = (-1)^k d^-k A_k (a_0 = A_0),
+//            Pv_o = d^-o sum_k c_binom[k][o] a_k + (o = 0) (log|d| + log r_b) A_0
+//   adjoint  (exact conjugate transpose of the forward map of the reversed pair)
+//            a_l = (-1)^l conj(d)^-l in_l,
+//            Pv_k = conj(d)^-k sum_l c_binom[k][l] a_l + (k = 0) (log|d| + log r_b) in_0
+// (the log r_b term is the level term of the box's own local expansion,
+// sum over V sources of r-scaled A_0 log r_b).  The source coefficients stay
+// in registers and the table entries come from constant memory, so nearly
+// every FP64 instruction is a useful FMA; every lane has a pair of its own.
+// tri = 1 keeps only the terms with k + o <= P (and exactly their transpose).
+// dsig[c][k] = (-1)^k d^-k (forward) or (-1)^k conj(d)^-k (adjoint),
+// dpow[c][o] = d^-o or conj(d)^-o.
+// -------------------------------------------------------------------------
+template <bool ADJ, int PMAX>
+__global__ void __launch_bounds__(128)
+k_m2l_pairs(int64_t npairs, const int32_t *__restrict__ v_box, const int32_t *__restrict__ v_src,
+            const int32_t *__restrict__ v_code, const int32_t *__restrict__ box_level,
+            const double2 *__restrict__ dsig, const double2 *__restrict__ dpow, const double *__restrict__ logd,
+            const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ Pv, int P1,
+            int tri)
+{
+    const int P = P1 - 1;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < npairs; e += int64_t(gridDim.x) * blockDim.x) {
+        const int b = v_box[e], s = v_src[e], c = v_code[e];
+        double ar[PMAX], ai[PMAX];
 #pragma unroll
-            for (int u = 0; u < 2; u++) {
-                const int o = lane + 32 * u;
-                if (o >= P1) continue;
-                double sr = 0.0, si = 0.0;
-                if (!ADJ) {
-                    // B_o += d^-o (sum_{k>=1} C(k+o-1, o) a_k + c_o A_0), c_0 = log|d| (d^0 = 1), c_o = -1/o
-                    const int kmax = tri ? P - o : P;
-                    for (int k = 1; k <= kmax; k++) {
-                        double cf = Cb[k * ldc + o];
-                        sr = fma(cf, a[k].x, sr);
-                        si = fma(cf, a[k].y, si);
-                    }
-                    const double c0 = o == 0 ? ld : -inv[o];
-                    sr = fma(c0, A0.x, sr);
-                    si = fma(c0, A0.y, si);
-                } else {
-                    // out_o += conj(d)^-o sum_{l} Cb[l][o] a_l  (+ log|d| in_0 for o = 0)
-                    const int lmax = (tri && o > 0) ? P - o : P;
-                    for (int l = 0; l <= lmax; l++) {
-                        double cf = Cb[l * ldc + o];
-                        sr = fma(cf, a[l].x, sr);
-                        si = fma(cf, a[l].y, si);
-                    }
-                    const double c0 = o == 0 ? ld : 0.0;
-                    sr = fma(c0, A0.x, sr);
-                    si = fma(c0, A0.y, si);
-                }
-                const double2 D = dp[o];
-                ar[u] += sr * D.x - si * D.y;
-                ai[u] += sr * D.y + si * D.x;
+        for (int k = 0; k < PMAX; k++) {
+            ar[k] = 0.0;
+            ai[k] = 0.0;
+            if (k < P1) {
+                const double2 A = in[int64_t(s) * P1 + k], D = dsig[c * P1 + k];
+                ar[k] = fma(A.x, D.x, -A.y * D.y);
+                ai[k] = fma(A.x, D.y, A.y * D.x);
             }
-            __syncwarp();
         }
-        // combine the two warps: thread tid owns coefficient tid
+        const double c0 = logd[c] + lvtab[kLvTab + box_level[b]];
+        double2 *out = Pv + e * P1;
 #pragma unroll
-        for (int u = 0; u < 2; u++) part[h * 64 + lane + 32 * u] = make_double2(ar[u], ai[u]);
-        if (lane == 0) mono[h] = make_double2(mr, mi);
-        __syncthreads();
-        double orr = 0.0, oi = 0.0;
-        if (tid < P1) {
-            orr = part[tid].x + part[64 + tid].x;
-            oi = part[tid].y + part[64 + tid].y;
-        }
-        if (tid == 0) {
-            const double logr = lvtab[kLvTab + lv];
-            orr += logr * (mono[0].x + mono[1].x);
-            oi += logr * (mono[0].y + mono[1].y);
-        }
-        // X list: leaf densities (forward) / leaf adjoint data (adjoint) of the
-        // coarser neighbour leaves.  The log term uses coefficient 0 of the
-        // leaf's own expansion from the upward pass: forward A_0 = r_c^2 (w.f)/2pi,
-        // adjoint B_0 = sum_j g_j, so the term is log(r_c) * that coefficient.
-        const double s1 = ADJ ? 1.0 : lvtab[lv - 1];   // r_c^2
-        const double logrc = lvtab[kLvTab + lv - 1];
-        for (int e = x_ptr[b]; e < x_ptr[b + 1] && PX; e++) {
-            // split path: the scaled product s1 * OpX x[c] comes from the tensor cores
-            if (tid < P1) {
-                orr += PX[size_t(e) * kSplitKE + 2 * tid];
-                oi += PX[size_t(e) * kSplitKE + 2 * tid + 1];
-                if (tid == 0) orr = fma(logrc, in[int64_t(leaf_box[x_src[e]]) * P1].x, orr);
-            }
-        }
-        for (int e = x_ptr[b]; e < x_ptr[b + 1] && !PX; e++) {
-            const int c = x_src[e];
-            const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
-            __syncthreads();
-            for (int j = tid; j < NP; j += blockDim.x) sx[j] = xvec[int64_t(c) * NP + j];
-            __syncthreads();
-            if (tid < P1) {
-                double xr0 = 0.0, xi0 = 0.0, xr1 = 0.0, xi1 = 0.0;
-                for (int j = 0; j < NP; j += 2) {
-                    double2 o0 = op[j * P1 + tid], o1 = op[(j + 1) * P1 + tid];
-                    xr0 = fma(o0.x, sx[j], xr0);
-                    xi0 = fma(o0.y, sx[j], xi0);
-                    xr1 = fma(o1.x, sx[j + 1], xr1);
-                    xi1 = fma(o1.y, sx[j + 1], xi1);
+        for (int o = 0; o < PMAX; o++) {
+            if (o >= P1) break;
+            double sr = 0.0, si = 0.0;
+#pragma unroll
+            for (int k = 0; k < PMAX; k++) {
+                if (k >= P1) break;
+                const bool keep = !tri || (ADJ ? (o == 0 || k + o <= P) : (k == 0 || k + o <= P));
+                if (keep) {
+                    const double cf = ADJ ? c_binom[o][k] : c_binom[k][o];
+                    sr = fma(cf, ar[k], sr);
+                    si = fma(cf, ai[k], si);
                 }
-                orr = fma(s1, xr0 + xr1, orr);
-                oi = fma(s1, xi0 + xi1, oi);
-                if (tid == 0) orr = fma(logrc, in[int64_t(leaf_box[c]) * P1].x, orr);
             }
+            if (o == 0) {
+                sr = fma(c0, ar[0], sr);
+                si = fma(c0, ai[0], si);
+            }
+            const double2 W = dpow[c * P1 + o];
+            out[o] = make_double2(fma(sr, W.x, -si * W.y), fma(sr, W.y, si * W.x));
         }
-        if (tid < P1) out[b * P1 + tid] = make_double2(orr, oi);
-        __syncthreads();
     }
 }
 
 // -------------------------------------------------------------------------
-// shift_levels: out[b] += Par_q * out[parent(b)] for every box of level >= 3,
-// level by level (one persistent launch, grid barriers between levels)
-//   forward: L2L; adjoint: M2M^H.  Two independent FMA chains per thread.
+// x_entries (FP64 path): the X-list products, one block per entry e (target
+// box b, source leaf c at level lv_b - 1):
+//   PX[e][l] = s1 * sum_j OpX[code][j][l] x[c][j]
+//   forward (P2L): s1 = r_c^2;  adjoint (M2P^H): s1 = 1
+// Four warps split the nodes; the partial sums meet in shared memory.
 // -------------------------------------------------------------------------
-__global__ void __launch_bounds__(64)
-k_shift_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_t *__restrict__ parent,
-               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
-               const double2 *__restrict__ OpPar, double2 *out, int P1, uint32_t *gbar, long long limit,
-               int32_t *err)
+template <bool ADJ>
+__global__ void __launch_bounds__(128)
+k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__restrict__ x_src,
+            const int32_t *__restrict__ x_code, const int32_t *__restrict__ box_level,
+            const double2 *__restrict__ OpX, const double *__restrict__ xvec, double2 *__restrict__ PX, int NP,
+            int P1, const double *__restrict__ lvtab)
 {
-    extern __shared__ double2 se[];
+    extern __shared__ double2 shx[];
+    double2 *part = shx;                                     // [4][P1]
+    double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nq = NP / 4;
+    for (int64_t e = blockIdx.x; e < nx; e += gridDim.x) {
+        const int c = x_src[e];
+        const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
+        const double s1 = ADJ ? 1.0 : lvtab[box_level[x_box[e]] - 1];
+        __syncthreads();
+        for (int j = threadIdx.x; j < NP; j += blockDim.x) sv[j] = xvec[int64_t(c) * NP + j];
+        __syncthreads();
+        for (int l = lane; l < P1; l += 32) {
+            double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+            for (int j = w * nq; j < (w + 1) * nq; j += 2) {
+                double2 o0 = op[j * P1 + l], o1 = op[(j + 1) * P1 + l];
+                re0 = fma(o0.x, sv[j], re0);
+                im0 = fma(o0.y, sv[j], im0);
+                re1 = fma(o1.x, sv[j + 1], re1);
+                im1 = fma(o1.y, sv[j + 1], im1);
+            }
+            part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < P1; l += blockDim.x) {
+            const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
+            PX[e * P1 + l] = make_double2(s1 * ((a0.x + a1.x) + (a2.x + a3.x)), s1 * ((a0.y + a1.y) + (a2.y + a3.y)));
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// down_levels: the local expansion (adjoint: multipole) of every box at
+// level >= 2, in one persistent launch:
+//   phase 1 (every box at once):
+//     out[b] = sum_{e in V(b)} Pv[e] + sum_{x in X(b)} (PX[x] + log(r_c) A_0(c) e_0)
+//   phase 2 (levels 3, 4, ..., grid barriers between levels):
+//     out[b] += Par_q out[parent(b)]      (forward L2L, adjoint M2M^H)
+// The X-list log term uses coefficient 0 of the source leaf's own expansion
+// from the upward pass (forward A_0 = r_c^2 (w.f)/2pi, adjoint B_0 = sum_j g_j).
+// Four warps per block: in phase 1 warp w sums every fourth V pair, in phase 2
+// warp w applies a quarter of the shift operator's columns (the shift chain
+// is the critical path, and one warp alone would serialise on its FP64 unit).
+// -------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_t *__restrict__ v_ptr,
+              const double2 *__restrict__ Pv, const int32_t *__restrict__ x_ptr, const int32_t *__restrict__ x_src,
+              const double2 *__restrict__ PX, int px_stride, const int32_t *__restrict__ leaf_box,
+              const double2 *__restrict__ first, const int32_t *__restrict__ parent,
+              const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
+              const double2 *__restrict__ OpPar, double2 *out, int P1, const double *__restrict__ lvtab,
+              uint32_t *gbar, long long limit, int32_t *err)
+{
+    extern __shared__ double2 sdn[];
+    double2 *se = sdn;             // [P1] parent expansion
+    double2 *part = sdn + P1;      // [4][P1] partial sums
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
+        const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
+        for (int o = lane; o < P1; o += 32) {
+            double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+            int e = v0 + w;
+            for (; e + 4 < v1; e += 8) {   // two loads in flight per warp step
+                const double2 t0 = Pv[int64_t(e) * P1 + o], t1 = Pv[int64_t(e + 4) * P1 + o];
+                re0 += t0.x;
+                im0 += t0.y;
+                re1 += t1.x;
+                im1 += t1.y;
+            }
+            if (e < v1) {
+                const double2 t0 = Pv[int64_t(e) * P1 + o];
+                re0 += t0.x;
+                im0 += t0.y;
+            }
+            part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+        }
+        __syncthreads();
+        if (w == 0) {
+            const double logrc = lvtab[kLvTab + lv_of(level_start, nlevels, b) - 1];
+            for (int o = lane; o < P1; o += 32) {
+                const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
+                double re = (a0.x + a1.x) + (a2.x + a3.x), im = (a0.y + a1.y) + (a2.y + a3.y);
+                for (int x = x_ptr[b]; x < x_ptr[b + 1]; x++) {
+                    const double2 t = PX[int64_t(x) * px_stride + o];
+                    re += t.x;
+                    im += t.y;
+                    if (o == 0) re = fma(logrc, first[int64_t(leaf_box[x_src[x]]) * P1].x, re);
+                }
+                out[b * P1 + o] = make_double2(re, im);
+            }
+        }
+        __syncthreads();
+    }
+    const int kq = (P1 + 3) / 4;
     for (int lv = 3; lv < nlevels; lv++) {
-        if (lv > 3) grid_sync(gbar, limit, err);   // the parents' level is complete
+        grid_sync(gbar, limit, err);   // phase 1 and the parents' level are complete
         for (int64_t b = level_start[lv] + blockIdx.x; b < level_start[lv + 1]; b += gridDim.x) {
             const int pb = parent[b];
             const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
             __syncthreads();
             for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
             __syncthreads();
-            for (int l = threadIdx.x; l < P1; l += blockDim.x) {
-                const double2 *op = OpPar + size_t(q) * P1 * P1;
-                const double2 acc = __ldcg(&out[b * P1 + l]);
-                double re0 = acc.x, im0 = acc.y, re1 = 0.0, im1 = 0.0;
-                int k = 0;
-                for (; k + 1 < P1; k += 2) {
-                    double2 o0 = op[k * P1 + l], a0 = se[k], o1 = op[(k + 1) * P1 + l], a1 = se[k + 1];
-                    re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
-                    im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
-                    re1 = fma(o1.x, a1.x, fma(-o1.y, a1.y, re1));
-                    im1 = fma(o1.x, a1.y, fma(o1.y, a1.x, im1));
+            const double2 *op = OpPar + size_t(q) * P1 * P1;
+            const int k0 = w * kq, k1 = min(P1, k0 + kq);
+            for (int o = lane; o < P1; o += 32) {
+                double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+                int k = k0;
+                for (; k + 1 < k1; k += 2) {
+                    const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k], w1 = __ldg(&op[(k + 1) * P1 + o]), a1 = se[k + 1];
+                    re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
+                    im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
+                    re1 = fma(w1.x, a1.x, fma(-w1.y, a1.y, re1));
+                    im1 = fma(w1.x, a1.y, fma(w1.y, a1.x, im1));
                 }
-                if (k < P1) {
-                    double2 o0 = op[k * P1 + l], a0 = se[k];
-                    re0 = fma(o0.x, a0.x, fma(-o0.y, a0.y, re0));
-                    im0 = fma(o0.x, a0.y, fma(o0.y, a0.x, im0));
+                if (k < k1) {
+                    const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k];
+                    re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
+                    im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
                 }
-                out[b * P1 + l] = make_double2(re0 + re1, im0 + im1);
+                part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+            }
+            __syncthreads();
+            if (w == 0) {
+                for (int o = lane; o < P1; o += 32) {
+                    const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
+                    const double2 cur = __ldcg(&out[b * P1 + o]);
+                    out[b * P1 + o] = make_double2(cur.x + ((a0.x + a1.x) + (a2.x + a3.x)),
+                                                   cur.y + ((a0.y + a1.y) + (a2.y + a3.y)));
+                }
             }
         }
     }
@@ -569,23 +606,38 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     }
     if (ev) cudaEventRecord(ev[3], st);
     if (far && h.nlevels > 2) {
-        const int64_t b0 = h.level_start[2], b1 = h.level_start[h.nlevels];
-        size_t shM = sizeof(double) * (size_t(P1) * (P1 + 1) + P1) + sizeof(double2) * (128 + 128 + 2) +
-                     sizeof(double) * NP;
-        int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : 12));
-        const double *PX = (parts & 4) ? sp->PX : nullptr;
-        if (adj)
-            k_m2l<true><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
-                                               d.x_code, tb.dpow_a, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
-                                               second, NP, P1, d.lvtab, m2l_tri, PX);
-        else
-            k_m2l<false><<<grid, 64, shM, st>>>(b0, b1, d.box_level, d.v_ptr, d.v_src, d.v_code, d.x_ptr, d.x_src,
-                                                d.x_code, tb.dpow_f, tb.logd, tb.binom, op.x, vin, d.leaf_box, first,
-                                                second, NP, P1, d.lvtab, m2l_tri, PX);
-        if (h.nlevels > 3)
-            k_shift_levels<<<a.shift_blocks, 64, sizeof(double2) * P1, st>>>(d.level_start, h.nlevels, d.box_parent,
-                                                                            d.box_ix, d.box_iy, op.par, second, P1,
-                                                                            d.gbar, glimit, a.err);
+        // M2L per V pair, then (FP64) the X-list products, then the level-by-level sum
+        const int64_t npairs = int64_t(h.v_src.size());
+        if (npairs > 0) {
+            const int grid = grid_for((npairs + 127) / 128, 152 * 24);
+            const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
+#define BC_M2L(A, PM)                                                                                      \
+    k_m2l_pairs<A, PM><<<grid, 128, 0, st>>>(npairs, d.v_box, d.v_src, d.v_code, d.box_level, dsig, dpw, tb.logd, \
+                                             d.lvtab, first, d.Pv, P1, m2l_tri)
+            if (P1 <= 16) { if (adj) BC_M2L(true, 16); else BC_M2L(false, 16); }
+            else { if (adj) BC_M2L(true, 32); else BC_M2L(false, 32); }
+#undef BC_M2L
+        }
+        const double2 *PX = nullptr;
+        int px_stride = P1;
+        if (parts & 4) {
+            PX = reinterpret_cast<const double2 *>(sp->PX);
+            px_stride = kSplitKE / 2;
+        } else if (!h.x_src.empty()) {
+            const int64_t nx = int64_t(h.x_src.size());
+            const size_t shX = sizeof(double2) * 4 * P1 + sizeof(double) * NP;
+            if (adj)
+                k_x_entries<true><<<grid_for(nx, 152 * 16), 128, shX, st>>>(nx, d.x_box, d.x_src, d.x_code, d.box_level,
+                                                                            op.x, vin, d.PX, NP, P1, d.lvtab);
+            else
+                k_x_entries<false><<<grid_for(nx, 152 * 16), 128, shX, st>>>(nx, d.x_box, d.x_src, d.x_code,
+                                                                             d.box_level, op.x, vin, d.PX, NP, P1,
+                                                                             d.lvtab);
+            PX = d.PX;
+        }
+        k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * 5 * P1, st>>>(
+            d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
+            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, d.gbar, glimit, a.err);
     }
     if (ev) cudaEventRecord(ev[4], st);
     if (split && far) {
@@ -625,6 +677,23 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 
 cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_blocks)
 {
+    {
+        // binomial table of the factored M2L (see c_binom)
+        double tab[32][32];
+        for (int k = 0; k < 32; k++)
+            for (int o = 0; o < 32; o++) {
+                if (k == 0) {
+                    tab[k][o] = o == 0 ? 0.0 : -1.0 / o;
+                    continue;
+                }
+                long double c = 1.0L;   // C(k + o - 1, o)
+                const int n = k + o - 1, m = std::min(o, n - o);
+                for (int t = 1; t <= m; t++) c = c * (n - m + t) / t;
+                tab[k][o] = double(c);
+            }
+        cudaError_t e = cudaMemcpyToSymbol(c_binom, tab, sizeof(tab));
+        if (e != cudaSuccess) return e;
+    }
     int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -632,7 +701,7 @@ cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false>, 128, shU);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true>, 128, shU);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_shift_levels, 64, sizeof(double2) * P1);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels, 128, sizeof(double2) * 5 * P1);
     if (e != cudaSuccess) return e;
     if (std::min(bu0, bu1) < 1 || bs < 1) return cudaErrorInvalidConfiguration;
     *up_blocks = sms * std::min(per_sm, std::min(bu0, bu1));

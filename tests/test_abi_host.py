@@ -71,6 +71,14 @@ def test_set_option_validation(hctx):
         hctx.set_option(name, good)
 
 
+def test_context_argument_checks():
+    """bc_create rejects orders and expansion lengths outside the provided range."""
+    for kw in ({"p": 3}, {"p": 17}, {"nterms": 3}, {"nterms": 33}):
+        with pytest.raises(bc.BoxCodeError) as e:
+            bc.Context(device=-1, cache_dir=None, **kw)
+        assert e.value.status == -1, kw
+
+
 def test_tree_validation_errors(hctx):
     lv, ix, iy = synth.uniform_leaves(2)
     with pytest.raises(bc.BoxCodeError) as e:   # gap

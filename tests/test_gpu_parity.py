@@ -151,6 +151,36 @@ def test_adjoint_dot_product(ctx16, adaptive):
     assert abs(lhs - rhs) <= 1e-14 * scale, (lhs, rhs, scale)
 
 
+def test_m2l_triangular_and_orders(ctx16, adaptive):
+    """The triangular M2L truncation (k + l <= P) keeps the exact-transpose
+    property and stays close to the full series; a context with a short
+    expansion (nterms 12, the 16-wide M2L kernel) agrees with nterms 30 to
+    its truncation level."""
+    lv, ix, iy, gd, tree, geom, fvals, f = adaptive
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    fr = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    gr = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    full = bc.apply(tree, f)
+    ctx16.set_option("m2l_triangular", 1)
+    try:
+        tri = bc.apply(tree, f)
+        lhs = torch.dot(bc.apply(tree, fr).ravel(), gr.ravel()).item()
+        rhs = torch.dot(fr.ravel(), bc.apply_adjoint(tree, gr).ravel()).item()
+        scale = (bc.apply(tree, fr).abs() * gr.abs()).sum().item()
+    finally:
+        ctx16.set_option("m2l_triangular", 0)
+    assert abs(lhs - rhs) <= 1e-14 * scale, (lhs, rhs, scale)
+    d = ((tri - full).abs().max() / full.abs().max()).item()
+    assert 0.0 < d < 1e-6, d
+    ctx12 = bc.Context(p=16, nterms=12, device=0)
+    t12 = bc.Tree(ctx12, lv, ix, iy)
+    d12 = ((bc.apply(t12, f) - full).abs().max() / full.abs().max()).item()
+    assert 0.0 < d12 < 1e-5, d12
+    lhs = torch.dot(bc.apply(t12, fr).ravel(), gr.ravel()).item()
+    rhs = torch.dot(fr.ravel(), bc.apply_adjoint(t12, gr).ravel()).item()
+    assert abs(lhs - rhs) <= 1e-14 * scale, (lhs, rhs)
+
+
 def test_adjoint_against_oracle_columns(ctx16):
     """Sampled entries of A^T g against the oracle's transposed operator."""
     p = 16

@@ -49,8 +49,8 @@ def test_noalloc_matches_regular_apply():
 def test_noalloc_rejects_trees_beyond_its_workspace():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    ctx = bc.Context(p=8, nterms=64, device=0)
-    lv, ix, iy = synth.uniform_leaves(7)   # 21845 boxes x 64 terms x 32 B > 16 MiB
+    ctx = bc.Context(p=8, nterms=32, device=0)
+    lv, ix, iy = synth.uniform_leaves(7)   # 21845 boxes x 32 terms x 32 B > 16 MiB
     tree = bc.Tree(ctx, lv, ix, iy)
     x = torch.zeros(tree.nleaf * 64, dtype=torch.float64, device="cuda")
     out = torch.empty_like(x)
