@@ -206,6 +206,11 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *   "wait_limit" (default 2^26): polls of each bounded device-side wait of the
  *     split-precision kernel before it gives up, records the failure (reported
  *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns.
+ *   "split_overlap" (0/1, default 0): the near-field tensor-core launch of a
+ *     split-precision apply runs in line on the apply's stream (0) or on an
+ *     internal stream, concurrently with the FP64 far-field passes (1; on the
+ *     20-Gaussian workload the passes then slow down as much as the launch
+ *     saves).
  *   "debug_split_parts" (integer 0..31, default 31): diagnostics; which
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,
@@ -219,15 +224,16 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
 /* Diagnostics.  pass_mask selects the parts of the operator an apply
  * evaluates: bit 0 the near field (leaf-to-leaf tables), bit 1 the far field
  * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
- * event on the apply's stream at each stage boundary:
- *   0 tensor group V (split precision: digits of the input, near field,
- *     leaf-to-expansion, X list), 1 counter reset, 2 upward pass (FP64:
- *     with the leaf-to-expansion step), 3 downward pass (M2L, shifts),
- *     4 tensor group E (split precision: digits of the expansions,
- *     expansion-to-leaf and W list), 5 leaf output;
- * bc_debug_stage_times then waits for the last event of the most recent
- * forward (adjoint = 0) or adjoint apply and writes the six stage durations
- * in milliseconds to ms[6] (stages 0 and 4 are empty for FP64 applies). */
+ * event at each stage boundary:
+ *   0 tensor group V, far part (split precision: digits of the input,
+ *     leaf-to-expansion, X list), 1 barrier reset, 2 upward pass (FP64: with
+ *     the leaf-to-expansion step), 3 downward pass (M2L, shifts), 4 tensor
+ *     group E (split precision: digits of the expansions, expansion-to-leaf
+ *     and W list), 5 leaf output; 6 the near-field tensor launch, which runs
+ *     on an internal stream beside stages 1-4;
+ * bc_debug_stage_times then waits for the last events of the most recent
+ * forward (adjoint = 0) or adjoint apply and writes the seven stage durations
+ * in milliseconds to ms[7] (stages 0, 4 and 6 are empty for FP64 applies). */
 bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
 /* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,

@@ -404,6 +404,12 @@ bc_status build_split_tables(bc_ctx *ctx)
     }
     cudaError_t e = split_prepare();
     if (e != cudaSuccess) return cuda_fail(e, "split kernel attributes");
+    if (!ctx->side.side) {
+        if ((e = cudaStreamCreateWithFlags(&ctx->side.side, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "split side stream");
+    }
     ctx->split_ready = true;
     return BC_OK;
 }
@@ -464,7 +470,7 @@ bc_status build_split_tree(bc_tree *t)
         const bool adj = dir == 1;
         double2 *first = adj ? t->d.expB : t->d.expA;
         const int first_which = adj ? 1 : 0, second_which = adj ? 0 : 1;   // expA = 0, expB = 1
-        TileBuilder V, E;
+        TileBuilder V, NV, E;
         // near entries, by table
         std::vector<std::vector<SplitCol>> by_tab(kNumNear);
         for (int64_t k = 0; k < nn; k++) {
@@ -476,7 +482,7 @@ bc_status build_split_tree(bc_tree *t)
             by_tab[h.near_tab[k]].push_back(c);
         }
         for (int tab = 0; tab < kNumNear; tab++)
-            if (!by_tab[tab].empty()) V.add(T.near_op[dir][tab], by_tab[tab]);
+            if (!by_tab[tab].empty()) NV.add(T.near_op[dir][tab], by_tab[tab]);
         // leafA of every leaf (Morton order), then the X entries by code
         std::vector<SplitCol> cl;
         for (int64_t i = 0; i < h.nleaf; i++) {
@@ -522,10 +528,13 @@ bc_status build_split_tree(bc_tree *t)
             if (!by_code[c].empty()) E.add(T.w_op[dir][c], by_code[c]);
         if ((e = dev_upload(al, &s.tV[dir], V.tiles.data(), V.tiles.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.cV[dir], V.cols.data(), V.cols.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.tN[dir], NV.tiles.data(), NV.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cN[dir], NV.cols.data(), NV.cols.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.tE[dir], E.tiles.data(), E.tiles.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess)
             return cuda_fail(e, "split tree upload");
         s.ntV[dir] = int(V.tiles.size());
+        s.ntN[dir] = int(NV.tiles.size());
         s.ntE[dir] = int(E.tiles.size());
     }
     s.err = t->ctx->dev_err;
@@ -555,7 +564,7 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     PassArgs a = pass_args(ctx, tree);
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
-    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts};
+    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr};
     const SplitLaunch *split = nullptr;
     bc_tree *tw = const_cast<bc_tree *>(tree);
     if (prec == BC_SPLIT_BF16) {
@@ -635,7 +644,7 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     PassArgs a = pass_args(ctx, b->u);
     a.leaf_bps = leaf_bps;
     a.m2l_bps = m2l_bps;
-    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts};
+    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr};
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
     cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,
@@ -714,6 +723,9 @@ void bc_destroy(bc_ctx *ctx)
     for (auto &dir : ctx->ev)
         for (auto &e : dir)
             if (e) cudaEventDestroy(e);
+    if (ctx->side.fork) cudaEventDestroy(ctx->side.fork);
+    if (ctx->side.join) cudaEventDestroy(ctx->side.join);
+    if (ctx->side.side) cudaStreamDestroy(ctx->side.side);
     free_all(ctx->dt.allocs);
     free_all(ctx->split_allocs);
     delete ctx;
@@ -764,7 +776,8 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
     }
     e = dev_upload<int32_t>(ctx->dt.allocs, &ctx->dev_err, nullptr, 1);
     if (e != cudaSuccess) return cuda_fail(e, "error flag");
-    e = fp64_prepare(ctx->NP, ctx->P1, 4, &ctx->up_blocks, &ctx->shift_blocks);
+    // two upward blocks per SM leave room for a tensor-core CTA beside them
+    e = fp64_prepare(ctx->NP, ctx->P1, 2, 4, &ctx->up_blocks, &ctx->shift_blocks);
     if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel occupancy");
     s = build_split_tables(ctx);
     if (s != BC_OK) return s;
@@ -1113,7 +1126,7 @@ bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing)
     if (timing && !ctx->ev[0][0]) {
         cudaError_t e = cudaSetDevice(ctx->device);
         for (int d = 0; d < 2; d++)
-            for (int i = 0; e == cudaSuccess && i <= kNumStages; i++) e = cudaEventCreate(&ctx->ev[d][i]);
+            for (int i = 0; e == cudaSuccess && i < kNumEvents; i++) e = cudaEventCreate(&ctx->ev[d][i]);
         if (e != cudaSuccess) return cuda_fail(e, "bc_debug_set: events");
     }
     ctx->timing = timing != 0;
@@ -1130,6 +1143,10 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
     if (std::strcmp(name, "wait_limit") == 0) {
         if (!(value >= 1.0 && value <= 1e15)) { set_error("bc_set_option: wait_limit must be in [1, 1e15]"); return BC_ERR_ARG; }
         ctx->split.wait_limit = (long long)value;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "split_overlap") == 0) {
+        ctx->split_overlap = value != 0.0;
         return BC_OK;
     }
     if (std::strcmp(name, "debug_split_parts") == 0) {
@@ -1153,10 +1170,11 @@ bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms)
     if (!ctx || !ms) { set_error("bc_debug_stage_times: NULL argument"); return BC_ERR_ARG; }
     if (!ctx->timing) { set_error("bc_debug_stage_times: timing is off"); return BC_ERR_STATE; }
     cudaEvent_t *ev = ctx->ev[adjoint ? 1 : 0];
-    cudaError_t e = cudaEventSynchronize(ev[kNumStages]);
+    cudaError_t e = cudaEventSynchronize(ev[6]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[8]);
     for (int i = 0; e == cudaSuccess && i < kNumStages; i++) {
         float t = 0.0f;
-        e = cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+        e = i < 6 ? cudaEventElapsedTime(&t, ev[i], ev[i + 1]) : cudaEventElapsedTime(&t, ev[7], ev[8]);
         ms[i] = t;
     }
     return e == cudaSuccess ? BC_OK : cuda_fail(e, "bc_debug_stage_times");

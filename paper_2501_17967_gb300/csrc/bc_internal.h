@@ -191,10 +191,11 @@ struct SplitGemm {
     const int32_t *dexp = nullptr;     // [nvec]
 };
 struct SplitTree {
-    // [forward, adjoint]
-    SplitTile *tV[2] = {}, *tE[2] = {};
-    SplitCol *cV[2] = {}, *cE[2] = {};
-    int ntV[2] = {}, ntE[2] = {};
+    // [forward, adjoint]; group V in two launches: far (leafA, X list: needed
+    // by the upward and downward passes) and near (needed at the leaf output)
+    SplitTile *tV[2] = {}, *tN[2] = {}, *tE[2] = {};
+    SplitCol *cV[2] = {}, *cN[2] = {}, *cE[2] = {};
+    int ntV[2] = {}, ntN[2] = {}, ntE[2] = {};
     double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
     double *PX = nullptr;         // [n_x][64] X-list result per entry
     double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf
@@ -214,6 +215,7 @@ struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
     int parts = kSplitAllParts;
+    const struct SideStream *side = nullptr;   // null: the near-field launch stays on the apply's stream
 };
 // Digits of the leaf vectors (times scale), of the two expansion arrays
 // (times scale), and the tensor-core operator products of one group.
@@ -240,7 +242,7 @@ struct PassArgs {
 };
 // Largest grids of the persistent FP64 passes whose blocks are all resident
 // (occupancy calculator), capped at `per_sm` blocks per SM.
-cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_blocks);
+cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up_blocks, int *shift_blocks);
 
 // Disjoint union of trees (batched applies): leaves and boxes renumbered,
 // boxes sorted by (level, tree, Morton order), lists concatenated.
@@ -249,15 +251,24 @@ bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree 
 
 // Forward (adj = false) or adjoint (adj = true) apply on `stream`.
 // vin: f (forward) or g (adjoint); vout: u or h.  Device pointers.
-// Stage boundaries recorded when timing is on:
-// tensor group V | clear | upward | downward | tensor group E | leaf output.
-// (The FP64 path leaves the two tensor stages empty.)
-constexpr int kNumStages = 6;
+// Stage boundaries recorded when timing is on (events 0..6 on the apply's
+// stream): tensor group V far part | clear | upward | downward | tensor group
+// E | leaf output; events 7, 8 bracket the near-field tensor launch on the side
+// stream (stage 6, overlapping stages 1-4).  The FP64 path leaves the tensor
+// stages empty.
+constexpr int kNumStages = 7;
+constexpr int kNumEvents = 9;
 // pass_mask bit 0: near field, bit 1: far field.  ev: kNumStages+1 events or null.
 // m2l_tri: triangular truncation of the M2L series (k + l <= P).
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          bool adj, const double *vin, double *vout, cudaStream_t stream, int pass_mask,
                          cudaEvent_t *ev, int m2l_tri, const struct SplitLaunch *split);
+// Fork/join resources of the split path: the near-field tensor launch runs on
+// `side` between the events.
+struct SideStream {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
 struct BatchPtrs {
@@ -281,8 +292,10 @@ struct bc_ctx {
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
     int split_parts = bc::kSplitAllParts;   // diagnostics: split-precision products in use
+    int split_overlap = 0;      // near-field tensor launch on the side stream (1) or inline (0)
     bool timing = false;        // record CUDA events around each stage
-    cudaEvent_t ev[2][bc::kNumStages + 1] = {};   // [forward, adjoint]
+    cudaEvent_t ev[2][bc::kNumEvents] = {};   // [forward, adjoint]
+    bc::SideStream side;
     bc::HostTables ht;
     bc::DevTables dt;
     bc::SplitTables split;

@@ -565,8 +565,9 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     cudaError_t ce;
     if (ev) cudaEventRecord(ev[0], st);
     if (split) {
-        // tensor group V: digits of alpha0 * vin; near field, leafA (P2M / L2P^H)
-        // into `first`, X list into PX
+        // tensor group V: digits of alpha0 * vin; leafA (P2M / L2P^H) into
+        // `first` and the X list into PX on this stream, then the near field
+        // into Pnear on the side stream (joined before the leaf output)
         ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
         if (ce != cudaSuccess) return ce;
         SplitGemm g;
@@ -575,6 +576,20 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         g.dig = sp->vdig; g.dexp = sp->vexp;
         ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
         if (ce != cudaSuccess) return ce;
+        const SideStream *sd = split->side;
+        cudaStream_t ns = sd ? sd->side : st;
+        if (sd && ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
+                   (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess))
+            return ce;
+        if (ev) cudaEventRecord(ev[7], ns);
+        g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
+        ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, ns);
+        if (ce != cudaSuccess) return ce;
+        if (ev) cudaEventRecord(ev[8], ns);
+        if (sd && (ce = cudaEventRecord(sd->join, sd->side)) != cudaSuccess) return ce;
+    } else if (ev) {
+        cudaEventRecord(ev[7], st);
+        cudaEventRecord(ev[8], st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     // the grid barrier of the persistent passes starts from zero (a barrier
@@ -655,6 +670,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (ce != cudaSuccess) return ce;
     }
     if (ev) cudaEventRecord(ev[5], st);
+    if (split && split->side && (ce = cudaStreamWaitEvent(st, split->side->join, 0)) != cudaSuccess) return ce;
     // leafB: own expansion = second (local / adjoint multipole), W sources and
     // near log aux = first (multipole / adjoint local)
     size_t shD = sizeof(double2) * P1 + sizeof(double) * NP;
@@ -675,7 +691,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     return cudaGetLastError();
 }
 
-cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_blocks)
+cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up_blocks, int *shift_blocks)
 {
     {
         // binomial table of the factored M2L (see c_binom)
@@ -704,8 +720,8 @@ cudaError_t fp64_prepare(int NP, int P1, int per_sm, int *up_blocks, int *shift_
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels, 128, sizeof(double2) * 5 * P1);
     if (e != cudaSuccess) return e;
     if (std::min(bu0, bu1) < 1 || bs < 1) return cudaErrorInvalidConfiguration;
-    *up_blocks = sms * std::min(per_sm, std::min(bu0, bu1));
-    *shift_blocks = sms * std::min(per_sm, bs);
+    *up_blocks = sms * std::min(up_per_sm, std::min(bu0, bu1));
+    *shift_blocks = sms * std::min(down_per_sm, bs);
     return cudaSuccess;
 }
 

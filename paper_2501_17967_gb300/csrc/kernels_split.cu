@@ -24,8 +24,9 @@
 //   B operand: the columns' digits, gathered into shared memory with 16-byte
 //              asynchronous copies (cp.async), resident for the whole tile;
 //   A operand: the operator's digits, 128 rows x KC columns per chunk, brought
-//              in by bulk asynchronous copies through three buffers so that the
-//              copy of chunk i+2 overlaps the MMAs of chunks i and i+1;
+//              in by bulk asynchronous copies through three buffers: the copy
+//              of chunk i+2 starts when the MMAs of chunk i-1 are done and
+//              overlaps those of chunks i and i+1;
 //   D:         5 levels x 2 row halves x 48 columns of FP32 in TMEM.
 // The gather of the next tile and its first operator chunks are issued before
 // the epilogue of the current tile, so they overlap it.  All waits are bounded:

@@ -420,3 +420,21 @@ def test_split_parts_each_within_tolerance(ctx16, adaptive):
             assert 0.0 < du < TOL and 0.0 < dh < TOL, (parts, du, dh)
     finally:
         ctx16.set_option("debug_split_parts", 31)
+
+
+def test_split_overlap_gives_identical_results(ctx16, adaptive):
+    """The near-field tensor launch on the internal stream (split_overlap = 1)
+    computes exactly what the in-line launch computes, in both directions."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    u0 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    h0 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
+    ctx16.set_option("split_overlap", 1)
+    try:
+        u1 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+        h1 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
+        bc._check(bc._load().bc_sync(ctx16.handle, None))
+    finally:
+        ctx16.set_option("split_overlap", 0)
+    assert torch.equal(u0, u1) and torch.equal(h0, h1)
