@@ -180,7 +180,25 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-STAGES = ("tensor_v", "clear", "upward", "downward", "tensor_e", "leaf_output", "tensor_near")
+STAGES = ("tensor_v", "clear", "upward", "m2l", "down_levels", "tensor_e", "leaf_output", "tensor_near")
+
+
+STAGE_KERNELS = {
+    "tensor_v": "k_split_vec + k_split_gemm<256> (leaf-to-expansion, X list)",
+    "clear": "memset",
+    "upward": "k_up_levels",
+    "m2l": "k_m2l_pairs (FP64 path: + k_x_entries)",
+    "down_levels": "k_down_levels",
+    "tensor_e": "k_split_exp + k_split_gemm<64>",
+    "leaf_output": "k_leaf_out",
+    "tensor_near": "k_split_gemm<256> (near field)",
+}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by
+# (workload, nterms, split); the adjoint apply of the bench configuration
+TRAFFIC = {
+    ("adaptive20", 24, True): {"tensor_v": 6.12e6, "upward": 0.57e6, "m2l": 1.50e6, "down_levels": 13.25e6,
+                               "tensor_e": 5.26e6, "tensor_near": 33.51e6},
+}
 
 
 def stage_work(st, nleaf, nleaf_far, P1, NP, split):
@@ -197,7 +215,8 @@ def stage_work(st, nleaf, nleaf_far, P1, NP, split):
             "tensor_near": (15 * 2.0 * NP * NP * st["n_near"], "tensor"),
             "clear": (0.0, "fp64"),
             "upward": (32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
-            "downward": (4.0 * P1 * P1 * st["n_v"] + 8.0 * P1 * P1 * n_shift, "fp64"),
+            "m2l": (4.0 * P1 * P1 * st["n_v"], "fp64"),
+            "down_levels": (8.0 * P1 * P1 * n_shift + 2.0 * P1 * (st["n_v"] + st["n_x"]), "fp64"),
             "tensor_e": (15 * 2.0 * R * NP * (nleaf_far + st["n_w"]), "tensor"),
             "leaf_output": (8.0 * NP * (st["n_near"] + st["n_w"] + nleaf_far + nleaf), "bytes"),
         }
@@ -206,7 +225,8 @@ def stage_work(st, nleaf, nleaf_far, P1, NP, split):
         "tensor_near": (0.0, "tensor"),
         "clear": (0.0, "fp64"),
         "upward": (4.0 * P1 * NP * nleaf + 32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
-        "downward": (4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"] + 8.0 * P1 * P1 * n_shift, "fp64"),
+        "m2l": (4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"], "fp64"),
+        "down_levels": (8.0 * P1 * P1 * n_shift + 2.0 * P1 * (st["n_v"] + st["n_x"]), "fp64"),
         "tensor_e": (0.0, "tensor"),
         "leaf_output": (2.0 * NP * NP * st["n_near"] + 4.0 * P1 * NP * (nleaf_far + st["n_w"]), "fp64"),
     }
@@ -392,6 +412,11 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     lv = tree.leaves()[0]
     wk = stage_work(st, tree.nleaf, int((lv >= 2).sum()), P1, 256, head == bc.SPLIT_BF16)
+    if not args.overlap:
+        stage_ms[:, 0] -= stage_ms[:, 7]   # the in-line near-field launch lies inside stage 0
+    # DRAM bytes per launch (read + write) from the ncu capture of this
+    # configuration (profiles/kernels_adaptive20_split.md); null elsewhere
+    traffic = TRAFFIC.get((args.workload, P1, head == bc.SPLIT_BF16), {})
     per_stage = {}
     for i, name in enumerate(STAGES):
         ms = float(stage_ms[:, i].mean())
@@ -403,23 +428,26 @@ def main():
         else:
             ach = amount / (ms * 1e-3) / 1e12
             pk, bound, unit = (bf16_peak, "tensor", "TFLOP/s") if kind == "tensor" else (fp64_peak, "alu", "TFLOP/s")
-        per_stage[name] = {"ms": round(ms, 4), "bound": bound, "achieved": round(ach, 4), "unit": unit,
-                           "peak": round(pk, 2), "frac": round(ach / pk, 4)}
+        per_stage[name] = {"ms": round(ms, 4), "kernel": STAGE_KERNELS[name], "bound": bound,
+                           "achieved": round(ach, 4), "unit": unit, "peak": round(pk, 2), "frac": round(ach / pk, 4),
+                           "traffic": traffic.get(name)}
     dom = max(per_stage, key=lambda k: per_stage[k]["ms"])
     d = per_stage[dom]
     src = {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
            "alu": "bc_debug_fp64_peak: measured FP64 FMA throughput, of measured",
            "hbm": "MEASURED_PEAKS.json hbm_gbs, of measured"}
     roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": None, "kernel": dom, "peak_source": src[d["bound"]],
+                "frac": d["frac"], "traffic": d["traffic"], "kernel": d["kernel"], "stage": dom,
+                "peak_source": src[d["bound"]],
                 "stages": per_stage}
 
     nl = st["nlevels"]
-    # upward pass, M2L + one shift per level >= 3, leaf output; split: + two
-    # digit kernels and two tensor-core launches
-    launches_per_apply = 1 + (1 + max(0, nl - 3) if nl > 2 else 0) + 1
-    if head == bc.SPLIT_BF16:
-        launches_per_apply += 4
+    # kernels per apply: upward pass, then (levels > 2) M2L pairs, the FP64
+    # X-list products (FP64 path with X entries) and the downward level pass,
+    # then the leaf output; split: + input digits, two group-V tensor launches,
+    # expansion digits, the group-E tensor launch
+    far_k = (2 + (1 if (head == bc.FP64 and st["n_x"] > 0) else 0)) if nl > 2 else 0
+    launches_per_apply = 1 + far_k + 1 + (5 if head == bc.SPLIT_BF16 else 0)
     pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

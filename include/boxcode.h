@@ -227,13 +227,15 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  * event at each stage boundary:
  *   0 tensor group V, far part (split precision: digits of the input,
  *     leaf-to-expansion, X list), 1 barrier reset, 2 upward pass (FP64: with
- *     the leaf-to-expansion step), 3 downward pass (M2L, shifts), 4 tensor
- *     group E (split precision: digits of the expansions, expansion-to-leaf
- *     and W list), 5 leaf output; 6 the near-field tensor launch, which runs
- *     on an internal stream beside stages 1-4;
+ *     the leaf-to-expansion step), 3 M2L per V pair (FP64 path: and the X-list
+ *     products), 4 downward level pass (sums, shifts), 5 tensor group E
+ *     (split precision: digits of the expansions, expansion-to-leaf and W
+ *     list), 6 leaf output; 7 the near-field tensor launch (in line: inside
+ *     stage 0, whose time includes it; with split_overlap: on an internal
+ *     stream beside stages 1-4);
  * bc_debug_stage_times then waits for the last events of the most recent
- * forward (adjoint = 0) or adjoint apply and writes the seven stage durations
- * in milliseconds to ms[7] (stages 0, 4 and 6 are empty for FP64 applies). */
+ * forward (adjoint = 0) or adjoint apply and writes the eight stage durations
+ * in milliseconds to ms[8] (stages 0, 5 and 7 are empty for FP64 applies). */
 bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
 /* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,

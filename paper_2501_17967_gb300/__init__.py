@@ -163,7 +163,7 @@ class Context:
         """Diagnostics: restrict applies to the near (1) / far (2) field; time stages."""
         _check(_load().bc_debug_set(self._h, pass_mask, int(timing)))
 
-    STAGES = ("tensor_v", "clear", "upward", "downward", "tensor_e", "leaf_output", "tensor_near")
+    STAGES = ("tensor_v", "clear", "upward", "m2l", "down_levels", "tensor_e", "leaf_output", "tensor_near")
 
     def stage_times(self, adjoint: bool = False):
         """Durations (ms) of the last forward/adjoint apply's stages (see STAGES)."""

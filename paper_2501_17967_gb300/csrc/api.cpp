@@ -1170,11 +1170,11 @@ bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms)
     if (!ctx || !ms) { set_error("bc_debug_stage_times: NULL argument"); return BC_ERR_ARG; }
     if (!ctx->timing) { set_error("bc_debug_stage_times: timing is off"); return BC_ERR_STATE; }
     cudaEvent_t *ev = ctx->ev[adjoint ? 1 : 0];
-    cudaError_t e = cudaEventSynchronize(ev[6]);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[8]);
+    cudaError_t e = cudaEventSynchronize(ev[7]);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[9]);
     for (int i = 0; e == cudaSuccess && i < kNumStages; i++) {
         float t = 0.0f;
-        e = i < 6 ? cudaEventElapsedTime(&t, ev[i], ev[i + 1]) : cudaEventElapsedTime(&t, ev[7], ev[8]);
+        e = i < 7 ? cudaEventElapsedTime(&t, ev[i], ev[i + 1]) : cudaEventElapsedTime(&t, ev[8], ev[9]);
         ms[i] = t;
     }
     return e == cudaSuccess ? BC_OK : cuda_fail(e, "bc_debug_stage_times");

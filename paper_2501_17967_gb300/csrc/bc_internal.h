@@ -251,13 +251,14 @@ bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree 
 
 // Forward (adj = false) or adjoint (adj = true) apply on `stream`.
 // vin: f (forward) or g (adjoint); vout: u or h.  Device pointers.
-// Stage boundaries recorded when timing is on (events 0..6 on the apply's
-// stream): tensor group V far part | clear | upward | downward | tensor group
-// E | leaf output; events 7, 8 bracket the near-field tensor launch on the side
-// stream (stage 6, overlapping stages 1-4).  The FP64 path leaves the tensor
+// Stage boundaries recorded when timing is on (events 0..7 on the apply's
+// stream): tensor group V | barrier reset | upward | M2L pairs (and the FP64
+// X-list products) | downward level pass | tensor group E | leaf output;
+// events 8, 9 bracket the near-field tensor launch (stage 7: in line it lies
+// inside stage 0, on the side stream it overlaps stages 1-4).  The FP64 path leaves the tensor
 // stages empty.
-constexpr int kNumStages = 7;
-constexpr int kNumEvents = 9;
+constexpr int kNumStages = 8;
+constexpr int kNumEvents = 10;
 // pass_mask bit 0: near field, bit 1: far field.  ev: kNumStages+1 events or null.
 // m2l_tri: triangular truncation of the M2L series (k + l <= P).
 cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,

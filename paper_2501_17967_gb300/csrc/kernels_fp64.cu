@@ -581,15 +581,15 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (sd && ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
                    (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess))
             return ce;
-        if (ev) cudaEventRecord(ev[7], ns);
+        if (ev) cudaEventRecord(ev[8], ns);
         g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
         ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, ns);
         if (ce != cudaSuccess) return ce;
-        if (ev) cudaEventRecord(ev[8], ns);
+        if (ev) cudaEventRecord(ev[9], ns);
         if (sd && (ce = cudaEventRecord(sd->join, sd->side)) != cudaSuccess) return ce;
     } else if (ev) {
-        cudaEventRecord(ev[7], st);
         cudaEventRecord(ev[8], st);
+        cudaEventRecord(ev[9], st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     // the grid barrier of the persistent passes starts from zero (a barrier
@@ -650,11 +650,14 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                                                                              d.lvtab);
             PX = d.PX;
         }
+        if (ev) cudaEventRecord(ev[4], st);
         k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * 5 * P1, st>>>(
             d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
             d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, d.gbar, glimit, a.err);
+    } else if (ev) {
+        cudaEventRecord(ev[4], st);
     }
-    if (ev) cudaEventRecord(ev[4], st);
+    if (ev) cudaEventRecord(ev[5], st);
     if (split && far) {
         // tensor group E: digits of both expansion arrays (times alpha0 in the
         // adjoint), then L2P (P2M^H) of `second` into PE and the W list of
@@ -669,7 +672,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
         if (ce != cudaSuccess) return ce;
     }
-    if (ev) cudaEventRecord(ev[5], st);
+    if (ev) cudaEventRecord(ev[6], st);
     if (split && split->side && (ce = cudaStreamWaitEvent(st, split->side->join, 0)) != cudaSuccess) return ce;
     // leafB: own expansion = second (local / adjoint multipole), W sources and
     // near log aux = first (multipole / adjoint local)
@@ -687,7 +690,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                                                       d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w,
                                                       op.t, tb.wvec, second, first, first, vin, vout, NP, P1,
                                                       d.lvtab, far, Pnear, PE, PW);
-    if (ev) cudaEventRecord(ev[6], st);
+    if (ev) cudaEventRecord(ev[7], st);
     return cudaGetLastError();
 }
 
