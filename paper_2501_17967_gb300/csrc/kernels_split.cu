@@ -82,25 +82,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
-// Bounded wait on an mbarrier phase by a whole warp; false when the limit ran
-// out.  The result is uniform over the warp.
-__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, long long limit)
-{
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < limit; it++) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (__any_sync(0xffffffffu, ok)) return true;
-    }
-    return false;
-}
-
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile(
@@ -117,17 +98,70 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// MMA and commit executed by a whole (converged) warp: one elected lane
-// issues them, so the operands stay warp-uniform.
-__device__ __forceinline__ void umma_bf16_warp(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                               uint32_t accumulate)
+// NK MMAs along K (16 columns each) issued from one elected lane of a
+// converged warp: the descriptors advance by 16 (256 bytes) per step; the
+// first MMA takes `first` as its accumulate flag, the others accumulate.
+template <int NK>
+__device__ __forceinline__ void umma_kchain_warp(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                 uint32_t first);
+template <>
+__device__ __forceinline__ void umma_kchain_warp<8>(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                    uint32_t first)
 {
     asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
+        "{\n\t.reg .pred p, q, e;\n\t.reg .b64 a, b;\n\t"
         "elect.sync _|e, 0xffffffff;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "setp.eq.u32 q, 0, 0;\n\t"
+        "mov.b64 a, %1;\n\t"
+        "mov.b64 b, %2;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(first)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void umma_kchain_warp<4>(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                                    uint32_t first)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, q, e;\n\t.reg .b64 a, b;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "setp.eq.u32 q, 0, 0;\n\t"
+        "mov.b64 a, %1;\n\t"
+        "mov.b64 b, %2;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, p;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;\n\t"
+        "add.s64 a, a, 16;\n\t"
+        "add.s64 b, b, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, q;}"
+        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(first)
         : "memory");
 }
 
@@ -141,13 +175,58 @@ __device__ __forceinline__ void umma_commit_warp(uint64_t *bar)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on an mbarrier phase by a whole warp that also gives up as soon
+// as another role of the CTA has failed (*fail != 0); on running out it sets
+// *fail.  The result is uniform over the warp.
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, long long limit, volatile int *fail)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < limit; it++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (__any_sync(0xffffffffu, ok)) return true;
+        if ((it & 31) == 31 && __any_sync(0xffffffffu, *fail != 0)) return false;
+    }
+    *fail = 1;
+    return false;
+}
+
+// Named barrier over the gather warps (id 1); the _or form returns whether any
+// of them passed a true predicate.
+__device__ __forceinline__ void gather_sync(int nthreads)
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool gather_sync_or(int nthreads, bool pred)
+{
+    uint32_t r;
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(uint32_t(pred)), "r"(nthreads)
+        : "memory");
+    return r != 0;
 }
 
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -261,15 +340,43 @@ template <int KD>
 struct GemmShape {
     static constexpr int KC = KD < 128 ? KD : 128;    // K columns per operator chunk
     static constexpr int NKC = KD / KC;
+    static constexpr int kChunksPerJob = kS * NKC;     // digit x K chunk
     static constexpr int kBSlice = kN * KD * 2;        // bytes of one B digit slice
     static constexpr int kChunk = 128 * KC * 2;        // bytes of one operator chunk
     static constexpr int kBSBO = (KD / 8) * 128;       // B: bytes between 8-row groups
     static constexpr int kASBO = (KC / 8) * 128;       // A: bytes between 8-row groups
     static constexpr size_t kSmem = size_t(kS) * kBSlice + size_t(kNBuf) * kChunk + 2 * kN * sizeof(ColMeta) +
-                                    2 * kNBuf * sizeof(uint64_t) + 16;
+                                    64 * sizeof(uint64_t);
 };
 
-constexpr int kGemmThreads = 256;   // 8 warps: warp 0 issues, all 8 run the epilogue
+// Roles (16 warps): warp 0 issues the MMAs; warp 1 copies the operator chunks;
+// warps 2-7 stage each tile's column metadata and gather its B digits, slice by
+// slice; warps 8-15 run the epilogues (two warps per TMEM lane quarter, 24
+// columns each).
+constexpr int kGemmThreads = 512;
+constexpr int kGatherWarp0 = 2;
+constexpr int kGatherThreads = 192;
+constexpr int kEpiWarp0 = 8;
+constexpr int kEpiWarps = 8;
+constexpr int kTmemBuf = 256;   // TMEM columns per job buffer (5 levels x 48 used)
+
+// Barriers (mbarriers in shared memory); counts in brackets:
+//   lbar[b] (1)        operator chunk in buffer b has landed (bulk-copy bytes)
+//   mbar[b] (1)        the MMAs reading buffer b have completed (commit)
+//   job_full[r] (1)    the MMAs of the job in TMEM buffer r have completed (commit)
+//   job_empty[r] (8)   the epilogue warps have read TMEM buffer r
+//   b_full[t][s] (1)   B digit slice s (and the metadata) of tile parity t is ready
+//   b_empty[s] (1)     no MMA of the previous tile reads B slice s any more (commit)
+//   meta_empty[t] (8)  the epilogue warps are done with metadata buffer t
+// Digit slice s (0-based) of B is read by the chunks of operator digit a <= 4 - s,
+// so in a tile's last job it is free after those chunks; the next tile's B is
+// gathered slice by slice from s = 4 down to 0 and its first chunk issues its
+// MMAs from slice 4 down, so only slice 0 is waited for at the tile change.
+struct GemmBars {
+    uint64_t lbar[kNBuf], mbar[kNBuf], job_full[2], job_empty[2], b_full[2][kS], b_empty[kS], meta_empty[2];
+    uint32_t tslot;
+    int fail;
+};
 
 template <int KD>
 __global__ void __launch_bounds__(kGemmThreads, 1)
@@ -280,195 +387,234 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
     uint8_t *Bs = smem;                                                      // kS x kBSlice
     uint8_t *As = smem + kS * Sh::kBSlice;                                   // kNBuf x kChunk
     ColMeta *meta = reinterpret_cast<ColMeta *>(As + kNBuf * Sh::kChunk);    // [2][kN]
-    uint64_t *lbar = reinterpret_cast<uint64_t *>(meta + 2 * kN);            // [kNBuf] chunk loaded
-    uint64_t *mbar = lbar + kNBuf;                                           // [kNBuf] MMAs on chunk done
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + kNBuf);
+    GemmBars *bars = reinterpret_cast<GemmBars *>(meta + 2 * kN);
+    volatile int *fail = &bars->fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tslot)),
                      "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
         for (int i = 0; i < kNBuf; i++) {
-            mbar_init(&lbar[i], 1);
-            mbar_init(&mbar[i], 1);
+            mbar_init(&bars->lbar[i], 1);
+            mbar_init(&bars->mbar[i], 1);
         }
+        for (int i = 0; i < 2; i++) {
+            mbar_init(&bars->job_full[i], 1);
+            mbar_init(&bars->job_empty[i], kEpiWarps);
+            mbar_init(&bars->meta_empty[i], kEpiWarps);
+            for (int sl = 0; sl < kS; sl++) mbar_init(&bars->b_full[i][sl], 1);
+        }
+        for (int sl = 0; sl < kS; sl++) mbar_init(&bars->b_empty[sl], 1);
+        bars->fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
-    const uint32_t idesc = umma_idesc(128, kN);
+    const uint32_t tmem = bars->tslot;
 
-    // Pipeline state, kept identically by every lane of warp 0 (lane 0 issues
-    // the copies, MMAs and commits): chunk loads issued (global chunk index),
-    // loads waited, and the last chunk whose MMAs were committed.
-    long long n_issued = 0, n_waited = 0, last_commit = -1;
-    const uint64_t adesc0 = umma_desc(smem_u32(As), 128, Sh::kASBO);
-    const uint64_t bdesc0 = umma_desc(smem_u32(Bs), 128, Sh::kBSBO);
-    bool failed = false;
-
-    // Stage the metadata of tile t into meta[mb] and gather its B digits.
-    auto stage = [&](int t, int mb) {
-        const SplitTile tl = gm.tiles[t];
-        ColMeta *M = meta + mb * kN;
-        if (tid < tl.cnt) {
-            const SplitCol c = gm.cols[tl.p0 + tid];
-            ColMeta m;
-            m.out = c.out;
-            m.exp = gm.dexp[c.vec] + (c.ctl >> 1) - 48;
-            m.flag = c.ctl & 1;
-            m.vec = c.vec;
-            m.pad = 0;
-            M[tid] = m;
-        }
-        __syncthreads();
-        constexpr int kItems = kS * (KD / 8);   // 16-byte pieces per column
-        for (int item = tid; item < tl.cnt * kItems; item += blockDim.x) {
-            const int c = item / kItems, r = item % kItems, b = r / (KD / 8), kg = r % (KD / 8);
-            const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + b) * KD + kg * 8;
-            cp_async16(Bs + b * Sh::kBSlice + ((c >> 3) * (KD / 8) + kg) * 128 + (c & 7) * 16, src);
-        }
-        cp_async_commit();
-    };
-    // Chunk g of tile tl: digit a, row half h, K chunk kc.
-    auto issue_load = [&](const SplitTile &tl, int g) {
-        const int mh = tl.rows > 128 ? 2 : 1;
-        const int a = g / (mh * Sh::NKC), h = (g / Sh::NKC) % mh, kc = g % Sh::NKC;
-        const int rows_h = min(128, tl.rows - 128 * h);
-        const uint32_t bytes = uint32_t((rows_h + 7) / 8) * 8 * Sh::KC * 2;
-        const uint8_t *src = gm.ops + tl.a_off + size_t((a * mh + h) * Sh::NKC + kc) * Sh::kChunk;
-        const int buf = int(n_issued % kNBuf);
-        if (!withhold) {
-            if (lane == 0) {
-                mbar_expect_tx(&lbar[buf], bytes);
-                uint8_t *dst = As + buf * Sh::kChunk;
-                for (uint32_t q = 0; q < bytes; q += 16384)
-                    bulk_g2s(dst + q, src + q, min(16384u, bytes - q), &lbar[buf]);
-            }
-            n_issued++;
-        }
-    };
-
-    int tile = blockIdx.x;
-    if (tile < gm.ntiles) {
-        stage(tile, 0);
-        if (warp == 0) {
+    if (warp == 0) {
+        // ---------------- MMAs ----------------
+        const uint32_t idesc = umma_idesc(128, kN);
+        const uint64_t adesc0 = umma_desc(smem_u32(As), 128, Sh::kASBO);
+        const uint64_t bdesc0 = umma_desc(smem_u32(Bs), 128, Sh::kBSBO);
+        long long G = 0, last_commit = -1;   // chunks consumed
+        int job = 0, k = 0;
+        bool failed = false;
+        for (int tile = blockIdx.x; tile < gm.ntiles && !failed; tile += gridDim.x, k++) {
             const SplitTile tl = gm.tiles[tile];
-            const int n = kS * (tl.rows > 128 ? 2 : 1) * Sh::NKC;
-            for (int g = 0; g < 2 && g < n; g++) issue_load(tl, g);
-        }
-    }
-    long long gbase = 0;   // global index of the current tile's first chunk
-    for (int it = 0; tile < gm.ntiles; it++) {
-        const SplitTile tl = gm.tiles[tile];
-        const int mh = tl.rows > 128 ? 2 : 1;
-        const int n = kS * mh * Sh::NKC;
-        cp_async_wait_all();
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (warp == 0) {
-            for (int g = 0; g < n; g++) {
-                const long long G = gbase + g;
-                const int buf = int(G % kNBuf);
-                if (G >= n_issued || !mbar_wait_warp(&lbar[buf], uint32_t((G / kNBuf) & 1), wait_limit)) {
+            const int mh = tl.rows > 128 ? 2 : 1;
+            uint32_t ready = 0;   // B slices of this tile known to be gathered
+            for (int h = 0; h < mh && !failed; h++, job++) {
+                const int r = job & 1;
+                const bool last_job = h == mh - 1;
+                if (job >= 2 && !wait_bar(&bars->job_empty[r], uint32_t(((job - 2) >> 1) & 1), wait_limit, fail)) {
                     failed = true;
                     break;
                 }
-                n_waited = G + 1;
                 tc_fence_after();
-                const int a = g / (mh * Sh::NKC) + 1, h = (g / Sh::NKC) % mh, kc = g % Sh::NKC;
-                // descriptors advance by 16 (= 256 bytes >> 4) per K step of 16
-                const uint64_t ad = adesc0 + uint64_t(buf) * (Sh::kChunk >> 4);
-                const uint32_t first = (a == 1 && kc == 0) ? 0u : 1u;
-                for (int b = 1; b + a <= kS + 1; b++) {
-                    const uint32_t dcol = tmem + uint32_t(((a + b - 2) * 2 + h) * kN);
-                    const uint64_t bd =
-                        bdesc0 + uint64_t(b - 1) * (Sh::kBSlice >> 4) + uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
-#pragma unroll
-                    for (int j = 0; j < Sh::KC / 16; j++)
-                        umma_bf16_warp(dcol, ad + 16 * j, bd + 16 * j, idesc, j == 0 ? first : 1u);
-                }
-                umma_commit_warp(&mbar[buf]);
-                last_commit = G;
-                if (g + 2 < n) {
-                    // the buffer of chunk G + 2 was last read by the MMAs of chunk G + 2 - kNBuf
-                    const long long P = G + 2 - kNBuf;
-                    if (P >= 0 && !mbar_wait_warp(&mbar[int(P % kNBuf)], uint32_t((P / kNBuf) & 1), wait_limit)) {
+                for (int g = 0; g < Sh::kChunksPerJob; g++, G++) {
+                    const int buf = int(G % kNBuf);
+                    if (!wait_bar(&bars->lbar[buf], uint32_t((G / kNBuf) & 1), wait_limit, fail)) {
                         failed = true;
                         break;
                     }
-                    issue_load(tl, g + 2);
+                    tc_fence_after();
+                    const int a = g / Sh::NKC, kc = g % Sh::NKC;   // 0-based digit of A
+                    const uint64_t ad = adesc0 + uint64_t(buf) * (Sh::kChunk >> 4);
+                    const uint32_t first = (a == 0 && kc == 0) ? 0u : 1u;
+                    for (int b = kS - 1 - a; b >= 0; b--) {   // B digit slices, last-gathered slice last
+                        if (!(ready >> b & 1u)) {
+                            if (!wait_bar(&bars->b_full[k & 1][b], uint32_t((k >> 1) & 1), wait_limit, fail)) {
+                                failed = true;
+                                break;
+                            }
+                            tc_fence_after();
+                            ready |= 1u << b;
+                        }
+                        const uint32_t dcol = tmem + uint32_t(r * kTmemBuf + (a + b) * kN);
+                        const uint64_t bd =
+                            bdesc0 + uint64_t(b) * (Sh::kBSlice >> 4) + uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
+                        umma_kchain_warp<Sh::KC / 16>(dcol, ad, bd, idesc, first);
+                    }
+                    if (failed) break;
+                    umma_commit_warp(&bars->mbar[buf]);
+                    last_commit = G;
+                    // in the tile's last job, slice kS-1-a is read by no later chunk
+                    if (last_job && kc == Sh::NKC - 1) umma_commit_warp(&bars->b_empty[kS - 1 - a]);
                 }
-            }
-            if (!failed &&
-                !mbar_wait_warp(&mbar[int(last_commit % kNBuf)], uint32_t((last_commit / kNBuf) & 1), wait_limit))
-                failed = true;
-            if (!failed) last_commit = -1;   // every committed MMA has completed
-        }
-        gbase += n;
-        failed = __syncthreads_or(failed);
-        if (failed) break;
-        tc_fence_after();
-        // next tile: metadata, B gather and first operator chunks, overlapping this epilogue
-        const int next = tile + gridDim.x;
-        if (next < gm.ntiles) {
-            stage(next, (it + 1) & 1);
-            if (warp == 0) {
-                const SplitTile tn = gm.tiles[next];
-                const int nn = kS * (tn.rows > 128 ? 2 : 1) * Sh::NKC;
-                for (int g = 0; g < 2 && g < nn; g++) issue_load(tn, g);
+                if (failed) break;
+                umma_commit_warp(&bars->job_full[r]);
             }
         }
-        // epilogue: warp w owns TMEM lanes 32(w%4)..32(w%4)+31 (rows 32(w%4)+lane
-        // of each half); the two warp groups take alternate (half, 16-column)
-        // items
-        const ColMeta *M = meta + (it & 1) * kN;
-        const int wq = warp & 3, wg = warp >> 2;
-        const int ncc = (tl.cnt + 15) / 16;
-        for (int item = wg; item < mh * ncc; item += 2) {   // uniform over the warp
-            const int h = item / ncc, cc = item % ncc;
-            const int row = h * 128 + wq * 32 + lane;
-            const bool live = row < tl.rows;
-            const int ea = live ? gm.op_exp[tl.exp_off + row] : 0;
-            {
-                uint32_t d[kS][16];
-#pragma unroll
-                for (int g = 0; g < kS; g++)
-                    tmem_ld16(tmem + (uint32_t(wq * 32) << 16) + uint32_t((g * 2 + h) * kN + cc * 16), d[g]);
-                tmem_ld_wait();
-                if (!live) continue;
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const int c = cc * 16 + q;
-                    if (c >= tl.cnt) continue;
-                    long long S = 0;
+        if (failed) {
+            *fail = 1;
+            int dummy = 0;   // bounded wait, without the failure shortcut
+            if (last_commit >= 0)
+                wait_bar(&bars->mbar[int(last_commit % kNBuf)], uint32_t((last_commit / kNBuf) & 1), wait_limit,
+                         &dummy);
+        }
+    } else if (warp == 1) {
+        // ---------------- operator chunk copies ----------------
+        long long n = 0;   // chunks issued
+        bool failed = false;
+        for (int tile = blockIdx.x; tile < gm.ntiles && !failed; tile += gridDim.x) {
+            const SplitTile tl = gm.tiles[tile];
+            const int mh = tl.rows > 128 ? 2 : 1;
+            for (int h = 0; h < mh && !failed; h++)
+                for (int g = 0; g < Sh::kChunksPerJob; g++, n++) {
+                    const int buf = int(n % kNBuf);
+                    // buffer free once the MMAs of chunk n - kNBuf have completed
+                    if (n >= kNBuf &&
+                        !wait_bar(&bars->mbar[buf], uint32_t(((n - kNBuf) / kNBuf) & 1), wait_limit, fail)) {
+                        failed = true;
+                        break;
+                    }
+                    if (withhold) continue;   // diagnostics: the MMA warp's first wait runs out
+                    const int a = g / Sh::NKC, kc = g % Sh::NKC;
+                    const int rows_h = min(128, tl.rows - 128 * h);
+                    const uint32_t bytes = uint32_t((rows_h + 7) / 8) * 8 * Sh::KC * 2;
+                    const uint8_t *src = gm.ops + tl.a_off + size_t((a * mh + h) * Sh::NKC + kc) * Sh::kChunk;
+                    if (lane == 0) {
+                        mbar_expect_tx(&bars->lbar[buf], bytes);
+                        uint8_t *dst = As + buf * Sh::kChunk;
+                        for (uint32_t q = 0; q < bytes; q += 16384)
+                            bulk_g2s(dst + q, src + q, min(16384u, bytes - q), &bars->lbar[buf]);
+                    }
+                    __syncwarp();
+                }
+        }
+        if (failed && !withhold) {
+            // copies still in flight: at most the last kNBuf issued
+            int dummy = 0;
+            for (long long q = n > kNBuf ? n - kNBuf : 0; q < n; q++)
+                wait_bar(&bars->lbar[int(q % kNBuf)], uint32_t((q / kNBuf) & 1), wait_limit, &dummy);
+        }
+    } else if (warp < kEpiWarp0) {
+        // ---------------- column metadata and B gather, slice by slice ----------------
+        const int gt = tid - 32 * kGatherWarp0;
+        constexpr int kPieces = KD / 8;   // 16-byte pieces per column and slice
+        int k = 0;
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < gm.ntiles && !stop; tile += gridDim.x, k++) {
+            bool ok = true;
+            // the epilogues of tile k - 2 no longer read this metadata buffer
+            if (k >= 2) ok = wait_bar(&bars->meta_empty[k & 1], uint32_t(((k - 2) >> 1) & 1), wait_limit, fail);
+            if (gather_sync_or(kGatherThreads, !ok)) break;   // uniform over the gather warps
+            const SplitTile tl = gm.tiles[tile];
+            ColMeta *M = meta + (k & 1) * kN;
+            if (gt < tl.cnt) {
+                const SplitCol c = gm.cols[tl.p0 + gt];
+                ColMeta m;
+                m.out = c.out;
+                m.exp = gm.dexp[c.vec] + (c.ctl >> 1) - 48;
+                m.flag = c.ctl & 1;
+                m.vec = c.vec;
+                m.pad = 0;
+                M[gt] = m;
+            }
+            gather_sync(kGatherThreads);
+            for (int sl = kS - 1; sl >= 0; sl--) {
+                bool ok2 = true;
+                // no MMA of the previous tile reads slice sl any more
+                if (k >= 1) ok2 = wait_bar(&bars->b_empty[sl], uint32_t((k - 1) & 1), wait_limit, fail);
+                if (gather_sync_or(kGatherThreads, !ok2)) {
+                    stop = true;
+                    break;
+                }
+                uint8_t *dst = Bs + sl * Sh::kBSlice;
+                for (int item = gt; item < tl.cnt * kPieces; item += kGatherThreads) {
+                    const int c = item / kPieces, kg = item % kPieces;
+                    const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + sl) * KD + kg * 8;
+                    cp_async16(dst + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
+                }
+                cp_async_commit();
+                cp_async_wait_all();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                gather_sync(kGatherThreads);
+                if (gt == 0) mbar_arrive(&bars->b_full[k & 1][sl]);
+            }
+        }
+        cp_async_wait_all();
+    } else {
+        // ---------------- epilogues ----------------
+        // warp w reads TMEM lanes 32(w%4)..32(w%4)+31 (rows 32(w%4)+lane of
+        // the job's row half); warps 8-11 take columns 0-23, warps 12-15 24-47
+        const int wq = warp & 3, half = (warp - kEpiWarp0) >> 2;
+        int job = 0, k = 0;
+        bool failed = false;
+        for (int tile = blockIdx.x; tile < gm.ntiles && !failed; tile += gridDim.x, k++) {
+            // the metadata is staged before the first slice (kS - 1) is gathered
+            if (!wait_bar(&bars->b_full[k & 1][kS - 1], uint32_t((k >> 1) & 1), wait_limit, fail)) break;
+            const SplitTile tl = gm.tiles[tile];
+            const int mh = tl.rows > 128 ? 2 : 1;
+            const ColMeta *M = meta + (k & 1) * kN;
+            for (int h = 0; h < mh; h++, job++) {
+                const int r = job & 1;
+                if (!wait_bar(&bars->job_full[r], uint32_t((job >> 1) & 1), wait_limit, fail)) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const int row = h * 128 + wq * 32 + lane;
+                const bool live = row < tl.rows;
+                const int ea = live ? gm.op_exp[tl.exp_off + row] : 0;
+                for (int gi = 0; gi < 3; gi++) {
+                    const int c0 = half * 24 + gi * 8;
+                    if (c0 >= tl.cnt) break;   // uniform over the warp
+                    uint32_t d[kS][8];
 #pragma unroll
                     for (int g = 0; g < kS; g++)
-                        S += (long long)__float2int_rn(__uint_as_float(d[g][q])) << (8 * (kS - 1 - g));
-                    double val = i64_scaled(S, ea + M[c].exp);
-                    if (M[c].flag) val *= inv_alpha0;
-                    M[c].out[row] = val;
+                        tmem_ld8(tmem + (uint32_t(wq * 32) << 16) + uint32_t(r * kTmemBuf + g * kN + c0), d[g]);
+                    tmem_ld_wait();
+                    if (!live) continue;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int c = c0 + q;
+                        if (c >= tl.cnt) continue;
+                        long long S = 0;
+#pragma unroll
+                        for (int g = 0; g < kS; g++)
+                            S += (long long)__float2int_rn(__uint_as_float(d[g][q])) << (8 * (kS - 1 - g));
+                        double val = i64_scaled(S, ea + M[c].exp);
+                        if (M[c].flag) val *= inv_alpha0;
+                        M[c].out[row] = val;
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars->job_empty[r]);
             }
+            if (failed) break;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->meta_empty[k & 1]);
         }
-        tc_fence_before();
-        tile = next;
     }
-    if (failed && warp == 0) {
-        if (lane == 0) atomicExch(err, 1);
-        // wait (bounded) for the copies and MMAs still in flight before the
-        // shared memory and TMEM are released
-        for (long long G = n_waited; G < n_issued; G++)
-            mbar_wait_warp(&lbar[int(G % kNBuf)], uint32_t((G / kNBuf) & 1), wait_limit);
-        if (last_commit >= 0)
-            mbar_wait_warp(&mbar[int(last_commit % kNBuf)], uint32_t((last_commit / kNBuf) & 1), wait_limit);
-    }
-    cp_async_wait_all();
+    if (*fail && tid == 0) atomicExch(err, 1);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
