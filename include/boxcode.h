@@ -230,9 +230,9 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  *     the leaf-to-expansion step), 3 M2L per V pair (FP64 path: and the X-list
  *     products), 4 downward level pass (sums, shifts), 5 tensor group E
  *     (split precision: digits of the expansions, expansion-to-leaf and W
- *     list), 6 leaf output; 7 the near-field tensor launch (in line: inside
- *     stage 0, whose time includes it; with split_overlap: on an internal
- *     stream beside stages 1-4);
+ *     list), 6 leaf output; 7 the near-field tensor launch when it runs
+ *     apart, on an internal stream beside stages 1-4 (split_overlap; in line
+ *     the near field is part of stage 0's tensor launch and stage 7 is empty);
  * bc_debug_stage_times then waits for the last events of the most recent
  * forward (adjoint = 0) or adjoint apply and writes the eight stage durations
  * in milliseconds to ms[8] (stages 0, 5 and 7 are empty for FP64 applies). */

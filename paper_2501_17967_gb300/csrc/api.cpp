@@ -271,7 +271,7 @@ uint16_t bf16_of_int(int d)
 SplitOp add_split_op(std::vector<uint16_t> &dig, std::vector<int32_t> &ex, const std::vector<double> &m, int rows,
                      int K)
 {
-    const int KC = std::min(K, 128), nkc = K / KC, mh = rows > 128 ? 2 : 1;
+    const int KC = std::min(K, kSplitKC), nkc = K / KC, mh = rows > 128 ? 2 : 1;
     const size_t chunk = size_t(128) * KC;   // elements per chunk
     SplitOp op;
     op.a_off = int64_t(dig.size()) * int64_t(sizeof(uint16_t));
@@ -526,6 +526,16 @@ bc_status build_split_tree(bc_tree *t)
         }
         for (int c = 0; c < kNumWX; c++)
             if (!by_code[c].empty()) E.add(T.w_op[dir][c], by_code[c]);
+        TileBuilder VN = NV;   // near tiles first (longest), then the far ones
+        for (SplitTile tl : V.tiles) {
+            tl.p0 += int32_t(NV.cols.size());
+            VN.tiles.push_back(tl);
+        }
+        VN.cols.insert(VN.cols.end(), V.cols.begin(), V.cols.end());
+        if ((e = dev_upload(al, &s.tVN[dir], VN.tiles.data(), VN.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cVN[dir], VN.cols.data(), VN.cols.size())) != cudaSuccess)
+            return cuda_fail(e, "split tree upload");
+        s.ntVN[dir] = int(VN.tiles.size());
         if ((e = dev_upload(al, &s.tV[dir], V.tiles.data(), V.tiles.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.cV[dir], V.cols.data(), V.cols.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.tN[dir], NV.tiles.data(), NV.tiles.size())) != cudaSuccess ||

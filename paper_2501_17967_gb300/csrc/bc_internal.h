@@ -146,10 +146,11 @@ struct DevTree {
 //            (adjoint P2M^H), W list (adjoint P2L^H)
 // An operator is a real matrix of `rows` <= 256 rows; its BF16 digits are
 // stored as chunks [digit a][row half h][K chunk kc] of 128 rows x KC
-// columns (KC = min(K, 128)) in the canonical K-major core-matrix layout.
+// columns (KC = min(K, kSplitKC)) in the canonical K-major core-matrix layout.
 constexpr int kSplitSlices = 5;
 constexpr int kSplitTileN = 48;
 constexpr int kSplitKE = 64;                 // K of group E (expansion reals, padded)
+constexpr int kSplitKC = 128;                // K columns per operator chunk (one bulk copy)
 struct SplitOp {
     int64_t a_off = 0;     // byte offset of the operator's first chunk
     int32_t rows = 0;      // valid rows
@@ -191,11 +192,13 @@ struct SplitGemm {
     const int32_t *dexp = nullptr;     // [nvec]
 };
 struct SplitTree {
-    // [forward, adjoint]; group V in two launches: far (leafA, X list: needed
-    // by the upward and downward passes) and near (needed at the leaf output)
-    SplitTile *tV[2] = {}, *tN[2] = {}, *tE[2] = {};
-    SplitCol *cV[2] = {}, *cN[2] = {}, *cE[2] = {};
-    int ntV[2] = {}, ntN[2] = {}, ntE[2] = {};
+    // [forward, adjoint]; group V as far part (leafA, X list: needed by the
+    // upward and downward passes) and near part (needed at the leaf output),
+    // launched apart when the near part runs on the side stream, and as one
+    // list (near tiles first: two jobs each) otherwise
+    SplitTile *tV[2] = {}, *tN[2] = {}, *tVN[2] = {}, *tE[2] = {};
+    SplitCol *cV[2] = {}, *cN[2] = {}, *cVN[2] = {}, *cE[2] = {};
+    int ntV[2] = {}, ntN[2] = {}, ntVN[2] = {}, ntE[2] = {};
     double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
     double *PX = nullptr;         // [n_x][64] X-list result per entry
     double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf
@@ -254,9 +257,9 @@ bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree 
 // Stage boundaries recorded when timing is on (events 0..7 on the apply's
 // stream): tensor group V | barrier reset | upward | M2L pairs (and the FP64
 // X-list products) | downward level pass | tensor group E | leaf output;
-// events 8, 9 bracket the near-field tensor launch (stage 7: in line it lies
-// inside stage 0, on the side stream it overlaps stages 1-4).  The FP64 path leaves the tensor
-// stages empty.
+// events 8, 9 bracket the near-field tensor launch on the side stream (stage
+// 7, overlapping stages 1-4; empty when the near field is part of the single
+// group-V launch of stage 0).  The FP64 path leaves the tensor stages empty.
 constexpr int kNumStages = 8;
 constexpr int kNumEvents = 10;
 // pass_mask bit 0: near field, bit 1: far field.  ev: kNumStages+1 events or null.

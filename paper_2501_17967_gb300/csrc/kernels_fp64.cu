@@ -565,28 +565,40 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     cudaError_t ce;
     if (ev) cudaEventRecord(ev[0], st);
     if (split) {
-        // tensor group V: digits of alpha0 * vin; leafA (P2M / L2P^H) into
-        // `first` and the X list into PX on this stream, then the near field
-        // into Pnear on the side stream (joined before the leaf output)
+        // tensor group V: digits of alpha0 * vin; the near field into Pnear,
+        // leafA (P2M / L2P^H) into `first` and the X list into PX, in one
+        // launch, or (split_overlap) the near field on the side stream,
+        // joined before the leaf output
         ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
         if (ce != cudaSuccess) return ce;
         SplitGemm g;
-        g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir];
         g.ops = sT->ops[0][dir]; g.op_exp = sT->op_exp[0][dir];
         g.dig = sp->vdig; g.dexp = sp->vexp;
-        ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
-        if (ce != cudaSuccess) return ce;
         const SideStream *sd = split->side;
-        cudaStream_t ns = sd ? sd->side : st;
-        if (sd && ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
-                   (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess))
-            return ce;
-        if (ev) cudaEventRecord(ev[8], ns);
-        g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
-        ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, ns);
-        if (ce != cudaSuccess) return ce;
-        if (ev) cudaEventRecord(ev[9], ns);
-        if (sd && (ce = cudaEventRecord(sd->join, sd->side)) != cudaSuccess) return ce;
+        if (!sd) {
+            // one launch: the near-field tiles (two jobs each) first, then the
+            // leaf-to-expansion and X-list tiles
+            g.tiles = sp->tVN[dir]; g.cols = sp->cVN[dir]; g.ntiles = sp->ntVN[dir];
+            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            if (ce != cudaSuccess) return ce;
+            if (ev) {
+                cudaEventRecord(ev[8], st);
+                cudaEventRecord(ev[9], st);
+            }
+        } else {
+            g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir];
+            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            if (ce != cudaSuccess) return ce;
+            if ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
+                (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess)
+                return ce;
+            if (ev) cudaEventRecord(ev[8], sd->side);
+            g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
+            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+            if (ce != cudaSuccess) return ce;
+            if (ev) cudaEventRecord(ev[9], sd->side);
+            if ((ce = cudaEventRecord(sd->join, sd->side)) != cudaSuccess) return ce;
+        }
     } else if (ev) {
         cudaEventRecord(ev[8], st);
         cudaEventRecord(ev[9], st);

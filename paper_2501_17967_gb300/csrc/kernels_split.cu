@@ -20,18 +20,25 @@
 //   * the five levels are combined in int64 and converted to FP64 once, by
 //     integer operations on the bit pattern (the FP64 pipe stays free).
 //
-// Work decomposition: a tile is one operator times up to 48 columns.
-//   B operand: the columns' digits, gathered into shared memory with 16-byte
-//              asynchronous copies (cp.async), resident for the whole tile;
-//   A operand: the operator's digits, 128 rows x KC columns per chunk, brought
-//              in by bulk asynchronous copies through three buffers: the copy
-//              of chunk i+2 starts when the MMAs of chunk i-1 are done and
-//              overlaps those of chunks i and i+1;
-//   D:         5 levels x 2 row halves x 48 columns of FP32 in TMEM.
-// The gather of the next tile and its first operator chunks are issued before
-// the epilogue of the current tile, so they overlap it.  All waits are bounded:
-// a wait that runs out sets the error flag, waits (bounded) for the copies and
-// MMAs in flight, frees TMEM and returns.
+// Work decomposition: a tile is one operator times up to 48 columns, done as
+// one job per 128-row half of the operator.
+//   B operand: the columns' digits, gathered into shared memory slice by slice
+//              with 16-byte asynchronous copies (cp.async), resident for the
+//              tile; the next tile's slices are gathered as the current tile's
+//              last job stops reading them;
+//   A operand: the operator's digits, 128 rows x 128 columns per chunk (32 KB),
+//              brought in by bulk asynchronous copies through three buffers;
+//              a tile's first row-half job takes the operator digits in the
+//              order 0, 4, 1, 3, 2 (long and short chunks alternate, so copies
+//              keep up), its last job in the order 0..4 (B slices are freed
+//              earliest);
+//   D:         5 levels x 48 columns of FP32 per job, two TMEM buffers, so one
+//              job's epilogue overlaps the next job's MMAs.
+// One tcgen05.mma of 128 x 48 x 16 takes about as long as one of 128 x 16 x 16
+// (a fixed cost per instruction), which the MMA warp now reaches.  All waits
+// are bounded: a wait that runs out sets the error flag, every role stops at
+// its next wait, copies and MMAs in flight are waited for (bounded), TMEM is
+// freed and the kernel returns.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -45,7 +52,7 @@ namespace {
 
 constexpr int kS = kSplitSlices;   // 5 digits
 constexpr int kN = kSplitTileN;    // 48 columns per tile
-constexpr int kNBuf = 3;           // operator chunk buffers
+constexpr int kNBuf = 3;           // operator chunk buffers (32 KB each)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -336,9 +343,17 @@ struct ColMeta {
     int32_t pad;
 };
 
+// Operator digit of the p-th chunk group of a job: the order 0, 4, 1, 3, 2
+// alternates long and short MMA runs (a tile's first row-half job); 0..4 frees
+// the B slices earliest (a tile's last job).
+__device__ __forceinline__ int chunk_digit(int p, bool interleave)
+{
+    return interleave ? ((0x23140 >> (4 * p)) & 0xF) : p;
+}
+
 template <int KD>
 struct GemmShape {
-    static constexpr int KC = KD < 128 ? KD : 128;    // K columns per operator chunk
+    static constexpr int KC = KD < kSplitKC ? KD : kSplitKC;   // K columns per operator chunk
     static constexpr int NKC = KD / KC;
     static constexpr int kChunksPerJob = kS * NKC;     // digit x K chunk
     static constexpr int kBSlice = kN * KD * 2;        // bytes of one B digit slice
@@ -444,7 +459,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                         break;
                     }
                     tc_fence_after();
-                    const int a = g / Sh::NKC, kc = g % Sh::NKC;   // 0-based digit of A
+                    const int a = chunk_digit(g / Sh::NKC, !last_job), kc = g % Sh::NKC;   // 0-based digit of A
                     const uint64_t ad = adesc0 + uint64_t(buf) * (Sh::kChunk >> 4);
                     const uint32_t first = (a == 0 && kc == 0) ? 0u : 1u;
                     for (int b = kS - 1 - a; b >= 0; b--) {   // B digit slices, last-gathered slice last
@@ -495,7 +510,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                         break;
                     }
                     if (withhold) continue;   // diagnostics: the MMA warp's first wait runs out
-                    const int a = g / Sh::NKC, kc = g % Sh::NKC;
+                    const int a = chunk_digit(g / Sh::NKC, h < mh - 1), kc = g % Sh::NKC;
                     const int rows_h = min(128, tl.rows - 128 * h);
                     const uint32_t bytes = uint32_t((rows_h + 7) / 8) * 8 * Sh::KC * 2;
                     const uint8_t *src = gm.ops + tl.a_off + size_t((a * mh + h) * Sh::NKC + kc) * Sh::kChunk;
@@ -538,25 +553,33 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                 M[gt] = m;
             }
             gather_sync(kGatherThreads);
-            for (int sl = kS - 1; sl >= 0; sl--) {
-                bool ok2 = true;
-                // no MMA of the previous tile reads slice sl any more
-                if (k >= 1) ok2 = wait_bar(&bars->b_empty[sl], uint32_t((k - 1) & 1), wait_limit, fail);
-                if (gather_sync_or(kGatherThreads, !ok2)) {
-                    stop = true;
-                    break;
+            // two slices in flight: issue slice sl, then complete slice sl + 1
+            for (int sl = kS - 1; sl >= -1; sl--) {
+                if (sl >= 0) {
+                    bool ok2 = true;
+                    // no MMA of the previous tile reads slice sl any more
+                    if (k >= 1) ok2 = wait_bar(&bars->b_empty[sl], uint32_t((k - 1) & 1), wait_limit, fail);
+                    if (gather_sync_or(kGatherThreads, !ok2)) {
+                        stop = true;
+                        break;
+                    }
+                    uint8_t *dst = Bs + sl * Sh::kBSlice;
+                    for (int item = gt; item < tl.cnt * kPieces; item += kGatherThreads) {
+                        const int c = item / kPieces, kg = item % kPieces;
+                        const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + sl) * KD + kg * 8;
+                        cp_async16(dst + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
+                    }
+                    cp_async_commit();
                 }
-                uint8_t *dst = Bs + sl * Sh::kBSlice;
-                for (int item = gt; item < tl.cnt * kPieces; item += kGatherThreads) {
-                    const int c = item / kPieces, kg = item % kPieces;
-                    const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + sl) * KD + kg * 8;
-                    cp_async16(dst + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
+                if (sl + 1 <= kS - 1) {
+                    if (sl >= 0)
+                        asm volatile("cp.async.wait_group 1;" ::: "memory");
+                    else
+                        asm volatile("cp.async.wait_group 0;" ::: "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    gather_sync(kGatherThreads);
+                    if (gt == 0) mbar_arrive(&bars->b_full[k & 1][sl + 1]);
                 }
-                cp_async_commit();
-                cp_async_wait_all();
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                gather_sync(kGatherThreads);
-                if (gt == 0) mbar_arrive(&bars->b_full[k & 1][sl]);
             }
         }
         cp_async_wait_all();
@@ -622,6 +645,11 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
 }
 
 int g_sms = 0;
+// The K = 64 kernel asks for more shared memory than it uses so that no two
+// CTAs of the tensor-core kernels share an SM (each holds all 512 TMEM columns
+// while it runs): 2 x 130 KB and 130 KB + the K = 256 kernel's both exceed an SM.
+constexpr int kSmem64 = 130 * 1024;
+static_assert(GemmShape<64>::kSmem <= size_t(kSmem64), "K = 64 shared memory");
 
 }  // namespace
 
@@ -631,11 +659,8 @@ cudaError_t split_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(k_split_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          int(GemmShape<256>::kSmem));
-    // The K = 64 kernel asks for more shared memory than it uses so that no
-    // two CTAs of the tensor-core kernels share an SM (each holds all 512 TMEM
-    // columns while it runs).
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+        e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -668,7 +693,7 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
     if (kd == 256)
         k_split_gemm<256><<<grid, kGemmThreads, GemmShape<256>::kSmem, st>>>(g, inv_alpha0, err, wait_limit, withhold);
     else
-        k_split_gemm<64><<<grid, kGemmThreads, 120 * 1024, st>>>(g, inv_alpha0, err, wait_limit, withhold);
+        k_split_gemm<64><<<grid, kGemmThreads, kSmem64, st>>>(g, inv_alpha0, err, wait_limit, withhold);
     return cudaGetLastError();
 }
 
