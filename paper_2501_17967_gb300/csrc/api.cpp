@@ -192,7 +192,7 @@ bc_status upload_tree(bc_tree *t)
     }
     e = dev_upload(d.allocs, &d.level_start, h.level_start.data(), h.level_start.size());
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
-    e = dev_upload<uint32_t>(d.allocs, &d.gbar, nullptr, 2);
+    e = dev_upload<int32_t>(d.allocs, &d.flag, nullptr, h.box_level.size());
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     size_t nexp = size_t(h.box_level.size()) * P1;
     e = dev_upload<double2>(d.allocs, &d.expA, nullptr, nexp);

@@ -132,7 +132,7 @@ struct DevTree {
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
     double *lvtab = nullptr;                   // [2][kLvTab]: r^2 and log r per level
     int64_t *level_start = nullptr;            // [nlevels + 1] first box of each level
-    uint32_t *gbar = nullptr;                  // [2] grid barrier of the persistent passes (count, generation)
+    int32_t *flag = nullptr;                   // [nbox] completion flags of the persistent level passes
     double *stage_in = nullptr, *stage_out = nullptr; // host-pointer staging [nleaf*NP]
     std::vector<void *> allocs;
 };

@@ -28,35 +28,42 @@ constexpr double kInvTwoPi = 0.15915494309189533576888376337251;   // 1 / (2 pi)
 // lvtab[lv] = r_lv^2, lvtab[kLvTab + lv] = log r_lv, r_lv = (L/2) 2^-lv.
 
 // -------------------------------------------------------------------------
-// Grid-wide barrier of the persistent level-synchronous passes.  Their grids
-// are sized so that every block is resident (occupancy calculator), so the
-// wait ends once all blocks arrive; it is bounded all the same: a block whose
-// wait runs out records the failure in *err (reported by bc_sync) and goes on.
-// bar[0] counts arrivals, bar[1] is the generation.  Data written before the
-// barrier is read after it with L2 loads (__ldcg).
+// Per-box completion flags of the persistent level passes.  A box's expansion
+// is published by flag[box] (1: upward result, 2: downward result) once every
+// thread of the producing block has written it; a consumer waits for the
+// flags of exactly the boxes it reads (a parent for its children, a box for
+// its parent) instead of for a whole level.  Each block takes its boxes in
+// dependency order and every block is resident (the grids come from the
+// occupancy calculator), so every wait ends; it is bounded all the same: a
+// wait that runs out records the failure in *err (reported by bc_sync) and
+// goes on.  Data published this way is read with L2 loads (__ldcg).
 // -------------------------------------------------------------------------
-__device__ void grid_sync(uint32_t *bar, long long limit, int32_t *err)
+__device__ __forceinline__ int flag_load(const int32_t *f)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    return v;
+}
+
+// called by every thread of the block after the box's expansion is written
+__device__ __forceinline__ void flag_publish(int32_t *f, int v)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile uint32_t *vb = bar;
-        const uint32_t gen = vb[1];
         __threadfence();
-        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
-            atomicExch(&bar[0], 0u);
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            for (long long it = 0; vb[1] == gen; it++) {
-                if (it >= limit) {
-                    atomicExch(err, 2);
-                    break;
-                }
-            }
-        }
-        __threadfence();
+        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
     }
-    __syncthreads();
+}
+
+// the calling thread waits until *f >= want
+__device__ __forceinline__ void flag_wait(const int32_t *f, int want, long long limit, int32_t *err)
+{
+    for (long long it = 0; flag_load(f) < want; it++) {
+        if (it >= limit) {
+            atomicExch(err, 2);
+            break;
+        }
+    }
 }
 
 // -------------------------------------------------------------------------
@@ -64,7 +71,8 @@ __device__ void grid_sync(uint32_t *bar, long long limit, int32_t *err)
 //   leaves: ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
 //           forward (P2M): OpA = Q^T, s = r^2;  adjoint (L2P^H): OpA = E^H, s = 1
 //           (OpA == nullptr: the leaf expansions are already in ex, split path)
-//   then level by level, deepest first, separated by grid barriers:
+//   then level by level, deepest first, each parent once its children are
+//   published (per-box flags):
 //   parent: ex[p][l] = sum_q sum_k OpUp[q][k][l] ex[child_q(p)][k]    (levels >= 2)
 //           forward: M2M; adjoint: L2L^H
 // Four warps per block: in the leaf step warp w sums over the w-th quarter of
@@ -77,7 +85,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
             const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, double2 *ex, int NP, int P1,
-            const double *__restrict__ lvtab, bool climb, uint32_t *gbar, long long limit, int32_t *err)
+            const double *__restrict__ lvtab, bool climb, int32_t *flag, long long limit, int32_t *err)
 {
     extern __shared__ double2 shu[];
     double2 *sc = shu;                                       // 4 * P1 children
@@ -109,13 +117,17 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             ex[int64_t(b) * P1 + l] =
                 make_double2(s * ((a0.x + a1.x) + (a2.x + a3.x)), s * ((a0.y + a1.y) + (a2.y + a3.y)));
         }
+        flag_publish(&flag[b], 1);
     }
     if (!climb) return;
     for (int lv = nlevels - 2; lv >= 2; lv--) {
-        grid_sync(gbar, limit, err);   // every box of the levels below is complete
         for (int64_t p = level_start[lv] + blockIdx.x; p < level_start[lv + 1]; p += gridDim.x) {
             const int c0 = box_child0[p];
             if (c0 < 0) continue;   // a leaf (uniform over the block)
+            // children computed in this launch: every child above the leaves,
+            // and the leaves too when their expansions come from the leaf step
+            if (threadIdx.x < 4 && (OpA || box_child0[c0 + threadIdx.x] >= 0))
+                flag_wait(&flag[c0 + threadIdx.x], 1, limit, err);
             __syncthreads();
             for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
             __syncthreads();
@@ -145,6 +157,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
                 ex[int64_t(p) * P1 + l] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
             }
+            flag_publish(&flag[p], 1);
         }
     }
 }
@@ -282,8 +295,11 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // level >= 2, in one persistent launch:
 //   phase 1 (every box at once):
 //     out[b] = sum_{e in V(b)} Pv[e] + sum_{x in X(b)} (PX[x] + log(r_c) A_0(c) e_0)
-//   phase 2 (levels 3, 4, ..., grid barriers between levels):
+//   phase 2 (levels 3, 4, ...; each box once its parent is published):
 //     out[b] += Par_q out[parent(b)]      (forward L2L, adjoint M2M^H)
+// Both phases give a block the same boxes (ascending index, so ascending
+// level): phase 2 of a box reads only its own block's phase-1 result and its
+// parent's flag; level-2 boxes are published at the end of phase 1.
 // The X-list log term uses coefficient 0 of the source leaf's own expansion
 // from the upward pass (forward A_0 = r_c^2 (w.f)/2pi, adjoint B_0 = sum_j g_j).
 // Four warps per block: in phase 1 warp w sums every fourth V pair, in phase 2
@@ -297,7 +313,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
               const double2 *__restrict__ first, const int32_t *__restrict__ parent,
               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
               const double2 *__restrict__ OpPar, double2 *out, int P1, const double *__restrict__ lvtab,
-              uint32_t *gbar, long long limit, int32_t *err)
+              int32_t *flag, long long limit, int32_t *err)
 {
     extern __shared__ double2 sdn[];
     double2 *se = sdn;             // [P1] parent expansion
@@ -337,14 +353,16 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                 out[b * P1 + o] = make_double2(re, im);
             }
         }
+        if (b < level_start[3]) flag_publish(&flag[b], 2);
         __syncthreads();
     }
     const int kq = (P1 + 3) / 4;
-    for (int lv = 3; lv < nlevels; lv++) {
-        grid_sync(gbar, limit, err);   // phase 1 and the parents' level are complete
-        for (int64_t b = level_start[lv] + blockIdx.x; b < level_start[lv + 1]; b += gridDim.x) {
+    if (nlevels > 3) {
+        for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
+            if (b < level_start[3]) continue;   // level 2: no parent shift
             const int pb = parent[b];
             const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+            if (threadIdx.x == 0) flag_wait(&flag[pb], 2, limit, err);
             __syncthreads();
             for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
             __syncthreads();
@@ -376,6 +394,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                                                    cur.y + ((a0.y + a1.y) + (a2.y + a3.y)));
                 }
             }
+            flag_publish(&flag[b], 2);
         }
     }
 }
@@ -604,13 +623,12 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         cudaEventRecord(ev[9], st);
     }
     if (ev) cudaEventRecord(ev[1], st);
-    // the grid barrier of the persistent passes starts from zero (a barrier
-    // wait that ran out in an earlier apply cannot leave it out of step)
-    ce = cudaMemsetAsync(d.gbar, 0, 2 * sizeof(uint32_t), st);
+    // the per-box flags of the persistent passes start from zero
+    ce = cudaMemsetAsync(d.flag, 0, sizeof(int32_t) * size_t(h.box_level.size()), st);
     if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[2], st);
-    // grid-barrier polls go to L2 (about a microsecond each): a sixteenth of
-    // the mbarrier poll limit
+    // flag polls go to L2 (several hundred cycles each): a sixteenth of the
+    // mbarrier poll limit
     const long long glimit = std::max(1ll, a.wait_limit / 16);
     // leafA + upward pass in one persistent launch (leafA always runs: the
     // near-field log term reads coefficient 0 of its output; without the far
@@ -623,12 +641,12 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (adj)
             k_up_levels<true><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                              d.level_start, h.nlevels, d.box_child0, vin, opA,
-                                                             op.up, first, NP, P1, d.lvtab, climb, d.gbar,
+                                                             op.up, first, NP, P1, d.lvtab, climb, d.flag,
                                                              glimit, a.err);
         else
             k_up_levels<false><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                                                               d.level_start, h.nlevels, d.box_child0, vin, opA,
-                                                              op.up, first, NP, P1, d.lvtab, climb, d.gbar,
+                                                              op.up, first, NP, P1, d.lvtab, climb, d.flag,
                                                               glimit, a.err);
     }
     if (ev) cudaEventRecord(ev[3], st);
@@ -665,7 +683,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (ev) cudaEventRecord(ev[4], st);
         k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * 5 * P1, st>>>(
             d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
-            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, d.gbar, glimit, a.err);
+            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, d.flag, glimit, a.err);
     } else if (ev) {
         cudaEventRecord(ev[4], st);
     }
