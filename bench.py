@@ -187,7 +187,7 @@ STAGE_KERNELS = {
     "tensor_v": "k_split_vec + k_split_gemm<256> (near field, leaf-to-expansion, X list)",
     "clear": "memset",
     "upward": "k_up_levels",
-    "m2l": "k_m2l_pairs (FP64 path: + k_x_entries)",
+    "m2l": "k_split_exp + k_split_gemm<64> (M2L per V pair; FP64 path: k_m2l_pairs + k_x_entries)",
     "down_levels": "k_down_levels",
     "tensor_e": "k_split_exp + k_split_gemm<64>",
     "leaf_output": "k_leaf_out",
@@ -196,7 +196,6 @@ STAGE_KERNELS = {
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, keyed by
 # (workload, nterms, split); the adjoint apply of the bench configuration
 TRAFFIC = {
-    ("adaptive20", 24, True): {"upward": 0.57e6, "m2l": 1.50e6, "down_levels": 13.25e6},
 }
 
 
@@ -214,7 +213,7 @@ def stage_work(st, nleaf, nleaf_far, P1, NP, split):
             "tensor_near": (15 * 2.0 * NP * NP * st["n_near"], "tensor"),
             "clear": (0.0, "fp64"),
             "upward": (32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
-            "m2l": (4.0 * P1 * P1 * st["n_v"], "fp64"),
+            "m2l": (15 * 2.0 * R * R * st["n_v"], "tensor"),
             "down_levels": (8.0 * P1 * P1 * n_shift + 2.0 * P1 * (st["n_v"] + st["n_x"]), "fp64"),
             "tensor_e": (15 * 2.0 * R * NP * (nleaf_far + st["n_w"]), "tensor"),
             "leaf_output": (8.0 * NP * (st["n_near"] + st["n_w"] + nleaf_far + nleaf), "bytes"),
@@ -443,12 +442,14 @@ def main():
                 "stages": per_stage}
 
     nl = st["nlevels"]
-    # kernels per apply: upward pass, then (levels > 2) M2L pairs, the FP64
-    # X-list products (FP64 path with X entries) and the downward level pass,
-    # then the leaf output; split: + input digits, two group-V tensor launches,
-    # expansion digits, the group-E tensor launch
-    far_k = (2 + (1 if (head == bc.FP64 and st["n_x"] > 0) else 0)) if nl > 2 else 0
-    launches_per_apply = 1 + far_k + 1 + (5 if head == bc.SPLIT_BF16 else 0)
+    # kernels per apply (trees of more than three levels): upward pass, M2L,
+    # downward level pass, leaf output; FP64: M2L pairs + X-list products;
+    # split: input digits, group-V tensor launch (two with --overlap), M2L
+    # digits + tensor launch, expansion digits + group-E tensor launch
+    if head == bc.SPLIT_BF16:
+        launches_per_apply = 2 + (1 if args.overlap else 0) + 1 + 2 + 1 + 2 + 1
+    else:
+        launches_per_apply = 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1
     pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

@@ -19,14 +19,14 @@ template <class T>
 cudaError_t dev_upload(std::vector<void *> &allocs, T **dst, const T *src, size_t n)
 {
     *dst = nullptr;
-    if (n == 0) n = 1;
+    const size_t nalloc = n ? n : 1;   // a valid pointer even for an empty list
     void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    cudaError_t e = cudaMalloc(&p, nalloc * sizeof(T));
     if (e != cudaSuccess) return e;
     allocs.push_back(p);
     *dst = static_cast<T *>(p);
-    if (src) return cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice);
-    return cudaMemset(p, 0, n * sizeof(T));
+    if (src && n) return cudaMemcpy(p, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return cudaMemset(p, 0, nalloc * sizeof(T));
 }
 
 void free_all(std::vector<void *> &allocs)
@@ -379,6 +379,35 @@ bc_status build_split_tables(bc_ctx *ctx)
         T.e_op[dir] = add_split_op(de, xe, me, NP, KE);
         T.w_op[dir].assign(kNumWX, SplitOp());
         for (int c = 0; c < kNumWX; c++) T.w_op[dir][c] = add_split_op(de, xe, mw[c], NP, KE);
+        // Group M: M2L per V code in real form (rows 2l, 2l+1 = Re, Im of
+        // output coefficient l; column 2k, 2k+1 = Re, Im of input k):
+        //   forward (l,k) = M2L_c[l][k];  adjoint (l,k) = conj(M2L_{-d}[k][l]),
+        // without the log term of (0,0): (log|d| + log r) A_0 stays in FP64
+        // (downward pass), like every log term of the method.  The input is
+        // the `first` array with the W-list scales 2^-k: the translation of a
+        // source two box widths away decays like C(k+l-1, k-1) 4^-(k+l) and
+        // its input grows at most like (sqrt 2)^k, so the rescaled rows stay
+        // within a few powers of two.
+        T.m2l_op[dir].assign(kNumV, SplitOp());
+        {
+            std::vector<double> mm(size_t(R) * KE, 0.0);
+            for (int c = 0; c < kNumV; c++) {
+                const int dx = c % 7 - 3, dy = c / 7 - 3, cr = kNumV - 1 - c;
+                if (std::max(std::abs(dx), std::abs(dy)) < 2) continue;
+                std::fill(mm.begin(), mm.end(), 0.0);
+                for (int l = 0; l < P1; l++)
+                    for (int k = 0; k < P1; k++) {
+                        cplx z = dir == 0 ? at2(ht.M2L, (size_t(c) * P1 + l) * P1 + k)
+                                          : std::conj(at2(ht.M2L, (size_t(cr) * P1 + k) * P1 + l));
+                        if (l == 0 && k == 0) z = 0.0;
+                        mm[size_t(2 * l) * KE + 2 * k] = z.real() / sw[2 * k];
+                        mm[size_t(2 * l) * KE + 2 * k + 1] = -z.imag() / sw[2 * k + 1];
+                        mm[size_t(2 * l + 1) * KE + 2 * k] = z.imag() / sw[2 * k];
+                        mm[size_t(2 * l + 1) * KE + 2 * k + 1] = z.real() / sw[2 * k + 1];
+                    }
+                T.m2l_op[dir][c] = add_split_op(de, xe, mm, R, KE);
+            }
+        }
         // expA is the W source (first) in the forward apply and the P2M^H input
         // (second) in the adjoint; expB the other way round
         std::vector<double> scl(2 * KE);
@@ -470,7 +499,7 @@ bc_status build_split_tree(bc_tree *t)
         const bool adj = dir == 1;
         double2 *first = adj ? t->d.expB : t->d.expA;
         const int first_which = adj ? 1 : 0, second_which = adj ? 0 : 1;   // expA = 0, expB = 1
-        TileBuilder V, NV, E;
+        TileBuilder V, NV, E, M;
         // near entries, by table
         std::vector<std::vector<SplitCol>> by_tab(kNumNear);
         for (int64_t k = 0; k < nn; k++) {
@@ -526,6 +555,20 @@ bc_status build_split_tree(bc_tree *t)
         }
         for (int c = 0; c < kNumWX; c++)
             if (!by_code[c].empty()) E.add(T.w_op[dir][c], by_code[c]);
+        // group M: one column per V pair (source box digits, result into Pv;
+        // the adjoint digits carry alpha0)
+        {
+            std::vector<std::vector<SplitCol>> by_v(kNumV);
+            for (size_t k = 0; k < h.v_src.size(); k++) {
+                SplitCol c;
+                c.vec = int32_t(first_which * nbox + h.v_src[k]);
+                c.ctl = col_ctl(0, adj);
+                c.out = reinterpret_cast<double *>(t->d.Pv + k * size_t(P1));
+                by_v[h.v_code[k]].push_back(c);
+            }
+            for (int c = 0; c < kNumV; c++)
+                if (!by_v[c].empty()) M.add(T.m2l_op[dir][c], by_v[c]);
+        }
         TileBuilder VN = NV;   // near tiles first (longest), then the far ones
         for (SplitTile tl : V.tiles) {
             tl.p0 += int32_t(NV.cols.size());
@@ -541,11 +584,14 @@ bc_status build_split_tree(bc_tree *t)
             (e = dev_upload(al, &s.tN[dir], NV.tiles.data(), NV.tiles.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.cN[dir], NV.cols.data(), NV.cols.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.tE[dir], E.tiles.data(), E.tiles.size())) != cudaSuccess ||
-            (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess)
+            (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.tM[dir], M.tiles.data(), M.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cM[dir], M.cols.data(), M.cols.size())) != cudaSuccess)
             return cuda_fail(e, "split tree upload");
         s.ntV[dir] = int(V.tiles.size());
         s.ntN[dir] = int(NV.tiles.size());
         s.ntE[dir] = int(E.tiles.size());
+        s.ntM[dir] = int(M.tiles.size());
     }
     s.err = t->ctx->dev_err;
     t->split_ready = true;

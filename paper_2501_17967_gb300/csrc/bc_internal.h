@@ -161,6 +161,7 @@ struct SplitTables {
     const uint8_t *ops[2][2] = {};
     const int32_t *op_exp[2][2] = {};
     std::vector<SplitOp> near_op[2], x_op[2], w_op[2];   // [dir][code]
+    std::vector<SplitOp> m2l_op[2];                       // [dir][V code] (group E, 2 P1 rows)
     SplitOp leafA_op[2], e_op[2];
     // group E column scales (powers of two) per direction: [expA][64], [expB][64].
     // Coefficient k of an expansion is multiplied by s_k before its digits are
@@ -195,10 +196,11 @@ struct SplitTree {
     // [forward, adjoint]; group V as far part (leafA, X list: needed by the
     // upward and downward passes) and near part (needed at the leaf output),
     // launched apart when the near part runs on the side stream, and as one
-    // list (near tiles first: two jobs each) otherwise
-    SplitTile *tV[2] = {}, *tN[2] = {}, *tVN[2] = {}, *tE[2] = {};
-    SplitCol *cV[2] = {}, *cN[2] = {}, *cVN[2] = {}, *cE[2] = {};
-    int ntV[2] = {}, ntN[2] = {}, ntVN[2] = {}, ntE[2] = {};
+    // list (near tiles first: two jobs each) otherwise; group E (L2P / P2M^H,
+    // W list); group M: the V-list translations (M2L) by offset code
+    SplitTile *tV[2] = {}, *tN[2] = {}, *tVN[2] = {}, *tE[2] = {}, *tM[2] = {};
+    SplitCol *cV[2] = {}, *cN[2] = {}, *cVN[2] = {}, *cE[2] = {}, *cM[2] = {};
+    int ntV[2] = {}, ntN[2] = {}, ntVN[2] = {}, ntE[2] = {}, ntM[2] = {};
     double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
     double *PX = nullptr;         // [n_x][64] X-list result per entry
     double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf
@@ -212,8 +214,8 @@ struct SplitTree {
 size_t split_smem_bytes(int kd);
 cudaError_t split_prepare();   // kernel attributes of the split path (before any capture)
 // parts: which products take the tensor-core results (bits: 1 near field,
-// 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list); the others run in FP64.
-constexpr int kSplitAllParts = 31;
+// 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list, 32 M2L); the others run in FP64.
+constexpr int kSplitAllParts = 63;
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
@@ -224,8 +226,11 @@ struct SplitLaunch {
 // (times scale), and the tensor-core operator products of one group.
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
                                     cudaStream_t st);
-cudaError_t launch_split_digits_exp(int64_t nbox, const double2 *ea, const double2 *eb, int P1, double scale,
-                                    const double *escale, uint16_t *dig, int32_t *dexp, cudaStream_t st);
+// Expansion digits of vectors [i0, i1) of the pair (expA: 0..nbox-1, expB:
+// nbox..2 nbox-1).
+cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,
+                                    int P1, double scale, const double *escale, uint16_t *dig, int32_t *dexp,
+                                    cudaStream_t st);
 cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int32_t *err, long long wait_limit,
                               int withhold, cudaStream_t st);
 

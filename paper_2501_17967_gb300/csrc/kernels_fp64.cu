@@ -302,6 +302,11 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // parent's flag; level-2 boxes are published at the end of phase 1.
 // The X-list log term uses coefficient 0 of the source leaf's own expansion
 // from the upward pass (forward A_0 = r_c^2 (w.f)/2pi, adjoint B_0 = sum_j g_j).
+// With v_lsrc non-null (M2L products from the tensor cores, which leave out
+// the log term) phase 1 adds it in FP64 as well:
+//     out[b][0] += sum_{e in V(b)} (log|d_e| + log r_b) first[s_e][0]
+// summed by the second warp (one pair per lane) while the first warp takes
+// the X list.
 // Four warps per block: in phase 1 warp w sums every fourth V pair, in phase 2
 // warp w applies a quarter of the shift operator's columns (the shift chain
 // is the critical path, and one warp alone would serialise on its FP64 unit).
@@ -313,11 +318,13 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
               const double2 *__restrict__ first, const int32_t *__restrict__ parent,
               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
               const double2 *__restrict__ OpPar, double2 *out, int P1, const double *__restrict__ lvtab,
-              int32_t *flag, long long limit, int32_t *err)
+              const int32_t *__restrict__ v_lsrc, const int32_t *__restrict__ v_code,
+              const double *__restrict__ logd, int32_t *flag, long long limit, int32_t *err)
 {
     extern __shared__ double2 sdn[];
     double2 *se = sdn;             // [P1] parent expansion
     double2 *part = sdn + P1;      // [4][P1] partial sums
+    double2 *slog = sdn + 5 * P1;  // [1] V-list log term
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
         const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
@@ -339,8 +346,25 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
             part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
         }
         __syncthreads();
+        const int lvb = lv_of(level_start, nlevels, b);
+        if (v_lsrc && w == 1) {
+            const double lgb = lvtab[kLvTab + lvb];
+            double re = 0.0, im = 0.0;
+            for (int e = v0 + lane; e < v1; e += 32) {
+                const double2 a0 = first[int64_t(v_lsrc[e]) * P1];
+                const double c0 = logd[v_code[e]] + lgb;
+                re = fma(c0, a0.x, re);
+                im = fma(c0, a0.y, im);
+            }
+            for (int s = 16; s > 0; s >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, s);
+                im += __shfl_xor_sync(0xffffffffu, im, s);
+            }
+            if (lane == 0) *slog = make_double2(re, im);
+        }
+        if (v_lsrc) __syncthreads();
         if (w == 0) {
-            const double logrc = lvtab[kLvTab + lv_of(level_start, nlevels, b) - 1];
+            const double logrc = lvtab[kLvTab + lvb - 1];
             for (int o = lane; o < P1; o += 32) {
                 const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
                 double re = (a0.x + a1.x) + (a2.x + a3.x), im = (a0.y + a1.y) + (a2.y + a3.y);
@@ -349,6 +373,10 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                     re += t.x;
                     im += t.y;
                     if (o == 0) re = fma(logrc, first[int64_t(leaf_box[x_src[x]]) * P1].x, re);
+                }
+                if (v_lsrc && o == 0) {
+                    re += slog->x;
+                    im += slog->y;
                 }
                 out[b * P1 + o] = make_double2(re, im);
             }
@@ -650,10 +678,25 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                                                               glimit, a.err);
     }
     if (ev) cudaEventRecord(ev[3], st);
+    bool first_digits = false;   // digits of `first` taken (tensor-core M2L)
     if (far && h.nlevels > 2) {
         // M2L per V pair, then (FP64) the X-list products, then the level-by-level sum
         const int64_t npairs = int64_t(h.v_src.size());
-        if (npairs > 0) {
+        if (npairs > 0 && (parts & 32)) {
+            // tensor group M: digits of `first` (times alpha0 in the adjoint),
+            // then every pair's translation but its log term
+            const int64_t f0 = adj ? a.nbox : 0;
+            ce = launch_split_digits_exp(f0, f0 + a.nbox, a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0,
+                                         sT->escale[dir], sp->edig, sp->eexp, st);
+            if (ce != cudaSuccess) return ce;
+            first_digits = true;
+            SplitGemm g;
+            g.tiles = sp->tM[dir]; g.cols = sp->cM[dir]; g.ntiles = sp->ntM[dir];
+            g.ops = sT->ops[1][dir]; g.op_exp = sT->op_exp[1][dir];
+            g.dig = sp->edig; g.dexp = sp->eexp;
+            ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            if (ce != cudaSuccess) return ce;
+        } else if (npairs > 0) {
             const int grid = grid_for((npairs + 127) / 128, 152 * 24);
             const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
 #define BC_M2L(A, PM)                                                                                      \
@@ -681,19 +724,21 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             PX = d.PX;
         }
         if (ev) cudaEventRecord(ev[4], st);
-        k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * 5 * P1, st>>>(
+        k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st>>>(
             d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
-            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, d.flag, glimit, a.err);
+            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd,
+            d.flag, glimit, a.err);
     } else if (ev) {
         cudaEventRecord(ev[4], st);
     }
     if (ev) cudaEventRecord(ev[5], st);
     if (split && far) {
         // tensor group E: digits of both expansion arrays (times alpha0 in the
-        // adjoint), then L2P (P2M^H) of `second` into PE and the W list of
-        // `first` into PW
-        ce = launch_split_digits_exp(a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0, sT->escale[dir], sp->edig,
-                                     sp->eexp, st);
+        // adjoint; those of `first` already taken for the M2L), then L2P
+        // (P2M^H) of `second` into PE and the W list of `first` into PW
+        const int64_t s0 = first_digits ? (adj ? 0 : a.nbox) : 0, s1 = first_digits ? s0 + a.nbox : 2 * a.nbox;
+        ce = launch_split_digits_exp(s0, s1, a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0, sT->escale[dir],
+                                     sp->edig, sp->eexp, st);
         if (ce != cudaSuccess) return ce;
         SplitGemm g;
         g.tiles = sp->tE[dir]; g.cols = sp->cE[dir]; g.ntiles = sp->ntE[dir];
@@ -750,7 +795,7 @@ cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false>, 128, shU);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true>, 128, shU);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels, 128, sizeof(double2) * 5 * P1);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels, 128, sizeof(double2) * (5 * P1 + 1));
     if (e != cudaSuccess) return e;
     if (std::min(bu0, bu1) < 1 || bs < 1) return cudaErrorInvalidConfiguration;
     *up_blocks = sms * std::min(up_per_sm, std::min(bu0, bu1));

@@ -305,23 +305,24 @@ __global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *
     }
 }
 
-// Digits of scale * s_k * (expansion coefficient k): vector i < nbox is ea[i]
-// with column scales escale[0..63], else eb[i - nbox] with escale[64..127];
-// its 2*P1 reals (re, im interleaved) padded with zeros to 64.  One warp per
-// vector: dig[i][a][64], dexp[i].
-__global__ void __launch_bounds__(256) k_split_exp(int64_t nbox, const double *__restrict__ ea,
-                                                   const double *__restrict__ eb, int nreal, double scale,
-                                                   const double *__restrict__ escale, uint16_t *__restrict__ dig,
-                                                   int32_t *__restrict__ dexp)
+// Digits of scale * s_k * (expansion coefficient k) for the vectors i in
+// [i0, i1): vector i < nbox is ea[i] with column scales escale[0..63], else
+// eb[i - nbox] with escale[64..127]; its 2*P1 reals (re, im interleaved)
+// padded with zeros to 64.  One warp per vector: dig[i][a][64], dexp[i].
+__global__ void __launch_bounds__(256) k_split_exp(int64_t i0, int64_t i1, int64_t nbox,
+                                                   const double *__restrict__ ea, const double *__restrict__ eb,
+                                                   int nreal, double scale, const double *__restrict__ escale,
+                                                   uint16_t *__restrict__ dig, int32_t *__restrict__ dexp)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < 2 * nbox; i += nw) {
-        const double *src = i < nbox ? ea + i * nreal : eb + (i - nbox) * nreal;
+    for (int64_t i = i0 + ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5); i < i1; i += nw) {
+        const int64_t box = i < nbox ? i : i - nbox;
+        const double *src = (i < nbox ? ea : eb) + box * nreal;
         const double *sc = escale + (i < nbox ? 0 : kSplitKE);
-        const long long b0 = lane < nreal ? __double_as_longlong(scale * sc[lane] * src[lane]) : 0ll;
-        const long long b1 =
-            lane + 32 < nreal ? __double_as_longlong(scale * sc[lane + 32] * src[lane + 32]) : 0ll;
+        const double v0 = lane < nreal ? src[lane] : 0.0, v1 = lane + 32 < nreal ? src[lane + 32] : 0.0;
+        const long long b0 = __double_as_longlong(scale * sc[lane] * v0);
+        const long long b1 = __double_as_longlong(scale * sc[lane + 32] * v1);
         int m = max(int((b0 >> 52) & 0x7FF), int((b1 >> 52) & 0x7FF));
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         const int E = m ? m - 1023 + 2 : 0;
@@ -675,13 +676,14 @@ cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_digits_exp(int64_t nbox, const double2 *ea, const double2 *eb, int P1, double scale,
-                                    const double *escale, uint16_t *dig, int32_t *dexp, cudaStream_t st)
+cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,
+                                    int P1, double scale, const double *escale, uint16_t *dig, int32_t *dexp,
+                                    cudaStream_t st)
 {
-    if (nbox <= 0) return cudaSuccess;
-    const int grid = int(std::min<int64_t>((2 * nbox + 7) / 8, 152 * 16));
-    k_split_exp<<<grid, 256, 0, st>>>(nbox, reinterpret_cast<const double *>(ea), reinterpret_cast<const double *>(eb),
-                                      2 * P1, scale, escale, dig, dexp);
+    if (i1 <= i0) return cudaSuccess;
+    const int grid = int(std::min<int64_t>((i1 - i0 + 7) / 8, 152 * 16));
+    k_split_exp<<<grid, 256, 0, st>>>(i0, i1, nbox, reinterpret_cast<const double *>(ea),
+                                      reinterpret_cast<const double *>(eb), 2 * P1, scale, escale, dig, dexp);
     return cudaGetLastError();
 }
 
