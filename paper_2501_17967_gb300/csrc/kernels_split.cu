@@ -43,6 +43,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "bc_internal.h"
 
@@ -240,22 +241,14 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// S * 2^ex as an FP64 value (round to nearest even) by integer operations on
-// the bit pattern, keeping the conversion off the FP64 pipe.  |S| < 2^62.
+// S * 2^ex as an FP64 value: the conversion rounds S to nearest even and the
+// scaling adds ex to the exponent field (exact; results below the normal
+// range, negligible here, become zero).  |S| < 2^62.
 __device__ __forceinline__ double i64_scaled(long long S, int ex)
 {
-    if (S == 0) return 0.0;
-    const unsigned long long sign = S < 0 ? (1ull << 63) : 0ull;
-    const unsigned long long m = S < 0 ? (unsigned long long)(-S) : (unsigned long long)S;
-    const int lz = __clzll(m);
-    const unsigned long long t = m << lz;                 // leading one at bit 63
-    unsigned long long mant = t >> 11;                    // 53 bits with the leading one
-    const unsigned long long rem = t & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;
-    const long long be = (long long)(63 - lz + ex) + 1023;   // biased exponent
-    if (be <= 0) return 0.0;                              // below the normal range: negligible here
-    const unsigned long long bits = ((unsigned long long)be << 52) + (mant - (1ull << 52));
-    return __longlong_as_double((long long)(bits | sign));
+    const long long b = __double_as_longlong(__ll2double_rn(S));
+    const int e = int((b >> 52) & 0x7FF) + ex;
+    return (S == 0 || e <= 0) ? 0.0 : __longlong_as_double(b + ((long long)ex << 52));
 }
 
 // Five balanced base-256 digits (BF16 bit patterns) of round(x * 2^(40 - E)),
@@ -374,7 +367,8 @@ constexpr int kGatherWarp0 = 2;
 constexpr int kGatherThreads = 192;
 constexpr int kEpiWarp0 = 8;
 constexpr int kEpiWarps = 8;
-constexpr int kTmemBuf = 256;   // TMEM columns per job buffer (5 levels x 48 used)
+constexpr int kTmemBuf = 256;
+constexpr int kNoExp = 0x7FFFFFFF;   // 1/alpha0 is not a power of two   // TMEM columns per job buffer (5 levels x 48 used)
 
 // Barriers (mbarriers in shared memory); counts in brackets:
 //   lbar[b] (1)        operator chunk in buffer b has landed (bulk-copy bytes)
@@ -396,7 +390,8 @@ struct GemmBars {
 
 template <int KD>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long long wait_limit, int withhold)
+k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__restrict__ err, long long wait_limit,
+             int withhold)
 {
     using Sh = GemmShape<KD>;
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -515,11 +510,16 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                     const int rows_h = min(128, tl.rows - 128 * h);
                     const uint32_t bytes = uint32_t((rows_h + 7) / 8) * 8 * Sh::KC * 2;
                     const uint8_t *src = gm.ops + tl.a_off + size_t((a * mh + h) * Sh::NKC + kc) * Sh::kChunk;
+                    // an operator of at most 64 rows is copied twice, to rows 0-63
+                    // and 64-127, so that every TMEM lane quarter holds a result
+                    const int copies = tl.rows <= 64 ? 2 : 1;
                     if (lane == 0) {
-                        mbar_expect_tx(&bars->lbar[buf], bytes);
-                        uint8_t *dst = As + buf * Sh::kChunk;
-                        for (uint32_t q = 0; q < bytes; q += 16384)
-                            bulk_g2s(dst + q, src + q, min(16384u, bytes - q), &bars->lbar[buf]);
+                        mbar_expect_tx(&bars->lbar[buf], bytes * copies);
+                        for (int cp = 0; cp < copies; cp++) {
+                            uint8_t *dst = As + buf * Sh::kChunk + cp * (Sh::kChunk / 2);
+                            for (uint32_t q = 0; q < bytes; q += 16384)
+                                bulk_g2s(dst + q, src + q, min(16384u, bytes - q), &bars->lbar[buf]);
+                        }
                     }
                     __syncwarp();
                 }
@@ -549,6 +549,10 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                 m.out = c.out;
                 m.exp = gm.dexp[c.vec] + (c.ctl >> 1) - 48;
                 m.flag = c.ctl & 1;
+                if (m.flag && inv_alpha_exp != kNoExp) {   // 1/alpha0 a power of two: an exponent shift
+                    m.exp += inv_alpha_exp;
+                    m.flag = 0;
+                }
                 m.vec = c.vec;
                 m.pad = 0;
                 M[gt] = m;
@@ -586,8 +590,11 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
         cp_async_wait_all();
     } else {
         // ---------------- epilogues ----------------
-        // warp w reads TMEM lanes 32(w%4)..32(w%4)+31 (rows 32(w%4)+lane of
-        // the job's row half); warps 8-11 take columns 0-23, warps 12-15 24-47
+        // warp w reads TMEM lanes 32(w%4)..32(w%4)+31.  Operators of more
+        // than 64 rows: rows 32(w%4)+lane of the job's row half, warps 8-11
+        // columns 0-23, warps 12-15 columns 24-47.  Up to 64 rows (held twice):
+        // rows 32(w%2)+lane, lane quarters 0-1 columns 0-23 and 2-3 columns
+        // 24-47, split 12 + 12 between the two warps of a quarter.
         const int wq = warp & 3, half = (warp - kEpiWarp0) >> 2;
         int job = 0, k = 0;
         bool failed = false;
@@ -604,12 +611,13 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
                     break;
                 }
                 tc_fence_after();
-                const int row = h * 128 + wq * 32 + lane;
+                const bool small = tl.rows <= 64;
+                const int row = small ? (wq & 1) * 32 + lane : h * 128 + wq * 32 + lane;
                 const bool live = row < tl.rows;
                 const int ea = live ? gm.op_exp[tl.exp_off + row] : 0;
-                for (int gi = 0; gi < 3; gi++) {
-                    const int c0 = half * 24 + gi * 8;
-                    if (c0 >= tl.cnt) break;   // uniform over the warp
+                const int cb = small ? (wq >> 1) * 24 + half * 12 : half * 24;
+                const int ce = min(tl.cnt, cb + (small ? 12 : 24));
+                for (int c0 = cb; c0 < ce; c0 += 8) {   // uniform over the warp
                     uint32_t d[kS][8];
 #pragma unroll
                     for (int g = 0; g < kS; g++)
@@ -619,7 +627,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int32_t *__restrict__ err, long lo
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
                         const int c = c0 + q;
-                        if (c >= tl.cnt) continue;
+                        if (c >= ce) continue;
                         long long S = 0;
 #pragma unroll
                         for (int g = 0; g < kS; g++)
@@ -692,10 +700,14 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
 {
     if (g.ntiles <= 0) return cudaSuccess;
     const int grid = std::min(g.ntiles, g_sms > 0 ? g_sms : 152);
+    int ie = 0;
+    const int inv_alpha_exp = std::frexp(inv_alpha0, &ie) == 0.5 ? ie - 1 : kNoExp;
     if (kd == 256)
-        k_split_gemm<256><<<grid, kGemmThreads, GemmShape<256>::kSmem, st>>>(g, inv_alpha0, err, wait_limit, withhold);
+        k_split_gemm<256><<<grid, kGemmThreads, GemmShape<256>::kSmem, st>>>(g, inv_alpha0, inv_alpha_exp, err,
+                                                                              wait_limit, withhold);
     else
-        k_split_gemm<64><<<grid, kGemmThreads, kSmem64, st>>>(g, inv_alpha0, err, wait_limit, withhold);
+        k_split_gemm<64><<<grid, kGemmThreads, kSmem64, st>>>(g, inv_alpha0, inv_alpha_exp, err, wait_limit,
+                                                              withhold);
     return cudaGetLastError();
 }
 
