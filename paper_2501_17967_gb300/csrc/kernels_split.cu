@@ -105,6 +105,17 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// waits until at most n (0..4) of this thread's cp.async groups are pending
+__device__ __forceinline__ void cp_async_wait_pending(int n)
+{
+    switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    }
+}
 
 // NK MMAs along K (16 columns each) issued from one elected lane of a
 // converged warp: the descriptors advance by 16 (256 bytes) per step; the
@@ -354,7 +365,11 @@ struct GemmShape {
     static constexpr int kChunk = 128 * KC * 2;        // bytes of one operator chunk
     static constexpr int kBSBO = (KD / 8) * 128;       // B: bytes between 8-row groups
     static constexpr int kASBO = (KC / 8) * 128;       // A: bytes between 8-row groups
-    static constexpr size_t kSmem = size_t(kS) * kBSlice + size_t(kNBuf) * kChunk + 2 * kN * sizeof(ColMeta) +
+    // B buffers: two for K = 64 (the next tile is gathered while this one's
+    // MMAs run), one for K = 256 (120 KB)
+    static constexpr int kBBuf = KD <= 64 ? 2 : 1;
+    static constexpr int kBTile = kS * kBSlice;         // bytes of one tile's B
+    static constexpr size_t kSmem = size_t(kBBuf) * kBTile + size_t(kNBuf) * kChunk + 2 * kN * sizeof(ColMeta) +
                                     64 * sizeof(uint64_t);
 };
 
@@ -367,8 +382,8 @@ constexpr int kGatherWarp0 = 2;
 constexpr int kGatherThreads = 192;
 constexpr int kEpiWarp0 = 8;
 constexpr int kEpiWarps = 8;
-constexpr int kTmemBuf = 256;
-constexpr int kNoExp = 0x7FFFFFFF;   // 1/alpha0 is not a power of two   // TMEM columns per job buffer (5 levels x 48 used)
+constexpr int kTmemBuf = 256;        // TMEM columns per job buffer (5 levels x 48 used)
+constexpr int kNoExp = 0x7FFFFFFF;   // 1/alpha0 is not a power of two
 
 // Barriers (mbarriers in shared memory); counts in brackets:
 //   lbar[b] (1)        operator chunk in buffer b has landed (bulk-copy bytes)
@@ -376,14 +391,15 @@ constexpr int kNoExp = 0x7FFFFFFF;   // 1/alpha0 is not a power of two   // TMEM
 //   job_full[r] (1)    the MMAs of the job in TMEM buffer r have completed (commit)
 //   job_empty[r] (8)   the epilogue warps have read TMEM buffer r
 //   b_full[t][s] (1)   B digit slice s (and the metadata) of tile parity t is ready
-//   b_empty[s] (1)     no MMA of the previous tile reads B slice s any more (commit)
+//   b_empty[u][s] (1)  no MMA of the tile last held in B buffer u reads slice s any more (commit)
 //   meta_empty[t] (8)  the epilogue warps are done with metadata buffer t
 // Digit slice s (0-based) of B is read by the chunks of operator digit a <= 4 - s,
 // so in a tile's last job it is free after those chunks; the next tile's B is
 // gathered slice by slice from s = 4 down to 0 and its first chunk issues its
-// MMAs from slice 4 down, so only slice 0 is waited for at the tile change.
+// MMAs from slice 4 down, so with one B buffer only slice 0 is waited for at
+// the tile change.  Tile k uses B buffer k % kBBuf.
 struct GemmBars {
-    uint64_t lbar[kNBuf], mbar[kNBuf], job_full[2], job_empty[2], b_full[2][kS], b_empty[kS], meta_empty[2];
+    uint64_t lbar[kNBuf], mbar[kNBuf], job_full[2], job_empty[2], b_full[2][kS], b_empty[2][kS], meta_empty[2];
     uint32_t tslot;
     int fail;
 };
@@ -395,8 +411,8 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
 {
     using Sh = GemmShape<KD>;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t *Bs = smem;                                                      // kS x kBSlice
-    uint8_t *As = smem + kS * Sh::kBSlice;                                   // kNBuf x kChunk
+    uint8_t *Bs = smem;                                                      // kBBuf x kS x kBSlice
+    uint8_t *As = smem + Sh::kBBuf * Sh::kBTile;                             // kNBuf x kChunk
     ColMeta *meta = reinterpret_cast<ColMeta *>(As + kNBuf * Sh::kChunk);    // [2][kN]
     GemmBars *bars = reinterpret_cast<GemmBars *>(meta + 2 * kN);
     volatile int *fail = &bars->fail;
@@ -419,7 +435,8 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
             mbar_init(&bars->meta_empty[i], kEpiWarps);
             for (int sl = 0; sl < kS; sl++) mbar_init(&bars->b_full[i][sl], 1);
         }
-        for (int sl = 0; sl < kS; sl++) mbar_init(&bars->b_empty[sl], 1);
+        for (int u = 0; u < 2; u++)
+            for (int sl = 0; sl < kS; sl++) mbar_init(&bars->b_empty[u][sl], 1);
         bars->fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -469,14 +486,15 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                         }
                         const uint32_t dcol = tmem + uint32_t(r * kTmemBuf + (a + b) * kN);
                         const uint64_t bd =
-                            bdesc0 + uint64_t(b) * (Sh::kBSlice >> 4) + uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
+                            bdesc0 + uint64_t(k % Sh::kBBuf) * (Sh::kBTile >> 4) + uint64_t(b) * (Sh::kBSlice >> 4) +
+                            uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
                         umma_kchain_warp<Sh::KC / 16>(dcol, ad, bd, idesc, first);
                     }
                     if (failed) break;
                     umma_commit_warp(&bars->mbar[buf]);
                     last_commit = G;
                     // in the tile's last job, slice kS-1-a is read by no later chunk
-                    if (last_job && kc == Sh::NKC - 1) umma_commit_warp(&bars->b_empty[kS - 1 - a]);
+                    if (last_job && kc == Sh::NKC - 1) umma_commit_warp(&bars->b_empty[k % Sh::kBBuf][kS - 1 - a]);
                 }
                 if (failed) break;
                 umma_commit_warp(&bars->job_full[r]);
@@ -531,9 +549,16 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                 wait_bar(&bars->lbar[int(q % kNBuf)], uint32_t((q / kNBuf) & 1), wait_limit, &dummy);
         }
     } else if (warp < kEpiWarp0) {
-        // ---------------- column metadata and B gather, slice by slice ----------------
+        // ---------------- column metadata and B gather ----------------
         const int gt = tid - 32 * kGatherWarp0;
         constexpr int kPieces = KD / 8;   // 16-byte pieces per column and slice
+        // two B buffers: the next tile's record, this thread's column of it and
+        // the column's digit exponent are fetched while the current tile's
+        // slices are in flight
+        SplitTile ntl{};
+        SplitCol ncol{};
+        int nexp = 0;
+        bool have = false;
         int k = 0;
         bool stop = false;
         for (int tile = blockIdx.x; tile < gm.ntiles && !stop; tile += gridDim.x, k++) {
@@ -541,13 +566,13 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
             // the epilogues of tile k - 2 no longer read this metadata buffer
             if (k >= 2) ok = wait_bar(&bars->meta_empty[k & 1], uint32_t(((k - 2) >> 1) & 1), wait_limit, fail);
             if (gather_sync_or(kGatherThreads, !ok)) break;   // uniform over the gather warps
-            const SplitTile tl = gm.tiles[tile];
+            const SplitTile tl = have ? ntl : gm.tiles[tile];
             ColMeta *M = meta + (k & 1) * kN;
             if (gt < tl.cnt) {
-                const SplitCol c = gm.cols[tl.p0 + gt];
+                const SplitCol c = have ? ncol : gm.cols[tl.p0 + gt];
                 ColMeta m;
                 m.out = c.out;
-                m.exp = gm.dexp[c.vec] + (c.ctl >> 1) - 48;
+                m.exp = (have ? nexp : gm.dexp[c.vec]) + (c.ctl >> 1) - 48;
                 m.flag = c.ctl & 1;
                 if (m.flag && inv_alpha_exp != kNoExp) {   // 1/alpha0 a power of two: an exponent shift
                     m.exp += inv_alpha_exp;
@@ -557,33 +582,68 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                 m.pad = 0;
                 M[gt] = m;
             }
+            have = false;
             gather_sync(kGatherThreads);
-            // two slices in flight: issue slice sl, then complete slice sl + 1
-            for (int sl = kS - 1; sl >= -1; sl--) {
-                if (sl >= 0) {
-                    bool ok2 = true;
-                    // no MMA of the previous tile reads slice sl any more
-                    if (k >= 1) ok2 = wait_bar(&bars->b_empty[sl], uint32_t((k - 1) & 1), wait_limit, fail);
-                    if (gather_sync_or(kGatherThreads, !ok2)) {
-                        stop = true;
-                        break;
-                    }
-                    uint8_t *dst = Bs + sl * Sh::kBSlice;
+            uint8_t *Bt = Bs + (k % Sh::kBBuf) * Sh::kBTile;
+            if constexpr (Sh::kBBuf == 2) {
+                // every slice at once: tile k - 2, the last one in this buffer,
+                // has released all of them
+                bool ok2 = true;
+                if (k >= 2)
+                    for (int sl = 0; sl < kS && ok2; sl++)
+                        ok2 = wait_bar(&bars->b_empty[k & 1][sl], uint32_t(((k - 2) >> 1) & 1), wait_limit, fail);
+                if (gather_sync_or(kGatherThreads, !ok2)) break;
+                for (int sl = kS - 1; sl >= 0; sl--) {
                     for (int item = gt; item < tl.cnt * kPieces; item += kGatherThreads) {
                         const int c = item / kPieces, kg = item % kPieces;
                         const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + sl) * KD + kg * 8;
-                        cp_async16(dst + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
+                        cp_async16(Bt + sl * Sh::kBSlice + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
                     }
                     cp_async_commit();
                 }
-                if (sl + 1 <= kS - 1) {
-                    if (sl >= 0)
-                        asm volatile("cp.async.wait_group 1;" ::: "memory");
-                    else
-                        asm volatile("cp.async.wait_group 0;" ::: "memory");
+                const int nt = tile + gridDim.x;
+#pragma unroll
+                for (int j = 0; j < kS; j++) {
+                    cp_async_wait_pending(kS - 1 - j);   // slices kS-1 .. kS-1-j have landed
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     gather_sync(kGatherThreads);
-                    if (gt == 0) mbar_arrive(&bars->b_full[k & 1][sl + 1]);
+                    if (gt == 0) mbar_arrive(&bars->b_full[k & 1][kS - 1 - j]);
+                    // one step of the next tile's metadata chain per slice
+                    if (nt < gm.ntiles) {
+                        if (j == 0) {
+                            ntl = gm.tiles[nt];
+                        } else if (j == 1) {
+                            if (gt < ntl.cnt) ncol = gm.cols[ntl.p0 + gt];
+                        } else if (j == 2) {
+                            if (gt < ntl.cnt) nexp = gm.dexp[ncol.vec];
+                            have = true;
+                        }
+                    }
+                }
+            } else {
+                // one B buffer: two slices in flight, each issued once the
+                // previous tile's MMAs have released it; complete slice sl + 1
+                for (int sl = kS - 1; sl >= -1; sl--) {
+                    if (sl >= 0) {
+                        bool ok2 = true;
+                        if (k >= 1) ok2 = wait_bar(&bars->b_empty[0][sl], uint32_t((k - 1) & 1), wait_limit, fail);
+                        if (gather_sync_or(kGatherThreads, !ok2)) {
+                            stop = true;
+                            break;
+                        }
+                        for (int item = gt; item < tl.cnt * kPieces; item += kGatherThreads) {
+                            const int c = item / kPieces, kg = item % kPieces;
+                            const uint16_t *src = gm.dig + (size_t(M[c].vec) * kS + sl) * KD + kg * 8;
+                            cp_async16(Bt + sl * Sh::kBSlice + ((c >> 3) * kPieces + kg) * 128 + (c & 7) * 16, src);
+                        }
+                        cp_async_commit();
+                    }
+                    if (sl + 1 <= kS - 1) {
+                        cp_async_wait_pending(sl >= 0 ? 1 : 0);
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        gather_sync(kGatherThreads);
+                        if (gt == 0) mbar_arrive(&bars->b_full[k & 1][sl + 1]);
+                    }
                 }
             }
         }
