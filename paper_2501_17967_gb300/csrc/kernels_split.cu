@@ -447,7 +447,6 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
 
     if (warp == 0) {
         // ---------------- MMAs ----------------
-        const uint32_t idesc = umma_idesc(128, kN);
         const uint64_t adesc0 = umma_desc(smem_u32(As), 128, Sh::kASBO);
         const uint64_t bdesc0 = umma_desc(smem_u32(Bs), 128, Sh::kBSBO);
         long long G = 0, last_commit = -1;   // chunks consumed
@@ -475,7 +474,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                     const int a = chunk_digit(g / Sh::NKC, !last_job), kc = g % Sh::NKC;   // 0-based digit of A
                     const uint64_t ad = adesc0 + uint64_t(buf) * (Sh::kChunk >> 4);
                     const uint32_t first = (a == 0 && kc == 0) ? 0u : 1u;
-                    for (int b = kS - 1 - a; b >= 0; b--) {   // B digit slices, last-gathered slice last
+                    for (int b = kS - 1 - a; b >= 0; b--) {   // B digit slices 0 .. kS-1-a present
                         if (!(ready >> b & 1u)) {
                             if (!wait_bar(&bars->b_full[k & 1][b], uint32_t((k >> 1) & 1), wait_limit, fail)) {
                                 failed = true;
@@ -484,13 +483,15 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                             tc_fence_after();
                             ready |= 1u << b;
                         }
-                        const uint32_t dcol = tmem + uint32_t(r * kTmemBuf + (a + b) * kN);
-                        const uint64_t bd =
-                            bdesc0 + uint64_t(k % Sh::kBBuf) * (Sh::kBTile >> 4) + uint64_t(b) * (Sh::kBSlice >> 4) +
-                            uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
-                        umma_kchain_warp<Sh::KC / 16>(dcol, ad, bd, idesc, first);
                     }
                     if (failed) break;
+                    // slices 0 .. kS-1-a lie one after another (a (kS-a) kN-row B
+                    // operand) and feed levels a .. kS-1, adjacent TMEM column
+                    // blocks: one MMA chain of N = (kS - a) kN per chunk
+                    const uint32_t dcol = tmem + uint32_t(r * kTmemBuf + a * kN);
+                    const uint64_t bd = bdesc0 + uint64_t(k % Sh::kBBuf) * (Sh::kBTile >> 4) +
+                                        uint64_t(kc) * ((Sh::KC / 8) * 128 >> 4);
+                    umma_kchain_warp<Sh::KC / 16>(dcol, ad, bd, umma_idesc(128, (kS - a) * kN), first);
                     umma_commit_warp(&bars->mbar[buf]);
                     last_commit = G;
                     // in the tile's last job, slice kS-1-a is read by no later chunk
