@@ -185,7 +185,7 @@ STAGES = ("tensor_v", "clear", "upward", "m2l", "down_levels", "tensor_e", "leaf
 
 STAGE_KERNELS = {
     "tensor_v": "k_split_vec + k_split_gemm<256> (near field, leaf-to-expansion, X list)",
-    "clear": "memset",
+    "clear": "k_clear_flags",
     "upward": "k_up_levels",
     "m2l": "k_split_exp + k_split_gemm<64> (M2L per V pair; FP64 path: k_m2l_pairs + k_x_entries)",
     "down_levels": "k_down_levels",
@@ -442,14 +442,14 @@ def main():
                 "stages": per_stage}
 
     nl = st["nlevels"]
-    # kernels per apply (trees of more than three levels): upward pass, M2L,
-    # downward level pass, leaf output; FP64: M2L pairs + X-list products;
+    # kernels per apply (trees of more than three levels): flag clear, upward
+    # pass, M2L, downward level pass, leaf output; FP64: M2L pairs + X-list products;
     # split: input digits, group-V tensor launch (two with --overlap), M2L
     # digits + tensor launch, expansion digits + group-E tensor launch
     if head == bc.SPLIT_BF16:
-        launches_per_apply = 2 + (1 if args.overlap else 0) + 1 + 2 + 1 + 2 + 1
+        launches_per_apply = 2 + (1 if args.overlap else 0) + 1 + 1 + 2 + 1 + 2 + 1
     else:
-        launches_per_apply = 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1
+        launches_per_apply = 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1
     pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

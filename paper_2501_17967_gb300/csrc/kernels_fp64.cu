@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "bc_internal.h"
+#include "pdl.h"
 
 namespace bc {
 
@@ -66,6 +67,16 @@ __device__ __forceinline__ void flag_wait(const int32_t *f, int want, long long 
     }
 }
 
+// Zeroes the per-box flags of the persistent passes (a kernel, not a memset,
+// so that it takes part in the programmatic launch chain).
+__global__ void __launch_bounds__(256) k_clear_flags(int32_t *__restrict__ flag, int64_t n)
+{
+    griddep_wait();
+    griddep_launch_dependents();
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        flag[i] = 0;
+}
+
 // -------------------------------------------------------------------------
 // upward pass, one persistent launch:
 //   leaves: ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
@@ -87,6 +98,8 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, double2 *ex, int NP, int P1,
             const double *__restrict__ lvtab, bool climb, int32_t *flag, long long limit, int32_t *err)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     extern __shared__ double2 shu[];
     double2 *sc = shu;                                       // 4 * P1 children
     double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
@@ -206,6 +219,8 @@ k_m2l_pairs(int64_t npairs, const int32_t *__restrict__ v_box, const int32_t *__
             const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ Pv, int P1,
             int tri)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     const int P = P1 - 1;
     for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < npairs; e += int64_t(gridDim.x) * blockDim.x) {
         const int b = v_box[e], s = v_src[e], c = v_code[e];
@@ -260,6 +275,8 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
             const double2 *__restrict__ OpX, const double *__restrict__ xvec, double2 *__restrict__ PX, int NP,
             int P1, const double *__restrict__ lvtab)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     extern __shared__ double2 shx[];
     double2 *part = shx;                                     // [4][P1]
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
@@ -321,6 +338,8 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
               const int32_t *__restrict__ v_lsrc, const int32_t *__restrict__ v_code,
               const double *__restrict__ logd, int32_t *flag, long long limit, int32_t *err)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     extern __shared__ double2 sdn[];
     double2 *se = sdn;             // [P1] parent expansion
     double2 *part = sdn + P1;      // [4][P1] partial sums
@@ -450,6 +469,8 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const double *__restrict__ Pnear, const double *__restrict__ PE,
                            const double *__restrict__ PW)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     extern __shared__ double2 sh[];
     double2 *se = sh;                                  // P1
     double *sv = reinterpret_cast<double *>(sh + P1);  // NP
@@ -652,8 +673,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     }
     if (ev) cudaEventRecord(ev[1], st);
     // the per-box flags of the persistent passes start from zero
-    ce = cudaMemsetAsync(d.flag, 0, sizeof(int32_t) * size_t(h.box_level.size()), st);
-    if (ce != cudaSuccess) return ce;
+    {
+        const int64_t nf = int64_t(h.box_level.size());
+        ce = launch_pdl(k_clear_flags, grid_for((nf + 255) / 256, 152), 256, 0, st, d.flag, nf);
+        if (ce != cudaSuccess) return ce;
+    }
     if (ev) cudaEventRecord(ev[2], st);
     // flag polls go to L2 (several hundred cycles each): a sixteenth of the
     // mbarrier poll limit
@@ -667,15 +691,14 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const bool climb = far && h.nlevels > 3;
     if (opA || climb) {
         if (adj)
-            k_up_levels<true><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                             d.level_start, h.nlevels, d.box_child0, vin, opA,
-                                                             op.up, first, NP, P1, d.lvtab, climb, d.flag,
-                                                             glimit, a.err);
+            ce = launch_pdl(k_up_levels<true>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
+                            d.leaf_level, d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, first, NP, P1,
+                            d.lvtab, climb, d.flag, glimit, a.err);
         else
-            k_up_levels<false><<<a.up_blocks, 128, shU, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
-                                                              d.level_start, h.nlevels, d.box_child0, vin, opA,
-                                                              op.up, first, NP, P1, d.lvtab, climb, d.flag,
-                                                              glimit, a.err);
+            ce = launch_pdl(k_up_levels<false>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
+                            d.leaf_level, d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, first, NP, P1,
+                            d.lvtab, climb, d.flag, glimit, a.err);
+        if (ce != cudaSuccess) return ce;
     }
     if (ev) cudaEventRecord(ev[3], st);
     bool first_digits = false;   // digits of `first` taken (tensor-core M2L)
@@ -699,12 +722,13 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         } else if (npairs > 0) {
             const int grid = grid_for((npairs + 127) / 128, 152 * 24);
             const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
-#define BC_M2L(A, PM)                                                                                      \
-    k_m2l_pairs<A, PM><<<grid, 128, 0, st>>>(npairs, d.v_box, d.v_src, d.v_code, d.box_level, dsig, dpw, tb.logd, \
-                                             d.lvtab, first, d.Pv, P1, m2l_tri)
+#define BC_M2L(A, PM)                                                                                  \
+    ce = launch_pdl(k_m2l_pairs<A, PM>, grid, 128, 0, st, npairs, d.v_box, d.v_src, d.v_code, d.box_level, dsig, \
+                    dpw, tb.logd, d.lvtab, first, d.Pv, P1, m2l_tri)
             if (P1 <= 16) { if (adj) BC_M2L(true, 16); else BC_M2L(false, 16); }
             else { if (adj) BC_M2L(true, 32); else BC_M2L(false, 32); }
 #undef BC_M2L
+            if (ce != cudaSuccess) return ce;
         }
         const double2 *PX = nullptr;
         int px_stride = P1;
@@ -715,19 +739,20 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             const int64_t nx = int64_t(h.x_src.size());
             const size_t shX = sizeof(double2) * 4 * P1 + sizeof(double) * NP;
             if (adj)
-                k_x_entries<true><<<grid_for(nx, 152 * 16), 128, shX, st>>>(nx, d.x_box, d.x_src, d.x_code, d.box_level,
-                                                                            op.x, vin, d.PX, NP, P1, d.lvtab);
+                ce = launch_pdl(k_x_entries<true>, grid_for(nx, 152 * 16), 128, shX, st, nx, d.x_box, d.x_src,
+                                d.x_code, d.box_level, op.x, vin, d.PX, NP, P1, d.lvtab);
             else
-                k_x_entries<false><<<grid_for(nx, 152 * 16), 128, shX, st>>>(nx, d.x_box, d.x_src, d.x_code,
-                                                                             d.box_level, op.x, vin, d.PX, NP, P1,
-                                                                             d.lvtab);
+                ce = launch_pdl(k_x_entries<false>, grid_for(nx, 152 * 16), 128, shX, st, nx, d.x_box, d.x_src,
+                                d.x_code, d.box_level, op.x, vin, d.PX, NP, P1, d.lvtab);
+            if (ce != cudaSuccess) return ce;
             PX = d.PX;
         }
         if (ev) cudaEventRecord(ev[4], st);
-        k_down_levels<<<a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st>>>(
+        ce = launch_pdl(k_down_levels, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st,
             d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
             d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd,
             d.flag, glimit, a.err);
+        if (ce != cudaSuccess) return ce;
     } else if (ev) {
         cudaEventRecord(ev[4], st);
     }
@@ -756,15 +781,14 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const double *Pnear = (parts & 1) ? sp->Pnear : nullptr, *PE = (parts & 8) ? sp->PE : nullptr,
                  *PW = (parts & 16) ? sp->PW : nullptr;
     if (adj)
-        k_leaf_out<true><<<grid_leaf, NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp, d.w_src,
-                                                     d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t,
-                                                     tb.wvec, second, first, first, vin, vout, NP, P1, d.lvtab, far,
-                                                     Pnear, PE, PW);
+        ce = launch_pdl(k_leaf_out<true>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                        wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW);
     else
-        k_leaf_out<false><<<grid_leaf, NP, shD, st>>>(a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, wp,
-                                                      d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w,
-                                                      op.t, tb.wvec, second, first, first, vin, vout, NP, P1,
-                                                      d.lvtab, far, Pnear, PE, PW);
+        ce = launch_pdl(k_leaf_out<false>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
+                        wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW);
+    if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[7], st);
     return cudaGetLastError();
 }

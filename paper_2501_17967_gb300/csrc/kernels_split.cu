@@ -46,6 +46,7 @@
 #include <cmath>
 
 #include "bc_internal.h"
+#include "pdl.h"
 
 namespace bc {
 
@@ -292,6 +293,8 @@ __device__ __forceinline__ void digits_of(long long bits, int E, uint16_t *out, 
 __global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *__restrict__ v, double scale,
                                                    uint16_t *__restrict__ dig, int32_t *__restrict__ dexp)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     __shared__ int wmax[8];
     const int k = threadIdx.x;
     for (int64_t leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
@@ -318,6 +321,8 @@ __global__ void __launch_bounds__(256) k_split_exp(int64_t i0, int64_t i1, int64
                                                    int nreal, double scale, const double *__restrict__ escale,
                                                    uint16_t *__restrict__ dig, int32_t *__restrict__ dexp)
 {
+    griddep_wait();
+    griddep_launch_dependents();
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t i = i0 + ((blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5); i < i1; i += nw) {
@@ -444,6 +449,9 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = bars->tslot;
+    // tensor memory and barriers are set up: now wait for the inputs
+    griddep_wait();
+    griddep_launch_dependents();
 
     if (warp == 0) {
         // ---------------- MMAs ----------------
@@ -741,8 +749,7 @@ cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale
                                     cudaStream_t st)
 {
     if (nleaf <= 0) return cudaSuccess;
-    k_split_vec<<<int(std::min<int64_t>(nleaf, 152 * 16)), 256, 0, st>>>(nleaf, v, scale, dig, dexp);
-    return cudaGetLastError();
+    return launch_pdl(k_split_vec, int(std::min<int64_t>(nleaf, 152 * 16)), 256, 0, st, nleaf, v, scale, dig, dexp);
 }
 
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,
@@ -751,9 +758,8 @@ cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const 
 {
     if (i1 <= i0) return cudaSuccess;
     const int grid = int(std::min<int64_t>((i1 - i0 + 7) / 8, 152 * 16));
-    k_split_exp<<<grid, 256, 0, st>>>(i0, i1, nbox, reinterpret_cast<const double *>(ea),
-                                      reinterpret_cast<const double *>(eb), 2 * P1, scale, escale, dig, dexp);
-    return cudaGetLastError();
+    return launch_pdl(k_split_exp, grid, 256, 0, st, i0, i1, nbox, reinterpret_cast<const double *>(ea),
+                      reinterpret_cast<const double *>(eb), 2 * P1, scale, escale, dig, dexp);
 }
 
 cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int32_t *err, long long wait_limit,
@@ -764,12 +770,10 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
     int ie = 0;
     const int inv_alpha_exp = std::frexp(inv_alpha0, &ie) == 0.5 ? ie - 1 : kNoExp;
     if (kd == 256)
-        k_split_gemm<256><<<grid, kGemmThreads, GemmShape<256>::kSmem, st>>>(g, inv_alpha0, inv_alpha_exp, err,
-                                                                              wait_limit, withhold);
-    else
-        k_split_gemm<64><<<grid, kGemmThreads, kSmem64, st>>>(g, inv_alpha0, inv_alpha_exp, err, wait_limit,
-                                                              withhold);
-    return cudaGetLastError();
+        return launch_pdl(k_split_gemm<256>, grid, kGemmThreads, GemmShape<256>::kSmem, st, g, inv_alpha0,
+                          inv_alpha_exp, err, wait_limit, withhold);
+    return launch_pdl(k_split_gemm<64>, grid, kGemmThreads, size_t(kSmem64), st, g, inv_alpha0, inv_alpha_exp, err,
+                      wait_limit, withhold);
 }
 
 }  // namespace bc
