@@ -211,11 +211,13 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *     internal stream, concurrently with the FP64 far-field passes (1; on the
  *     20-Gaussian workload the passes then slow down as much as the launch
  *     saves).
- *   "debug_split_parts" (integer 0..63, default 63): diagnostics; which
+ *   "debug_split_parts" (integer 0..127, default 127): diagnostics; which
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,
- *     16 W list, 32 M2L translations; the last needs nterms <= 30); the
- *     others are evaluated in FP64.
+ *     16 W list, 32 M2L translations); the others are evaluated in FP64.
+ *     Bit 64: the shifts of the upward and downward level passes in
+ *     double-float arithmetic (pairs of FP32 numbers, about 48 bits) instead
+ *     of FP64.
  *   "debug_withhold_copy" (0/1, default 0): diagnostics; the split-precision
  *     kernel never starts its table copy, so its first wait runs out (tests of
  *     the timeout path).

@@ -144,6 +144,26 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
     os.field = p;
     UP2(leafA) UP2(up) UP2(par) UP2(v) UP2(x) UP2(e) UP2(w)
 #undef UP2
+    {
+        // double-float copies of the shift operators: x = hi + lo, hi the FP32
+        // rounding of x and lo that of the remainder
+        auto dfs = [](double x) {
+            const float h = float(x);
+            return std::make_pair(h, float(x - double(h)));
+        };
+        for (int which = 0; which < 2; which++) {
+            const std::vector<double2> &src = which ? b.par : b.up;
+            std::vector<float4> f(src.size());
+            for (size_t i = 0; i < src.size(); i++) {
+                const auto re = dfs(src[i].x), im = dfs(src[i].y);
+                f[i] = make_float4(re.first, re.second, im.first, im.second);
+            }
+            float4 *pf = nullptr;
+            e = dev_upload(dt.allocs, &pf, f.data(), f.size());
+            if (e != cudaSuccess) return cuda_fail(e, "tables upload");
+            (which ? os.par_df : os.up_df) = pf;
+        }
+    }
     e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
     os.t = q;

@@ -103,6 +103,9 @@ struct OpSet {
     const double2 *e = nullptr;       // [P1][NP]        expansion -> leaf nodes (real part)
     const double2 *w = nullptr;       // [kNumWX][P1][NP] expansion -> leaf nodes (W list)
     const double *t = nullptr;        // [kNumNear][NP][NP] near tables, element (j,k) at [k][j]
+    // up and par as double-float pairs {Re hi, Re lo, Im hi, Im lo} (each
+    // entry the sum of two FP32 numbers, about 48 significant bits)
+    const float4 *up_df = nullptr, *par_df = nullptr;
 };
 
 struct DevTables {
@@ -215,7 +218,9 @@ size_t split_smem_bytes(int kd);
 cudaError_t split_prepare();   // kernel attributes of the split path (before any capture)
 // parts: which products take the tensor-core results (bits: 1 near field,
 // 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list, 32 M2L); the others run in FP64.
-constexpr int kSplitAllParts = 63;
+// Bit 64: the shifts of the two level passes in double-float arithmetic on
+// the FP32 units instead of FP64.
+constexpr int kSplitAllParts = 127;
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;

@@ -78,6 +78,43 @@ __global__ void __launch_bounds__(256) k_clear_flags(int32_t *__restrict__ flag,
 }
 
 // -------------------------------------------------------------------------
+// Double-float arithmetic for the shifts of the split path.  GB300 runs FP64
+// at a small fraction of its FP32 rate, and the level passes are chains of
+// small products whose every step waits for FP64 issue.  A value is carried
+// as hi + lo (two FP32 numbers, about 48 significant bits); a product is made
+// exact with an FMA and added by an error-free two-sum, the rounding errors
+// gathering in lo.  Accuracy about 2^-46 of the sum of |terms|, far inside the
+// 2^-40 of the split products.  The explicitly rounded intrinsics keep the
+// compiler from contracting the error-free steps.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ float4 df4_of(double2 v)
+{
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, __double2float_rn(v.x - double(rh)), ih, __double2float_rn(v.y - double(ih)));
+}
+
+// (sh, sl) += (xh + xl)(yh + yl)
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float xh, float xl, float yh, float yl)
+{
+    const float pr = __fmul_rn(xh, yh);
+    const float e = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -pr)));
+    const float t = __fadd_rn(sh, pr);
+    const float v = __fsub_rn(t, sh);
+    const float r = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(pr, v));   // sh + pr = t + r
+    sl = __fadd_rn(sl, __fadd_rn(r, e));
+    sh = t;
+}
+
+// (re, im) += o * x for double-float complex numbers {Re hi, Re lo, Im hi, Im lo}
+__device__ __forceinline__ void df_cmac(float &rh, float &rl, float &ih, float &il, float4 o, float4 x)
+{
+    df_mac(rh, rl, o.x, o.y, x.x, x.y);
+    df_mac(rh, rl, -o.z, -o.w, x.z, x.w);
+    df_mac(ih, il, o.x, o.y, x.z, x.w);
+    df_mac(ih, il, o.z, o.w, x.x, x.y);
+}
+
+// -------------------------------------------------------------------------
 // upward pass, one persistent launch:
 //   leaves: ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
 //           forward (P2M): OpA = Q^T, s = r^2;  adjoint (L2P^H): OpA = E^H, s = 1
@@ -90,13 +127,14 @@ __global__ void __launch_bounds__(256) k_clear_flags(int32_t *__restrict__ flag,
 // the nodes, in a parent step warp q applies the operator of child q; the four
 // partial sums meet in shared memory.
 // -------------------------------------------------------------------------
-template <bool ADJ>
+template <bool ADJ, bool DF>
 __global__ void __launch_bounds__(128)
 k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
-            const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, double2 *ex, int NP, int P1,
-            const double *__restrict__ lvtab, bool climb, int32_t *flag, long long limit, int32_t *err)
+            const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, const float4 *__restrict__ OpUpDF,
+            double2 *ex, int NP, int P1, const double *__restrict__ lvtab, bool climb, int32_t *flag,
+            long long limit, int32_t *err)
 {
     griddep_wait();
     griddep_launch_dependents();
@@ -142,6 +180,32 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             if (threadIdx.x < 4 && (OpA || box_child0[c0 + threadIdx.x] >= 0))
                 flag_wait(&flag[c0 + threadIdx.x], 1, limit, err);
             __syncthreads();
+            if constexpr (DF) {
+                // double-float: the children in shared memory as {hi, lo} pairs
+                float4 *scf = reinterpret_cast<float4 *>(sc);
+                for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x)
+                    scf[i] = df4_of(__ldcg(&ex[int64_t(c0) * P1 + i]));
+                __syncthreads();
+                const float4 *op = OpUpDF + size_t(w) * P1 * P1;
+                const float4 *a = scf + w * P1;
+                for (int l = lane; l < P1; l += 32) {
+                    float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+                    for (int k0 = 0; k0 < P1; k0 += 8) {   // 8 operator loads in flight, two chains
+                        float4 o[8];
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            o[u] = k0 + u < P1 ? __ldg(&op[(k0 + u) * P1 + l]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < 8; u += 2) {
+                            if (k0 + u >= P1) break;
+                            df_cmac(r0h, r0l, i0h, i0l, o[u], a[k0 + u]);
+                            if (k0 + u + 1 < P1) df_cmac(r1h, r1l, i1h, i1l, o[u + 1], a[k0 + u + 1]);
+                        }
+                    }
+                    part[w * P1 + l] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
+                                                    (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
+                }
+            } else {
             for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
             __syncthreads();
             const double2 *op = OpUp + size_t(w) * P1 * P1;
@@ -164,6 +228,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                     }
                 }
                 part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
+            }
             }
             __syncthreads();
             for (int l = threadIdx.x; l < P1; l += blockDim.x) {
@@ -328,13 +393,15 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // warp w applies a quarter of the shift operator's columns (the shift chain
 // is the critical path, and one warp alone would serialise on its FP64 unit).
 // -------------------------------------------------------------------------
+template <bool DF>
 __global__ void __launch_bounds__(128)
 k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_t *__restrict__ v_ptr,
               const double2 *__restrict__ Pv, const int32_t *__restrict__ x_ptr, const int32_t *__restrict__ x_src,
               const double2 *__restrict__ PX, int px_stride, const int32_t *__restrict__ leaf_box,
               const double2 *__restrict__ first, const int32_t *__restrict__ parent,
               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
-              const double2 *__restrict__ OpPar, double2 *out, int P1, const double *__restrict__ lvtab,
+              const double2 *__restrict__ OpPar, const float4 *__restrict__ OpParDF, double2 *out, int P1,
+              const double *__restrict__ lvtab,
               const int32_t *__restrict__ v_lsrc, const int32_t *__restrict__ v_code,
               const double *__restrict__ logd, int32_t *flag, long long limit, int32_t *err)
 {
@@ -411,10 +478,34 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
             const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
             if (threadIdx.x == 0) flag_wait(&flag[pb], 2, limit, err);
             __syncthreads();
+            const int k0 = w * kq, k1 = min(P1, k0 + kq);
+            if constexpr (DF) {
+                float4 *sef = reinterpret_cast<float4 *>(se);   // the parent as double-float pairs
+                for (int i = threadIdx.x; i < P1; i += blockDim.x)
+                    sef[i] = df4_of(__ldcg(&out[int64_t(pb) * P1 + i]));
+                __syncthreads();
+                const float4 *op = OpParDF + size_t(q) * P1 * P1;
+                for (int o = lane; o < P1; o += 32) {
+                    float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+                    for (int kb = k0; kb < k1; kb += 8) {   // 8 operator loads in flight, two chains
+                        float4 wv[8];
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            wv[u] = kb + u < k1 ? __ldg(&op[(kb + u) * P1 + o]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                        for (int u = 0; u < 8; u += 2) {
+                            if (kb + u >= k1) break;
+                            df_cmac(r0h, r0l, i0h, i0l, wv[u], sef[kb + u]);
+                            if (kb + u + 1 < k1) df_cmac(r1h, r1l, i1h, i1l, wv[u + 1], sef[kb + u + 1]);
+                        }
+                    }
+                    part[w * P1 + o] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
+                                                    (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
+                }
+            } else {
             for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
             __syncthreads();
             const double2 *op = OpPar + size_t(q) * P1 * P1;
-            const int k0 = w * kq, k1 = min(P1, k0 + kq);
             for (int o = lane; o < P1; o += 32) {
                 double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
                 int k = k0;
@@ -431,6 +522,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                     im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
                 }
                 part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+            }
             }
             __syncthreads();
             if (w == 0) {
@@ -689,15 +781,15 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const int grid_leaf = grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16));
     const double2 *opA = (parts & 2) ? nullptr : op.leafA;
     const bool climb = far && h.nlevels > 3;
+    const bool dfp = (parts & 64) != 0;   // double-float shifts
     if (opA || climb) {
-        if (adj)
-            ce = launch_pdl(k_up_levels<true>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
-                            d.leaf_level, d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, first, NP, P1,
-                            d.lvtab, climb, d.flag, glimit, a.err);
-        else
-            ce = launch_pdl(k_up_levels<false>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
-                            d.leaf_level, d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, first, NP, P1,
-                            d.lvtab, climb, d.flag, glimit, a.err);
+#define BC_UP(A, D)                                                                                          \
+    launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
+               d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, op.up_df, first, NP, P1, d.lvtab, climb, \
+               d.flag, glimit, a.err)
+        if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
+        else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
+#undef BC_UP
         if (ce != cudaSuccess) return ce;
     }
     if (ev) cudaEventRecord(ev[3], st);
@@ -748,10 +840,13 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             PX = d.PX;
         }
         if (ev) cudaEventRecord(ev[4], st);
-        ce = launch_pdl(k_down_levels, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st,
-            d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent,
-            d.box_ix, d.box_iy, op.par, second, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd,
-            d.flag, glimit, a.err);
+#define BC_DOWN(D)                                                                                           \
+    launch_pdl(k_down_levels<D>, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st, d.level_start, h.nlevels, \
+               d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent, d.box_ix, d.box_iy, \
+               op.par, op.par_df, second, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd, d.flag, \
+               glimit, a.err)
+        ce = dfp ? BC_DOWN(true) : BC_DOWN(false);
+#undef BC_DOWN
         if (ce != cudaSuccess) return ce;
     } else if (ev) {
         cudaEventRecord(ev[4], st);
@@ -816,13 +911,24 @@ cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const size_t shU = sizeof(double) * NP + sizeof(double2) * 8 * P1;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false>, 128, shU);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true>, 128, shU);
+    // every block of a persistent pass must be resident: the smallest
+    // occupancy over the variants that share the grid
+    int bu2 = 0, bu3 = 0, bs2 = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false, false>, 128, shU);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true, false>, 128, shU);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu2, k_up_levels<false, true>, 128, shU);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu3, k_up_levels<true, true>, 128, shU);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels, 128, sizeof(double2) * (5 * P1 + 1));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels<false>, 128,
+                                                          sizeof(double2) * (5 * P1 + 1));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs2, k_down_levels<true>, 128,
+                                                          sizeof(double2) * (5 * P1 + 1));
     if (e != cudaSuccess) return e;
-    if (std::min(bu0, bu1) < 1 || bs < 1) return cudaErrorInvalidConfiguration;
-    *up_blocks = sms * std::min(up_per_sm, std::min(bu0, bu1));
+    const int bu = std::min(std::min(bu0, bu1), std::min(bu2, bu3));
+    bs = std::min(bs, bs2);
+    if (bu < 1 || bs < 1) return cudaErrorInvalidConfiguration;
+    *up_blocks = sms * std::min(up_per_sm, bu);
     *shift_blocks = sms * std::min(down_per_sm, bs);
     return cudaSuccess;
 }

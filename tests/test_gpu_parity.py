@@ -406,7 +406,7 @@ def test_split_parts_each_within_tolerance(ctx16, adaptive):
     gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
     u64, h64 = bc.apply(tree, f), bc.apply_adjoint(tree, gg)
     try:
-        for parts in (0, 1, 2, 4, 8, 16, 32):
+        for parts in (0, 1, 2, 4, 8, 16, 32, 64):
             ctx16.set_option("debug_split_parts", parts)
             us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
             hs = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
@@ -419,7 +419,7 @@ def test_split_parts_each_within_tolerance(ctx16, adaptive):
             print(f"split part {parts}: fwd {du:.2e} adj {dh:.2e}")
             assert 0.0 < du < TOL and 0.0 < dh < TOL, (parts, du, dh)
     finally:
-        ctx16.set_option("debug_split_parts", 63)
+        ctx16.set_option("debug_split_parts", 127)
 
 
 def test_split_overlap_gives_identical_results(ctx16, adaptive):
