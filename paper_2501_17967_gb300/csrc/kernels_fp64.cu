@@ -46,14 +46,13 @@ __device__ __forceinline__ int flag_load(const int32_t *f)
     return v;
 }
 
-// called by every thread of the block after the box's expansion is written
+// called by every thread of the block after the box's expansion is written:
+// the barrier orders the block's writes before thread 0's release store,
+// which makes them visible at GPU scope to a reader that acquires the flag
 __device__ __forceinline__ void flag_publish(int32_t *f, int v)
 {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
-    }
+    if (threadIdx.x == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(v) : "memory");
 }
 
 // the calling thread waits until *f >= want
