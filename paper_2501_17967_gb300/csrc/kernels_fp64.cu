@@ -545,6 +545,10 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
 //   forward: sE = 1, sW = 1, cW = log r_o, sN = r_s^2, cN = log r_s (aux = multipoles: A_0 = r^2 w.f / 2pi)
 //   adjoint: sE = r_o^2, sW = r_o^2, cW = r_o^2 log r_o w_j / 2pi, sN = r_o^2,
 //            cN = r_o^2 log r_o w_j / 2pi (aux = adjoint locals: B_0 = sum_i g_i)
+// The log terms factor per leaf (cW_j, and in the adjoint cN_j, do not depend
+// on the entry; in the forward apply cN = log r_s does not depend on j): the
+// first warp sums them over the W and near lists, one entry per lane, so the
+// products of the lists are plain streams of independent loads.
 // -------------------------------------------------------------------------
 template <bool ADJ>
 __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
@@ -565,6 +569,8 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
     extern __shared__ double2 sh[];
     double2 *se = sh;                                  // P1
     double *sv = reinterpret_cast<double *>(sh + P1);  // NP
+    __shared__ double s_log[2];
+    const int lane = threadIdx.x & 31;
     for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int o = order[li];
         const int lvo = leaf_level[o];
@@ -573,6 +579,29 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
         const double wj = wvec[j];
         // adjoint log term of a target leaf o: r_o^2 log(r_o) w_j / (2 pi)
         const double cO = ADJ ? r2o * lgo * wj * kInvTwoPi : lgo;
+        const int w0 = w_ptr[o], w1 = w_ptr[o + 1], n0 = n_ptr[o], n1 = n_ptr[o + 1];
+        __syncthreads();   // s_log of the previous leaf has been read
+        if (threadIdx.x < 32) {
+            // The log terms of the W and near sources, gathered by the first
+            // warp (one entry per lane) while the others start on the products:
+            //   lw = sum_W A_0(w)              (times cO below)
+            //   ln = sum_near log(r_s) A_0(s)  forward,  sum_near B_0(s) adjoint (times cO)
+            double lw = 0.0, ln = 0.0;
+            for (int e = w0 + lane; e < w1; e += 32) lw += src[int64_t(w_src[e]) * P1].x;
+            for (int e = n0 + lane; e < n1; e += 32) {
+                const int s = n_src[e];
+                const double a0 = aux[int64_t(leaf_box[s]) * P1].x;
+                ln += ADJ ? a0 : lvtab[kLvTab + leaf_level[s]] * a0;
+            }
+            for (int m = 16; m > 0; m >>= 1) {
+                lw += __shfl_xor_sync(0xffffffffu, lw, m);
+                ln += __shfl_xor_sync(0xffffffffu, ln, m);
+            }
+            if (lane == 0) {
+                s_log[0] = lw;
+                s_log[1] = ln;
+            }
+        }
         double acc = 0.0;
         if (far && lvo >= 2 && PE) {
             acc = PE[int64_t(o) * NP + j];   // split path: scaled L2P from the tensor cores
@@ -588,47 +617,42 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
             acc = ADJ ? r2o * s : s;
         }
         const double sW = ADJ ? r2o : 1.0;
-        const double cW = cO;
-        for (int e = w_ptr[o]; e < w_ptr[o + 1] && PW; e++)
-            acc = PW[size_t(e) * NP + j] + fma(cW, src[int64_t(w_src[e]) * P1].x, acc);
-        for (int e = w_ptr[o]; e < w_ptr[o + 1] && !PW; e++) {
-            const double2 *op = OpW + size_t(w_code[e]) * P1 * NP;
-            __syncthreads();
-            for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = src[int64_t(w_src[e]) * P1 + i];
-            __syncthreads();
-            double s = 0.0;
-            for (int k = 0; k < P1; k++) {
-                double2 opk = op[k * NP + j], b = se[k];
-                s = fma(opk.x, b.x, fma(-opk.y, b.y, s));
+        if (PW) {
+#pragma unroll 4
+            for (int e = w0; e < w1; e++) acc += PW[size_t(e) * NP + j];
+        } else {
+            for (int e = w0; e < w1; e++) {
+                const double2 *op = OpW + size_t(w_code[e]) * P1 * NP;
+                __syncthreads();
+                for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = src[int64_t(w_src[e]) * P1 + i];
+                __syncthreads();
+                double s = 0.0;
+                for (int k = 0; k < P1; k++) {
+                    double2 opk = op[k * NP + j], b = se[k];
+                    s = fma(opk.x, b.x, fma(-opk.y, b.y, s));
+                }
+                acc = fma(sW, s, acc);
             }
-            acc = fma(sW, s, fma(cW, se[0].x, acc));
         }
-        for (int e = n_ptr[o]; e < n_ptr[o + 1]; e++) {
-            const int s = n_src[e];
-            double t = 0.0;
-            if (Pnear) {
-                // split-precision result of this entry, alpha already applied
-                t = Pnear[size_t(e) * NP + j];
-            } else {
+        if (Pnear) {
+            // split-precision results of the entries, scale already applied
+#pragma unroll 4
+            for (int e = n0; e < n1; e++) acc += Pnear[size_t(e) * NP + j];
+        } else {
+            for (int e = n0; e < n1; e++) {
+                const int s = n_src[e];
                 const double *tb = T + size_t(n_tab[e]) * NP * NP;
                 __syncthreads();
                 for (int i = threadIdx.x; i < NP; i += blockDim.x) sv[i] = vnear[int64_t(s) * NP + i];
                 __syncthreads();
+                double t = 0.0;
                 for (int k = 0; k < NP; k++) t = fma(tb[k * NP + j], sv[k], t);
+                acc = fma(ADJ ? r2o : lvtab[leaf_level[s]], t, acc);
             }
-            double a0 = aux[int64_t(leaf_box[s]) * P1].x;
-            double sN, cN;
-            if (ADJ) {
-                sN = r2o;
-                cN = cO;
-            } else {
-                const int ls = leaf_level[s];
-                sN = lvtab[ls];
-                cN = lvtab[kLvTab + ls];
-            }
-            if (Pnear) sN = 1.0;
-            acc = fma(sN, t, fma(cN, a0, acc));
         }
+        __syncthreads();   // s_log written
+        acc = fma(cO, s_log[0], acc);
+        acc = ADJ ? fma(cO, s_log[1], acc) : acc + s_log[1];
         vout[int64_t(o) * NP + j] = acc;
     }
 }
