@@ -374,23 +374,24 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // -------------------------------------------------------------------------
 // down_levels: the local expansion (adjoint: multipole) of every box at
 // level >= 2, in one persistent launch:
-//   phase 1 (every box at once):
+//   the box's own sums:
 //     out[b] = sum_{e in V(b)} Pv[e] + sum_{x in X(b)} (PX[x] + log(r_c) A_0(c) e_0)
-//   phase 2 (levels 3, 4, ...; each box once its parent is published):
+//   then (levels 3, 4, ...; once the parent is published):
 //     out[b] += Par_q out[parent(b)]      (forward L2L, adjoint M2M^H)
-// Both phases give a block the same boxes (ascending index, so ascending
-// level): phase 2 of a box reads only its own block's phase-1 result and its
-// parent's flag; level-2 boxes are published at the end of phase 1.
+// A block takes its boxes in ascending index (so ascending level) and does
+// both steps for one box before the next, then publishes the box: the sums of
+// deep boxes overlap the chain of the shallower levels, and a box waits only
+// for its parent, a box of smaller index (so every wait ends).
 // The X-list log term uses coefficient 0 of the source leaf's own expansion
 // from the upward pass (forward A_0 = r_c^2 (w.f)/2pi, adjoint B_0 = sum_j g_j).
 // With v_lsrc non-null (M2L products from the tensor cores, which leave out
-// the log term) phase 1 adds it in FP64 as well:
+// the log term) the sums add it in FP64 as well:
 //     out[b][0] += sum_{e in V(b)} (log|d_e| + log r_b) first[s_e][0]
 // summed by the second warp (one pair per lane) while the first warp takes
 // the X list.
-// Four warps per block: in phase 1 warp w sums every fourth V pair, in phase 2
-// warp w applies a quarter of the shift operator's columns (the shift chain
-// is the critical path, and one warp alone would serialise on its FP64 unit).
+// Four warps per block: in the sums warp w takes every fourth V pair, in the
+// shift warp w applies a quarter of the shift operator's columns (the shift
+// chain is the critical path, and one warp alone would serialise on it).
 // -------------------------------------------------------------------------
 template <bool DF>
 __global__ void __launch_bounds__(128)
@@ -411,9 +412,12 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
     double2 *part = sdn + P1;      // [4][P1] partial sums
     double2 *slog = sdn + 5 * P1;  // [1] V-list log term
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kq = (P1 + 3) / 4;
+    const int o = lane;   // coefficient of this lane (P1 <= 32)
     for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
+        // ---- the box's own sums (V pairs, X entries, log terms)
         const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
-        for (int o = lane; o < P1; o += 32) {
+        if (o < P1) {
             double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
             int e = v0 + w;
             for (; e + 4 < v1; e += 8) {   // two loads in flight per warp step
@@ -441,42 +445,36 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                 re = fma(c0, a0.x, re);
                 im = fma(c0, a0.y, im);
             }
-            for (int s = 16; s > 0; s >>= 1) {
-                re += __shfl_xor_sync(0xffffffffu, re, s);
-                im += __shfl_xor_sync(0xffffffffu, im, s);
+            for (int m = 16; m > 0; m >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, m);
+                im += __shfl_xor_sync(0xffffffffu, im, m);
             }
             if (lane == 0) *slog = make_double2(re, im);
         }
         if (v_lsrc) __syncthreads();
-        if (w == 0) {
+        double2 acc = make_double2(0.0, 0.0);   // meaningful in warp 0, lanes o < P1
+        if (w == 0 && o < P1) {
             const double logrc = lvtab[kLvTab + lvb - 1];
-            for (int o = lane; o < P1; o += 32) {
-                const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
-                double re = (a0.x + a1.x) + (a2.x + a3.x), im = (a0.y + a1.y) + (a2.y + a3.y);
-                for (int x = x_ptr[b]; x < x_ptr[b + 1]; x++) {
-                    const double2 t = PX[int64_t(x) * px_stride + o];
-                    re += t.x;
-                    im += t.y;
-                    if (o == 0) re = fma(logrc, first[int64_t(leaf_box[x_src[x]]) * P1].x, re);
-                }
-                if (v_lsrc && o == 0) {
-                    re += slog->x;
-                    im += slog->y;
-                }
-                out[b * P1 + o] = make_double2(re, im);
+            const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
+            double re = (a0.x + a1.x) + (a2.x + a3.x), im = (a0.y + a1.y) + (a2.y + a3.y);
+            for (int x = x_ptr[b]; x < x_ptr[b + 1]; x++) {
+                const double2 t = PX[int64_t(x) * px_stride + o];
+                re += t.x;
+                im += t.y;
+                if (o == 0) re = fma(logrc, first[int64_t(leaf_box[x_src[x]]) * P1].x, re);
             }
+            if (v_lsrc && o == 0) {
+                re += slog->x;
+                im += slog->y;
+            }
+            acc = make_double2(re, im);
         }
-        if (b < level_start[3]) flag_publish(&flag[b], 2);
-        __syncthreads();
-    }
-    const int kq = (P1 + 3) / 4;
-    if (nlevels > 3) {
-        for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
-            if (b < level_start[3]) continue;   // level 2: no parent shift
+        // ---- plus the parent's expansion shifted to this box (levels >= 3)
+        if (lvb >= 3) {
             const int pb = parent[b];
             const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
             if (threadIdx.x == 0) flag_wait(&flag[pb], 2, limit, err);
-            __syncthreads();
+            __syncthreads();   // also: warp 0 has read its partial sums
             const int k0 = w * kq, k1 = min(P1, k0 + kq);
             if constexpr (DF) {
                 float4 *sef = reinterpret_cast<float4 *>(se);   // the parent as double-float pairs
@@ -484,7 +482,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                     sef[i] = df4_of(__ldcg(&out[int64_t(pb) * P1 + i]));
                 __syncthreads();
                 const float4 *op = OpParDF + size_t(q) * P1 * P1;
-                for (int o = lane; o < P1; o += 32) {
+                if (o < P1) {
                     float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
                     for (int kb = k0; kb < k1; kb += 8) {   // 8 operator loads in flight, two chains
                         float4 wv[8];
@@ -502,38 +500,37 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                                                     (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
                 }
             } else {
-            for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
+                for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
+                __syncthreads();
+                const double2 *op = OpPar + size_t(q) * P1 * P1;
+                if (o < P1) {
+                    double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+                    int k = k0;
+                    for (; k + 1 < k1; k += 2) {
+                        const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k], w1 = __ldg(&op[(k + 1) * P1 + o]),
+                                      a1 = se[k + 1];
+                        re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
+                        im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
+                        re1 = fma(w1.x, a1.x, fma(-w1.y, a1.y, re1));
+                        im1 = fma(w1.x, a1.y, fma(w1.y, a1.x, im1));
+                    }
+                    if (k < k1) {
+                        const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k];
+                        re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
+                        im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
+                    }
+                    part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+                }
+            }
             __syncthreads();
-            const double2 *op = OpPar + size_t(q) * P1 * P1;
-            for (int o = lane; o < P1; o += 32) {
-                double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-                int k = k0;
-                for (; k + 1 < k1; k += 2) {
-                    const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k], w1 = __ldg(&op[(k + 1) * P1 + o]), a1 = se[k + 1];
-                    re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
-                    im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
-                    re1 = fma(w1.x, a1.x, fma(-w1.y, a1.y, re1));
-                    im1 = fma(w1.x, a1.y, fma(w1.y, a1.x, im1));
-                }
-                if (k < k1) {
-                    const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k];
-                    re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
-                    im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
-                }
-                part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+            if (w == 0 && o < P1) {
+                const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
+                acc.x += (a0.x + a1.x) + (a2.x + a3.x);
+                acc.y += (a0.y + a1.y) + (a2.y + a3.y);
             }
-            }
-            __syncthreads();
-            if (w == 0) {
-                for (int o = lane; o < P1; o += 32) {
-                    const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
-                    const double2 cur = __ldcg(&out[b * P1 + o]);
-                    out[b * P1 + o] = make_double2(cur.x + ((a0.x + a1.x) + (a2.x + a3.x)),
-                                                   cur.y + ((a0.y + a1.y) + (a2.y + a3.y)));
-                }
-            }
-            flag_publish(&flag[b], 2);
         }
+        if (w == 0 && o < P1) out[b * P1 + o] = acc;
+        flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
     }
 }
 
