@@ -387,11 +387,11 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // With v_lsrc non-null (M2L products from the tensor cores, which leave out
 // the log term) the sums add it in FP64 as well:
 //     out[b][0] += sum_{e in V(b)} (log|d_e| + log r_b) first[s_e][0]
-// summed by the second warp (one pair per lane) while the first warp takes
-// the X list.
-// Four warps per block: in the sums warp w takes every fourth V pair, in the
-// shift warp w applies a quarter of the shift operator's columns (the shift
-// chain is the critical path, and one warp alone would serialise on it).
+// Four warps per block.  The sums run side by side: warp 0 the X list (its
+// log term gathered one entry per lane), warp 1 the V-list log term (one pair
+// per lane), warps 2 and 3 the V pairs.  In the shift warp w applies a quarter
+// of the operator's columns, fetched into registers before the wait for the
+// parent (the shift chain is the critical path).
 // -------------------------------------------------------------------------
 template <bool DF>
 __global__ void __launch_bounds__(128)
@@ -410,91 +410,109 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
     extern __shared__ double2 sdn[];
     double2 *se = sdn;             // [P1] parent expansion
     double2 *part = sdn + P1;      // [4][P1] partial sums
-    double2 *slog = sdn + 5 * P1;  // [1] V-list log term
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int kq = (P1 + 3) / 4;
+    const int kq = (P1 + 3) / 4, k0 = w * kq, k1 = min(P1, k0 + kq);   // this warp's shift columns (<= 8)
     const int o = lane;   // coefficient of this lane (P1 <= 32)
     for (int64_t b = level_start[2] + blockIdx.x; b < level_start[nlevels]; b += gridDim.x) {
-        // ---- the box's own sums (V pairs, X entries, log terms)
-        const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
-        if (o < P1) {
-            double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-            int e = v0 + w;
-            for (; e + 4 < v1; e += 8) {   // two loads in flight per warp step
-                const double2 t0 = Pv[int64_t(e) * P1 + o], t1 = Pv[int64_t(e + 4) * P1 + o];
-                re0 += t0.x;
-                im0 += t0.y;
+        const int lvb = lv_of(level_start, nlevels, b);
+        const bool shift = lvb >= 3;
+        const int pb = shift ? parent[b] : 0;
+        const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+        // the shift operator does not depend on the parent's values: fetched
+        // before the wait for them
+        float4 wf[8];
+        double2 wd[8];
+        if (shift && o < P1) {
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if constexpr (DF) {
+                    wf[u] = k0 + u < k1 ? __ldg(&OpParDF[(size_t(q) * P1 + k0 + u) * P1 + o])
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+                } else {
+                    wd[u] = k0 + u < k1 ? __ldg(&OpPar[(size_t(q) * P1 + k0 + u) * P1 + o]) : make_double2(0.0, 0.0);
+                }
+            }
+        }
+        // ---- the box's own sums, one kind per warp: warp 0 the X list and
+        // its log term, warp 1 the log term of the V list (tensor-core M2L),
+        // warps 2 and 3 the V pairs
+        double re = 0.0, im = 0.0;
+        if (w == 0) {
+            const int x0 = x_ptr[b], x1 = x_ptr[b + 1];
+            if (o < P1) {
+#pragma unroll 4
+                for (int x = x0; x < x1; x++) {
+                    const double2 t = PX[int64_t(x) * px_stride + o];
+                    re += t.x;
+                    im += t.y;
+                }
+            }
+            double lx = 0.0;
+            for (int x = x0 + lane; x < x1; x += 32) lx += first[int64_t(leaf_box[x_src[x]]) * P1].x;
+            for (int m = 16; m > 0; m >>= 1) lx += __shfl_xor_sync(0xffffffffu, lx, m);
+            if (o == 0) re = fma(lvtab[kLvTab + lvb - 1], lx, re);
+        } else if (w == 1) {
+            if (v_lsrc) {
+                const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
+                const double lgb = lvtab[kLvTab + lvb];
+                double lr = 0.0, li = 0.0;
+                for (int e = v0 + lane; e < v1; e += 32) {
+                    const double2 a0 = first[int64_t(v_lsrc[e]) * P1];
+                    const double c0 = logd[v_code[e]] + lgb;
+                    lr = fma(c0, a0.x, lr);
+                    li = fma(c0, a0.y, li);
+                }
+                for (int m = 16; m > 0; m >>= 1) {
+                    lr += __shfl_xor_sync(0xffffffffu, lr, m);
+                    li += __shfl_xor_sync(0xffffffffu, li, m);
+                }
+                if (o == 0) {
+                    re = lr;
+                    im = li;
+                }
+            }
+        } else if (o < P1) {
+            const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
+            double re1 = 0.0, im1 = 0.0;
+            int e = v0 + (w - 2);
+            for (; e + 2 < v1; e += 4) {   // two loads in flight per step
+                const double2 t0 = Pv[int64_t(e) * P1 + o], t1 = Pv[int64_t(e + 2) * P1 + o];
+                re += t0.x;
+                im += t0.y;
                 re1 += t1.x;
                 im1 += t1.y;
             }
             if (e < v1) {
                 const double2 t0 = Pv[int64_t(e) * P1 + o];
-                re0 += t0.x;
-                im0 += t0.y;
+                re += t0.x;
+                im += t0.y;
             }
-            part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+            re += re1;
+            im += im1;
         }
+        if (o < P1) part[w * P1 + o] = make_double2(re, im);
         __syncthreads();
-        const int lvb = lv_of(level_start, nlevels, b);
-        if (v_lsrc && w == 1) {
-            const double lgb = lvtab[kLvTab + lvb];
-            double re = 0.0, im = 0.0;
-            for (int e = v0 + lane; e < v1; e += 32) {
-                const double2 a0 = first[int64_t(v_lsrc[e]) * P1];
-                const double c0 = logd[v_code[e]] + lgb;
-                re = fma(c0, a0.x, re);
-                im = fma(c0, a0.y, im);
-            }
-            for (int m = 16; m > 0; m >>= 1) {
-                re += __shfl_xor_sync(0xffffffffu, re, m);
-                im += __shfl_xor_sync(0xffffffffu, im, m);
-            }
-            if (lane == 0) *slog = make_double2(re, im);
-        }
-        if (v_lsrc) __syncthreads();
         double2 acc = make_double2(0.0, 0.0);   // meaningful in warp 0, lanes o < P1
         if (w == 0 && o < P1) {
-            const double logrc = lvtab[kLvTab + lvb - 1];
             const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
-            double re = (a0.x + a1.x) + (a2.x + a3.x), im = (a0.y + a1.y) + (a2.y + a3.y);
-            for (int x = x_ptr[b]; x < x_ptr[b + 1]; x++) {
-                const double2 t = PX[int64_t(x) * px_stride + o];
-                re += t.x;
-                im += t.y;
-                if (o == 0) re = fma(logrc, first[int64_t(leaf_box[x_src[x]]) * P1].x, re);
-            }
-            if (v_lsrc && o == 0) {
-                re += slog->x;
-                im += slog->y;
-            }
-            acc = make_double2(re, im);
+            acc = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
         }
         // ---- plus the parent's expansion shifted to this box (levels >= 3)
-        if (lvb >= 3) {
-            const int pb = parent[b];
-            const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+        if (shift) {
             if (threadIdx.x == 0) flag_wait(&flag[pb], 2, limit, err);
             __syncthreads();   // also: warp 0 has read its partial sums
-            const int k0 = w * kq, k1 = min(P1, k0 + kq);
             if constexpr (DF) {
                 float4 *sef = reinterpret_cast<float4 *>(se);   // the parent as double-float pairs
                 for (int i = threadIdx.x; i < P1; i += blockDim.x)
                     sef[i] = df4_of(__ldcg(&out[int64_t(pb) * P1 + i]));
                 __syncthreads();
-                const float4 *op = OpParDF + size_t(q) * P1 * P1;
                 if (o < P1) {
                     float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
-                    for (int kb = k0; kb < k1; kb += 8) {   // 8 operator loads in flight, two chains
-                        float4 wv[8];
 #pragma unroll
-                        for (int u = 0; u < 8; u++)
-                            wv[u] = kb + u < k1 ? __ldg(&op[(kb + u) * P1 + o]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                        for (int u = 0; u < 8; u += 2) {
-                            if (kb + u >= k1) break;
-                            df_cmac(r0h, r0l, i0h, i0l, wv[u], sef[kb + u]);
-                            if (kb + u + 1 < k1) df_cmac(r1h, r1l, i1h, i1l, wv[u + 1], sef[kb + u + 1]);
-                        }
+                    for (int u = 0; u < 8; u += 2) {   // two chains
+                        if (k0 + u >= k1) break;
+                        df_cmac(r0h, r0l, i0h, i0l, wf[u], sef[k0 + u]);
+                        if (k0 + u + 1 < k1) df_cmac(r1h, r1l, i1h, i1l, wf[u + 1], sef[k0 + u + 1]);
                     }
                     part[w * P1 + o] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
                                                     (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
@@ -502,22 +520,19 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
             } else {
                 for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
                 __syncthreads();
-                const double2 *op = OpPar + size_t(q) * P1 * P1;
                 if (o < P1) {
                     double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-                    int k = k0;
-                    for (; k + 1 < k1; k += 2) {
-                        const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k], w1 = __ldg(&op[(k + 1) * P1 + o]),
-                                      a1 = se[k + 1];
-                        re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
-                        im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
-                        re1 = fma(w1.x, a1.x, fma(-w1.y, a1.y, re1));
-                        im1 = fma(w1.x, a1.y, fma(w1.y, a1.x, im1));
-                    }
-                    if (k < k1) {
-                        const double2 w0 = __ldg(&op[k * P1 + o]), a0 = se[k];
-                        re0 = fma(w0.x, a0.x, fma(-w0.y, a0.y, re0));
-                        im0 = fma(w0.x, a0.y, fma(w0.y, a0.x, im0));
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        if (k0 + u >= k1) break;
+                        const double2 a0 = se[k0 + u];
+                        re0 = fma(wd[u].x, a0.x, fma(-wd[u].y, a0.y, re0));
+                        im0 = fma(wd[u].x, a0.y, fma(wd[u].y, a0.x, im0));
+                        if (k0 + u + 1 < k1) {
+                            const double2 a1 = se[k0 + u + 1];
+                            re1 = fma(wd[u + 1].x, a1.x, fma(-wd[u + 1].y, a1.y, re1));
+                            im1 = fma(wd[u + 1].x, a1.y, fma(wd[u + 1].y, a1.x, im1));
+                        }
                     }
                     part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
                 }
