@@ -142,7 +142,8 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
     double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nq = NP / 4;
+    // leaf step: warp w sums the nodes [j0, j1) (any number of nodes)
+    const int nq = (NP + 3) / 4, j0 = min(NP, w * nq), j1 = min(NP, j0 + nq);
     for (int64_t li = blockIdx.x; OpA && li < nleaf; li += gridDim.x) {
         const int leaf = order[li];
         const int b = leaf_box[leaf];
@@ -152,12 +153,18 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         __syncthreads();
         for (int l = lane; l < P1; l += 32) {
             double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-            for (int j = w * nq; j < (w + 1) * nq; j += 2) {
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
                 double2 o0 = OpA[j * P1 + l], o1 = OpA[(j + 1) * P1 + l];
                 re0 = fma(o0.x, sv[j], re0);
                 im0 = fma(o0.y, sv[j], im0);
                 re1 = fma(o1.x, sv[j + 1], re1);
                 im1 = fma(o1.y, sv[j + 1], im1);
+            }
+            if (j < j1) {
+                double2 o0 = OpA[j * P1 + l];
+                re0 = fma(o0.x, sv[j], re0);
+                im0 = fma(o0.y, sv[j], im0);
             }
             part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
         }
@@ -344,7 +351,8 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
     extern __shared__ double2 shx[];
     double2 *part = shx;                                     // [4][P1]
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nq = NP / 4;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nq = (NP + 3) / 4, j0 = min(NP, w * nq), j1 = min(NP, j0 + nq);   // warp w's nodes
     for (int64_t e = blockIdx.x; e < nx; e += gridDim.x) {
         const int c = x_src[e];
         const double2 *op = OpX + size_t(x_code[e]) * NP * P1;
@@ -354,12 +362,18 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
         __syncthreads();
         for (int l = lane; l < P1; l += 32) {
             double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-            for (int j = w * nq; j < (w + 1) * nq; j += 2) {
+            int j = j0;
+            for (; j + 1 < j1; j += 2) {
                 double2 o0 = op[j * P1 + l], o1 = op[(j + 1) * P1 + l];
                 re0 = fma(o0.x, sv[j], re0);
                 im0 = fma(o0.y, sv[j], im0);
                 re1 = fma(o1.x, sv[j + 1], re1);
                 im1 = fma(o1.y, sv[j + 1], im1);
+            }
+            if (j < j1) {
+                double2 o0 = op[j * P1 + l];
+                re0 = fma(o0.x, sv[j], re0);
+                im0 = fma(o0.y, sv[j], im0);
             }
             part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
         }

@@ -119,6 +119,33 @@ def test_adaptive_full(ctx16, adaptive):
     assert err < TOL, err
 
 
+@pytest.mark.parametrize("p", [6, 9])
+def test_fp64_node_counts_not_multiple_of_eight(p):
+    """Orders whose node count does not split evenly over the four warps of the
+    leaf-to-expansion and X-list products (p = 6: 36 nodes, 9 per warp; p = 9:
+    81 nodes): FP64 apply on an adaptive tree with W and X lists against the
+    oracle, and the adjoint identity <A f, g> = <f, A^T g>."""
+    ctx = bc.Context(p=p, device=0)
+    g = synth.gaussians(8, 21, wlog10=(-2.3, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, kappa=1.0, max_level=7)
+    tree, geom, fvals, f = make(ctx, lv, ix, iy, g)
+    s = tree.stats()
+    assert s["n_w"] > 0 and s["n_x"] > 0
+    u = bc.apply(tree, f)
+    un = u.cpu().numpy().reshape(-1, p * p)
+    pick = synth.sample_leaves_per_level(np.asarray(lv), 2, seed=4)
+    ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
+    err = relerr(un[pick], ref)
+    print(f"p = {p}: FP64 rel err {err:.3e}")
+    assert err < TOL, err
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    lhs = torch.dot(u.ravel(), gg.ravel()).item()
+    rhs = torch.dot(f.ravel(), bc.apply_adjoint(tree, gg).ravel()).item()
+    scale = (u.abs() * gg.abs()).sum().item()
+    assert abs(lhs - rhs) <= 1e-13 * scale, (lhs, rhs, scale)
+
+
 def test_adaptive_near_and_far_split(ctx16, adaptive):
     """near-only + far-only applies add up to the full apply (linearity of the passes)."""
     lv, ix, iy, g, tree, geom, fvals, f = adaptive
