@@ -206,11 +206,11 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *   "wait_limit" (default 2^26): polls of each bounded device-side wait of the
  *     split-precision kernel before it gives up, records the failure (reported
  *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns.
- *   "split_overlap" (0/1, default 0): the near-field tensor-core launch of a
- *     split-precision apply runs in line on the apply's stream (0) or on an
- *     internal stream, concurrently with the FP64 far-field passes (1; on the
- *     20-Gaussian workload the passes then slow down as much as the launch
- *     saves).
+ *   "split_overlap" (0/1, default 1): the near-field tensor-core launch of a
+ *     split-precision apply runs on an internal stream, concurrently with the
+ *     far-field passes, and is joined before the leaf output (1), or in line
+ *     on the apply's stream (0).  The level passes are latency-bound chains
+ *     that leave most SMs idle, so the near field mostly hides behind them.
  *   "debug_split_parts" (integer 0..127, default 127): diagnostics; which
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,

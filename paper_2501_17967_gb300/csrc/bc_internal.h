@@ -306,7 +306,7 @@ struct bc_ctx {
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
     int split_parts = bc::kSplitAllParts;   // diagnostics: split-precision products in use
-    int split_overlap = 0;      // near-field tensor launch on the side stream (1) or inline (0)
+    int split_overlap = 1;      // near-field tensor launch on the side stream (1) or inline (0)
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumEvents] = {};   // [forward, adjoint]
     bc::SideStream side;
