@@ -229,7 +229,7 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
  * event at each stage boundary:
  *   0 tensor group V, far part (split precision: digits of the input,
- *     leaf-to-expansion, X list), 1 barrier reset, 2 upward pass (FP64: with
+ *     leaf-to-expansion, X list), 1 flag clearing, 2 upward pass (FP64: with
  *     the leaf-to-expansion step), 3 M2L per V pair (FP64 path: and the X-list
  *     products), 4 downward level pass (sums, shifts), 5 tensor group E
  *     (split precision: digits of the expansions, expansion-to-leaf and W
