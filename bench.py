@@ -185,21 +185,21 @@ STAGES = ("tensor_v", "clear", "upward", "m2l", "down_levels", "tensor_e", "leaf
 
 
 STAGE_KERNELS = {
-    "tensor_v": "k_split_vec + k_split_gemm<256> (leaf-to-expansion, X list; near field too with --no-overlap)",
+    "tensor_v": "k_split_vec + k_split_gemm<256> (leaf-to-expansion; X list and near field too with --no-overlap)",
     "clear": "k_clear_flags",
     "upward": "k_up_levels",
     "m2l": "k_split_exp + k_split_gemm<64> (M2L per V pair; FP64 path: k_m2l_pairs + k_x_entries)",
     "down_levels": "k_down_levels",
     "tensor_e": "k_split_exp + k_split_gemm<64>",
     "leaf_output": "k_leaf_out",
-    "tensor_near": "k_split_gemm<256> (near field, on the internal stream beside stages 1-4)",
+    "tensor_near": "k_split_gemm<256> (X list, then near field, on the internal stream beside stages 1-4)",
 }
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
 # main kernel (cold cache), keyed by (workload, nterms, split): the launch
 # list of the bench configuration (profiles/launches_adaptive20_split.md)
 TRAFFIC = {
-    ("adaptive20", 24, True): {"tensor_v": 6.11e6, "tensor_near": 25.30e6, "upward": 0.59e6, "m2l": 2.95e6,
-                               "down_levels": 13.68e6, "tensor_e": 5.27e6, "leaf_output": 32.39e6},
+    ("adaptive20", 24, True): {"upward": 0.59e6, "m2l": 2.95e6, "down_levels": 13.68e6, "tensor_e": 5.27e6,
+                               "leaf_output": 32.39e6},
 }
 
 
@@ -418,6 +418,11 @@ def main():
         # one group-V tensor launch (near field included) in stage 0
         wk["tensor_v"] = (wk["tensor_v"][0] + wk["tensor_near"][0], "tensor")
         wk["tensor_near"] = (0.0, "tensor")
+    elif head == bc.SPLIT_BF16:
+        # the X-list tiles run on the internal stream, before the near field
+        xw = 15 * 2.0 * 256 * 2 * P1 * st["n_x"]
+        wk["tensor_v"] = (wk["tensor_v"][0] - xw, "tensor")
+        wk["tensor_near"] = (wk["tensor_near"][0] + xw, "tensor")
     # DRAM bytes per launch (read + write) from the ncu capture of this
     # configuration (profiles/kernels_adaptive20_split.md); null elsewhere
     traffic = TRAFFIC.get((args.workload, P1, head == bc.SPLIT_BF16), {})
@@ -464,7 +469,7 @@ def main():
     # split: input digits, group-V tensor launch (two when the near field runs apart), M2L
     # digits + tensor launch, expansion digits + group-E tensor launch
     if head == bc.SPLIT_BF16:
-        launches_per_apply = 2 + (1 if args.overlap else 0) + 1 + 1 + 2 + 1 + 2 + 1
+        launches_per_apply = 2 + (2 if args.overlap else 0) + 1 + 1 + 2 + 1 + 2 + 1
     else:
         launches_per_apply = 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1
     pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}

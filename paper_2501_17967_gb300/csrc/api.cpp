@@ -456,7 +456,8 @@ bc_status build_split_tables(bc_ctx *ctx)
     if (!ctx->side.side) {
         if ((e = cudaStreamCreateWithFlags(&ctx->side.side, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&ctx->side.fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&ctx->side.join, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ctx->side.xdone, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(e, "split side stream");
     }
     ctx->split_ready = true;
@@ -543,6 +544,7 @@ bc_status build_split_tree(bc_tree *t)
             cl.push_back(c);
         }
         V.add(T.leafA_op[dir], cl);
+        s.ntA[dir] = int(V.tiles.size());
         std::vector<std::vector<SplitCol>> by_code(kNumWX);
         for (int64_t k = 0; k < nx; k++) {
             SplitCol c;
@@ -801,6 +803,7 @@ void bc_destroy(bc_ctx *ctx)
             if (e) cudaEventDestroy(e);
     if (ctx->side.fork) cudaEventDestroy(ctx->side.fork);
     if (ctx->side.join) cudaEventDestroy(ctx->side.join);
+    if (ctx->side.xdone) cudaEventDestroy(ctx->side.xdone);
     if (ctx->side.side) cudaStreamDestroy(ctx->side.side);
     free_all(ctx->dt.allocs);
     free_all(ctx->split_allocs);

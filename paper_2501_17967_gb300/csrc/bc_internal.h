@@ -204,6 +204,7 @@ struct SplitTree {
     SplitTile *tV[2] = {}, *tN[2] = {}, *tVN[2] = {}, *tE[2] = {}, *tM[2] = {};
     SplitCol *cV[2] = {}, *cN[2] = {}, *cVN[2] = {}, *cE[2] = {}, *cM[2] = {};
     int ntV[2] = {}, ntN[2] = {}, ntVN[2] = {}, ntE[2] = {}, ntM[2] = {};
+    int ntA[2] = {};   // the first ntA tiles of tV: leaf-to-expansion (the rest: X list)
     double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
     double *PX = nullptr;         // [n_x][64] X-list result per entry
     double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf
@@ -282,6 +283,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 struct SideStream {
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    cudaEvent_t xdone = nullptr;   // the X-list tiles (first on the side stream) are done
 };
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)

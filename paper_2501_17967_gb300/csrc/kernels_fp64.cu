@@ -776,8 +776,9 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (split) {
         // tensor group V: digits of alpha0 * vin; the near field into Pnear,
         // leafA (P2M / L2P^H) into `first` and the X list into PX, in one
-        // launch, or (split_overlap) the near field on the side stream,
-        // joined before the leaf output
+        // launch, or (split_overlap) leafA in line and the X list and the near
+        // field on the side stream (joined before the downward pass and
+        // before the leaf output)
         ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
         if (ce != cudaSuccess) return ce;
         SplitGemm g;
@@ -795,13 +796,20 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                 cudaEventRecord(ev[9], st);
             }
         } else {
-            g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir];
-            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
-            if (ce != cudaSuccess) return ce;
+            // in line only the leaf-to-expansion tiles (the upward pass needs
+            // them next); on the internal stream the X-list tiles (needed by
+            // the downward pass, which waits for xdone) and the near field
             if ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
                 (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess)
                 return ce;
+            g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntA[dir];
+            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            if (ce != cudaSuccess) return ce;
             if (ev) cudaEventRecord(ev[8], sd->side);
+            g.tiles = sp->tV[dir] + sp->ntA[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
+            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+            if (ce != cudaSuccess) return ce;
+            if ((ce = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return ce;
             g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
             ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
             if (ce != cudaSuccess) return ce;
@@ -889,6 +897,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             PX = d.PX;
         }
         if (ev) cudaEventRecord(ev[4], st);
+        // the X-list products come from the internal stream
+        if (split && split->side && (ce = cudaStreamWaitEvent(st, split->side->xdone, 0)) != cudaSuccess) return ce;
 #define BC_DOWN(D)                                                                                           \
     launch_pdl(k_down_levels<D>, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st, d.level_start, h.nlevels, \
                d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent, d.box_ix, d.box_iy, \
