@@ -211,6 +211,10 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *     far-field passes, and is joined before the leaf output (1), or in line
  *     on the apply's stream (0).  The level passes are latency-bound chains
  *     that leave most SMs idle, so the near field mostly hides behind them.
+ *   "split_overlap_ctas" (integer >= 0, default 0): CTAs (one per SM) of
+ *     that near-field launch; 0 takes three quarters of the SMs, which leaves
+ *     the rest to the level passes undisturbed (on the 20-Gaussian workload
+ *     76 to 152 CTAs are within 1%, 40 to 56 about 5% slower).
  *   "debug_split_parts" (integer 0..127, default 127): diagnostics; which
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,

@@ -642,7 +642,8 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     PassArgs a = pass_args(ctx, tree);
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
-    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr};
+    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr,
+                   ctx->overlap_ctas > 0 ? ctx->overlap_ctas : std::max(1, 3 * split_sm_count() / 4)};
     const SplitLaunch *split = nullptr;
     bc_tree *tw = const_cast<bc_tree *>(tree);
     if (prec == BC_SPLIT_BF16) {
@@ -722,7 +723,8 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     PassArgs a = pass_args(ctx, b->u);
     a.leaf_bps = leaf_bps;
     a.m2l_bps = m2l_bps;
-    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr};
+    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr,
+                   ctx->overlap_ctas > 0 ? ctx->overlap_ctas : std::max(1, 3 * split_sm_count() / 4)};
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
     cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,
@@ -1226,6 +1228,14 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
     }
     if (std::strcmp(name, "split_overlap") == 0) {
         ctx->split_overlap = value != 0.0;
+        return BC_OK;
+    }
+    if (std::strcmp(name, "split_overlap_ctas") == 0) {
+        if (!(value >= 0.0 && value <= 65536.0) || value != std::floor(value)) {
+            set_error("bc_set_option: split_overlap_ctas must be an integer in [0, 65536]");
+            return BC_ERR_ARG;
+        }
+        ctx->overlap_ctas = int(value);
         return BC_OK;
     }
     if (std::strcmp(name, "debug_split_parts") == 0) {

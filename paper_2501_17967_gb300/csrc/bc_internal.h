@@ -194,6 +194,7 @@ struct SplitGemm {
     const int32_t *op_exp = nullptr;
     const uint16_t *dig = nullptr;     // [nvec][5][K] BF16 digit bits
     const int32_t *dexp = nullptr;     // [nvec]
+    int max_ctas = 0;                  // CTAs of the launch at most (0: one per SM)
 };
 struct SplitTree {
     // [forward, adjoint]; group V as far part (leafA, X list: needed by the
@@ -217,6 +218,7 @@ struct SplitTree {
 };
 size_t split_smem_bytes(int kd);
 cudaError_t split_prepare();   // kernel attributes of the split path (before any capture)
+int split_sm_count();          // SMs of the device (after split_prepare)
 // parts: which products take the tensor-core results (bits: 1 near field,
 // 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list, 32 M2L); the others run in FP64.
 // Bit 64: the shifts of the two level passes in double-float arithmetic on
@@ -227,6 +229,7 @@ struct SplitLaunch {
     const SplitTree *tree;
     int parts = kSplitAllParts;
     const struct SideStream *side = nullptr;   // null: the near-field launch stays on the apply's stream
+    int near_ctas = 0;                          // CTAs of the near-field launch on the side stream (0: all SMs)
 };
 // Digits of the leaf vectors (times scale), of the two expansion arrays
 // (times scale), and the tensor-core operator products of one group.
@@ -309,6 +312,7 @@ struct bc_ctx {
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
     int split_parts = bc::kSplitAllParts;   // diagnostics: split-precision products in use
     int split_overlap = 1;      // near-field tensor launch on the side stream (1) or inline (0)
+    int overlap_ctas = 0;       // CTAs of that launch (0: three quarters of the SMs)
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumEvents] = {};   // [forward, adjoint]
     bc::SideStream side;

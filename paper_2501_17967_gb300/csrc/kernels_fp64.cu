@@ -811,6 +811,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             if (ce != cudaSuccess) return ce;
             if ((ce = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return ce;
             g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
+            g.max_ctas = split->near_ctas;
             ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
             if (ce != cudaSuccess) return ce;
             if (ev) cudaEventRecord(ev[9], sd->side);

@@ -745,6 +745,8 @@ cudaError_t split_prepare()
     return e;
 }
 
+int split_sm_count() { return g_sms > 0 ? g_sms : 152; }
+
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
                                     cudaStream_t st)
 {
@@ -766,7 +768,8 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
                               int withhold, cudaStream_t st)
 {
     if (g.ntiles <= 0) return cudaSuccess;
-    const int grid = std::min(g.ntiles, g_sms > 0 ? g_sms : 152);
+    const int sms = g_sms > 0 ? g_sms : 152;
+    const int grid = std::min(g.ntiles, g.max_ctas > 0 ? std::min(g.max_ctas, sms) : sms);
     int ie = 0;
     const int inv_alpha_exp = std::frexp(inv_alpha0, &ie) == 0.5 ? ie - 1 : kNoExp;
     if (kd == 256)
