@@ -219,9 +219,11 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,
  *     16 W list, 32 M2L translations); the others are evaluated in FP64.
- *     Bit 64: the shifts of the upward and downward level passes in
- *     double-float arithmetic (pairs of FP32 numbers, about 48 bits) instead
- *     of FP64.
+ *     Bit 64: the shifts of the upward and downward level passes, and with
+ *     bit 2 off the leaf-to-expansion step, in double-float arithmetic (pairs
+ *     of FP32 numbers, about 48 bits) instead of FP64 (inside the upward
+ *     pass, which is then slower on the 20-Gaussian workload than the tensor
+ *     launch of bit 2).
  *   "debug_withhold_copy" (0/1, default 0): diagnostics; the split-precision
  *     kernel never starts its table copy, so its first wait runs out (tests of
  *     the timeout path).

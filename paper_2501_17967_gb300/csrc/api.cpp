@@ -151,8 +151,8 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
             const float h = float(x);
             return std::make_pair(h, float(x - double(h)));
         };
-        for (int which = 0; which < 2; which++) {
-            const std::vector<double2> &src = which ? b.par : b.up;
+        for (int which = 0; which < 3; which++) {
+            const std::vector<double2> &src = which == 2 ? b.leafA : which ? b.par : b.up;
             std::vector<float4> f(src.size());
             for (size_t i = 0; i < src.size(); i++) {
                 const auto re = dfs(src[i].x), im = dfs(src[i].y);
@@ -161,7 +161,7 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
             float4 *pf = nullptr;
             e = dev_upload(dt.allocs, &pf, f.data(), f.size());
             if (e != cudaSuccess) return cuda_fail(e, "tables upload");
-            (which ? os.par_df : os.up_df) = pf;
+            (which == 2 ? os.leafA_df : which ? os.par_df : os.up_df) = pf;
         }
     }
     e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());

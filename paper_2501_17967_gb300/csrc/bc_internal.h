@@ -106,6 +106,7 @@ struct OpSet {
     // up and par as double-float pairs {Re hi, Re lo, Im hi, Im lo} (each
     // entry the sum of two FP32 numbers, about 48 significant bits)
     const float4 *up_df = nullptr, *par_df = nullptr;
+    const float4 *leafA_df = nullptr;   // leafA as double-float pairs
 };
 
 struct DevTables {
@@ -222,12 +223,17 @@ int split_sm_count();          // SMs of the device (after split_prepare)
 // parts: which products take the tensor-core results (bits: 1 near field,
 // 2 leafA, 4 X list, 8 L2P / P2M^H, 16 W list, 32 M2L); the others run in FP64.
 // Bit 64: the shifts of the two level passes in double-float arithmetic on
-// the FP32 units instead of FP64.
+// the FP32 units instead of FP64, and, with bit 2 off, the leaf-to-expansion
+// step too (inside the upward pass; then the input digits run on the side
+// stream).  The default has every part: on the 20-Gaussian workload the leaf
+// step in the upward pass doubles that pass (each block streams the 98 KB
+// operator for its ~4 leaves before it can climb).
 constexpr int kSplitAllParts = 127;
+constexpr int kSplitDefaultParts = kSplitAllParts;
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
-    int parts = kSplitAllParts;
+    int parts = kSplitDefaultParts;
     const struct SideStream *side = nullptr;   // null: the near-field launch stays on the apply's stream
     int near_ctas = 0;                          // CTAs of the near-field launch on the side stream (0: all SMs)
 };
@@ -310,7 +316,7 @@ struct bc_ctx {
     bool tables_ready = false;
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
-    int split_parts = bc::kSplitAllParts;   // diagnostics: split-precision products in use
+    int split_parts = bc::kSplitDefaultParts;   // diagnostics: split-precision products in use
     int split_overlap = 1;      // near-field tensor launch on the side stream (1) or inline (0)
     int overlap_ctas = 0;       // CTAs of that launch (0: three quarters of the SMs)
     bool timing = false;        // record CUDA events around each stage

@@ -131,8 +131,9 @@ __global__ void __launch_bounds__(128)
 k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
-            const double2 *__restrict__ OpA, const double2 *__restrict__ OpUp, const float4 *__restrict__ OpUpDF,
-            double2 *ex, int NP, int P1, const double *__restrict__ lvtab, bool climb, int32_t *flag,
+            const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, const double2 *__restrict__ OpUp,
+            const float4 *__restrict__ OpUpDF, double2 *ex, int NP, int P1, const double *__restrict__ lvtab,
+            bool climb, int32_t *flag,
             long long limit, int32_t *err)
 {
     griddep_wait();
@@ -149,6 +150,39 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         const int b = leaf_box[leaf];
         const double s = ADJ ? 1.0 : lvtab[leaf_level[leaf]];   // r^2
         __syncthreads();
+        if constexpr (DF) {
+            // double-float: the leaf values as {hi, lo} pairs, OpA as pairs
+            float2 *svf = reinterpret_cast<float2 *>(sv);
+            for (int j = threadIdx.x; j < NP; j += blockDim.x) {
+                const double v = vin[int64_t(leaf) * NP + j];
+                const float h = __double2float_rn(v);
+                svf[j] = make_float2(h, __double2float_rn(v - double(h)));
+            }
+            __syncthreads();
+            for (int l = lane; l < P1; l += 32) {
+                float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
+                for (int jb = j0; jb < j1; jb += 8) {   // 8 operator loads in flight, two chains
+                    float4 o[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        o[u] = jb + u < j1 ? __ldg(&OpADF[(jb + u) * P1 + l]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        if (jb + u >= j1) break;
+                        const float2 v0 = svf[jb + u];
+                        df_mac(r0h, r0l, o[u].x, o[u].y, v0.x, v0.y);
+                        df_mac(i0h, i0l, o[u].z, o[u].w, v0.x, v0.y);
+                        if (jb + u + 1 < j1) {
+                            const float2 v1 = svf[jb + u + 1];
+                            df_mac(r1h, r1l, o[u + 1].x, o[u + 1].y, v1.x, v1.y);
+                            df_mac(i1h, i1l, o[u + 1].z, o[u + 1].w, v1.x, v1.y);
+                        }
+                    }
+                }
+                part[w * P1 + l] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
+                                                (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
+            }
+        } else {
         for (int j = threadIdx.x; j < NP; j += blockDim.x) sv[j] = vin[int64_t(leaf) * NP + j];
         __syncthreads();
         for (int l = lane; l < P1; l += 32) {
@@ -167,6 +201,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 im0 = fma(o0.y, sv[j], im0);
             }
             part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
+        }
         }
         __syncthreads();
         for (int l = threadIdx.x; l < P1; l += blockDim.x) {
@@ -775,12 +810,10 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (ev) cudaEventRecord(ev[0], st);
     if (split) {
         // tensor group V: digits of alpha0 * vin; the near field into Pnear,
-        // leafA (P2M / L2P^H) into `first` and the X list into PX, in one
-        // launch, or (split_overlap) leafA in line and the X list and the near
-        // field on the side stream (joined before the downward pass and
-        // before the leaf output)
-        ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
-        if (ce != cudaSuccess) return ce;
+        // leafA (P2M / L2P^H, part 2) into `first` and the X list into PX, in
+        // one launch, or (split_overlap) the X list and the near field on the
+        // side stream (joined before the downward pass and before the leaf
+        // output)
         SplitGemm g;
         g.ops = sT->ops[0][dir]; g.op_exp = sT->op_exp[0][dir];
         g.dig = sp->vdig; g.dexp = sp->vexp;
@@ -788,6 +821,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (!sd) {
             // one launch: the near-field tiles (two jobs each) first, then the
             // leaf-to-expansion and X-list tiles
+            ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
+            if (ce != cudaSuccess) return ce;
             g.tiles = sp->tVN[dir]; g.cols = sp->cVN[dir]; g.ntiles = sp->ntVN[dir];
             ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
             if (ce != cudaSuccess) return ce;
@@ -796,17 +831,29 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                 cudaEventRecord(ev[9], st);
             }
         } else {
-            // in line only the leaf-to-expansion tiles (the upward pass needs
-            // them next); on the internal stream the X-list tiles (needed by
-            // the downward pass, which waits for xdone) and the near field
+            // On the internal stream the X-list tiles (needed by the downward
+            // pass, which waits for xdone) and the near field.  The upward pass
+            // needs the leaf-to-expansion step first: as tensor tiles in line
+            // (part 2, after the digits), else in double-float inside the
+            // upward pass, and then the digits run on the internal stream too.
+            const bool leaf_tc = (parts & 2) != 0;
+            if (leaf_tc) {
+                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
+                if (ce != cudaSuccess) return ce;
+            }
             if ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
                 (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess)
                 return ce;
-            g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntA[dir];
-            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
-            if (ce != cudaSuccess) return ce;
             if (ev) cudaEventRecord(ev[8], sd->side);
-            g.tiles = sp->tV[dir] + sp->ntA[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
+            if (leaf_tc) {
+                g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntA[dir];
+                ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+                if (ce != cudaSuccess) return ce;
+            } else {
+                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side);
+                if (ce != cudaSuccess) return ce;
+            }
+            g.tiles = sp->tV[dir] + sp->ntA[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
             ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
             if (ce != cudaSuccess) return ce;
             if ((ce = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return ce;
@@ -843,8 +890,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (opA || climb) {
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
-               d.level_start, h.nlevels, d.box_child0, vin, opA, op.up, op.up_df, first, NP, P1, d.lvtab, climb, \
-               d.flag, glimit, a.err)
+               d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up, op.up_df, first, NP, P1,    \
+               d.lvtab, climb, d.flag, glimit, a.err)
         if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
         else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
 #undef BC_UP
