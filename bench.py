@@ -194,12 +194,13 @@ STAGE_KERNELS = {
     "leaf_output": "k_leaf_out",
     "tensor_near": "k_split_gemm<256> (X list, then near field, on the internal stream beside stages 1-4)",
 }
-# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
-# main kernel (cold cache), keyed by (workload, nterms, split): the launch
-# list of the bench configuration (profiles/launches_adaptive20_split.md)
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of each stage's tensor or
+# pass kernel (cold cache; tensor_near: its X-list and near-field launches
+# together), keyed by (workload, nterms, split): the launch list of the bench
+# configuration (profiles/launches_adaptive20_split.md)
 TRAFFIC = {
-    ("adaptive20", 24, True): {"upward": 0.59e6, "m2l": 2.95e6, "down_levels": 13.68e6, "tensor_e": 5.27e6,
-                               "leaf_output": 32.39e6},
+    ("adaptive20", 24, True): {"tensor_v": 3.59e6, "tensor_near": 29.24e6, "upward": 0.59e6, "m2l": 2.95e6,
+                               "down_levels": 13.68e6, "tensor_e": 5.27e6, "leaf_output": 32.39e6},
 }
 
 
