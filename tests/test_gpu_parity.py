@@ -450,18 +450,28 @@ def test_split_parts_each_within_tolerance(ctx16, adaptive):
 
 
 def test_split_overlap_gives_identical_results(ctx16, adaptive):
-    """The near-field tensor launch on the internal stream (split_overlap = 1)
-    computes exactly what the in-line launch computes, in both directions."""
+    """The X-list and near-field tensor launches on the internal stream (the
+    default, split_overlap = 1), on any number of CTAs, compute exactly what
+    the in-line launch computes, in both directions."""
     lv, ix, iy, g, tree, geom, fvals, f = adaptive
     gen = torch.Generator(device="cuda").manual_seed(13)
     gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
-    u0 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
-    h0 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
-    ctx16.set_option("split_overlap", 1)
+    u1 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    h1 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
     try:
-        u1 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
-        h1 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
+        ctx16.set_option("split_overlap", 0)
+        u0 = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+        h0 = bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)
+        ctx16.set_option("split_overlap", 1)
+        outs = []
+        for ctas in (7, 40, 152):
+            ctx16.set_option("split_overlap_ctas", ctas)
+            outs.append((bc.apply(tree, f, precision=bc.SPLIT_BF16),
+                         bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16)))
         bc._check(bc._load().bc_sync(ctx16.handle, None))
     finally:
-        ctx16.set_option("split_overlap", 0)
+        ctx16.set_option("split_overlap", 1)
+        ctx16.set_option("split_overlap_ctas", 0)
     assert torch.equal(u0, u1) and torch.equal(h0, h1)
+    for uc, hc in outs:
+        assert torch.equal(uc, u1) and torch.equal(hc, h1)
