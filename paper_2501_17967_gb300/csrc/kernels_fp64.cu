@@ -113,6 +113,13 @@ __device__ __forceinline__ void df_cmac(float &rh, float &rl, float &ih, float &
     df_mac(ih, il, o.z, o.w, x.x, x.y);
 }
 
+// Dynamic shared memory of the upward pass: children, partial sums, the leaf
+// values, and (double-float variant) the four shift operators.
+inline size_t up_smem_bytes(int NP, int P1, bool df)
+{
+    return sizeof(double2) * 8 * P1 + sizeof(double) * ((NP + 1) & ~1) + (df ? sizeof(float4) * 4 * P1 * P1 : 0);
+}
+
 // -------------------------------------------------------------------------
 // upward pass, one persistent launch:
 //   leaves: ex[box(leaf)][l] = s * sum_j OpA[j][l] v[leaf][j]
@@ -136,12 +143,20 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             bool climb, int32_t *flag,
             long long limit, int32_t *err)
 {
-    griddep_wait();
-    griddep_launch_dependents();
     extern __shared__ double2 shu[];
     double2 *sc = shu;                                       // 4 * P1 children
     double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
+    // double-float path: the four shift operators in shared memory, copied
+    // while the preceding kernel drains (the climb reads them at every level;
+    // from L1/L2 each batch of a step would wait for a cold line)
+    float4 *sopf = reinterpret_cast<float4 *>(sv + ((NP + 1) & ~1));   // [4][P1][P1] (DF only)
+    if constexpr (DF) {
+        if (climb)
+            for (int i = threadIdx.x; i < 4 * P1 * P1; i += blockDim.x) sopf[i] = __ldg(&OpUpDF[i]);
+    }
+    griddep_wait();
+    griddep_launch_dependents();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // leaf step: warp w sums the nodes [j0, j1) (any number of nodes)
     const int nq = (NP + 3) / 4, j0 = min(NP, w * nq), j1 = min(NP, j0 + nq);
@@ -227,7 +242,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x)
                     scf[i] = df4_of(__ldcg(&ex[int64_t(c0) * P1 + i]));
                 __syncthreads();
-                const float4 *op = OpUpDF + size_t(w) * P1 * P1;
+                const float4 *op = sopf + w * P1 * P1;
                 const float4 *a = scf + w * P1;
                 for (int l = lane; l < P1; l += 32) {
                     float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
@@ -235,7 +250,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                         float4 o[8];
 #pragma unroll
                         for (int u = 0; u < 8; u++)
-                            o[u] = k0 + u < P1 ? __ldg(&op[(k0 + u) * P1 + l]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                            o[u] = k0 + u < P1 ? op[(k0 + u) * P1 + l] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                         for (int u = 0; u < 8; u += 2) {
                             if (k0 + u >= P1) break;
@@ -882,11 +897,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     // leafA + upward pass in one persistent launch (leafA always runs: the
     // near-field log term reads coefficient 0 of its output; without the far
     // field no climb).  Split path: leafA came from the tensor cores.
-    const size_t shU = sizeof(double) * NP + sizeof(double2) * 8 * P1;
     const int grid_leaf = grid_for(a.nleaf, 152 * (a.leaf_bps ? a.leaf_bps : 16));
     const double2 *opA = (parts & 2) ? nullptr : op.leafA;
     const bool climb = far && h.nlevels > 3;
     const bool dfp = (parts & 64) != 0;   // double-float shifts
+    const size_t shU = up_smem_bytes(NP, P1, dfp);
     if (opA || climb) {
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
@@ -1017,14 +1032,23 @@ cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up
     int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t shU = sizeof(double) * NP + sizeof(double2) * 8 * P1;
+    const size_t shU = up_smem_bytes(NP, P1, false), shUd = up_smem_bytes(NP, P1, true);
+    // the double-float variants hold the shift operators in shared memory,
+    // beyond the default 48 KB from 28 terms on; the limit is per kernel, so
+    // it is only ever raised (contexts of different orders share the kernels)
+    for (const void *k : {(const void *)k_up_levels<false, true>, (const void *)k_up_levels<true, true>}) {
+        cudaFuncAttributes fa;
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
+        if (e == cudaSuccess && size_t(fa.maxDynamicSharedSizeBytes) < shUd)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shUd));
+    }
     // every block of a persistent pass must be resident: the smallest
     // occupancy over the variants that share the grid
     int bu2 = 0, bu3 = 0, bs2 = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu0, k_up_levels<false, false>, 128, shU);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true, false>, 128, shU);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu2, k_up_levels<false, true>, 128, shU);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu3, k_up_levels<true, true>, 128, shU);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu2, k_up_levels<false, true>, 128, shUd);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu3, k_up_levels<true, true>, 128, shUd);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels<false>, 128,
                                                           sizeof(double2) * (5 * P1 + 1));
