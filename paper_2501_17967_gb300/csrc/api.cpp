@@ -151,8 +151,8 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
             const float h = float(x);
             return std::make_pair(h, float(x - double(h)));
         };
-        for (int which = 0; which < 3; which++) {
-            const std::vector<double2> &src = which == 2 ? b.leafA : which ? b.par : b.up;
+        for (int which = 1; which < 3; which++) {   // par, leafA (up: the schedule below)
+            const std::vector<double2> &src = which == 2 ? b.leafA : b.par;
             std::vector<float4> f(src.size());
             for (size_t i = 0; i < src.size(); i++) {
                 const auto re = dfs(src[i].x), im = dfs(src[i].y);
@@ -161,8 +161,60 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
             float4 *pf = nullptr;
             e = dev_upload(dt.allocs, &pf, f.data(), f.size());
             if (e != cudaSuccess) return cuda_fail(e, "tables upload");
-            (which == 2 ? os.leafA_df : which ? os.par_df : os.up_df) = pf;
+            (which == 2 ? os.leafA_df : os.par_df) = pf;
         }
+        // the term schedule of the double-float climb (DfSched): the k range
+        // of each output over the four children, exact zeros left out
+        int P1 = 0;   // up is [4][P1][P1]
+        while (size_t(4) * (P1 + 1) * (P1 + 1) <= b.up.size()) P1++;
+        std::vector<int> klo(P1, P1), khi(P1, -1);
+        for (int q = 0; q < 4; q++)
+            for (int k = 0; k < P1; k++)
+                for (int l = 0; l < P1; l++) {
+                    const double2 o = b.up[(size_t(q) * P1 + k) * P1 + l];
+                    if (o.x != 0.0 || o.y != 0.0) {
+                        klo[l] = std::min(klo[l], k);
+                        khi[l] = std::max(khi[l], k);
+                    }
+                }
+        std::vector<std::pair<int, int>> terms;   // (l, k), output by output
+        for (int l = 0; l < P1; l++) {
+            if (khi[l] < klo[l]) klo[l] = khi[l] = 0;   // an all-zero output keeps one (zero) term
+            for (int k = klo[l]; k <= khi[l]; k++) terms.emplace_back(l, k);
+        }
+        const int N = int(terms.size()), T = (N + 31) / 32;
+        std::vector<int> lf(P1, -1), np(P1, 0);
+        for (int i = 0; i < N; i++) {
+            const int l = terms[i].first, lane = i / T;
+            if (lf[l] < 0) lf[l] = lane;
+            np[l] = lane - lf[l] + 1;
+        }
+        const int maxp = *std::max_element(np.begin(), np.end());
+        std::vector<uint32_t> code(size_t(T) * 32, 0u);
+        std::vector<float4> ops(size_t(4) * T * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+        for (int i = 0; i < N; i++) {
+            const int l = terms[i].first, k = terms[i].second, lane = i / T, t = i % T;
+            const bool last = i + 1 == N || terms[i + 1].first != l || (i + 1) % T == 0;
+            const uint32_t slot = uint32_t(l * maxp + lane - lf[l]);
+            code[size_t(t) * 32 + lane] = uint32_t(k) | (last ? (slot + 1u) << 8 : 0u);
+            for (int q = 0; q < 4; q++) {
+                const double2 o = b.up[(size_t(q) * P1 + k) * P1 + l];
+                const auto re = dfs(o.x), im = dfs(o.y);
+                ops[(size_t(q) * T + t) * 32 + lane] = make_float4(re.first, re.second, im.first, im.second);
+            }
+        }
+        uint32_t *pc = nullptr;
+        float4 *po = nullptr;
+        int32_t *pn = nullptr;
+        if ((e = dev_upload(dt.allocs, &pc, code.data(), code.size())) != cudaSuccess ||
+            (e = dev_upload(dt.allocs, &po, ops.data(), ops.size())) != cudaSuccess ||
+            (e = dev_upload(dt.allocs, &pn, np.data(), np.size())) != cudaSuccess)
+            return cuda_fail(e, "tables upload");
+        os.up_s.code = pc;
+        os.up_s.ops = po;
+        os.up_s.np = pn;
+        os.up_s.T = T;
+        os.up_s.maxp = maxp;
     }
     e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
@@ -215,6 +267,8 @@ bc_status upload_tree(bc_tree *t)
     e = dev_upload<int32_t>(d.allocs, &d.flag, nullptr, h.box_level.size());
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     size_t nexp = size_t(h.box_level.size()) * P1;
+    e = dev_upload<float4>(d.allocs, &d.exdf, nullptr, nexp);
+    if (e != cudaSuccess) return cuda_fail(e, "tree workspace");
     e = dev_upload<double2>(d.allocs, &d.expA, nullptr, nexp);
     if (e != cudaSuccess) return cuda_fail(e, "tree workspace");
     e = dev_upload<double2>(d.allocs, &d.expB, nullptr, nexp);
@@ -858,7 +912,9 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
     e = dev_upload<int32_t>(ctx->dt.allocs, &ctx->dev_err, nullptr, 1);
     if (e != cudaSuccess) return cuda_fail(e, "error flag");
     // two upward blocks per SM leave room for a tensor-core CTA beside them
-    e = fp64_prepare(ctx->NP, ctx->P1, 2, 4, &ctx->up_blocks, &ctx->shift_blocks);
+    e = fp64_prepare(ctx->NP, ctx->P1, std::max(ctx->dt.fwd.up_s.T, ctx->dt.adj.up_s.T),
+                     std::max(ctx->dt.fwd.up_s.maxp, ctx->dt.adj.up_s.maxp), 2, 4, &ctx->up_blocks,
+                     &ctx->shift_blocks);
     if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel occupancy");
     s = build_split_tables(ctx);
     if (s != BC_OK) return s;

@@ -94,6 +94,19 @@ bc_status build_tables(HostTables &ht, int p, int P1, const char *cache_dir);
 // One operator set drives one direction (forward or adjoint) of the apply.
 // Every complex operator is stored so that the kernel computes
 // out[l] = sum_k Op[k*P1 + l] * in[k]  ("element (l,k) at [k][l]").
+// Term schedule of the double-float upward shift.  The nonzero terms
+// (output l, input k) of the four child operators (the shift is triangular:
+// k <= l) are taken output by output and cut into 32 runs of T terms, one
+// run per lane, so that the lanes share the triangle evenly; each lane ends a
+// partial sum where its run leaves an output, and the partial sums of an
+// output (np[l] of them, consecutive lanes) are added afterwards.
+struct DfSched {
+    const uint32_t *code = nullptr;   // [T][32] input k (bits 0-7); (slot + 1) << 8 where a partial sum ends
+    const float4 *ops = nullptr;      // [4][T][32] the operator entry of each term, per child, {Re hi, lo, Im hi, lo}
+    const int32_t *np = nullptr;      // [P1] partial sums per output; output l owns slots l * maxp + [0, np[l])
+    int T = 0, maxp = 0;
+};
+
 struct OpSet {
     const double2 *leafA = nullptr;   // [NP][P1]        leaf vector -> box expansion
     const double2 *up = nullptr;      // [4][P1][P1]     child -> parent
@@ -103,10 +116,11 @@ struct OpSet {
     const double2 *e = nullptr;       // [P1][NP]        expansion -> leaf nodes (real part)
     const double2 *w = nullptr;       // [kNumWX][P1][NP] expansion -> leaf nodes (W list)
     const double *t = nullptr;        // [kNumNear][NP][NP] near tables, element (j,k) at [k][j]
-    // up and par as double-float pairs {Re hi, Re lo, Im hi, Im lo} (each
-    // entry the sum of two FP32 numbers, about 48 significant bits)
-    const float4 *up_df = nullptr, *par_df = nullptr;
+    // par as double-float pairs {Re hi, Re lo, Im hi, Im lo} (each entry the
+    // sum of two FP32 numbers, about 48 significant bits)
+    const float4 *par_df = nullptr;
     const float4 *leafA_df = nullptr;   // leafA as double-float pairs
+    DfSched up_s;                       // up, scheduled for the double-float climb
 };
 
 struct DevTables {
@@ -137,6 +151,7 @@ struct DevTree {
     double *lvtab = nullptr;                   // [2][kLvTab]: r^2 and log r per level
     int64_t *level_start = nullptr;            // [nlevels + 1] first box of each level
     int32_t *flag = nullptr;                   // [nbox] completion flags of the persistent level passes
+    float4 *exdf = nullptr;                    // [nbox][P1] double-float upward expansions of the climb
     double *stage_in = nullptr, *stage_out = nullptr; // host-pointer staging [nleaf*NP]
     std::vector<void *> allocs;
 };
@@ -265,7 +280,8 @@ struct PassArgs {
 };
 // Largest grids of the persistent FP64 passes whose blocks are all resident
 // (occupancy calculator), capped at `per_sm` blocks per SM.
-cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up_blocks, int *shift_blocks);
+cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, int down_per_sm, int *up_blocks,
+                         int *shift_blocks);
 
 // Disjoint union of trees (batched applies): leaves and boxes renumbered,
 // boxes sorted by (level, tree, Morton order), lists concatenated.

@@ -113,11 +113,33 @@ __device__ __forceinline__ void df_cmac(float &rh, float &rl, float &ih, float &
     df_mac(ih, il, o.z, o.w, x.x, x.y);
 }
 
-// Dynamic shared memory of the upward pass: children, partial sums, the leaf
-// values, and (double-float variant) the four shift operators.
-inline size_t up_smem_bytes(int NP, int P1, bool df)
+// Two double-float numbers (h0 + l0) + (h1 + l1), with the error of the hi
+// sum kept (Knuth's two-sum) and the result renormalised.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
 {
-    return sizeof(double2) * 8 * P1 + sizeof(double) * ((NP + 1) & ~1) + (df ? sizeof(float4) * 4 * P1 * P1 : 0);
+    const float s = __fadd_rn(a.x, b.x);
+    const float v = __fsub_rn(s, a.x);
+    const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.x, __fsub_rn(s, v)), __fsub_rn(b.x, v)), __fadd_rn(a.y, b.y));
+    const float h = __fadd_rn(s, e);
+    return make_float2(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ float4 df4_add(float4 a, float4 b)
+{
+    const float2 r = df_add(make_float2(a.x, a.y), make_float2(b.x, b.y));
+    const float2 i = df_add(make_float2(a.z, a.w), make_float2(b.z, b.w));
+    return make_float4(r.x, r.y, i.x, i.y);
+}
+
+// Dynamic shared memory of the upward pass: children, partial sums, the leaf
+// values, and (double-float variant, schedule of T terms per lane) the
+// scheduled operator entries, the partial-sum slots, the term codes and the
+// per-output slot counts.
+inline size_t up_smem_bytes(int NP, int P1, int T, int maxp)
+{
+    return sizeof(double2) * 8 * P1 + sizeof(double) * ((NP + 1) & ~1) +
+           (T > 0 ? sizeof(float4) * (size_t(4) * T * 32 + size_t(4) * P1 * maxp) + sizeof(uint32_t) * T * 32 +
+                        sizeof(int32_t) * ((P1 + 3) & ~3)
+                  : 0);
 }
 
 // -------------------------------------------------------------------------
@@ -131,7 +153,11 @@ inline size_t up_smem_bytes(int NP, int P1, bool df)
 //           forward: M2M; adjoint: L2L^H
 // Four warps per block: in the leaf step warp w sums over the w-th quarter of
 // the nodes, in a parent step warp q applies the operator of child q; the four
-// partial sums meet in shared memory.
+// partial sums meet in shared memory.  The double-float variant runs the
+// parent step on the term schedule (DfSched), keeps its sums in double-float
+// until the one conversion of each result, and publishes every climbed
+// expansion twice: ex in FP64 and exdf as double-float pairs, which the
+// parent's step reads without conversion.
 // -------------------------------------------------------------------------
 template <bool ADJ, bool DF>
 __global__ void __launch_bounds__(128)
@@ -139,7 +165,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
             const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, const double2 *__restrict__ OpUp,
-            const float4 *__restrict__ OpUpDF, double2 *ex, int NP, int P1, const double *__restrict__ lvtab,
+            DfSched us, double2 *ex, float4 *exdf, int NP, int P1, const double *__restrict__ lvtab,
             bool climb, int32_t *flag,
             long long limit, int32_t *err)
 {
@@ -147,13 +173,20 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
     double2 *sc = shu;                                       // 4 * P1 children
     double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
-    // double-float path: the four shift operators in shared memory, copied
-    // while the preceding kernel drains (the climb reads them at every level;
-    // from L1/L2 each batch of a step would wait for a cold line)
-    float4 *sopf = reinterpret_cast<float4 *>(sv + ((NP + 1) & ~1));   // [4][P1][P1] (DF only)
+    // double-float path: the scheduled operator entries in shared memory,
+    // copied while the preceding kernel drains (every parent step reads them)
+    const int T = us.T, SL = P1 * us.maxp;   // terms per lane, slots per child
+    float4 *sops = reinterpret_cast<float4 *>(sv + ((NP + 1) & ~1));   // [4][T][32] (DF only)
+    float4 *sslot = sops + 4 * T * 32;                                 // [4][SL]
+    uint32_t *scode = reinterpret_cast<uint32_t *>(sslot + 4 * SL);    // [T][32]
+    int32_t *snp = reinterpret_cast<int32_t *>(scode + T * 32);        // [P1]
+    __shared__ int s_leafc[4];   // which children of the current parent are leaves
     if constexpr (DF) {
-        if (climb)
-            for (int i = threadIdx.x; i < 4 * P1 * P1; i += blockDim.x) sopf[i] = __ldg(&OpUpDF[i]);
+        if (climb) {
+            for (int i = threadIdx.x; i < 4 * T * 32; i += blockDim.x) sops[i] = __ldg(&us.ops[i]);
+            for (int i = threadIdx.x; i < T * 32; i += blockDim.x) scode[i] = __ldg(&us.code[i]);
+            for (int i = threadIdx.x; i < P1; i += blockDim.x) snp[i] = __ldg(&us.np[i]);
+        }
     }
     griddep_wait();
     griddep_launch_dependents();
@@ -233,34 +266,53 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             if (c0 < 0) continue;   // a leaf (uniform over the block)
             // children computed in this launch: every child above the leaves,
             // and the leaves too when their expansions come from the leaf step
-            if (threadIdx.x < 4 && (OpA || box_child0[c0 + threadIdx.x] >= 0))
-                flag_wait(&flag[c0 + threadIdx.x], 1, limit, err);
+            if (threadIdx.x < 4) {
+                const bool leafc = box_child0[c0 + threadIdx.x] < 0;
+                if (DF) s_leafc[threadIdx.x] = leafc;
+                if (OpA || !leafc) flag_wait(&flag[c0 + threadIdx.x], 1, limit, err);
+            }
             __syncthreads();
             if constexpr (DF) {
-                // double-float: the children in shared memory as {hi, lo} pairs
+                // the children as double-float pairs: climbed ones from exdf,
+                // leaves (expansions of the leaf products) from ex
                 float4 *scf = reinterpret_cast<float4 *>(sc);
-                for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x)
-                    scf[i] = df4_of(__ldcg(&ex[int64_t(c0) * P1 + i]));
-                __syncthreads();
-                const float4 *op = sopf + w * P1 * P1;
-                const float4 *a = scf + w * P1;
-                for (int l = lane; l < P1; l += 32) {
-                    float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
-                    for (int k0 = 0; k0 < P1; k0 += 8) {   // 8 operator loads in flight, two chains
-                        float4 o[8];
-#pragma unroll
-                        for (int u = 0; u < 8; u++)
-                            o[u] = k0 + u < P1 ? op[(k0 + u) * P1 + l] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                        for (int u = 0; u < 8; u += 2) {
-                            if (k0 + u >= P1) break;
-                            df_cmac(r0h, r0l, i0h, i0l, o[u], a[k0 + u]);
-                            if (k0 + u + 1 < P1) df_cmac(r1h, r1l, i1h, i1l, o[u + 1], a[k0 + u + 1]);
-                        }
-                    }
-                    part[w * P1 + l] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
-                                                    (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
+                for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) {
+                    const int64_t g = int64_t(c0) * P1 + i;
+                    scf[i] = s_leafc[i / P1] ? df4_of(__ldcg(&ex[g])) : __ldcg(&exdf[g]);
                 }
+                __syncthreads();
+                // warp w: the terms of child w, each lane its run of the schedule
+                const float4 *opw = sops + w * T * 32 + lane;
+                const float4 *a = scf + w * P1;
+                float4 *slot = sslot + w * SL;
+                float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 2
+                for (int t = 0; t < T; t++) {
+                    const uint32_t code = scode[t * 32 + lane];
+                    df_cmac(rh, rl, ih, il, opw[t * 32], a[code & 255u]);
+                    if (code >> 8) {   // the run leaves an output here
+                        slot[(code >> 8) - 1u] = make_float4(rh, rl, ih, il);
+                        rh = rl = ih = il = 0.f;
+                    }
+                }
+                __syncwarp();
+                // lane l: the partial sums of output l for child w
+                float4 *pf = reinterpret_cast<float4 *>(part);   // [4][P1]
+                for (int l = lane; l < P1; l += 32) {
+                    float4 v = slot[l * us.maxp];
+                    for (int j = 1; j < snp[l]; j++) v = df4_add(v, slot[l * us.maxp + j]);
+                    pf[w * P1 + l] = v;
+                }
+                __syncthreads();
+                // thread (l, Re or Im): the four children, one conversion to FP64
+                const float2 *pf2 = reinterpret_cast<const float2 *>(pf);
+                for (int i = threadIdx.x; i < 2 * P1; i += blockDim.x) {
+                    float2 v = df_add(df_add(pf2[i], pf2[2 * P1 + i]), df_add(pf2[4 * P1 + i], pf2[6 * P1 + i]));
+                    const int64_t g = int64_t(p) * P1 * 2 + i;
+                    reinterpret_cast<double *>(ex)[g] = double(v.x) + double(v.y);
+                    reinterpret_cast<float2 *>(exdf)[g] = v;
+                }
+                flag_publish(&flag[p], 1);
             } else {
             for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
             __syncthreads();
@@ -285,13 +337,13 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 }
                 part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
             }
-            }
             __syncthreads();
             for (int l = threadIdx.x; l < P1; l += blockDim.x) {
                 const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
                 ex[int64_t(p) * P1 + l] = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
             }
             flag_publish(&flag[p], 1);
+            }
         }
     }
 }
@@ -901,11 +953,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const double2 *opA = (parts & 2) ? nullptr : op.leafA;
     const bool climb = far && h.nlevels > 3;
     const bool dfp = (parts & 64) != 0;   // double-float shifts
-    const size_t shU = up_smem_bytes(NP, P1, dfp);
+    const size_t shU = dfp ? up_smem_bytes(NP, P1, op.up_s.T, op.up_s.maxp) : up_smem_bytes(NP, P1, 0, 0);
     if (opA || climb) {
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
-               d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up, op.up_df, first, NP, P1,    \
+               d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up, op.up_s, first, d.exdf, NP, P1, \
                d.lvtab, climb, d.flag, glimit, a.err)
         if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
         else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
@@ -1010,7 +1062,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     return cudaGetLastError();
 }
 
-cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up_blocks, int *shift_blocks)
+cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, int down_per_sm, int *up_blocks,
+                         int *shift_blocks)
 {
     {
         // binomial table of the factored M2L (see c_binom)
@@ -1032,10 +1085,11 @@ cudaError_t fp64_prepare(int NP, int P1, int up_per_sm, int down_per_sm, int *up
     int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t shU = up_smem_bytes(NP, P1, false), shUd = up_smem_bytes(NP, P1, true);
-    // the double-float variants hold the shift operators in shared memory,
-    // beyond the default 48 KB from 28 terms on; the limit is per kernel, so
-    // it is only ever raised (contexts of different orders share the kernels)
+    const size_t shU = up_smem_bytes(NP, P1, 0, 0), shUd = up_smem_bytes(NP, P1, df_T, df_maxp);
+    // the double-float variants hold the scheduled shift operators in shared
+    // memory, beyond the default 48 KB at high orders; the limit is per
+    // kernel, so it is only ever raised (contexts of different orders share
+    // the kernels)
     for (const void *k : {(const void *)k_up_levels<false, true>, (const void *)k_up_levels<true, true>}) {
         cudaFuncAttributes fa;
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k);
