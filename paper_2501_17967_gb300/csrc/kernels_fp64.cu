@@ -507,7 +507,11 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // log term gathered one entry per lane), warp 1 the V-list log term (one pair
 // per lane), warps 2 and 3 the V pairs.  In the shift warp w applies a quarter
 // of the operator's columns, fetched into registers before the wait for the
-// parent (the shift chain is the critical path).
+// parent (the shift chain is the critical path).  The double-float variant
+// keeps that chain free of FP64 work: the box's sums are converted to pairs
+// before the wait, the parent is read as pairs (outdf), the partial sums are
+// added as pairs, and the FP64 result, read only by later kernels, is stored
+// after the box's flag.
 // -------------------------------------------------------------------------
 template <bool DF>
 __global__ void __launch_bounds__(128)
@@ -516,7 +520,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
               const double2 *__restrict__ PX, int px_stride, const int32_t *__restrict__ leaf_box,
               const double2 *__restrict__ first, const int32_t *__restrict__ parent,
               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
-              const double2 *__restrict__ OpPar, const float4 *__restrict__ OpParDF, double2 *out, int P1,
+              const double2 *__restrict__ OpPar, const float4 *__restrict__ OpParDF, double2 *out, float4 *outdf, int P1,
               const double *__restrict__ lvtab,
               const int32_t *__restrict__ v_lsrc, const int32_t *__restrict__ v_code,
               const double *__restrict__ logd, int32_t *flag, long long limit, int32_t *err)
@@ -609,18 +613,19 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
         if (o < P1) part[w * P1 + o] = make_double2(re, im);
         __syncthreads();
         double2 acc = make_double2(0.0, 0.0);   // meaningful in warp 0, lanes o < P1
+        float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);   // the same as double-float pairs (DF)
         if (w == 0 && o < P1) {
             const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
             acc = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
+            if (DF) accf = df4_of(acc);   // before the wait for the parent
         }
         // ---- plus the parent's expansion shifted to this box (levels >= 3)
         if (shift) {
             if (threadIdx.x == 0) flag_wait(&flag[pb], 2, limit, err);
             __syncthreads();   // also: warp 0 has read its partial sums
             if constexpr (DF) {
-                float4 *sef = reinterpret_cast<float4 *>(se);   // the parent as double-float pairs
-                for (int i = threadIdx.x; i < P1; i += blockDim.x)
-                    sef[i] = df4_of(__ldcg(&out[int64_t(pb) * P1 + i]));
+                float4 *sef = reinterpret_cast<float4 *>(se);   // the parent's double-float pairs
+                for (int i = threadIdx.x; i < P1; i += blockDim.x) sef[i] = __ldcg(&outdf[int64_t(pb) * P1 + i]);
                 __syncthreads();
                 if (o < P1) {
                     float r0h = 0.f, r0l = 0.f, i0h = 0.f, i0l = 0.f, r1h = 0.f, r1l = 0.f, i1h = 0.f, i1l = 0.f;
@@ -630,8 +635,8 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                         df_cmac(r0h, r0l, i0h, i0l, wf[u], sef[k0 + u]);
                         if (k0 + u + 1 < k1) df_cmac(r1h, r1l, i1h, i1l, wf[u + 1], sef[k0 + u + 1]);
                     }
-                    part[w * P1 + o] = make_double2((double(r0h) + double(r1h)) + (double(r0l) + double(r1l)),
-                                                    (double(i0h) + double(i1h)) + (double(i0l) + double(i1l)));
+                    reinterpret_cast<float4 *>(part)[w * P1 + o] =
+                        df4_add(make_float4(r0h, r0l, i0h, i0l), make_float4(r1h, r1l, i1h, i1l));
                 }
             } else {
                 for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
@@ -655,13 +660,28 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
             }
             __syncthreads();
             if (w == 0 && o < P1) {
-                const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
-                acc.x += (a0.x + a1.x) + (a2.x + a3.x);
-                acc.y += (a0.y + a1.y) + (a2.y + a3.y);
+                if constexpr (DF) {
+                    const float4 *pf = reinterpret_cast<const float4 *>(part);
+                    accf = df4_add(df4_add(accf, pf[o]), df4_add(pf[P1 + o], df4_add(pf[2 * P1 + o], pf[3 * P1 + o])));
+                } else {
+                    const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
+                    acc.x += (a0.x + a1.x) + (a2.x + a3.x);
+                    acc.y += (a0.y + a1.y) + (a2.y + a3.y);
+                }
             }
         }
-        if (w == 0 && o < P1) out[b * P1 + o] = acc;
-        flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
+        if constexpr (DF) {
+            // the children read the pairs; the FP64 result (for the later
+            // kernels only) is stored after the flag, off the level chain
+            if (w == 0 && o < P1) outdf[b * P1 + o] = accf;
+            flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
+            if (w == 0 && o < P1)
+                out[b * P1 + o] =
+                    shift ? make_double2(double(accf.x) + double(accf.y), double(accf.z) + double(accf.w)) : acc;
+        } else {
+            if (w == 0 && o < P1) out[b * P1 + o] = acc;
+            flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
+        }
     }
 }
 
@@ -1017,8 +1037,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 #define BC_DOWN(D)                                                                                           \
     launch_pdl(k_down_levels<D>, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st, d.level_start, h.nlevels, \
                d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent, d.box_ix, d.box_iy, \
-               op.par, op.par_df, second, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd, d.flag, \
-               glimit, a.err)
+               op.par, op.par_df, second, d.exdf, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd,  \
+               d.flag, glimit, a.err)
         ce = dfp ? BC_DOWN(true) : BC_DOWN(false);
 #undef BC_DOWN
         if (ce != cudaSuccess) return ce;
