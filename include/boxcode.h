@@ -205,7 +205,8 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *     adjoint), which halves the M2L arithmetic but loses accuracy.
  *   "wait_limit" (default 2^26): polls of each bounded device-side wait of the
  *     split-precision kernel before it gives up, records the failure (reported
- *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns.
+ *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns; the
+ *     level passes' box flags poll a sixteenth of it and report the same way.
  *   "split_overlap" (0/1, default 1): the near-field tensor-core launch of a
  *     split-precision apply runs on an internal stream, concurrently with the
  *     far-field passes, and is joined before the leaf output (1), or in line

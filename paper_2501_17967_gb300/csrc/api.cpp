@@ -1339,7 +1339,9 @@ bc_status bc_sync(bc_ctx *ctx, void *stream)
         if (e != cudaSuccess) return cuda_fail(e, "bc_sync");
         if (flag) {
             cudaMemset(ctx->dev_err, 0, sizeof(int32_t));
-            set_error("bc_sync: a bounded device-side wait gave up (tensor-core operand copy or grid barrier)");
+            // 1: tensor-core operand copy, 2: level-pass box flag
+            static const char *what[] = {"", " (tensor-core operand copy)", " (level-pass box flag)"};
+            set_error("bc_sync: a bounded device-side wait gave up%s", what[flag >= 1 && flag <= 2 ? flag : 0]);
             return BC_ERR_TIMEOUT;
         }
     }
