@@ -475,3 +475,40 @@ def test_split_overlap_gives_identical_results(ctx16, adaptive):
     assert torch.equal(u0, u1) and torch.equal(h0, h1)
     for uc, hc in outs:
         assert torch.equal(uc, u1) and torch.equal(hc, h1)
+
+
+@pytest.mark.parametrize("nterms", [8, 12, 31])
+def test_split_double_float_shifts_other_orders(nterms):
+    """At other expansion orders, in both directions: the double-float level
+    shifts alone (part 64, every product in FP64) agree with the FP64 shifts
+    to double-float rounding; the upward one runs on its triangular term
+    schedule (at 8, 12 and 31 terms: 2, 3 and 17 terms per lane, up to 5
+    partial sums per coefficient).  The full split apply stays within the
+    split tolerance of the FP64 apply.  (Two split applies that differ only
+    in the shifts differ by up to one step of the 40-bit digit grid, about
+    1e-12: the expansions feed the digits of later products.)"""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = bc.Context(p=16, nterms=nterms, device=0)
+    g = synth.gaussians(8, 21, wlog10=(-2.3, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, kappa=1.0, max_level=9)
+    tree, geom, fvals, f = make(ctx, lv, ix, iy, g)
+    gen = torch.Generator(device="cuda").manual_seed(17)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    u64, h64 = bc.apply(tree, f), bc.apply_adjoint(tree, gg)
+    try:
+        out = {}
+        for parts in (0, 64, 127):
+            ctx.set_option("debug_split_parts", parts)
+            out[parts] = (bc.apply(tree, f, precision=bc.SPLIT_BF16),
+                          bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16))
+        bc._check(bc._load().bc_sync(ctx.handle, None))
+    finally:
+        ctx.set_option("debug_split_parts", 127)
+    for k, ref in enumerate((u64, h64)):
+        tag = "adj" if k else "fwd"
+        d_df = ((out[64][k] - out[0][k]).abs().max() / out[0][k].abs().max()).item()
+        d_all = ((out[127][k] - ref).abs().max() / ref.abs().max()).item()
+        print(f"nterms {nterms} {tag}: double-float vs FP64 shifts {d_df:.2e}, split vs FP64 {d_all:.2e}")
+        assert 0.0 < d_df < 1e-13, (nterms, tag, d_df)
+        assert d_all < TOL, (nterms, tag, d_all)
