@@ -199,7 +199,7 @@ STAGE_KERNELS = {
 # together), keyed by (workload, nterms, split): the launch list of the bench
 # configuration (profiles/launches_adaptive20_split.md)
 TRAFFIC = {
-    ("adaptive20", 24, True): {"tensor_v": 3.59e6, "tensor_near": 29.24e6, "upward": 0.59e6, "m2l": 2.95e6,
+    ("adaptive20", 24, True): {"tensor_v": 3.59e6, "tensor_near": 29.24e6, "upward": 0.57e6, "m2l": 2.95e6,
                                "down_levels": 13.68e6, "tensor_e": 5.27e6, "leaf_output": 32.39e6},
 }
 
