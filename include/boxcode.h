@@ -140,10 +140,11 @@ bc_status bc_tree_boxes(const bc_tree *tree, int32_t *level, int32_t *ix, int32_
 void bc_tree_destroy(bc_tree *tree);
 
 /* u = A f: the volume potential at every leaf node (definition above).
- * f, u: [nleaf][p][p] FP64.  Device pointers are used in place; host
- * pointers (pageable or pinned) are staged through the tree's device
- * buffers, and the call then returns after u is written back.  u must not
- * alias f. */
+ * f, u: [nleaf][p][p] FP64.  Device pointers are used in place.  Host
+ * pointers are staged through the tree's device buffers, except pinned
+ * (page-locked) ones on the split path with the near field, leaf-to-expansion
+ * and X list on the tensor cores, which the kernels read and write in place;
+ * either way the call returns after u is written.  u must not alias f. */
 bc_status bc_apply(bc_ctx *ctx, const bc_tree *tree, const double *f, double *u,
                    bc_precision prec, void *stream);
 

@@ -51,6 +51,17 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked (pinned, mapped) host memory, else nullptr.
+const void *pinned_device_ptr(const void *p)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 // Operator layouts (see OpSet): element (l,k) of a complex operator at [k][l].
 using cplx = std::complex<double>;
 inline cplx at2(const std::vector<double> &v, size_t i) { return cplx(v[2 * i], v[2 * i + 1]); }
@@ -715,7 +726,22 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
         if (e != cudaSuccess) return cuda_fail(e, "apply launch");
         return BC_OK;
     }
-    // host arrays: stage through the tree's device buffers
+    // Host arrays.  Pinned ones are read and written in place by the kernels
+    // when only the first kernel reads the input: the split path with the
+    // near field, leaf-to-expansion and X list on the tensor cores (parts 1, 2
+    // and 4), where the input digits (k_split_vec) read it and the leaf output
+    // writes the result, so that no copy stands between the calls' kernels.
+    // Otherwise they are staged through the tree's device buffers.
+    const double *pin_in = static_cast<const double *>(pinned_device_ptr(vin));
+    double *pin_out = static_cast<double *>(const_cast<void *>(pinned_device_ptr(vout)));
+    if (split && (ctx->split_parts & 7) == 7 && pin_in && pin_out) {
+        e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, pin_in, pin_out, st, ctx->pass_mask,
+                         ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr, ctx->m2l_tri, split);
+        if (e != cudaSuccess) return cuda_fail(e, "apply launch");
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "apply sync");
+        return BC_OK;
+    }
     bc_tree *t = const_cast<bc_tree *>(tree);
     size_t n = size_t(a.nleaf) * a.NP;
     if (!t->d.stage_in) {

@@ -249,6 +249,26 @@ def test_host_pointer_path_matches_device(ctx16, adaptive):
     assert torch.equal(ud, up)
 
 
+def test_split_pinned_host_arrays_in_place(ctx16, adaptive):
+    """Split precision with host arrays: pinned ones are read and written in
+    place by the kernels, pageable ones are staged, and a pinned input with a
+    pageable output is staged; each gives the device result bit for bit, in
+    both directions."""
+    lv, ix, iy, g, tree, geom, fvals, f = adaptive
+    gen = torch.Generator(device="cuda").manual_seed(19)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    S = bc.SPLIT_BF16
+    ud = bc.apply(tree, f, precision=S).cpu()
+    hd = bc.apply_adjoint(tree, gg, precision=S).cpu()
+    fp, gp = f.cpu().pin_memory(), gg.cpu().pin_memory()
+    up = bc.apply(tree, fp, out=torch.empty_like(fp).pin_memory(), precision=S)
+    hp = bc.apply_adjoint(tree, gp, out=torch.empty_like(gp).pin_memory(), precision=S)
+    assert torch.equal(up, ud) and torch.equal(hp, hd)
+    assert torch.equal(bc.apply(tree, f.cpu(), precision=S), ud)
+    assert torch.equal(bc.apply_adjoint(tree, gg.cpu(), precision=S), hd)
+    assert torch.equal(bc.apply(tree, fp, out=torch.zeros(fp.shape, dtype=fp.dtype), precision=S), ud)
+
+
 def test_eval_points(ctx16, adaptive):
     """Off-grid targets: interpolation of the leaf-node potential vs the oracle's
     potential at the points (bounded by the interpolation error), and vs an
