@@ -249,6 +249,21 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  * in milliseconds to ms[8] (stages 0, 5 and 7 are empty for FP64 applies). */
 bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
+/* The term schedule of the double-float upward shift of the split path, for
+ * the forward (adjoint = 0: M2M) or adjoint (L2L^H) operator of a context
+ * whose tables are built (host-only contexts too).  The nonzero terms
+ * (output l, input k) of the four child operators, output by output, are cut
+ * into 32 runs of *T terms, run i on lane i; a lane ends a partial sum where
+ * its run leaves an output, in slot l * (*maxp) + (its place among the
+ * output's lanes).  code: [T][32], input k in bits 0-7 and, where a partial
+ * sum ends, slot + 1 from bit 8 (0 elsewhere, and for the zero terms that
+ * pad the last runs); ops: [4][T][32][4], child q's entry of each term as
+ * {Re hi, Re lo, Im hi, Im lo} (x = hi + lo, both FP32); np: [nterms], the
+ * partial sums of each output.  With code, ops and np NULL only *T and
+ * *maxp are written; otherwise each non-NULL array receives its full size.
+ * BC_ERR_STATE before the tables are built. */
+bc_status bc_debug_up_schedule(const bc_ctx *ctx, int adjoint, int32_t *T, int32_t *maxp, uint32_t *code,
+                               float *ops, int32_t *np);
 /* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,
  * 8 blocks per SM, best of three timed runs).  The roofline denominator of
  * the FP64 passes. */

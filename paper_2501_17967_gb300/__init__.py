@@ -85,6 +85,8 @@ SIGNATURES = [
     ("bc_set_option", ctypes.c_int, [_VP, ctypes.c_char_p, ctypes.c_double]),
     ("bc_debug_set", ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int]),
     ("bc_debug_stage_times", ctypes.c_int, [_VP, ctypes.c_int, _DP]),
+    ("bc_debug_up_schedule", ctypes.c_int, [_VP, ctypes.c_int, _I32P, _I32P, ctypes.POINTER(ctypes.c_uint32),
+                                            ctypes.POINTER(ctypes.c_float), _I32P]),
     ("bc_debug_fp64_peak", ctypes.c_int, [ctypes.c_int, _DP]),
     ("bc_apply_noalloc", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_sync", ctypes.c_int, [_VP, _VP]),

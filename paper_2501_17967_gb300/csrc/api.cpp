@@ -144,6 +144,71 @@ void build_opsets(const HostTables &ht, OpBuild &F, OpBuild &A)
     }
 }
 
+// Term schedule of the double-float upward shift (DfSched) from the operator
+// of the four children, up[q][k][l] (output l, input k).  The k range of
+// each output over the four children (exact zeros left out; an all-zero
+// output keeps one zero term) gives the nonzero terms, taken output by
+// output; they are cut into 32 runs of T, lane i taking run i.  A lane ends
+// a partial sum (slot l * maxp + its place among the output's lanes) where
+// its run leaves an output.  Entries are split as x = hi + lo, hi the FP32
+// rounding of x and lo that of the remainder.
+struct UpScheduleHost {
+    int T = 0, maxp = 0;
+    std::vector<uint32_t> code;   // [T][32]
+    std::vector<float4> ops;      // [4][T][32]
+    std::vector<int32_t> np;      // [P1]
+};
+
+UpScheduleHost build_up_schedule(const std::vector<double2> &up)
+{
+    int P1 = 0;   // up is [4][P1][P1]
+    while (size_t(4) * (P1 + 1) * (P1 + 1) <= up.size()) P1++;
+    auto dfs = [](double x) {
+        const float h = float(x);
+        return std::make_pair(h, float(x - double(h)));
+    };
+    std::vector<int> klo(P1, P1), khi(P1, -1);
+    for (int q = 0; q < 4; q++)
+        for (int k = 0; k < P1; k++)
+            for (int l = 0; l < P1; l++) {
+                const double2 o = up[(size_t(q) * P1 + k) * P1 + l];
+                if (o.x != 0.0 || o.y != 0.0) {
+                    klo[l] = std::min(klo[l], k);
+                    khi[l] = std::max(khi[l], k);
+                }
+            }
+    std::vector<std::pair<int, int>> terms;   // (l, k), output by output
+    for (int l = 0; l < P1; l++) {
+        if (khi[l] < klo[l]) klo[l] = khi[l] = 0;
+        for (int k = klo[l]; k <= khi[l]; k++) terms.emplace_back(l, k);
+    }
+    UpScheduleHost r;
+    const int N = int(terms.size());
+    r.T = (N + 31) / 32;
+    std::vector<int> lf(P1, -1);
+    r.np.assign(P1, 0);
+    for (int i = 0; i < N; i++) {
+        const int l = terms[i].first, lane = i / r.T;
+        if (lf[l] < 0) lf[l] = lane;
+        r.np[l] = lane - lf[l] + 1;
+    }
+    r.maxp = P1 > 0 ? *std::max_element(r.np.begin(), r.np.end()) : 0;
+    r.code.assign(size_t(r.T) * 32, 0u);
+    r.ops.assign(size_t(4) * r.T * 32, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int i = 0; i < N; i++) {
+        const int l = terms[i].first, k = terms[i].second, lane = i / r.T, t = i % r.T;
+        const bool last = i + 1 == N || terms[i + 1].first != l || (i + 1) % r.T == 0;
+        const uint32_t slot = uint32_t(l * r.maxp + lane - lf[l]);
+        r.code[size_t(t) * 32 + lane] = uint32_t(k) | (last ? (slot + 1u) << 8 : 0u);
+        for (int q = 0; q < 4; q++) {
+            const double2 o = up[(size_t(q) * P1 + k) * P1 + l];
+            const auto re = dfs(o.x), im = dfs(o.y);
+            r.ops[(size_t(q) * r.T + t) * 32 + lane] = make_float4(re.first, re.second, im.first, im.second);
+        }
+    }
+    return r;
+}
+
 bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
 {
     cudaError_t e;
@@ -174,58 +239,20 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
             if (e != cudaSuccess) return cuda_fail(e, "tables upload");
             (which == 2 ? os.leafA_df : os.par_df) = pf;
         }
-        // the term schedule of the double-float climb (DfSched): the k range
-        // of each output over the four children, exact zeros left out
-        int P1 = 0;   // up is [4][P1][P1]
-        while (size_t(4) * (P1 + 1) * (P1 + 1) <= b.up.size()) P1++;
-        std::vector<int> klo(P1, P1), khi(P1, -1);
-        for (int q = 0; q < 4; q++)
-            for (int k = 0; k < P1; k++)
-                for (int l = 0; l < P1; l++) {
-                    const double2 o = b.up[(size_t(q) * P1 + k) * P1 + l];
-                    if (o.x != 0.0 || o.y != 0.0) {
-                        klo[l] = std::min(klo[l], k);
-                        khi[l] = std::max(khi[l], k);
-                    }
-                }
-        std::vector<std::pair<int, int>> terms;   // (l, k), output by output
-        for (int l = 0; l < P1; l++) {
-            if (khi[l] < klo[l]) klo[l] = khi[l] = 0;   // an all-zero output keeps one (zero) term
-            for (int k = klo[l]; k <= khi[l]; k++) terms.emplace_back(l, k);
-        }
-        const int N = int(terms.size()), T = (N + 31) / 32;
-        std::vector<int> lf(P1, -1), np(P1, 0);
-        for (int i = 0; i < N; i++) {
-            const int l = terms[i].first, lane = i / T;
-            if (lf[l] < 0) lf[l] = lane;
-            np[l] = lane - lf[l] + 1;
-        }
-        const int maxp = *std::max_element(np.begin(), np.end());
-        std::vector<uint32_t> code(size_t(T) * 32, 0u);
-        std::vector<float4> ops(size_t(4) * T * 32, make_float4(0.f, 0.f, 0.f, 0.f));
-        for (int i = 0; i < N; i++) {
-            const int l = terms[i].first, k = terms[i].second, lane = i / T, t = i % T;
-            const bool last = i + 1 == N || terms[i + 1].first != l || (i + 1) % T == 0;
-            const uint32_t slot = uint32_t(l * maxp + lane - lf[l]);
-            code[size_t(t) * 32 + lane] = uint32_t(k) | (last ? (slot + 1u) << 8 : 0u);
-            for (int q = 0; q < 4; q++) {
-                const double2 o = b.up[(size_t(q) * P1 + k) * P1 + l];
-                const auto re = dfs(o.x), im = dfs(o.y);
-                ops[(size_t(q) * T + t) * 32 + lane] = make_float4(re.first, re.second, im.first, im.second);
-            }
-        }
+        // the term schedule of the double-float climb (DfSched)
+        const UpScheduleHost us = build_up_schedule(b.up);
         uint32_t *pc = nullptr;
         float4 *po = nullptr;
         int32_t *pn = nullptr;
-        if ((e = dev_upload(dt.allocs, &pc, code.data(), code.size())) != cudaSuccess ||
-            (e = dev_upload(dt.allocs, &po, ops.data(), ops.size())) != cudaSuccess ||
-            (e = dev_upload(dt.allocs, &pn, np.data(), np.size())) != cudaSuccess)
+        if ((e = dev_upload(dt.allocs, &pc, us.code.data(), us.code.size())) != cudaSuccess ||
+            (e = dev_upload(dt.allocs, &po, us.ops.data(), us.ops.size())) != cudaSuccess ||
+            (e = dev_upload(dt.allocs, &pn, us.np.data(), us.np.size())) != cudaSuccess)
             return cuda_fail(e, "tables upload");
         os.up_s.code = pc;
         os.up_s.ops = po;
         os.up_s.np = pn;
-        os.up_s.T = T;
-        os.up_s.maxp = maxp;
+        os.up_s.T = us.T;
+        os.up_s.maxp = us.maxp;
     }
     e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
@@ -1278,6 +1305,28 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
     if (which < 0 || which >= int(sizeof(v) / sizeof(v[0]))) { set_error("bc_table_export: which must be 0..9"); return BC_ERR_ARG; }
     *count = int64_t(v[which]->size());
     if (out) std::copy(v[which]->begin(), v[which]->end(), out);
+    return BC_OK;
+}
+
+bc_status bc_debug_up_schedule(const bc_ctx *ctx, int adjoint, int32_t *T, int32_t *maxp, uint32_t *code,
+                               float *ops, int32_t *np)
+{
+    if (!ctx || !T || !maxp) { set_error("bc_debug_up_schedule: NULL argument"); return BC_ERR_ARG; }
+    if (!ctx->tables_ready) { set_error("bc_debug_up_schedule: tables not built"); return BC_ERR_STATE; }
+    OpBuild F, A;
+    build_opsets(ctx->ht, F, A);
+    const UpScheduleHost us = build_up_schedule(adjoint ? A.up : F.up);
+    *T = us.T;
+    *maxp = us.maxp;
+    if (code) std::copy(us.code.begin(), us.code.end(), code);
+    if (ops)
+        for (size_t i = 0; i < us.ops.size(); i++) {
+            ops[4 * i] = us.ops[i].x;
+            ops[4 * i + 1] = us.ops[i].y;
+            ops[4 * i + 2] = us.ops[i].z;
+            ops[4 * i + 3] = us.ops[i].w;
+        }
+    if (np) std::copy(us.np.begin(), us.np.end(), np);
     return BC_OK;
 }
 

@@ -12,6 +12,7 @@
   value 2 ln 2 + pi - 6, and tables related by a reflection agree after the
   matching node permutation.
 """
+import ctypes
 import math
 import os
 import re
@@ -285,3 +286,72 @@ def test_far_operators_consistency():
         A_child = 0.25 * (Q @ poly(cx + 0.5 * X, cy + 0.5 * Y).ravel())
         A_sum += M2M[q] @ A_child
     assert np.abs(A_sum - A_par).max() < 1e-14 * np.abs(A_par).max()
+
+
+@pytest.mark.parametrize("nterms", [8, 24, 31])
+def test_up_schedule_covers_each_term_once(nterms):
+    """Host logic of the double-float climb's term schedule, both directions:
+    the shifts are lower-triangular (output l reads inputs k <= l); the lane
+    runs cover every term exactly once, with zero padding only after a lane's
+    last partial sum; every partial-sum slot of an output is ended by exactly
+    one lane; the entries are the operator's to double-float rounding; and
+    the scheduled sums reproduce the dense shift."""
+    P1 = nterms
+    ctx = bc.Context(p=8, nterms=P1, device=-1, cache_dir=None)
+    lib = bc._load()
+    M2M = ctx.table(5).view(complex).reshape(4, P1, P1)
+    L2L = ctx.table(6).view(complex).reshape(4, P1, P1)
+    rng = np.random.default_rng(P1)
+    for adj in (0, 1):
+        # the operator in the schedule's layout up[q][k][l] (output l, input k):
+        # forward M2M_q[l][k], adjoint conj(L2L_q[k][l])
+        up = np.conj(L2L) if adj else np.transpose(M2M, (0, 2, 1))
+        nz = np.abs(up).max(axis=0) != 0
+        terms = {(l, k) for k in range(P1) for l in range(P1) if nz[k, l]}
+        assert terms == {(l, k) for l in range(P1) for k in range(l + 1)}
+        Tc, mc = ctypes.c_int32(), ctypes.c_int32()
+        bc._check(lib.bc_debug_up_schedule(ctx.handle, adj, ctypes.byref(Tc), ctypes.byref(mc), None, None, None))
+        T, maxp = Tc.value, mc.value
+        assert T == -(-len(terms) // 32)
+        code = np.zeros((T, 32), np.uint32)
+        ops = np.zeros((4, T, 32, 4), np.float32)
+        nps = np.zeros(P1, np.int32)
+        bc._check(lib.bc_debug_up_schedule(ctx.handle, adj, ctypes.byref(Tc), ctypes.byref(mc),
+                                           code.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                           ops.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                           nps.ctypes.data_as(bc._I32P)))
+        opv = (ops[..., 0].astype(np.float64) + ops[..., 1]) + 1j * (ops[..., 2].astype(np.float64) + ops[..., 3])
+        seen, ends = [], {}
+        for lane in range(32):
+            run = []
+            for t in range(T):
+                c = int(code[t, lane])
+                run.append((t, c & 255))
+                if c >> 8:
+                    slot = (c >> 8) - 1
+                    l = slot // maxp
+                    assert slot % maxp < nps[l], (lane, t, slot)
+                    ends[slot] = ends.get(slot, 0) + 1
+                    for tt, k in run:
+                        seen.append((l, k))
+                        err = np.abs(opv[:, tt, lane] - up[:, k, l])
+                        assert np.all(err <= 2.0 ** -46 * np.abs(up[:, k, l])), (l, k)
+                    run = []
+            for tt, k in run:   # padding after the lane's last partial sum
+                assert k == 0 and not ops[:, tt, lane].any()
+        assert len(seen) == len(terms) and set(seen) == terms
+        assert len(ends) == int(nps.sum())
+        assert all(ends.get(l * maxp + j) == 1 for l in range(P1) for j in range(nps[l]))
+        x = rng.standard_normal((4, P1)) + 1j * rng.standard_normal((4, P1))
+        out = np.zeros(P1, complex)
+        for q in range(4):
+            for lane in range(32):
+                acc = 0.0
+                for t in range(T):
+                    c = int(code[t, lane])
+                    acc += opv[q, t, lane] * x[q, c & 255]
+                    if c >> 8:
+                        out[((c >> 8) - 1) // maxp] += acc
+                        acc = 0.0
+        ref = np.einsum("qkl,qk->l", up, x)
+        assert np.abs(out - ref).max() < 1e-13 * np.abs(ref).max()
