@@ -57,12 +57,28 @@ typedef enum {
     BC_ERR_STATE = -7        /* call order violated (e.g. apply before tables) */
 } bc_status;
 
+/* Arithmetic of an apply.  "BF16 digits" means: each FP64 operand row (an
+ * operator row, an input vector) is scaled by a power of two, rounded to a
+ * 40-bit fixed-point integer and cut into five BF16 digits; the digit
+ * products run on the tensor cores (tcgen05, FP32 accumulation, exact), and
+ * the recombination is integer/FP64.  The rounding of the operands to 40 bits
+ * is the only error (about 2^-40 of sum |A_ik v_k| per output). */
 typedef enum {
-    BC_FP64 = 0,       /* every stage in native FP64 */
-    BC_SPLIT_BF16 = 1  /* near-field table contractions on BF16 tensor cores with
-                          FP64 data split into exact BF16 slices, FP32
-                          accumulation, integer/FP64 recombination; the far
-                          field, log corrections and final sums stay FP64 */
+    BC_FP64 = 0,           /* every step in native FP64 */
+    BC_SPLIT_BF16 = 1,     /* BF16 digits for the fixed-operator products: the
+                              near-field tables, P2M, L2P, the W list (M2P) and
+                              the X list (P2L), and their adjoints.  Native FP64
+                              for the multipole-to-local translations, the
+                              M2M and L2L shifts, every log-kernel scaling
+                              term and every sum of partial results
+                              (p = 16 only) */
+    BC_SPLIT_BF16_ALL = 2  /* BC_SPLIT_BF16 plus the multipole-to-local
+                              translations on BF16 digits (their log terms
+                              stay FP64) and the M2M / L2L shifts in
+                              double-float arithmetic (pairs of FP32 numbers,
+                              about 48 bits, on the FP32 units); the V- and
+                              X-list sums and the local expansions handed to
+                              later steps stay FP64 (p = 16 only) */
 } bc_precision;
 
 typedef struct {
@@ -282,7 +298,10 @@ bc_status bc_debug_fp64_peak(int device, double *tflops);
  * a device looks up the array's device address (cudaGetSymbolAddress) and so
  * should come before any stream capture.  All calls share the array and it
  * keeps what the last call left in it (nothing in it needs clearing); calls
- * that overlap on the GPU race with each other, so serialise them. */
+ * that overlap on the GPU race with each other, so serialise them.  The call
+ * also uses the tree's own per-box flags and X-list buffer, so it races with
+ * an overlapping bc_apply or bc_apply_adjoint on the same tree as well: the
+ * caller serialises every apply of one tree. */
 bc_status bc_apply_noalloc(bc_ctx *ctx, const bc_tree *tree, const double *in, double *out, int adjoint,
                            void *stream);
 

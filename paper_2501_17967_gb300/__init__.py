@@ -19,12 +19,17 @@ import numpy as np
 
 from . import build as _build_mod
 
-__all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "apply", "apply_adjoint",
-           "eval_points", "BoxCodeApply", "lib_path"]
+__all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "SPLIT_BF16_ALL", "apply",
+           "apply_adjoint", "eval_points", "BoxCodeApply", "lib_path"]
 
+# precision modes (bc_precision): FP64 everywhere; BF16 digit products for the
+# fixed-operator contractions (near field, P2M, L2P, W and X lists) with the
+# M2L, the shifts, the log terms and every sum in FP64; the same plus the M2L
+# on BF16 digits and the shifts in double-float
 FP64 = 0
 SPLIT_BF16 = 1
-SPLIT_ORDERS = (16,)    # orders p with a split-precision near field
+SPLIT_BF16_ALL = 2
+SPLIT_ORDERS = (16,)    # orders p with a split-precision path
 _STATUS = {0: "BC_OK", -1: "BC_ERR_ARG", -2: "BC_ERR_TREE", -3: "BC_ERR_CUDA", -4: "BC_ERR_OOM",
            -5: "BC_ERR_TIMEOUT", -6: "BC_ERR_UNSUPPORTED", -7: "BC_ERR_STATE"}
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tables")

@@ -209,7 +209,139 @@ UpScheduleHost build_up_schedule(const std::vector<double2> &up)
     return r;
 }
 
-bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
+// Factored FP64 shifts (ShiftFac).  With delta_q = (2qx - 1) + i (2qy - 1)
+// the child's centre offset in child radii, the four shifts of the scaled
+// expansions (host tables: M2M[l][k] = C(l-1,k-1) 2^-l delta^(l-k), M2M[l][0] =
+// -(delta/2)^l / l, L2L[m][l] = C(l,m) 2^-l delta^(l-m)) factor as
+//   forward up (M2M):     so = (delta/2)^l,        si = delta^-k,         B[l][k] = C(l-1,k-1), B[l][0] = -1/l
+//   forward par (L2L):    so = delta^-m,           si = (delta/2)^l,      B[m][l] = C(l,m)
+//   adjoint up (L2L^H):   so = (conj delta/2)^l,   si = conj(delta)^-k,   B[l][k] = C(l,k)
+//   adjoint par (M2M^H):  so = conj(delta)^-l,     si = (conj delta/2)^k, B[l][k] = C(k-1,l-1), B[0][k] = -1/k
+// (B[0][0] = 1 in the M2M cases).  The products are checked against the
+// dense operators (`dense`, layout [q][k][l]) before they are used.
+struct ShiftFacHost {
+    int T = 0, maxp = 0;
+    std::vector<double2> si, so;   // [4][P1]
+    std::vector<uint32_t> code;    // [T][32]
+    std::vector<double> coef;      // [T][32]
+    std::vector<int32_t> np;       // [P1]
+};
+
+bc_status build_shift_fac(int P1, bool par, bool adj, const std::vector<double2> &dense, ShiftFacHost &r)
+{
+    using lcplx = std::complex<long double>;
+    std::vector<long double> bin(size_t(2 * P1 + 2) * (2 * P1 + 2), 0.0L);
+    auto C = [&](int n, int k) -> long double & { return bin[size_t(n) * (2 * P1 + 2) + k]; };
+    for (int n = 0; n < 2 * P1 + 2; n++) {
+        C(n, 0) = 1.0L;
+        for (int k = 1; k <= n; k++) C(n, k) = C(n - 1, k - 1) + (k <= n - 1 ? C(n - 1, k) : 0.0L);
+    }
+    // B[l][k] (output l, input k)
+    std::vector<long double> B(size_t(P1) * P1, 0.0L);
+    for (int l = 0; l < P1; l++)
+        for (int k = 0; k < P1; k++) {
+            long double v = 0.0L;
+            const bool m2m = par == adj;   // forward up and adjoint par come from M2M
+            if (m2m) {
+                const int o = adj ? k : l, i = adj ? l : k;   // M2M element (o, i), o >= i
+                if (o == 0 && i == 0) v = 1.0L;
+                else if (o >= 1 && i == 0) v = -1.0L / o;
+                else if (i >= 1 && i <= o) v = C(o - 1, i - 1);
+            } else {
+                const int o = adj ? l : k, i = adj ? k : l;   // L2L element (m = i, l = o), o >= i
+                if (o >= i) v = C(o, i);
+            }
+            B[size_t(l) * P1 + k] = v;
+        }
+    r.si.assign(size_t(4) * P1, make_double2(0, 0));
+    r.so.assign(size_t(4) * P1, make_double2(0, 0));
+    long double worst = 0.0L;
+    for (int q = 0; q < 4; q++) {
+        lcplx dl(2.0L * (q & 1) - 1.0L, 2.0L * (q >> 1) - 1.0L);
+        if (adj) dl = std::conj(dl);
+        std::vector<lcplx> si(P1), so(P1);
+        lcplx ph = 1.0L, pinv = 1.0L;   // (delta/2)^n, delta^-n
+        for (int n = 0; n < P1; n++) {
+            // child -> parent: so = (delta/2)^l, si = delta^-k; parent -> child: the reverse
+            if (!par) { so[n] = ph; si[n] = pinv; }
+            else { so[n] = pinv; si[n] = ph; }
+            ph *= dl / 2.0L;
+            pinv /= dl;
+        }
+        for (int n = 0; n < P1; n++) {
+            r.si[size_t(q) * P1 + n] = make_double2(double(si[n].real()), double(si[n].imag()));
+            r.so[size_t(q) * P1 + n] = make_double2(double(so[n].real()), double(so[n].imag()));
+        }
+        // check against the dense operator, element by element, relative to
+        // the largest entry of its output row
+        for (int l = 0; l < P1; l++) {
+            long double rowmax = 0.0L;
+            for (int k = 0; k < P1; k++) {
+                const double2 d = dense[(size_t(q) * P1 + k) * P1 + l];
+                rowmax = std::max(rowmax, std::abs(lcplx(d.x, d.y)));
+            }
+            for (int k = 0; k < P1; k++) {
+                const double2 d = dense[(size_t(q) * P1 + k) * P1 + l];
+                const lcplx f = so[l] * B[size_t(l) * P1 + k] * si[k];
+                const long double e = std::abs(f - lcplx(d.x, d.y)) / (rowmax > 0 ? rowmax : 1.0L);
+                worst = std::max(worst, e);
+            }
+        }
+    }
+    if (!(worst < 1e-14L)) {
+        set_error("tables: factored %s shift (%s) differs from the dense operator by %.3Le", par ? "parent" : "child",
+                  adj ? "adjoint" : "forward", worst);
+        return BC_ERR_STATE;
+    }
+    // term schedule over B's nonzeros, output by output, 32 runs
+    std::vector<std::pair<int, int>> terms;
+    for (int l = 0; l < P1; l++) {
+        bool any = false;
+        for (int k = 0; k < P1; k++)
+            if (B[size_t(l) * P1 + k] != 0.0L) { terms.emplace_back(l, k); any = true; }
+        if (!any) terms.emplace_back(l, 0);   // an all-zero output keeps one zero term
+    }
+    const int N = int(terms.size());
+    r.T = (N + 31) / 32;
+    std::vector<int> lf(P1, -1);
+    r.np.assign(P1, 0);
+    for (int i = 0; i < N; i++) {
+        const int l = terms[i].first, lane = i / r.T;
+        if (lf[l] < 0) lf[l] = lane;
+        r.np[l] = lane - lf[l] + 1;
+    }
+    r.maxp = *std::max_element(r.np.begin(), r.np.end());
+    r.code.assign(size_t(r.T) * 32, 0u);
+    r.coef.assign(size_t(r.T) * 32, 0.0);
+    for (int i = 0; i < N; i++) {
+        const int l = terms[i].first, k = terms[i].second, lane = i / r.T, t = i % r.T;
+        const bool last = i + 1 == N || terms[i + 1].first != l || (i + 1) % r.T == 0;
+        const uint32_t slot = uint32_t(l * r.maxp + lane - lf[l]);
+        r.code[size_t(t) * 32 + lane] = uint32_t(k) | (last ? (slot + 1u) << 8 : 0u);
+        r.coef[size_t(t) * 32 + lane] = double(B[size_t(l) * P1 + k]);
+    }
+    return BC_OK;
+}
+
+bc_status upload_shift_fac(DevTables &dt, ShiftFac &f, const ShiftFacHost &h)
+{
+    double2 *psi = nullptr, *pso = nullptr;
+    uint32_t *pc = nullptr;
+    double *pf = nullptr;
+    int32_t *pn = nullptr;
+    cudaError_t e;
+    if ((e = dev_upload(dt.allocs, &psi, h.si.data(), h.si.size())) != cudaSuccess ||
+        (e = dev_upload(dt.allocs, &pso, h.so.data(), h.so.size())) != cudaSuccess ||
+        (e = dev_upload(dt.allocs, &pc, h.code.data(), h.code.size())) != cudaSuccess ||
+        (e = dev_upload(dt.allocs, &pf, h.coef.data(), h.coef.size())) != cudaSuccess ||
+        (e = dev_upload(dt.allocs, &pn, h.np.data(), h.np.size())) != cudaSuccess)
+        return cuda_fail(e, "tables upload");
+    f.si = psi; f.so = pso; f.code = pc; f.coef = pf; f.np = pn;
+    f.T = h.T; f.maxp = h.maxp;
+    return BC_OK;
+}
+
+bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b, bool adj)
 {
     cudaError_t e;
     double2 *p;
@@ -254,6 +386,15 @@ bc_status upload_opset(DevTables &dt, OpSet &os, const OpBuild &b)
         os.up_s.T = us.T;
         os.up_s.maxp = us.maxp;
     }
+    {
+        const int P1 = int(std::lround(std::sqrt(double(b.up.size() / 4))));
+        ShiftFacHost fu, fp;
+        bc_status s;
+        if ((s = build_shift_fac(P1, false, adj, b.up, fu)) != BC_OK ||
+            (s = build_shift_fac(P1, true, adj, b.par, fp)) != BC_OK ||
+            (s = upload_shift_fac(dt, os.up_f, fu)) != BC_OK || (s = upload_shift_fac(dt, os.par_f, fp)) != BC_OK)
+            return s;
+    }
     e = dev_upload(dt.allocs, &q, b.t.data(), b.t.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
     os.t = q;
@@ -296,7 +437,6 @@ bc_status upload_tree(bc_tree *t)
             for (int32_t k = h.x_ptr[b]; k < h.x_ptr[b + 1]; k++) xb[k] = int32_t(b);
         if ((e = dev_upload(d.allocs, &d.v_box, vb.data(), vb.size())) != cudaSuccess ||
             (e = dev_upload(d.allocs, &d.x_box, xb.data(), xb.size())) != cudaSuccess ||
-            (e = dev_upload<double2>(d.allocs, &d.Pv, nullptr, h.v_src.size() * size_t(P1))) != cudaSuccess ||
             (e = dev_upload<double2>(d.allocs, &d.PX, nullptr, h.x_src.size() * size_t(P1))) != cudaSuccess)
             return cuda_fail(e, "tree upload");
     }
@@ -329,6 +469,8 @@ bc_status finish_tree(bc_ctx *ctx, bc_tree **out, bc_tree *t)
     return BC_OK;
 }
 
+}  // namespace
+
 PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
 {
     PassArgs a;
@@ -338,10 +480,14 @@ PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
     a.nbox = int64_t(t->h.box_level.size());
     a.up_blocks = ctx->up_blocks;
     a.shift_blocks = ctx->shift_blocks;
+    a.down_blocks = ctx->down_blocks;
+    a.m2l_bps = ctx->m2l_bps;
     a.wait_limit = ctx->split.wait_limit;
     a.err = ctx->dev_err;
     return a;
 }
+
+namespace {
 
 // Digits of one FP64 matrix row for the split near field: row scaled by 2^-E
 // into (-1/2, 1/2), rounded to a 40-bit integer, five balanced base-256 digits.
@@ -598,7 +744,8 @@ bc_status build_split_tree(bc_tree *t)
         (e = dev_upload<uint16_t>(al, &s.vdig, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
         (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess ||
         (e = dev_upload<uint16_t>(al, &s.edig, nullptr, size_t(2 * nbox) * kSplitSlices * kSplitKE)) != cudaSuccess ||
-        (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess)
+        (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess ||
+        (e = dev_upload<double2>(al, &t->d.Pv, nullptr, h.v_src.size() * size_t(P1))) != cudaSuccess)
         return cuda_fail(e, "split tree upload");
     // owners of the near and W entries, box of each X entry
     std::vector<int32_t> near_owner(nn), w_owner(nw), x_box(nx);
@@ -712,6 +859,15 @@ bc_status build_split_tree(bc_tree *t)
     return BC_OK;
 }
 
+// CTAs of the near-field launch on the internal stream: the option, else all
+// SMs when it runs beside the FP64 M2L (one tensor CTA per SM next to the M2L
+// blocks), three quarters of them when it runs beside the level passes
+int near_ctas_for(const bc_ctx *ctx, int parts)
+{
+    if (ctx->overlap_ctas > 0) return ctx->overlap_ctas;
+    return (parts & 32) ? std::max(1, 3 * split_sm_count() / 4) : split_sm_count();
+}
+
 bc_status check_apply_args(bc_ctx *ctx, const bc_tree *tree, const void *in, const void *out, bc_precision prec)
 {
     if (!ctx || !tree || !in || !out) { set_error("apply: NULL argument"); return BC_ERR_ARG; }
@@ -719,7 +875,7 @@ bc_status check_apply_args(bc_ctx *ctx, const bc_tree *tree, const void *in, con
     if (ctx->device < 0) { set_error("apply: host-only context (device -1) cannot apply"); return BC_ERR_STATE; }
     if (!ctx->tables_ready) { set_error("apply: call bc_tables_build first"); return BC_ERR_STATE; }
     if (in == out) { set_error("apply: output must not alias input"); return BC_ERR_ARG; }
-    if (prec != BC_FP64 && prec != BC_SPLIT_BF16) { set_error("apply: unknown precision %d", int(prec)); return BC_ERR_ARG; }
+    if (prec != BC_FP64 && !is_split(prec)) { set_error("apply: unknown precision %d", int(prec)); return BC_ERR_ARG; }
     return BC_OK;
 }
 
@@ -734,11 +890,12 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     PassArgs a = pass_args(ctx, tree);
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
-    SplitLaunch sl{&ctx->split, nullptr, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr,
-                   ctx->overlap_ctas > 0 ? ctx->overlap_ctas : std::max(1, 3 * split_sm_count() / 4)};
+    const int parts = split_parts_for(int(prec), ctx->split_parts);
+    SplitLaunch sl{&ctx->split, nullptr, parts, ctx->split_overlap ? &ctx->side : nullptr,
+                   near_ctas_for(ctx, parts)};
     const SplitLaunch *split = nullptr;
     bc_tree *tw = const_cast<bc_tree *>(tree);
-    if (prec == BC_SPLIT_BF16) {
+    if (is_split(prec)) {
         if (!ctx->split_ready) {
             set_error("apply: split precision is provided for p = 16 with nterms <= 32 only");
             return BC_ERR_UNSUPPORTED;
@@ -761,7 +918,7 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     // Otherwise they are staged through the tree's device buffers.
     const double *pin_in = static_cast<const double *>(pinned_device_ptr(vin));
     double *pin_out = static_cast<double *>(const_cast<void *>(pinned_device_ptr(vout)));
-    if (split && (ctx->split_parts & 7) == 7 && pin_in && pin_out) {
+    if (split && (parts & 7) == 7 && pin_in && pin_out) {
         e = launch_apply(a, tree->h, tree->d, ctx->dt, adj, pin_in, pin_out, st, ctx->pass_mask,
                          ctx->timing ? ctx->ev[adj ? 1 : 0] : nullptr, ctx->m2l_tri, split);
         if (e != cudaSuccess) return cuda_fail(e, "apply launch");
@@ -810,7 +967,7 @@ struct bc_batch {
     struct Graph {
         cudaGraphExec_t exec = nullptr;
         int leaf_bps = 0, m2l_bps = 0;
-    } g[2][2];   // [precision][adjoint]
+    } g[3][2];   // [precision][adjoint]
     std::vector<void *> allocs;
 };
 
@@ -829,13 +986,14 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     bc_ctx *ctx = b->ctx;
     PassArgs a = pass_args(ctx, b->u);
     a.leaf_bps = leaf_bps;
-    a.m2l_bps = m2l_bps;
-    SplitLaunch sl{&ctx->split, &b->u->sp, ctx->split_parts, ctx->split_overlap ? &ctx->side : nullptr,
-                   ctx->overlap_ctas > 0 ? ctx->overlap_ctas : std::max(1, 3 * split_sm_count() / 4)};
+    if (m2l_bps) a.m2l_bps = m2l_bps;
+    const int parts = split_parts_for(prec, ctx->split_parts);
+    SplitLaunch sl{&ctx->split, &b->u->sp, parts, ctx->split_overlap ? &ctx->side : nullptr,
+                   near_ctas_for(ctx, parts)};
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
     cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,
-                                  ctx->m2l_tri, prec == BC_SPLIT_BF16 ? &sl : nullptr);
+                                  ctx->m2l_tri, is_split(prec) ? &sl : nullptr);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(b->cap, &graph);
     if (le != cudaSuccess) {
@@ -926,13 +1084,25 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
     if (ctx->tables_ready) return BC_OK;
     bc_status s = build_tables(ctx->ht, ctx->p, ctx->P1, cache_dir);
     if (s != BC_OK) return s;
-    if (ctx->device < 0) { ctx->tables_ready = true; return BC_OK; }
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     OpBuild F, A;
     build_opsets(ctx->ht, F, A);
-    if ((s = upload_opset(ctx->dt, ctx->dt.fwd, F)) != BC_OK) return s;
-    if ((s = upload_opset(ctx->dt, ctx->dt.adj, A)) != BC_OK) return s;
+    if (ctx->device < 0) {
+        // host-only: the factored shifts are built and checked against the
+        // dense operators all the same (nothing is uploaded)
+        for (int adj = 0; adj < 2; adj++) {
+            ShiftFacHost fu, fp;
+            const OpBuild &b = adj ? A : F;
+            if ((s = build_shift_fac(ctx->P1, false, adj != 0, b.up, fu)) != BC_OK ||
+                (s = build_shift_fac(ctx->P1, true, adj != 0, b.par, fp)) != BC_OK)
+                return s;
+        }
+        ctx->tables_ready = true;
+        return BC_OK;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    if ((s = upload_opset(ctx->dt, ctx->dt.fwd, F, false)) != BC_OK) return s;
+    if ((s = upload_opset(ctx->dt, ctx->dt.adj, A, true)) != BC_OK) return s;
     e = dev_upload(ctx->dt.allocs, &ctx->dt.wvec, ctx->ht.w.data(), ctx->ht.w.size());
     if (e != cudaSuccess) return cuda_fail(e, "tables upload");
     {
@@ -965,9 +1135,13 @@ bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir)
     e = dev_upload<int32_t>(ctx->dt.allocs, &ctx->dev_err, nullptr, 1);
     if (e != cudaSuccess) return cuda_fail(e, "error flag");
     // two upward blocks per SM leave room for a tensor-core CTA beside them
-    e = fp64_prepare(ctx->NP, ctx->P1, std::max(ctx->dt.fwd.up_s.T, ctx->dt.adj.up_s.T),
-                     std::max(ctx->dt.fwd.up_s.maxp, ctx->dt.adj.up_s.maxp), 2, 4, &ctx->up_blocks,
-                     &ctx->shift_blocks);
+    {
+        const OpSet &F = ctx->dt.fwd, &A = ctx->dt.adj;
+        const int fT = std::max(std::max(F.up_f.T, A.up_f.T), std::max(F.par_f.T, A.par_f.T));
+        const int fm = std::max(std::max(F.up_f.maxp, A.up_f.maxp), std::max(F.par_f.maxp, A.par_f.maxp));
+        e = fp64_prepare(ctx->NP, ctx->P1, std::max(F.up_s.T, A.up_s.T), std::max(F.up_s.maxp, A.up_s.maxp), fT, fm,
+                         2, 4, &ctx->up_blocks, &ctx->shift_blocks, &ctx->down_blocks);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "FP64 kernel occupancy");
     s = build_split_tables(ctx);
     if (s != BC_OK) return s;
@@ -1201,7 +1375,8 @@ void bc_batch_destroy(bc_batch *b)
 bc_status bc_batch_autotune(bc_ctx *ctx, bc_batch *b, bc_precision prec, void *stream)
 {
     if (!ctx || !b || b->ctx != ctx) { set_error("bc_batch_autotune: bad argument"); return BC_ERR_ARG; }
-    if (prec == BC_SPLIT_BF16 && !ctx->split_ready) { set_error("bc_batch_autotune: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    if (prec != BC_FP64 && !is_split(prec)) { set_error("bc_batch_autotune: unknown precision"); return BC_ERR_ARG; }
+    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_autotune: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     static const int cand[][2] = {{16, 12}, {8, 8}, {4, 4}, {16, 16}, {8, 12}, {32, 12}, {16, 6}};
     cudaEvent_t e0, e1;
@@ -1251,8 +1426,8 @@ bc_status bc_batch_run(bc_ctx *ctx, bc_batch *b, const double *const *in, double
                        int adjoint, void *stream)
 {
     if (!ctx || !b || b->ctx != ctx || !in || !out) { set_error("bc_batch_run: bad argument"); return BC_ERR_ARG; }
-    if (prec != BC_FP64 && prec != BC_SPLIT_BF16) { set_error("bc_batch_run: unknown precision"); return BC_ERR_ARG; }
-    if (prec == BC_SPLIT_BF16 && !ctx->split_ready) { set_error("bc_batch_run: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    if (prec != BC_FP64 && !is_split(prec)) { set_error("bc_batch_run: unknown precision"); return BC_ERR_ARG; }
+    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_run: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
     const int n = int(b->trees.size());
     for (int k = 0; k < n; k++)
         if (!in[k] || !out[k] || !is_device_ptr(in[k]) || !is_device_ptr(out[k]) || in[k] == out[k]) {
@@ -1289,7 +1464,7 @@ int64_t bc_batch_nleaf(const bc_batch *b) { return b ? b->u->h.nleaf : 0; }
 
 bc_status bc_batch_shape(const bc_batch *b, int precision, int adjoint, int *leaf_blocks_per_sm, int *m2l_blocks_per_sm)
 {
-    if (!b || precision < 0 || precision > 1 || !leaf_blocks_per_sm || !m2l_blocks_per_sm) { set_error("bc_batch_shape: bad argument"); return BC_ERR_ARG; }
+    if (!b || precision < 0 || precision > 2 || !leaf_blocks_per_sm || !m2l_blocks_per_sm) { set_error("bc_batch_shape: bad argument"); return BC_ERR_ARG; }
     const auto &g = b->g[precision][adjoint != 0];
     *leaf_blocks_per_sm = g.leaf_bps;
     *m2l_blocks_per_sm = g.m2l_bps;
@@ -1369,9 +1544,17 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
         ctx->overlap_ctas = int(value);
         return BC_OK;
     }
+    if (std::strcmp(name, "m2l_blocks_per_sm") == 0) {
+        if (!(value >= 0.0 && value <= 32.0) || value != std::floor(value)) {
+            set_error("bc_set_option: m2l_blocks_per_sm must be an integer in [0, 32]");
+            return BC_ERR_ARG;
+        }
+        ctx->m2l_bps = int(value);
+        return BC_OK;
+    }
     if (std::strcmp(name, "debug_split_parts") == 0) {
-        if (!(value >= 0.0 && value <= double(kSplitAllParts)) || value != std::floor(value)) {
-            set_error("bc_set_option: debug_split_parts must be an integer in [0, %d]", kSplitAllParts);
+        if (!(value >= -1.0 && value <= double(kSplitAllParts)) || value != std::floor(value)) {
+            set_error("bc_set_option: debug_split_parts must be an integer in [-1, %d]", kSplitAllParts);
             return BC_ERR_ARG;
         }
         ctx->split_parts = int(value);

@@ -107,6 +107,22 @@ struct DfSched {
     int T = 0, maxp = 0;
 };
 
+// FP64 shift in factored form (kernels compute the same operator as `up` /
+// `par`): for child q,
+//     out[l] = so[q][l] * sum_k B[l][k] * (si[q][k] * in[k])
+// with B real and triangular (binomial coefficients, the same for the four
+// children) and si, so complex diagonals (powers of the child offset delta_q
+// = +-1 +- i or of delta_q / 2).  B's nonzero terms, taken output by output,
+// are cut into 32 runs of T terms, one run per lane of a warp (the scheme of
+// DfSched); each lane ends a partial sum where its run leaves an output.
+struct ShiftFac {
+    const double2 *si = nullptr, *so = nullptr;   // [4][P1]
+    const uint32_t *code = nullptr;   // [T][32] input k (bits 0-7); (slot + 1) << 8 where a partial sum ends
+    const double *coef = nullptr;     // [T][32] B[l][k] of each term (0 for padding)
+    const int32_t *np = nullptr;      // [P1] partial sums per output; output l owns slots l * maxp + [0, np[l])
+    int T = 0, maxp = 0;
+};
+
 struct OpSet {
     const double2 *leafA = nullptr;   // [NP][P1]        leaf vector -> box expansion
     const double2 *up = nullptr;      // [4][P1][P1]     child -> parent
@@ -121,6 +137,7 @@ struct OpSet {
     const float4 *par_df = nullptr;
     const float4 *leafA_df = nullptr;   // leafA as double-float pairs
     DfSched up_s;                       // up, scheduled for the double-float climb
+    ShiftFac up_f, par_f;               // up and par in factored form (FP64 level passes)
 };
 
 struct DevTables {
@@ -144,7 +161,7 @@ struct DevTree {
     int32_t *w_ptr = nullptr, *w_src = nullptr, *w_code = nullptr;
     int32_t *x_ptr = nullptr, *x_src = nullptr, *x_code = nullptr;
     int32_t *v_box = nullptr, *x_box = nullptr;       // target box of each V / X entry
-    double2 *Pv = nullptr;                             // [n_v][P1] M2L contribution of each V pair
+    double2 *Pv = nullptr;                             // [n_v][P1] M2L of each V pair (tensor-core M2L only; split set-up)
     double2 *PX = nullptr;                             // [n_x][P1] X-list product of each entry (FP64 path)
     double2 *expA = nullptr, *expB = nullptr;  // [nbox][P1] workspaces
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
@@ -156,13 +173,14 @@ struct DevTree {
     std::vector<void *> allocs;
 };
 
-// Split precision (p = 16 only).  Every fixed-operator product of the apply
-// except the multipole-to-local translations runs on the tensor cores as
-// exact BF16 digit products (kernels_split.cu):
+// Split precision (p = 16 only).  The fixed-operator products of the apply
+// run on the tensor cores as exact BF16 digit products (kernels_split.cu):
 //   group V (K = 256, input = leaf vectors): near tables, P2M (adjoint L2P^H),
 //            X list (adjoint M2P^H)
 //   group E (K = 64, input = expansions, 2*P1 reals padded to 64): L2P
 //            (adjoint P2M^H), W list (adjoint P2L^H)
+//   group M (K = 64, BC_SPLIT_BF16_ALL only): the V-list translations, one
+//            operator per offset
 // An operator is a real matrix of `rows` <= 256 rows; its BF16 digits are
 // stored as chunks [digit a][row half h][K chunk kc] of 128 rows x KC
 // columns (KC = min(K, kSplitKC)) in the canonical K-major core-matrix layout.
@@ -240,15 +258,23 @@ int split_sm_count();          // SMs of the device (after split_prepare)
 // Bit 64: the shifts of the two level passes in double-float arithmetic on
 // the FP32 units instead of FP64, and, with bit 2 off, the leaf-to-expansion
 // step too (inside the upward pass; then the input digits run on the side
-// stream).  The default has every part: on the 20-Gaussian workload the leaf
-// step in the upward pass doubles that pass (each block streams the 98 KB
-// operator for its ~4 leaves before it can climb).
+// stream; on the 20-Gaussian workload the leaf step in the upward pass
+// doubles that pass, since each block streams the 98 KB operator for its ~4
+// leaves before it can climb).
+// BC_SPLIT_BF16 takes the fixed-operator products (bits 1-16: the M2L, the
+// shifts, the log terms and the sums stay FP64), BC_SPLIT_BF16_ALL every part.
 constexpr int kSplitAllParts = 127;
-constexpr int kSplitDefaultParts = kSplitAllParts;
+constexpr int kSplitTableParts = 31;
+inline bool is_split(int prec) { return prec == BC_SPLIT_BF16 || prec == BC_SPLIT_BF16_ALL; }
+// parts of a split apply: the mode's set, or the diagnostic override (>= 0)
+inline int split_parts_for(int prec, int override_parts)
+{
+    return override_parts >= 0 ? override_parts : (prec == BC_SPLIT_BF16_ALL ? kSplitAllParts : kSplitTableParts);
+}
 struct SplitLaunch {
     const SplitTables *tables;
     const SplitTree *tree;
-    int parts = kSplitDefaultParts;
+    int parts = kSplitTableParts;
     const struct SideStream *side = nullptr;   // null: the near-field launch stays on the apply's stream
     int near_ctas = 0;                          // CTAs of the near-field launch on the side stream (0: all SMs)
 };
@@ -274,14 +300,18 @@ struct PassArgs {
     int leaf_bps = 0, m2l_bps = 0;
     // persistent level-synchronous passes: resident blocks of the upward and
     // shift kernels (all blocks must be resident), bounded barrier waits
-    int up_blocks = 0, shift_blocks = 0;
+    int up_blocks = 0, shift_blocks = 0, down_blocks = 0;   // down_blocks: the one-warp-per-box FP64 pass
     long long wait_limit = 1ll << 26;
     int32_t *err = nullptr;
 };
+// Launch parameters of an apply of `t` on the context (grids, limits, flags).
+PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t);
 // Largest grids of the persistent FP64 passes whose blocks are all resident
 // (occupancy calculator), capped at `per_sm` blocks per SM.
-cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, int down_per_sm, int *up_blocks,
-                         int *shift_blocks);
+// (df_T, df_maxp: the double-float climb's schedule; f_T, f_maxp: the largest
+// factored FP64 shift schedule of the context.)
+cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int f_T, int f_maxp, int up_per_sm, int down_per_sm,
+                         int *up_blocks, int *shift_blocks, int *down_blocks);
 
 // Disjoint union of trees (batched applies): leaves and boxes renumbered,
 // boxes sorted by (level, tree, Morton order), lists concatenated.
@@ -332,9 +362,10 @@ struct bc_ctx {
     bool tables_ready = false;
     int pass_mask = 3;          // diagnostics: bit 0 near field, bit 1 far field
     int m2l_tri = 0;            // 1: keep only M2L terms with k + l <= P (triangular truncation)
-    int split_parts = bc::kSplitDefaultParts;   // diagnostics: split-precision products in use
+    int split_parts = -1;       // diagnostics: split-precision products in use (-1: the precision mode's set)
     int split_overlap = 1;      // near-field tensor launch on the side stream (1) or inline (0)
-    int overlap_ctas = 0;       // CTAs of that launch (0: three quarters of the SMs)
+    int overlap_ctas = 0;       // CTAs of that launch (0: by arrangement, see near_ctas_for)
+    int m2l_bps = 0;            // resident blocks per SM of the FP64 M2L kernel (0: by arrangement)
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumEvents] = {};   // [forward, adjoint]
     bc::SideStream side;
@@ -344,7 +375,7 @@ struct bc_ctx {
     std::vector<void *> split_allocs;
     bool split_ready = false;
     int32_t *dev_err = nullptr;   // device flag set by kernels whose bounded waits gave up
-    int up_blocks = 0, shift_blocks = 0;   // grids of the persistent passes
+    int up_blocks = 0, shift_blocks = 0, down_blocks = 0;   // grids of the persistent passes
     // launch shapes chosen by the autotuner: key = precision*1024 + adjoint*512 + log2(nleaf)
     std::vector<std::pair<int, std::pair<int, int>>> tuned;
     std::mutex mu;

@@ -141,6 +141,23 @@ inline size_t up_smem_bytes(int NP, int P1, int T, int maxp)
                         sizeof(int32_t) * ((P1 + 3) & ~3)
                   : 0);
 }
+// Dynamic shared memory of the downward pass: the parent expansion and the
+// partial sums; the FP64 variant adds the factored shift's run sums and its
+// schedule (coefficients, codes, slot counts).
+inline size_t down_smem_bytes(int P1, int T, int maxp, bool df)
+{
+    return sizeof(double2) * (5 * P1 + 1) +
+           (df ? 0 : sizeof(double2) * size_t(P1) * maxp + (sizeof(double) + sizeof(uint32_t)) * T * 32 +
+                         sizeof(int32_t) * P1);
+}
+// The FP64 variant: children, partial sums, leaf values, then the factored
+// shift's schedule (coefficients, codes, slot counts) and the four children's
+// partial-sum slots.
+inline size_t up_smem_bytes_f64(int NP, int P1, int T, int maxp)
+{
+    return sizeof(double2) * 8 * P1 + sizeof(double) * ((NP + 1) & ~1) + sizeof(double) * T * 32 +
+           sizeof(double2) * size_t(4) * P1 * maxp + sizeof(uint32_t) * T * 32 + sizeof(int32_t) * ((P1 + 3) & ~3);
+}
 
 // -------------------------------------------------------------------------
 // upward pass, one persistent launch:
@@ -149,11 +166,15 @@ inline size_t up_smem_bytes(int NP, int P1, int T, int maxp)
 //           (OpA == nullptr: the leaf expansions are already in ex, split path)
 //   then level by level, deepest first, each parent once its children are
 //   published (per-box flags):
-//   parent: ex[p][l] = sum_q sum_k OpUp[q][k][l] ex[child_q(p)][k]    (levels >= 2)
+//   parent: ex[p][l] = sum_q sum_k Up_q[l][k] ex[child_q(p)][k]    (levels >= 2)
 //           forward: M2M; adjoint: L2L^H
 // Four warps per block: in the leaf step warp w sums over the w-th quarter of
 // the nodes, in a parent step warp q applies the operator of child q; the four
-// partial sums meet in shared memory.  The double-float variant runs the
+// partial sums meet in shared memory.  The FP64 variant applies Up_q in
+// factored form (ShiftFac: so_q[l] sum_k B[l][k] si_q[k]), B's terms on a
+// schedule that gives the 32 lanes equal shares of the triangle; about a
+// third of the FP64 instructions of the dense complex product.  The
+// double-float variant runs the
 // parent step on the term schedule (DfSched), keeps its sums in double-float
 // until the one conversion of each result, and publishes every climbed
 // expansion twice: ex in FP64 and exdf as double-float pairs, which the
@@ -164,8 +185,7 @@ __global__ void __launch_bounds__(128)
 k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
-            const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, const double2 *__restrict__ OpUp,
-            DfSched us, double2 *ex, float4 *exdf, int NP, int P1, const double *__restrict__ lvtab,
+            const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, DfSched us, ShiftFac uf, double2 *ex, float4 *exdf, int NP, int P1, const double *__restrict__ lvtab,
             bool climb, int32_t *flag,
             long long limit, int32_t *err)
 {
@@ -173,19 +193,32 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
     double2 *sc = shu;                                       // 4 * P1 children
     double2 *part = sc + 4 * P1;                             // [4][P1] partial sums
     double *sv = reinterpret_cast<double *>(part + 4 * P1);  // NP
-    // double-float path: the scheduled operator entries in shared memory,
-    // copied while the preceding kernel drains (every parent step reads them)
+    // the shift schedule in shared memory, copied while the preceding kernel
+    // drains (every parent step reads it)
+    // double-float path: scheduled operator entries of the four children
     const int T = us.T, SL = P1 * us.maxp;   // terms per lane, slots per child
     float4 *sops = reinterpret_cast<float4 *>(sv + ((NP + 1) & ~1));   // [4][T][32] (DF only)
     float4 *sslot = sops + 4 * T * 32;                                 // [4][SL]
     uint32_t *scode = reinterpret_cast<uint32_t *>(sslot + 4 * SL);    // [T][32]
     int32_t *snp = reinterpret_cast<int32_t *>(scode + T * 32);        // [P1]
+    // FP64 path: the factored shift's coefficients and codes (ShiftFac)
+    const int TF = uf.T, SLF = P1 * uf.maxp;
+    double *fcoef = sv + ((NP + 1) & ~1);                              // [TF][32] (FP64 only)
+    double2 *fslot = reinterpret_cast<double2 *>(fcoef + TF * 32);     // [4][SLF]
+    uint32_t *fcode = reinterpret_cast<uint32_t *>(fslot + 4 * SLF);   // [TF][32]
+    int32_t *fnp = reinterpret_cast<int32_t *>(fcode + TF * 32);       // [P1]
     __shared__ int s_leafc[4];   // which children of the current parent are leaves
-    if constexpr (DF) {
-        if (climb) {
+    if (climb) {
+        if constexpr (DF) {
             for (int i = threadIdx.x; i < 4 * T * 32; i += blockDim.x) sops[i] = __ldg(&us.ops[i]);
             for (int i = threadIdx.x; i < T * 32; i += blockDim.x) scode[i] = __ldg(&us.code[i]);
             for (int i = threadIdx.x; i < P1; i += blockDim.x) snp[i] = __ldg(&us.np[i]);
+        } else {
+            for (int i = threadIdx.x; i < TF * 32; i += blockDim.x) {
+                fcoef[i] = __ldg(&uf.coef[i]);
+                fcode[i] = __ldg(&uf.code[i]);
+            }
+            for (int i = threadIdx.x; i < P1; i += blockDim.x) fnp[i] = __ldg(&uf.np[i]);
         }
     }
     griddep_wait();
@@ -314,28 +347,39 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 }
                 flag_publish(&flag[p], 1);
             } else {
-            for (int i = threadIdx.x; i < 4 * P1; i += blockDim.x) sc[i] = __ldcg(&ex[int64_t(c0) * P1 + i]);
-            __syncthreads();
-            const double2 *op = OpUp + size_t(w) * P1 * P1;
-            const double2 *a = sc + w * P1;
-            for (int l = lane; l < P1; l += 32) {
-                double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-                for (int k0 = 0; k0 < P1; k0 += 8) {   // 8 operator loads in flight
-                    double2 o[8];
-#pragma unroll
-                    for (int u = 0; u < 8; u++)
-                        o[u] = k0 + u < P1 ? __ldg(&op[(k0 + u) * P1 + l]) : make_double2(0.0, 0.0);
-#pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
-                        if (k0 + u >= P1) break;
-                        const double2 a0 = a[k0 + u], a1 = k0 + u + 1 < P1 ? a[k0 + u + 1] : make_double2(0.0, 0.0);
-                        re0 = fma(o[u].x, a0.x, fma(-o[u].y, a0.y, re0));
-                        im0 = fma(o[u].x, a0.y, fma(o[u].y, a0.x, im0));
-                        re1 = fma(o[u + 1].x, a1.x, fma(-o[u + 1].y, a1.y, re1));
-                        im1 = fma(o[u + 1].x, a1.y, fma(o[u + 1].y, a1.x, im1));
-                    }
+            // factored FP64 shift (ShiftFac), warp w = child w: a = si_w * child
+            // (lane k), then B's terms on the schedule, each output's partial
+            // sums added and scaled by so_w, and the four children summed
+            double2 *a = sc + w * P1;
+            for (int k = lane; k < P1; k += 32) {
+                const double2 A = __ldcg(&ex[int64_t(c0 + w) * P1 + k]), S = __ldg(&uf.si[w * P1 + k]);
+                a[k] = make_double2(fma(A.x, S.x, -A.y * S.y), fma(A.x, S.y, A.y * S.x));
+            }
+            __syncwarp();
+            double2 *slot = fslot + w * SLF;
+            double re = 0.0, im = 0.0;
+#pragma unroll 2
+            for (int t = 0; t < TF; t++) {
+                const uint32_t code = fcode[t * 32 + lane];
+                const double cf = fcoef[t * 32 + lane];
+                const double2 x = a[code & 255u];
+                re = fma(cf, x.x, re);
+                im = fma(cf, x.y, im);
+                if (code >> 8) {   // the run leaves an output here
+                    slot[(code >> 8) - 1u] = make_double2(re, im);
+                    re = im = 0.0;
                 }
-                part[w * P1 + l] = make_double2(re0 + re1, im0 + im1);
+            }
+            __syncwarp();
+            for (int l = lane; l < P1; l += 32) {
+                double2 y = slot[l * uf.maxp];
+                for (int j = 1; j < fnp[l]; j++) {
+                    const double2 v = slot[l * uf.maxp + j];
+                    y.x += v.x;
+                    y.y += v.y;
+                }
+                const double2 S = __ldg(&uf.so[w * P1 + l]);
+                part[w * P1 + l] = make_double2(fma(y.x, S.x, -y.y * S.y), fma(y.x, S.y, y.y * S.x));
             }
             __syncthreads();
             for (int l = threadIdx.x; l < P1; l += blockDim.x) {
@@ -369,70 +413,116 @@ __device__ __forceinline__ int lv_of(const int64_t *__restrict__ level_start, in
 __constant__ double c_binom[32][32];
 
 // -------------------------------------------------------------------------
-// m2l_pairs: one thread per V-list pair e (target box b, source box s, offset
-// code c, d = (c_s - c_b)/r), writing the pair's contribution Pv[e][0..P]:
-//   forward  a_k = (-1)^k d^-k A_k (a_0 = A_0),
-//            Pv_o = d^-o sum_k c_binom[k][o] a_k + (o = 0) (log|d| + log r_b) A_0
-//   adjoint  (exact conjugate transpose of the forward map of the reversed pair)
-//            a_l = (-1)^l conj(d)^-l in_l,
-//            Pv_k = conj(d)^-k sum_l c_binom[k][l] a_l + (k = 0) (log|d| + log r_b) in_0
-// (the log r_b term is the level term of the box's own local expansion,
-// sum over V sources of r-scaled A_0 log r_b).  The source coefficients stay
-// in registers and the table entries come from constant memory, so nearly
-// every FP64 instruction is a useful FMA; every lane has a pair of its own.
-// tri = 1 keeps only the terms with k + o <= P (and exactly their transpose).
-// dsig[c][k] = (-1)^k d^-k (forward) or (-1)^k conj(d)^-k (adjoint),
-// dpow[c][o] = d^-o or conj(d)^-o.
+// m2l_boxes: the whole V-list sum of one target box b per block, in FP64,
+// written once:
+//   out[b][o] = sum_{e in V(b)} [ W_c[o] sum_k B[k][o] a_k(e) + (o = 0) (log|d_c| + log r_b) a_0(e) ]
+//   a_k(e) = S_c[k] in[s_e][k]
+// with (forward) S_c[k] = (-1)^k d^-k, W_c[o] = d^-o, B = c_binom, and
+// (adjoint, the conjugate transpose of the reversed pair) S_c[k] =
+// (-1)^k conj(d)^-k, W_c[o] = conj(d)^-o, B = c_binom transposed.  The log
+// r_b term is the level term of the box's own local expansion (r-scaled A_0
+// of each source times log r_b).  Boxes without V entries get 0.
+// The block is NG groups of P1 threads: thread (g, o) owns output o of the
+// pairs v0 + g, v0 + g + NG, ...; per pair the group first forms a(e) in
+// shared memory (thread o its coefficient o), then every thread contracts it
+// with its column of B, held in registers (constant-memory reads with a
+// different index per lane would serialise).  The sums stay in registers
+// until the groups meet in shared memory at the end of the box.  Nearly every
+// instruction is an FP64 FMA: 2 P1 per pair and thread, plus 8 for the two
+// diagonal scalings; NG P1 is a multiple of 32 wherever possible so that no
+// lane idles.
 // -------------------------------------------------------------------------
 template <bool ADJ, int PMAX>
-__global__ void __launch_bounds__(128)
-k_m2l_pairs(int64_t npairs, const int32_t *__restrict__ v_box, const int32_t *__restrict__ v_src,
+__global__ void __launch_bounds__(256)
+k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int32_t *__restrict__ v_src,
             const int32_t *__restrict__ v_code, const int32_t *__restrict__ box_level,
             const double2 *__restrict__ dsig, const double2 *__restrict__ dpow, const double *__restrict__ logd,
-            const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ Pv, int P1,
-            int tri)
+            const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ out, int P1,
+            int NG, int tri)
 {
-    griddep_wait();
-    griddep_launch_dependents();
-    const int P = P1 - 1;
-    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < npairs; e += int64_t(gridDim.x) * blockDim.x) {
-        const int b = v_box[e], s = v_src[e], c = v_code[e];
-        double ar[PMAX], ai[PMAX];
+    extern __shared__ double2 sm2l[];   // [NG][P1 + 1]: a(e) of each group's pair, then the group sums
+    const int t = threadIdx.x, g = t / P1, o = t - g * P1;
+    const bool act = g < NG;
+    const int ld = P1 + 1;   // padded row: the groups' rows start in different banks
+    double bcol[PMAX];
 #pragma unroll
-        for (int k = 0; k < PMAX; k++) {
-            ar[k] = 0.0;
-            ai[k] = 0.0;
-            if (k < P1) {
-                const double2 A = in[int64_t(s) * P1 + k], D = dsig[c * P1 + k];
-                ar[k] = fma(A.x, D.x, -A.y * D.y);
-                ai[k] = fma(A.x, D.y, A.y * D.x);
+    for (int k = 0; k < PMAX; k++) {
+        // tri = 1 keeps only the terms with k + o <= P (and exactly their transpose)
+        const bool keep = !tri || (ADJ ? (o == 0 || k + o < P1) : (k == 0 || k + o < P1));
+        bcol[k] = (act && k < P1 && keep) ? (ADJ ? c_binom[o][k] : c_binom[k][o]) : 0.0;
+    }
+    // The dependents (the persistent downward pass) are released only at the
+    // end: released early, their resident blocks would take the SM space that
+    // a near-field tensor CTA on the internal stream needs beside this kernel.
+    griddep_wait();
+    double2 *arow = sm2l + (act ? g : 0) * ld;
+    for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
+        const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
+        const double lgb = lvtab[kLvTab + box_level[b]];
+        double accr = 0.0, acci = 0.0;
+        for (int e0 = v0; e0 < v1; e0 += NG) {
+            const int e = e0 + g;
+            const bool live = act && e < v1;
+            int c = 0;
+            __syncthreads();   // the previous pair's a(e) has been read
+            if (live) {
+                c = v_code[e];
+                const double2 A = in[int64_t(v_src[e]) * P1 + o], S = dsig[c * P1 + o];
+                arow[o] = make_double2(fma(A.x, S.x, -A.y * S.y), fma(A.x, S.y, A.y * S.x));
+            }
+            __syncthreads();
+            if (live) {
+                double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
+#pragma unroll
+                for (int k = 0; k < PMAX; k += 2) {
+                    if (k < P1) {
+                        const double2 a = arow[k];
+                        sr0 = fma(bcol[k], a.x, sr0);
+                        si0 = fma(bcol[k], a.y, si0);
+                    }
+                    if (k + 1 < P1) {
+                        const double2 a = arow[k + 1];
+                        sr1 = fma(bcol[k + 1], a.x, sr1);
+                        si1 = fma(bcol[k + 1], a.y, si1);
+                    }
+                }
+                double sr = sr0 + sr1, si = si0 + si1;
+                if (o == 0) {
+                    const double c0 = logd[c] + lgb;
+                    const double2 a = arow[0];
+                    sr = fma(c0, a.x, sr);
+                    si = fma(c0, a.y, si);
+                }
+                const double2 W = dpow[c * P1 + o];
+                accr = fma(sr, W.x, fma(-si, W.y, accr));
+                acci = fma(sr, W.y, fma(si, W.x, acci));
             }
         }
-        const double c0 = logd[c] + lvtab[kLvTab + box_level[b]];
-        double2 *out = Pv + e * P1;
-#pragma unroll
-        for (int o = 0; o < PMAX; o++) {
-            if (o >= P1) break;
-            double sr = 0.0, si = 0.0;
-#pragma unroll
-            for (int k = 0; k < PMAX; k++) {
-                if (k >= P1) break;
-                const bool keep = !tri || (ADJ ? (o == 0 || k + o <= P) : (k == 0 || k + o <= P));
-                if (keep) {
-                    const double cf = ADJ ? c_binom[o][k] : c_binom[k][o];
-                    sr = fma(cf, ar[k], sr);
-                    si = fma(cf, ai[k], si);
-                }
+        __syncthreads();   // last a(e) read
+        if (act) sm2l[g * ld + o] = make_double2(accr, acci);
+        __syncthreads();
+        if (t < P1) {
+            double2 s = sm2l[t];
+            for (int q = 1; q < NG; q++) {
+                const double2 v = sm2l[q * ld + t];
+                s.x += v.x;
+                s.y += v.y;
             }
-            if (o == 0) {
-                sr = fma(c0, ar[0], sr);
-                si = fma(c0, ai[0], si);
-            }
-            const double2 W = dpow[c * P1 + o];
-            out[o] = make_double2(fma(sr, W.x, -si * W.y), fma(sr, W.y, si * W.x));
+            out[b * P1 + t] = s;
         }
     }
+    griddep_launch_dependents();
 }
+
+// Groups per block of the M2L kernel: the smallest NG >= 4 with NG * P1 a
+// multiple of 32 (no idle lane) and at most 256 threads, else 4.
+inline int m2l_groups(int P1)
+{
+    for (int ng = 4; ng * P1 <= 256; ng++)
+        if ((ng * P1) % 32 == 0) return ng;
+    return 4;
+}
+inline int m2l_threads(int P1) { return (m2l_groups(P1) * P1 + 31) / 32 * 32; }
 
 // -------------------------------------------------------------------------
 // x_entries (FP64 path): the X-list products, one block per entry e (target
@@ -491,7 +581,10 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 // down_levels: the local expansion (adjoint: multipole) of every box at
 // level >= 2, in one persistent launch:
 //   the box's own sums:
-//     out[b] = sum_{e in V(b)} Pv[e] + sum_{x in X(b)} (PX[x] + log(r_c) A_0(c) e_0)
+//     out[b] = V(b) + sum_{x in X(b)} (PX[x] + log(r_c) A_0(c) e_0)
+//   where V(b) is out[b] itself on entry (vsum: the whole V-list sum, written
+//   by k_m2l_boxes) or sum_{e in V(b)} Pv[e] (one row per pair, from the
+//   tensor cores)
 //   then (levels 3, 4, ...; once the parent is published):
 //     out[b] += Par_q out[parent(b)]      (forward L2L, adjoint M2M^H)
 // A block takes its boxes in ascending index (so ascending level) and does
@@ -505,13 +598,14 @@ k_x_entries(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__rest
 //     out[b][0] += sum_{e in V(b)} (log|d_e| + log r_b) first[s_e][0]
 // Four warps per block.  The sums run side by side: warp 0 the X list (its
 // log term gathered one entry per lane), warp 1 the V-list log term (one pair
-// per lane), warps 2 and 3 the V pairs.  In the shift warp w applies a quarter
-// of the operator's columns, fetched into registers before the wait for the
-// parent (the shift chain is the critical path).  The double-float variant
-// keeps that chain free of FP64 work: the box's sums are converted to pairs
-// before the wait, the parent is read as pairs (outdf), the partial sums are
-// added as pairs, and the FP64 result, read only by later kernels, is stored
-// after the box's flag.
+// per lane), warps 2 and 3 the V pairs (vsum: warp 2 reads the V sum).  In
+// the shift warp w applies a quarter of the operator's columns, fetched into
+// registers before the wait for the parent (the shift chain is the critical
+// path).  The double-float variant keeps that chain free of FP64 work: a copy
+// of the box's sums is converted to pairs before the wait, the parent is read
+// as pairs (outdf), the shift and its sum with the copy are formed as pairs
+// and published for the children; the FP64 result, read only by later
+// kernels, is the FP64 sums plus the shift, stored after the box's flag.
 // -------------------------------------------------------------------------
 template <bool DF>
 __global__ void __launch_bounds__(128)
@@ -520,16 +614,30 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
               const double2 *__restrict__ PX, int px_stride, const int32_t *__restrict__ leaf_box,
               const double2 *__restrict__ first, const int32_t *__restrict__ parent,
               const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy,
-              const double2 *__restrict__ OpPar, const float4 *__restrict__ OpParDF, double2 *out, float4 *outdf, int P1,
+              const float4 *__restrict__ OpParDF, ShiftFac pf, double2 *out, float4 *outdf, int P1,
               const double *__restrict__ lvtab,
               const int32_t *__restrict__ v_lsrc, const int32_t *__restrict__ v_code,
-              const double *__restrict__ logd, int32_t *flag, long long limit, int32_t *err)
+              const double *__restrict__ logd, bool vsum, int32_t *flag, long long limit, int32_t *err)
 {
+    extern __shared__ double2 sdn[];
+    double2 *se = sdn;             // [P1] parent expansion (FP64 variant: times si_q)
+    double2 *part = sdn + P1;      // [4][P1] partial sums
+    // FP64 variant: the factored shift's schedule (ShiftFac) and the partial
+    // sums of its runs, staged before the wait for the preceding kernel
+    const int TF = DF ? 0 : pf.T, SLF = DF ? 0 : P1 * pf.maxp;
+    double2 *fslot = part + 4 * P1;                                    // [SLF]
+    double *fcoef = reinterpret_cast<double *>(fslot + SLF);           // [TF][32]
+    uint32_t *fcode = reinterpret_cast<uint32_t *>(fcoef + TF * 32);   // [TF][32]
+    int32_t *fnp = reinterpret_cast<int32_t *>(fcode + TF * 32);       // [P1]
+    if constexpr (!DF) {
+        for (int i = threadIdx.x; i < TF * 32; i += blockDim.x) {
+            fcoef[i] = __ldg(&pf.coef[i]);
+            fcode[i] = __ldg(&pf.code[i]);
+        }
+        for (int i = threadIdx.x; i < P1; i += blockDim.x) fnp[i] = __ldg(&pf.np[i]);
+    }
     griddep_wait();
     griddep_launch_dependents();
-    extern __shared__ double2 sdn[];
-    double2 *se = sdn;             // [P1] parent expansion
-    double2 *part = sdn + P1;      // [4][P1] partial sums
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kq = (P1 + 3) / 4, k0 = w * kq, k1 = min(P1, k0 + kq);   // this warp's shift columns (<= 8)
     const int o = lane;   // coefficient of this lane (P1 <= 32)
@@ -539,18 +647,18 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
         const int pb = shift ? parent[b] : 0;
         const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
         // the shift operator does not depend on the parent's values: fetched
-        // before the wait for them
+        // before the wait for them (FP64: warp 0's diagonals si_q, so_q)
         float4 wf[8];
-        double2 wd[8];
+        double2 fsi = make_double2(0.0, 0.0), fso = make_double2(0.0, 0.0);
         if (shift && o < P1) {
+            if constexpr (DF) {
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                if constexpr (DF) {
+                for (int u = 0; u < 8; u++)
                     wf[u] = k0 + u < k1 ? __ldg(&OpParDF[(size_t(q) * P1 + k0 + u) * P1 + o])
                                         : make_float4(0.f, 0.f, 0.f, 0.f);
-                } else {
-                    wd[u] = k0 + u < k1 ? __ldg(&OpPar[(size_t(q) * P1 + k0 + u) * P1 + o]) : make_double2(0.0, 0.0);
-                }
+            } else if (w == 0) {
+                fsi = __ldg(&pf.si[q * P1 + o]);
+                fso = __ldg(&pf.so[q * P1 + o]);
             }
         }
         // ---- the box's own sums, one kind per warp: warp 0 the X list and
@@ -591,6 +699,12 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                     im = li;
                 }
             }
+        } else if (vsum) {
+            if (w == 2 && o < P1) {
+                const double2 t = out[b * P1 + o];
+                re = t.x;
+                im = t.y;
+            }
         } else if (o < P1) {
             const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
             double re1 = 0.0, im1 = 0.0;
@@ -614,6 +728,7 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
         __syncthreads();
         double2 acc = make_double2(0.0, 0.0);   // meaningful in warp 0, lanes o < P1
         float4 accf = make_float4(0.f, 0.f, 0.f, 0.f);   // the same as double-float pairs (DF)
+        float4 shf = make_float4(0.f, 0.f, 0.f, 0.f);    // the shifted parent (DF)
         if (w == 0 && o < P1) {
             const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
             acc = make_double2((a0.x + a1.x) + (a2.x + a3.x), (a0.y + a1.y) + (a2.y + a3.y));
@@ -638,51 +753,212 @@ k_down_levels(const int64_t *__restrict__ level_start, int nlevels, const int32_
                     reinterpret_cast<float4 *>(part)[w * P1 + o] =
                         df4_add(make_float4(r0h, r0l, i0h, i0l), make_float4(r1h, r1l, i1h, i1l));
                 }
-            } else {
-                for (int i = threadIdx.x; i < P1; i += blockDim.x) se[i] = __ldcg(&out[int64_t(pb) * P1 + i]);
-                __syncthreads();
+            } else if (w == 0) {
+                // factored FP64 shift (ShiftFac) by warp 0: a = si_q * parent
+                // (lane k), B's terms on the schedule, each output's partial
+                // sums added and scaled by so_q
                 if (o < P1) {
-                    double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
-#pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
-                        if (k0 + u >= k1) break;
-                        const double2 a0 = se[k0 + u];
-                        re0 = fma(wd[u].x, a0.x, fma(-wd[u].y, a0.y, re0));
-                        im0 = fma(wd[u].x, a0.y, fma(wd[u].y, a0.x, im0));
-                        if (k0 + u + 1 < k1) {
-                            const double2 a1 = se[k0 + u + 1];
-                            re1 = fma(wd[u + 1].x, a1.x, fma(-wd[u + 1].y, a1.y, re1));
-                            im1 = fma(wd[u + 1].x, a1.y, fma(wd[u + 1].y, a1.x, im1));
-                        }
+                    const double2 A = __ldcg(&out[int64_t(pb) * P1 + o]);
+                    se[o] = make_double2(fma(A.x, fsi.x, -A.y * fsi.y), fma(A.x, fsi.y, A.y * fsi.x));
+                }
+                __syncwarp();
+                double re = 0.0, im = 0.0;
+#pragma unroll 2
+                for (int t = 0; t < TF; t++) {
+                    const uint32_t code = fcode[t * 32 + lane];
+                    const double cf = fcoef[t * 32 + lane];
+                    const double2 x = se[code & 255u];
+                    re = fma(cf, x.x, re);
+                    im = fma(cf, x.y, im);
+                    if (code >> 8) {   // the run leaves an output here
+                        fslot[(code >> 8) - 1u] = make_double2(re, im);
+                        re = im = 0.0;
                     }
-                    part[w * P1 + o] = make_double2(re0 + re1, im0 + im1);
+                }
+                __syncwarp();
+                if (o < P1) {
+                    double2 y = fslot[o * pf.maxp];
+                    for (int j = 1; j < fnp[o]; j++) {
+                        const double2 v = fslot[o * pf.maxp + j];
+                        y.x += v.x;
+                        y.y += v.y;
+                    }
+                    acc.x += fma(y.x, fso.x, -y.y * fso.y);
+                    acc.y += fma(y.x, fso.y, y.y * fso.x);
                 }
             }
-            __syncthreads();
-            if (w == 0 && o < P1) {
-                if constexpr (DF) {
-                    const float4 *pf = reinterpret_cast<const float4 *>(part);
-                    accf = df4_add(df4_add(accf, pf[o]), df4_add(pf[P1 + o], df4_add(pf[2 * P1 + o], pf[3 * P1 + o])));
-                } else {
-                    const double2 a0 = part[o], a1 = part[P1 + o], a2 = part[2 * P1 + o], a3 = part[3 * P1 + o];
-                    acc.x += (a0.x + a1.x) + (a2.x + a3.x);
-                    acc.y += (a0.y + a1.y) + (a2.y + a3.y);
+            if constexpr (DF) {
+                __syncthreads();
+                if (w == 0 && o < P1) {
+                    const float4 *pf4 = reinterpret_cast<const float4 *>(part);
+                    shf = df4_add(pf4[o], df4_add(pf4[P1 + o], df4_add(pf4[2 * P1 + o], pf4[3 * P1 + o])));
+                    accf = df4_add(accf, shf);
                 }
             }
         }
         if constexpr (DF) {
-            // the children read the pairs; the FP64 result (for the later
-            // kernels only) is stored after the flag, off the level chain
+            // the children read the pairs (the input of their shifts); the
+            // FP64 result, read by the later kernels only, is the FP64 sums
+            // plus the shifted parent, stored after the flag, off the chain
             if (w == 0 && o < P1) outdf[b * P1 + o] = accf;
             flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
             if (w == 0 && o < P1)
-                out[b * P1 + o] =
-                    shift ? make_double2(double(accf.x) + double(accf.y), double(accf.z) + double(accf.w)) : acc;
+                out[b * P1 + o] = make_double2(acc.x + (double(shf.x) + double(shf.y)),
+                                               acc.y + (double(shf.z) + double(shf.w)));
         } else {
             if (w == 0 && o < P1) out[b * P1 + o] = acc;
             flag_publish(&flag[b], 2);   // its barrier also frees the shared buffers
         }
     }
+}
+
+// -------------------------------------------------------------------------
+// down_warps: the FP64 downward pass with one warp per box (the same result
+// as k_down_levels<false>).  Warp g of the grid takes the boxes
+// level_start[2] + g, + G, ... (G warps in all), in ascending order, and for
+// each:
+//   the box's own sums (lane o = coefficient o): the V-list sum (vsum: the
+//     row k_m2l_boxes wrote into out[b]; else the rows Pv[e] of the pairs and
+//     the V-list log term), the X-list rows PX[x] and the X-list log term;
+//   then (levels >= 3), once the parent is published, the parent's expansion
+//     shifted to this box in factored form (ShiftFac: so_q[l] sum_k B[l][k]
+//     si_q[k] parent[k], B's terms on the 32-lane schedule);
+//   the result is written to out[b] and published by flag[b] = 2.
+// A box waits only for its parent, a box of smaller index, so every wait
+// ends once every warp is resident (the grid comes from the occupancy
+// calculator).  Each warp of a block sits on its own SM sub-partition, so the
+// shifts of concurrently processed boxes use all four FP64 pipes.
+// -------------------------------------------------------------------------
+__global__ void __launch_bounds__(128)
+k_down_warps(const int64_t *__restrict__ level_start, int nlevels, const int32_t *__restrict__ v_ptr,
+             const double2 *__restrict__ Pv, const int32_t *__restrict__ x_ptr, const int32_t *__restrict__ x_src,
+             const double2 *__restrict__ PX, int px_stride, const int32_t *__restrict__ leaf_box,
+             const double2 *__restrict__ first, const int32_t *__restrict__ parent,
+             const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy, ShiftFac pf, double2 *out, int P1,
+             const double *__restrict__ lvtab, const int32_t *__restrict__ v_lsrc,
+             const int32_t *__restrict__ v_code, const double *__restrict__ logd, bool vsum, int32_t *flag,
+             long long limit, int32_t *err)
+{
+    extern __shared__ double2 sdw[];
+    const int TF = pf.T, SLF = P1 * pf.maxp;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    double2 *se = sdw + w * (P1 + SLF);                                   // [P1] si_q * parent
+    double2 *fslot = se + P1;                                             // [SLF] run sums
+    double *fcoef = reinterpret_cast<double *>(sdw + nw * (P1 + SLF));    // [TF][32]
+    uint32_t *fcode = reinterpret_cast<uint32_t *>(fcoef + TF * 32);      // [TF][32]
+    int32_t *fnp = reinterpret_cast<int32_t *>(fcode + TF * 32);          // [P1]
+    for (int i = threadIdx.x; i < TF * 32; i += blockDim.x) {
+        fcoef[i] = __ldg(&pf.coef[i]);
+        fcode[i] = __ldg(&pf.code[i]);
+    }
+    for (int i = threadIdx.x; i < P1; i += blockDim.x) fnp[i] = __ldg(&pf.np[i]);
+    __syncthreads();
+    griddep_wait();
+    griddep_launch_dependents();
+    const int o = lane;   // coefficient of this lane (P1 <= 32)
+    const int64_t G = int64_t(gridDim.x) * nw;
+    for (int64_t b = level_start[2] + int64_t(blockIdx.x) * nw + w; b < level_start[nlevels]; b += G) {
+        const int lvb = lv_of(level_start, nlevels, b);
+        const bool shift = lvb >= 3;
+        const int pb = shift ? parent[b] : 0;
+        const int q = (box_ix[b] & 1) + 2 * (box_iy[b] & 1);
+        double2 fsi = make_double2(0.0, 0.0), fso = make_double2(0.0, 0.0);
+        if (shift && o < P1) {   // the shift's diagonals do not depend on the parent's values
+            fsi = __ldg(&pf.si[q * P1 + o]);
+            fso = __ldg(&pf.so[q * P1 + o]);
+        }
+        // ---- the box's own sums
+        double re = 0.0, im = 0.0;
+        if (o < P1) {
+            if (vsum) {
+                const double2 t = out[b * P1 + o];
+                re = t.x;
+                im = t.y;
+            } else {
+                for (int e = v_ptr[b]; e < v_ptr[b + 1]; e++) {
+                    const double2 t = Pv[int64_t(e) * P1 + o];
+                    re += t.x;
+                    im += t.y;
+                }
+            }
+        }
+        const int x0 = x_ptr[b], x1 = x_ptr[b + 1];
+        if (o < P1) {
+#pragma unroll 4
+            for (int x = x0; x < x1; x++) {
+                const double2 t = PX[int64_t(x) * px_stride + o];
+                re += t.x;
+                im += t.y;
+            }
+        }
+        // log terms, one entry per lane: the X list (times log r of the
+        // source level) and, for tensor-core M2L rows, the V list
+        double lx = 0.0, lr = 0.0, li = 0.0;
+        for (int x = x0 + lane; x < x1; x += 32) lx += first[int64_t(leaf_box[x_src[x]]) * P1].x;
+        if (!vsum && v_lsrc) {
+            const double lgb = lvtab[kLvTab + lvb];
+            for (int e = v_ptr[b] + lane; e < v_ptr[b + 1]; e += 32) {
+                const double2 a0 = first[int64_t(v_lsrc[e]) * P1];
+                const double c0 = logd[v_code[e]] + lgb;
+                lr = fma(c0, a0.x, lr);
+                li = fma(c0, a0.y, li);
+            }
+        }
+        for (int m = 16; m > 0; m >>= 1) {
+            lx += __shfl_xor_sync(0xffffffffu, lx, m);
+            lr += __shfl_xor_sync(0xffffffffu, lr, m);
+            li += __shfl_xor_sync(0xffffffffu, li, m);
+        }
+        if (o == 0) {
+            re = fma(lvtab[kLvTab + lvb - 1], lx, re + lr);
+            im += li;
+        }
+        // ---- plus the parent's expansion shifted to this box (levels >= 3)
+        if (shift) {
+            if (lane == 0) flag_wait(&flag[pb], 2, limit, err);
+            __syncwarp();
+            if (o < P1) {
+                const double2 A = __ldcg(&out[int64_t(pb) * P1 + o]);
+                se[o] = make_double2(fma(A.x, fsi.x, -A.y * fsi.y), fma(A.x, fsi.y, A.y * fsi.x));
+            }
+            __syncwarp();
+            double sr = 0.0, si = 0.0;
+#pragma unroll 2
+            for (int t = 0; t < TF; t++) {
+                const uint32_t code = fcode[t * 32 + lane];
+                const double cf = fcoef[t * 32 + lane];
+                const double2 xv = se[code & 255u];
+                sr = fma(cf, xv.x, sr);
+                si = fma(cf, xv.y, si);
+                if (code >> 8) {   // the run leaves an output here
+                    fslot[(code >> 8) - 1u] = make_double2(sr, si);
+                    sr = si = 0.0;
+                }
+            }
+            __syncwarp();
+            if (o < P1) {
+                double2 y = fslot[o * pf.maxp];
+                for (int j = 1; j < fnp[o]; j++) {
+                    const double2 v = fslot[o * pf.maxp + j];
+                    y.x += v.x;
+                    y.y += v.y;
+                }
+                re += fma(y.x, fso.x, -y.y * fso.y);
+                im += fma(y.x, fso.y, y.y * fso.x);
+            }
+        }
+        if (o < P1) out[b * P1 + o] = make_double2(re, im);
+        // the warp's writes are ordered before lane 0's release store; the
+        // next box's shared-memory writes come after every lane's reads
+        __syncwarp();
+        if (lane == 0) asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(&flag[b]), "r"(2) : "memory");
+    }
+}
+
+inline size_t down_warps_smem_bytes(int P1, int T, int maxp, int nwarps)
+{
+    return sizeof(double2) * size_t(nwarps) * (P1 + size_t(P1) * maxp) + (sizeof(double) + sizeof(uint32_t)) * T * 32 +
+           sizeof(int32_t) * P1;
 }
 
 // -------------------------------------------------------------------------
@@ -895,21 +1171,55 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const int parts = split ? split->parts : 0;
     cudaError_t ce;
     if (ev) cudaEventRecord(ev[0], st);
+    const SideStream *sd = split ? split->side : nullptr;
+    SplitGemm gv;   // tensor group V
+    if (split) {
+        gv.ops = sT->ops[0][dir]; gv.op_exp = sT->op_exp[0][dir];
+        gv.dig = sp->vdig; gv.dexp = sp->vexp;
+    }
+    const bool leaf_tc = (parts & 2) != 0;
+    // Late fork: with the M2L in FP64 (part 32 off) the internal stream's
+    // tensor launches (X list, near field) start after the upward pass and run
+    // beside the FP64 M2L, which leaves room for one tensor CTA per SM; the
+    // upward pass runs alone before it.  Otherwise they start at once, beside
+    // the level passes.
+    const bool late = sd && !(parts & 32) && leaf_tc;
+    // the internal stream's launches: X-list tiles (needed by the downward
+    // pass, which waits for xdone), then the near field (joined before the
+    // leaf output)
+    auto side_launches = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess)
+            return e;
+        if (ev) cudaEventRecord(ev[8], sd->side);
+        if (!leaf_tc) {
+            e = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side);
+            if (e != cudaSuccess) return e;
+        }
+        SplitGemm g = gv;
+        g.tiles = sp->tV[dir] + sp->ntA[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
+        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return e;
+        g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
+        g.max_ctas = split->near_ctas;
+        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+        if (e != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[9], sd->side);
+        return cudaEventRecord(sd->join, sd->side);
+    };
     if (split) {
         // tensor group V: digits of alpha0 * vin; the near field into Pnear,
         // leafA (P2M / L2P^H, part 2) into `first` and the X list into PX, in
-        // one launch, or (split_overlap) the X list and the near field on the
-        // side stream (joined before the downward pass and before the leaf
-        // output)
-        SplitGemm g;
-        g.ops = sT->ops[0][dir]; g.op_exp = sT->op_exp[0][dir];
-        g.dig = sp->vdig; g.dexp = sp->vexp;
-        const SideStream *sd = split->side;
+        // one launch, or (split_overlap) the leaf-to-expansion tiles in line
+        // and the X list and the near field on the internal stream
         if (!sd) {
             // one launch: the near-field tiles (two jobs each) first, then the
             // leaf-to-expansion and X-list tiles
             ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
             if (ce != cudaSuccess) return ce;
+            SplitGemm g = gv;
             g.tiles = sp->tVN[dir]; g.cols = sp->cVN[dir]; g.ntiles = sp->ntVN[dir];
             ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
             if (ce != cudaSuccess) return ce;
@@ -918,38 +1228,21 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
                 cudaEventRecord(ev[9], st);
             }
         } else {
-            // On the internal stream the X-list tiles (needed by the downward
-            // pass, which waits for xdone) and the near field.  The upward pass
-            // needs the leaf-to-expansion step first: as tensor tiles in line
-            // (part 2, after the digits), else in double-float inside the
-            // upward pass, and then the digits run on the internal stream too.
-            const bool leaf_tc = (parts & 2) != 0;
+            // The upward pass needs the leaf-to-expansion step first: as
+            // tensor tiles in line (part 2, after the digits), else in
+            // double-float inside the upward pass, and then the digits run on
+            // the internal stream too.
             if (leaf_tc) {
                 ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
                 if (ce != cudaSuccess) return ce;
             }
-            if ((ce = cudaEventRecord(sd->fork, st)) != cudaSuccess ||
-                (ce = cudaStreamWaitEvent(sd->side, sd->fork, 0)) != cudaSuccess)
-                return ce;
-            if (ev) cudaEventRecord(ev[8], sd->side);
+            if (!late && (ce = side_launches()) != cudaSuccess) return ce;
             if (leaf_tc) {
+                SplitGemm g = gv;
                 g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntA[dir];
                 ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
                 if (ce != cudaSuccess) return ce;
-            } else {
-                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side);
-                if (ce != cudaSuccess) return ce;
             }
-            g.tiles = sp->tV[dir] + sp->ntA[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
-            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
-            if (ce != cudaSuccess) return ce;
-            if ((ce = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return ce;
-            g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
-            g.max_ctas = split->near_ctas;
-            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
-            if (ce != cudaSuccess) return ce;
-            if (ev) cudaEventRecord(ev[9], sd->side);
-            if ((ce = cudaEventRecord(sd->join, sd->side)) != cudaSuccess) return ce;
         }
     } else if (ev) {
         cudaEventRecord(ev[8], st);
@@ -973,21 +1266,26 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     const double2 *opA = (parts & 2) ? nullptr : op.leafA;
     const bool climb = far && h.nlevels > 3;
     const bool dfp = (parts & 64) != 0;   // double-float shifts
-    const size_t shU = dfp ? up_smem_bytes(NP, P1, op.up_s.T, op.up_s.maxp) : up_smem_bytes(NP, P1, 0, 0);
+    const size_t shU = dfp ? up_smem_bytes(NP, P1, op.up_s.T, op.up_s.maxp)
+                           : up_smem_bytes_f64(NP, P1, op.up_f.T, op.up_f.maxp);
     if (opA || climb) {
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
-               d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up, op.up_s, first, d.exdf, NP, P1, \
-               d.lvtab, climb, d.flag, glimit, a.err)
+               d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up_s, op.up_f, first, d.exdf, NP, \
+               P1, d.lvtab, climb, d.flag, glimit, a.err)
         if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
         else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
 #undef BC_UP
         if (ce != cudaSuccess) return ce;
     }
+    if (late && (ce = side_launches()) != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[3], st);
     bool first_digits = false;   // digits of `first` taken (tensor-core M2L)
     if (far && h.nlevels > 2) {
-        // M2L per V pair, then (FP64) the X-list products, then the level-by-level sum
+        // M2L: per V pair on the tensor cores (part 32; results one row per
+        // pair, summed by the downward pass), else every box's V-list sum in
+        // FP64, written into its row of `second`; then (FP64) the X-list
+        // products, then the level-by-level sum
         const int64_t npairs = int64_t(h.v_src.size());
         if (npairs > 0 && (parts & 32)) {
             // tensor group M: digits of `first` (times alpha0 in the adjoint),
@@ -1003,13 +1301,19 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             g.dig = sp->edig; g.dexp = sp->eexp;
             ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
             if (ce != cudaSuccess) return ce;
-        } else if (npairs > 0) {
-            const int grid = grid_for((npairs + 127) / 128, 152 * 24);
+        } else {
+            const int64_t b0 = h.level_start[2], b1 = a.nbox;
+            const int ng = m2l_groups(P1), nth = m2l_threads(P1);
+            const size_t shM = sizeof(double2) * ng * (P1 + 1);
+            // beside the near-field tensor CTAs (late fork): 3 blocks per SM
+            // fit next to one of them (registers and shared memory)
+            const int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : (late ? 3 : 8)));
             const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
-#define BC_M2L(A, PM)                                                                                  \
-    ce = launch_pdl(k_m2l_pairs<A, PM>, grid, 128, 0, st, npairs, d.v_box, d.v_src, d.v_code, d.box_level, dsig, \
-                    dpw, tb.logd, d.lvtab, first, d.Pv, P1, m2l_tri)
+#define BC_M2L(A, PM)                                                                                           \
+    ce = launch_pdl(k_m2l_boxes<A, PM>, grid, nth, shM, st, b0, b1, d.v_ptr, d.v_src, d.v_code, d.box_level, dsig, \
+                    dpw, tb.logd, d.lvtab, first, second, P1, ng, m2l_tri)
             if (P1 <= 16) { if (adj) BC_M2L(true, 16); else BC_M2L(false, 16); }
+            else if (P1 <= 24) { if (adj) BC_M2L(true, 24); else BC_M2L(false, 24); }
             else { if (adj) BC_M2L(true, 32); else BC_M2L(false, 32); }
 #undef BC_M2L
             if (ce != cudaSuccess) return ce;
@@ -1034,13 +1338,18 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (ev) cudaEventRecord(ev[4], st);
         // the X-list products come from the internal stream
         if (split && split->side && (ce = cudaStreamWaitEvent(st, split->side->xdone, 0)) != cudaSuccess) return ce;
-#define BC_DOWN(D)                                                                                           \
-    launch_pdl(k_down_levels<D>, a.shift_blocks, 128, sizeof(double2) * (5 * P1 + 1), st, d.level_start, h.nlevels, \
-               d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box, first, d.box_parent, d.box_ix, d.box_iy, \
-               op.par, op.par_df, second, d.exdf, P1, d.lvtab, first_digits ? d.v_src : nullptr, d.v_code, tb.logd,  \
-               d.flag, glimit, a.err)
-        ce = dfp ? BC_DOWN(true) : BC_DOWN(false);
-#undef BC_DOWN
+        if (dfp)
+            ce = launch_pdl(k_down_levels<true>, a.shift_blocks, 128, down_smem_bytes(P1, 0, 0, true), st,
+                            d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride, d.leaf_box,
+                            first, d.box_parent, d.box_ix, d.box_iy, op.par_df, op.par_f, second, d.exdf, P1, d.lvtab,
+                            first_digits ? d.v_src : nullptr, d.v_code, tb.logd, !first_digits, d.flag, glimit,
+                            a.err);
+        else
+            ce = launch_pdl(k_down_warps, a.down_blocks, 128, down_warps_smem_bytes(P1, op.par_f.T, op.par_f.maxp, 4),
+                            st, d.level_start, h.nlevels, d.v_ptr, d.Pv, d.x_ptr, d.x_src, PX, px_stride,
+                            d.leaf_box, first, d.box_parent, d.box_ix, d.box_iy, op.par_f, second, P1, d.lvtab,
+                            first_digits ? d.v_src : nullptr, d.v_code, tb.logd, !first_digits, d.flag, glimit,
+                            a.err);
         if (ce != cudaSuccess) return ce;
     } else if (ev) {
         cudaEventRecord(ev[4], st);
@@ -1082,8 +1391,8 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     return cudaGetLastError();
 }
 
-cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, int down_per_sm, int *up_blocks,
-                         int *shift_blocks)
+cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int f_T, int f_maxp, int up_per_sm, int down_per_sm,
+                         int *up_blocks, int *shift_blocks, int *down_blocks)
 {
     {
         // binomial table of the factored M2L (see c_binom)
@@ -1105,7 +1414,8 @@ cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, i
     int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t shU = up_smem_bytes(NP, P1, 0, 0), shUd = up_smem_bytes(NP, P1, df_T, df_maxp);
+    const size_t shU = up_smem_bytes_f64(NP, P1, f_T, f_maxp), shUd = up_smem_bytes(NP, P1, df_T, df_maxp);
+    const size_t shD = down_smem_bytes(P1, f_T, f_maxp, false), shDd = down_smem_bytes(P1, 0, 0, true);
     // the double-float variants hold the scheduled shift operators in shared
     // memory, beyond the default 48 KB at high orders; the limit is per
     // kernel, so it is only ever raised (contexts of different orders share
@@ -1116,6 +1426,20 @@ cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, i
         if (e == cudaSuccess && size_t(fa.maxDynamicSharedSizeBytes) < shUd)
             e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(shUd));
     }
+    // The kernels that run before and beside the near-field tensor launch
+    // prefer the largest shared-memory carveout: an SM's split between L1 and
+    // shared memory is fixed while any block is resident on it, and a smaller
+    // one, set by these kernels' blocks, would keep the tensor CTA (about
+    // 220 KB of shared memory) off that SM until they have all exited.
+    for (const void *k : {(const void *)k_clear_flags, (const void *)k_up_levels<false, false>,
+                          (const void *)k_up_levels<true, false>, (const void *)k_up_levels<false, true>,
+                          (const void *)k_up_levels<true, true>, (const void *)k_m2l_boxes<false, 16>,
+                          (const void *)k_m2l_boxes<true, 16>, (const void *)k_m2l_boxes<false, 24>,
+                          (const void *)k_m2l_boxes<true, 24>, (const void *)k_m2l_boxes<false, 32>,
+                          (const void *)k_m2l_boxes<true, 32>, (const void *)k_down_warps,
+                          (const void *)k_down_levels<false>, (const void *)k_down_levels<true>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     // every block of a persistent pass must be resident: the smallest
     // occupancy over the variants that share the grid
     int bu2 = 0, bu3 = 0, bs2 = 0;
@@ -1123,18 +1447,19 @@ cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int up_per_sm, i
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu1, k_up_levels<true, false>, 128, shU);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu2, k_up_levels<false, true>, 128, shUd);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bu3, k_up_levels<true, true>, 128, shUd);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels<false>, 128, shD);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs2, k_down_levels<true>, 128, shDd);
+    int bw = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_down_levels<false>, 128,
-                                                          sizeof(double2) * (5 * P1 + 1));
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs2, k_down_levels<true>, 128,
-                                                          sizeof(double2) * (5 * P1 + 1));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bw, k_down_warps, 128,
+                                                          down_warps_smem_bytes(P1, f_T, f_maxp, 4));
     if (e != cudaSuccess) return e;
     const int bu = std::min(std::min(bu0, bu1), std::min(bu2, bu3));
     bs = std::min(bs, bs2);
-    if (bu < 1 || bs < 1) return cudaErrorInvalidConfiguration;
+    if (bu < 1 || bs < 1 || bw < 1) return cudaErrorInvalidConfiguration;
     *up_blocks = sms * std::min(up_per_sm, bu);
     *shift_blocks = sms * std::min(down_per_sm, bs);
+    *down_blocks = sms * std::min(down_per_sm, bw);
     return cudaSuccess;
 }
 

@@ -1,11 +1,12 @@
 // Split-precision operator products on the 5th-generation tensor cores
 // (tcgen05), p = 16.
 //
-// Every fixed-operator product of the apply except the multipole-to-local
-// translations -- the near-field tables, P2M, L2P, the W list (M2P) and the
-// X list (P2L), and their adjoints -- is a dense real matrix (the operator)
-// times many vectors (leaf values or expansion coefficients).  Each product
-// is evaluated exactly in integer arithmetic on BF16 tensor cores:
+// The fixed-operator products of a split-precision apply -- the near-field
+// tables, P2M, L2P, the W list (M2P) and the X list (P2L), their adjoints,
+// and in BC_SPLIT_BF16_ALL also the multipole-to-local translations -- are
+// dense real matrices (the operators) times many vectors (leaf values or
+// expansion coefficients).  Each product is evaluated exactly in integer
+// arithmetic on BF16 tensor cores:
 //   * each FP64 operand row (operator row, input vector) is scaled by a power
 //     of two 2^E so that its entries lie in (-1/2, 1/2), rounded to a 40-bit
 //     fixed-point integer X and cut into five balanced base-256 digits,
@@ -17,8 +18,9 @@
 //   * each D_g (g = 2..6) accumulates in its own FP32 TMEM accumulator: every
 //     product is an integer of magnitude <= 2^14 and a level sums at most
 //     4 x 256 of them for g <= 5, so the accumulation is exact (< 2^24);
-//   * the five levels are combined in int64 and converted to FP64 once, by
-//     integer operations on the bit pattern (the FP64 pipe stays free).
+//   * the five levels are combined in int64 and converted to FP64 once (a
+//     hardware conversion; the power-of-two scale is then added to the
+//     exponent field of the bit pattern).
 //
 // Work decomposition: a tile is one operator times up to 48 columns, done as
 // one job per 128-row half of the operator.
@@ -409,8 +411,12 @@ struct GemmBars {
     int fail;
 };
 
+// The second launch bound caps the registers at 64 per thread: 16 warps x 64
+// leave room, in each SM sub-partition's register file, for the FP64 M2L
+// blocks that run beside a near-field CTA.  Two CTAs never share an SM (shared
+// memory allows one).
 template <int KD>
-__global__ void __launch_bounds__(kGemmThreads, 1)
+__global__ void __launch_bounds__(kGemmThreads, 2)
 k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__restrict__ err, long long wait_limit,
              int withhold)
 {
@@ -739,6 +745,14 @@ cudaError_t split_prepare()
                                          int(GemmShape<256>::kSmem));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64);
+    // the digit kernels run before and beside the tensor launches: the
+    // largest shared-memory carveout (see fp64_prepare)
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_vec, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_exp, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     int dev = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);

@@ -9,9 +9,11 @@
 //
 // Sharing rules: every call, on every stream, uses the same array; calls that
 // overlap on the GPU race with each other and must be serialised by the
-// caller.  The array keeps what the last call left in it.  Every workspace
-// element the apply reads is written earlier in the same apply, so nothing
-// needs clearing between calls.
+// caller.  The call also uses the tree's own per-box flags and X-list buffer,
+// so an overlapping apply of any kind on the same tree races with it too.  The
+// array keeps what the last call left in it.  Every workspace element the
+// apply reads is written earlier in the same apply, so nothing needs clearing
+// between calls.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -91,15 +93,7 @@ extern "C" bc_status bc_apply_noalloc(bc_ctx *ctx, const bc_tree *tree, const do
     DevTree d = tree->d;   // lists as uploaded with the tree; workspaces replaced
     d.expA = static_cast<double2 *>(base);
     d.expB = d.expA + nbox * size_t(ctx->P1);
-    PassArgs a;
-    a.p = ctx->p; a.NP = ctx->NP; a.P1 = ctx->P1;
-    a.half_L = 0.5 * tree->h.L;
-    a.nleaf = tree->h.nleaf;
-    a.nbox = int64_t(nbox);
-    a.up_blocks = ctx->up_blocks;
-    a.shift_blocks = ctx->shift_blocks;
-    a.wait_limit = ctx->split.wait_limit;
-    a.err = ctx->dev_err;
+    const PassArgs a = pass_args(ctx, tree);
     e = launch_apply(a, tree->h, d, ctx->dt, adjoint != 0, in, out, static_cast<cudaStream_t>(stream), 3, nullptr,
                      ctx->m2l_tri, nullptr);
     if (e != cudaSuccess) { set_error("bc_apply_noalloc: launch: %s", cudaGetErrorString(e)); return BC_ERR_CUDA; }

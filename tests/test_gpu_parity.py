@@ -361,33 +361,38 @@ def test_autograd_matches_finite_differences(ctx16):
 # near field alone stays at the 1e-12 level (SPLIT_NEAR_TOL).
 # ---------------------------------------------------------------------------
 SPLIT_NEAR_TOL = 1e-11
-def test_split_config1_vs_oracle(ctx16):
+SPLIT_MODES = pytest.mark.parametrize("mode", [1, 2], ids=["split", "split_all"])
+
+
+@SPLIT_MODES
+def test_split_config1_vs_oracle(ctx16, mode):
     p = 16
     g = synth.config_density(1)
     lv, ix, iy = synth.uniform_leaves(3)
     tree, geom, fvals, f = make(ctx16, lv, ix, iy, g)
-    us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    us = bc.apply(tree, f, precision=mode)
     bc._check(bc._load().bc_sync(ctx16.handle, None))
     u = us.cpu().numpy().reshape(-1, p * p)
     pick = np.arange(0, 64, 3)
     ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
     err = relerr(u[pick], ref)
-    print(f"config1 split rel err {err:.3e}")
+    print(f"config1 split mode {mode} rel err {err:.3e}")
     assert err < TOL, err
 
 
-def test_split_adaptive_vs_fp64_and_oracle(ctx16, adaptive):
+@SPLIT_MODES
+def test_split_adaptive_vs_fp64_and_oracle(ctx16, adaptive, mode):
     lv, ix, iy, g, tree, geom, fvals, f = adaptive
     p = 16
     u64 = bc.apply(tree, f)
-    us = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    us = bc.apply(tree, f, precision=mode)
     bc._check(bc._load().bc_sync(ctx16.handle, None))
     d = ((us - u64).abs().max() / u64.abs().max()).item()
     assert d < TOL, d
     pick = synth.sample_leaves_per_level(np.asarray(lv), 2, seed=9)
     ref = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=pick)
     err = relerr(us.cpu().numpy().reshape(-1, p * p)[pick], ref)
-    print(f"adaptive split rel err {err:.3e} (vs fp64 {d:.3e})")
+    print(f"adaptive split mode {mode} rel err {err:.3e} (vs fp64 {d:.3e})")
     assert err < TOL, err
 
 
@@ -466,7 +471,7 @@ def test_split_parts_each_within_tolerance(ctx16, adaptive):
             print(f"split part {parts}: fwd {du:.2e} adj {dh:.2e}")
             assert 0.0 < du < TOL and 0.0 < dh < TOL, (parts, du, dh)
     finally:
-        ctx16.set_option("debug_split_parts", 127)
+        ctx16.set_option("debug_split_parts", -1)
 
 
 def test_split_overlap_gives_identical_results(ctx16, adaptive):
@@ -524,7 +529,7 @@ def test_split_double_float_shifts_other_orders(nterms):
                           bc.apply_adjoint(tree, gg, precision=bc.SPLIT_BF16))
         bc._check(bc._load().bc_sync(ctx.handle, None))
     finally:
-        ctx.set_option("debug_split_parts", 127)
+        ctx.set_option("debug_split_parts", -1)
     for k, ref in enumerate((u64, h64)):
         tag = "adj" if k else "fwd"
         d_df = ((out[64][k] - out[0][k]).abs().max() / out[0][k].abs().max()).item()
