@@ -136,15 +136,24 @@ def potential_at_nodes(p, geom, f, leaf_ids=None, sources=None, nthreads=0):
     return u.reshape(nodes.shape[0], p * p)
 
 
-def adjoint_columns(p, geom, g, columns, nthreads=0):
+def adjoint_columns(p, geom, g, columns, nthreads=0, target_leaves=None):
     """(A^T g)_j for sampled columns j = (leaf, node) of the discrete operator
-    A_ij = (1/2pi) int_{B(j)} log|x_i - y| l_j(y) dy, x_i all leaf nodes.
+    A_ij = (1/2pi) int_{B(j)} log|x_i - y| l_j(y) dy, x_i the leaf nodes.
 
     Each column is the potential of the Lagrange basis function l_j on its leaf,
-    evaluated at every node and contracted with g (plain definition of A^T).
+    evaluated at the nodes and contracted with g (plain definition of A^T).
+    g: values at every node ([nleaf, p*p]).  target_leaves: optional leaf ids;
+    the contraction then runs over the nodes of those leaves only, which is
+    (A^T g)_j itself when g vanishes at every other node.
+    Pinned by tests/test_oracle_pins.py (transpose of oracle columns, scipy).
     """
-    nodes = leaf_nodes(geom, p).reshape(-1, 2)
-    g = np.asarray(g, dtype=np.float64).reshape(-1)
+    nodes = leaf_nodes(geom, p)
+    g = np.asarray(g, dtype=np.float64).reshape(nodes.shape[0], p * p)
+    if target_leaves is not None:
+        tl = np.asarray(target_leaves, dtype=np.int64)
+        nodes, g = nodes[tl], g[tl]
+    nodes = nodes.reshape(-1, 2)
+    g = g.reshape(-1)
     out = []
     for (b, j) in columns:
         e = np.zeros((1, p * p))

@@ -281,3 +281,69 @@ def test_linearity_and_source_split(oracle_mod):
     uA = oracle_mod.potential(p, g, f1, pts, sources=(np.arange(n + 1) * len(A), np.tile(A, n)))
     uB = oracle_mod.potential(p, g, f1, pts, sources=(np.arange(n + 1) * len(B), np.tile(B, n)))
     assert np.abs(uA + uB - u1).max() < 1e-14 * np.abs(u1).max()
+
+
+def _lagrange_1d(p, m, t):
+    """l_m(t) on the first-kind Chebyshev nodes, by the product formula
+    (independent of the oracle's barycentric interpolation)."""
+    k = np.arange(p)
+    x = -np.cos((2 * k + 1) * np.pi / (2 * p))
+    t = np.asarray(t, dtype=np.float64)
+    out = np.ones_like(t)
+    for q in range(p):
+        if q != m:
+            out = out * (t - x[q]) / (x[m] - x[q])
+    return out
+
+
+def test_adjoint_columns_are_the_transpose(oracle_mod):
+    """Each adjoint column contracted with the density equals the bilinear form
+    <A f, g> taken from the forward oracle: sum_{j in B1, B2} f_j (A^T g)_j =
+    <A f_r, g>, f_r = f on leaves B1, B2 and 0 elsewhere (every column of two
+    leaves of a 2:1-refined tree, one of them finer).  The restricted form
+    (target_leaves) gives the same columns when g vanishes outside those
+    leaves.  A layout slip (the (jx, jy) order of a column, the wrong target
+    set or a transposed index) fails it."""
+    p = 6
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: r > 0.9 or (cx < 0 and cy < 0 and r > 0.3), 3)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    n = len(lv)
+    rng = np.random.default_rng(5)
+    f = rng.standard_normal((n, p * p))
+    g = rng.standard_normal((n, p * p))
+    pick = [int(np.argmax(np.array(lv))), int(np.argmin(np.array(lv)))]   # a fine and a coarse leaf
+    assert n == 7 and lv[pick[0]] == 2 and lv[pick[1]] == 1
+    fr = np.zeros_like(f)
+    fr[pick] = f[pick]
+    nodes = oracle_mod.leaf_nodes(geom, p).reshape(-1, 2)
+    lhs = float(np.dot(oracle_mod.potential(p, geom, fr, nodes), g.ravel()))
+    cols = [(b, j) for b in pick for j in range(p * p)]
+    at = oracle_mod.adjoint_columns(p, geom, g, cols)
+    rhs = float(np.dot(at, np.concatenate([f[b] for b in pick])))
+    assert abs(lhs - rhs) <= 1e-13 * (abs(lhs) + 1.0), (lhs, rhs)
+    # restricted contraction: g supported on a few leaves
+    tl = [0, 3, n - 1]
+    gs = np.zeros_like(g)
+    gs[tl] = g[tl]
+    full = oracle_mod.adjoint_columns(p, geom, gs, cols[:12])
+    part = oracle_mod.adjoint_columns(p, geom, gs, cols[:12], target_leaves=tl)
+    assert np.abs(full - part).max() <= 1e-15 * np.abs(full).max()
+
+
+def test_adjoint_column_against_scipy(oracle_mod):
+    """One column of A^T on a single leaf against scipy dblquad of the Lagrange
+    basis function: (A^T e_i)_j = (1/2pi) int log|x_i - y| l_j(y) dy for a
+    target node i inside the leaf, with j = (jx, jy) off the diagonal so that a
+    swapped x/y order of the column would show."""
+    pytest.importorskip("scipy")
+    p = 4
+    geom = oracle_mod.leaf_geometry([0], [0], [0])
+    x = oracle_mod.cheb_nodes(p)
+    jx, jy, i = 1, 3, 6              # column node (x index 1, y index 3); target node 6 = (2, 1)
+    j = jy * p + jx
+    g = np.zeros((1, p * p))
+    g[0, i] = 1.0
+    got = oracle_mod.adjoint_columns(p, geom, g, [(0, j)])[0]
+    xi, eta = x[i % p], x[i // p]
+    ref = _dblquad_leaf(lambda a, b: _lagrange_1d(p, jx, a) * _lagrange_1d(p, jy, b), xi, eta) / (2 * math.pi)
+    assert abs(got - ref) <= 1e-13 * max(1.0, abs(ref)), (got, ref)
