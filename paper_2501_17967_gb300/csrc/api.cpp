@@ -744,8 +744,7 @@ bc_status build_split_tree(bc_tree *t)
         (e = dev_upload<uint16_t>(al, &s.vdig, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
         (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess ||
         (e = dev_upload<uint16_t>(al, &s.edig, nullptr, size_t(2 * nbox) * kSplitSlices * kSplitKE)) != cudaSuccess ||
-        (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess ||
-        (e = dev_upload<double2>(al, &t->d.Pv, nullptr, h.v_src.size() * size_t(P1))) != cudaSuccess)
+        (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess)
         return cuda_fail(e, "split tree upload");
     // owners of the near and W entries, box of each X entry
     std::vector<int32_t> near_owner(nn), w_owner(nw), x_box(nx);
@@ -759,7 +758,7 @@ bc_status build_split_tree(bc_tree *t)
         const bool adj = dir == 1;
         double2 *first = adj ? t->d.expB : t->d.expA;
         const int first_which = adj ? 1 : 0, second_which = adj ? 0 : 1;   // expA = 0, expB = 1
-        TileBuilder V, NV, E, M;
+        TileBuilder V, NV, E;
         // near entries, by table
         std::vector<std::vector<SplitCol>> by_tab(kNumNear);
         for (int64_t k = 0; k < nn; k++) {
@@ -816,20 +815,6 @@ bc_status build_split_tree(bc_tree *t)
         }
         for (int c = 0; c < kNumWX; c++)
             if (!by_code[c].empty()) E.add(T.w_op[dir][c], by_code[c]);
-        // group M: one column per V pair (source box digits, result into Pv;
-        // the adjoint digits carry alpha0)
-        {
-            std::vector<std::vector<SplitCol>> by_v(kNumV);
-            for (size_t k = 0; k < h.v_src.size(); k++) {
-                SplitCol c;
-                c.vec = int32_t(first_which * nbox + h.v_src[k]);
-                c.ctl = col_ctl(0, adj);
-                c.out = reinterpret_cast<double *>(t->d.Pv + k * size_t(P1));
-                by_v[h.v_code[k]].push_back(c);
-            }
-            for (int c = 0; c < kNumV; c++)
-                if (!by_v[c].empty()) M.add(T.m2l_op[dir][c], by_v[c]);
-        }
         TileBuilder VN = NV;   // near tiles first (longest), then the far ones
         for (SplitTile tl : V.tiles) {
             tl.p0 += int32_t(NV.cols.size());
@@ -845,17 +830,50 @@ bc_status build_split_tree(bc_tree *t)
             (e = dev_upload(al, &s.tN[dir], NV.tiles.data(), NV.tiles.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.cN[dir], NV.cols.data(), NV.cols.size())) != cudaSuccess ||
             (e = dev_upload(al, &s.tE[dir], E.tiles.data(), E.tiles.size())) != cudaSuccess ||
-            (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess ||
-            (e = dev_upload(al, &s.tM[dir], M.tiles.data(), M.tiles.size())) != cudaSuccess ||
-            (e = dev_upload(al, &s.cM[dir], M.cols.data(), M.cols.size())) != cudaSuccess)
+            (e = dev_upload(al, &s.cE[dir], E.cols.data(), E.cols.size())) != cudaSuccess)
             return cuda_fail(e, "split tree upload");
         s.ntV[dir] = int(V.tiles.size());
         s.ntN[dir] = int(NV.tiles.size());
         s.ntE[dir] = int(E.tiles.size());
-        s.ntM[dir] = int(M.tiles.size());
     }
     s.err = t->ctx->dev_err;
     t->split_ready = true;
+    return BC_OK;
+}
+
+// Tensor-core M2L (part 32, BC_SPLIT_BF16_ALL): one column per V pair
+// (source box digits, the result row into Pv, allocated here on first use:
+// n_v x nterms x 16 bytes; the adjoint digits carry alpha0).
+bc_status build_split_m2l(bc_tree *t)
+{
+    if (t->m2l_ready) return BC_OK;
+    const HostTree &h = t->h;
+    const SplitTables &T = t->ctx->split;
+    const int P1 = t->ctx->P1;
+    const int64_t nbox = int64_t(h.box_level.size());
+    SplitTree &s = t->sp;
+    std::vector<void *> &al = t->d.allocs;
+    cudaError_t e = dev_upload<double2>(al, &t->d.Pv, nullptr, h.v_src.size() * size_t(P1));
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core M2L rows");
+    for (int dir = 0; dir < 2; dir++) {
+        const int first_which = dir == 1 ? 1 : 0;   // expA = 0, expB = 1
+        TileBuilder M;
+        std::vector<std::vector<SplitCol>> by_v(kNumV);
+        for (size_t k = 0; k < h.v_src.size(); k++) {
+            SplitCol c;
+            c.vec = int32_t(first_which * nbox + h.v_src[k]);
+            c.ctl = col_ctl(0, dir == 1);
+            c.out = reinterpret_cast<double *>(t->d.Pv + k * size_t(P1));
+            by_v[h.v_code[k]].push_back(c);
+        }
+        for (int c = 0; c < kNumV; c++)
+            if (!by_v[c].empty()) M.add(T.m2l_op[dir][c], by_v[c]);
+        if ((e = dev_upload(al, &s.tM[dir], M.tiles.data(), M.tiles.size())) != cudaSuccess ||
+            (e = dev_upload(al, &s.cM[dir], M.cols.data(), M.cols.size())) != cudaSuccess)
+            return cuda_fail(e, "tensor-core M2L tiles");
+        s.ntM[dir] = int(M.tiles.size());
+    }
+    t->m2l_ready = true;
     return BC_OK;
 }
 
@@ -901,6 +919,7 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
             return BC_ERR_UNSUPPORTED;
         }
         s = build_split_tree(tw);
+        if (s == BC_OK && (parts & 32)) s = build_split_m2l(tw);
         if (s != BC_OK) return s;
         sl.tree = &tw->sp;
         split = &sl;
@@ -990,6 +1009,10 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     const int parts = split_parts_for(prec, ctx->split_parts);
     SplitLaunch sl{&ctx->split, &b->u->sp, parts, ctx->split_overlap ? &ctx->side : nullptr,
                    near_ctas_for(ctx, parts)};
+    if (is_split(prec) && (parts & 32)) {   // before the capture: it allocates
+        bc_status s = build_split_m2l(b->u);
+        if (s != BC_OK) return s;
+    }
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "batch: begin capture");
     cudaError_t le = launch_apply(a, b->u->h, b->u->d, ctx->dt, adj != 0, b->in_buf, b->out_buf, b->cap, 3, nullptr,

@@ -388,4 +388,5 @@ struct bc_tree {
     bc::DevTree d;
     bc::SplitTree sp;
     bool split_ready = false;
+    bool m2l_ready = false;   // tensor-core M2L tiles and rows (BC_SPLIT_BF16_ALL)
 };
