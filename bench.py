@@ -1,14 +1,22 @@
 """Throughput of the GB300 machine code: leaf nodes per second for one forward plus
-one adjoint volume-potential apply on the adaptive 20-Gaussian workload.
+one adjoint volume-potential apply, on the 200-Gaussian adaptive workload.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split]
+    python bench.py [--gpus N] [--steps K] [--warmup W]
+                    [--precision split|split_all|fp64] [--workload adaptive200|adaptive20|batch64]
                     [--impl ours|reference]
 
-Workload: root [-1,1]^2, p = 16, density = 20 Gaussians (centres U[-0.5,0.5]^2,
-widths log-uniform in [1e-3, 1e-1], amplitudes N(0,1), seed 1), quadtree
-refined by the library (Alg. 2 resolution criterion, eps = 1e-11) and 2:1
-balanced.  A step is one forward apply u = A f and one adjoint apply
-h = A^T g of the whole tree; value = leaf nodes / (time of a step).
+Workload (default): root [-1,1]^2, p = 16, density = 200 Gaussians (centres
+U[-0.5,0.5]^2, widths log-uniform in [1e-4, 1e-1], amplitudes N(0,1), seed
+2), quadtree refined by the library (Alg. 2 resolution criterion,
+eps = 1e-11) and 2:1 balanced: 14,191 leaves, 15 levels, 3.63M leaf nodes.
+A step is one forward apply u = A f and one adjoint apply h = A^T g of the
+whole tree; value = leaf nodes / (time of a step).  The headline precision
+("split") takes the fixed-operator products (near field, P2M, L2P, W and X
+lists) on BF16 tensor cores as exact digit products and keeps the
+multipole-to-local translations, the M2M/L2L shifts, the log terms and
+every sum in native FP64.  The same JSON line carries the native FP64 path,
+the all-tensor split variant and the 20-Gaussian workload as extra keys, and
+the error against the oracle per level, forward and adjoint.
 With --gpus N every rank runs its own replica (the path does not shard; no
 collective on the data path) and value is the total over ranks.
 --impl reference times the CPU FP64 oracle (direct quadrature) on a bounded
@@ -30,9 +38,23 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"
 METRIC = "leaf nodes/sec (p=16, <=1e-10 rel err) fwd+adjoint"
 UNIT = "leaf nodes/s"
+P = 16
+
+WORKLOADS = {
+    "adaptive200": (3, "adaptive 200-Gaussian quadtree (widths 1e-4..1e-1), p=16, eps=1e-11"),
+    "adaptive20": (2, "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"),
+    "batch64": (None, "64 adaptive trees (about 2e2..2e4 leaves, log-uniform), p in {8,12,16}, batched"),
+}
+PRECISIONS = {"fp64": 0, "split": 1, "split_all": 2}
+DTYPES = {
+    0: "f64",
+    1: "bf16 digits (5 slices, exact FP32 accumulation) for the near field, P2M, L2P, W and X lists; "
+       "f64 for M2L, M2M/L2L, log terms and sums",
+    2: "bf16 digits for every fixed-operator product including M2L; double-float (2 x f32) M2M/L2L; "
+       "f64 log terms and sums",
+}
 
 
 def parse():
@@ -40,15 +62,14 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split", choices=list(PRECISIONS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", default="adaptive20", choices=list(WORKLOADS),
-                    help="adaptive20: the benchmark workload; adaptive200: 200 Gaussians, widths 1e-4..1e-1")
+    ap.add_argument("--workload", default="adaptive200", choices=list(WORKLOADS))
     ap.add_argument("--nterms", type=int, default=24,
                     help="far-field expansion terms P+1: 24 keeps the truncation near 1e-12, inside the "
                          "1e-10 target of the metric (30 reaches FP64 rounding)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline only: no FP64 / all-tensor / 20-Gaussian lines, no oracle checks")
     ap.add_argument("--no-overlap", dest="overlap", action="store_false",
                     help="run the near-field tensor launch in line instead of beside the far-field passes "
                          "(the library's default, on an internal stream)")
@@ -57,14 +78,7 @@ def parse():
     return ap.parse_args()
 
 
-WORKLOADS = {
-    "adaptive20": (2, "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"),
-    "adaptive200": (3, "adaptive 200-Gaussian quadtree (widths 1e-4..1e-1), p=16, eps=1e-11"),
-    "batch64": (None, "64 adaptive trees (about 2e2..2e4 leaves, log-uniform), p in {8,12,16}, batched"),
-}
-
-
-def density(workload="adaptive20"):
+def density(workload):
     from paper_2501_17967_gb300 import synth
     return synth.config_density(WORKLOADS[workload][0])
 
@@ -118,121 +132,169 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------------------- oracle arm
-def oracle_rate(tree_leaves, fvals, seconds, seed=11):
-    """Oracle forward throughput (target nodes/s) on sampled leaves, bounded in time.
-    The oracle's transposed operator costs the same per entry, so a fwd+adjoint
-    step is twice the forward cost."""
+# ---------------------------------------------------------------- oracle samples
+def touching(lv, ix, iy, t):
+    """Leaves touching leaf t (edge or corner), t included, from the dyadic indices."""
+    L = int(lv.max())
+    s = L - lv
+    x0, x1 = ix << s, (ix + 1) << s
+    y0, y1 = iy << s, (iy + 1) << s
+    ok = (x0 <= x1[t]) & (x0[t] <= x1) & (y0 <= y1[t]) & (y0[t] <= y1)
+    return np.nonzero(ok)[0]
+
+
+def oracle_forward_sample(leaves, fvals, per_level, seed=11):
+    """Oracle u at every node of per_level leaves of every level (timed)."""
     import oracle
     from paper_2501_17967_gb300 import synth
-    lv, ix, iy = tree_leaves
-    p = 16
+    lv, ix, iy = leaves
     geom = synth.leaf_geometry(lv, ix, iy)
+    pick = synth.sample_leaves_per_level(lv, per_level, seed=seed)
+    t0 = time.perf_counter()
+    ref = oracle.potential_at_nodes(P, geom, fvals, leaf_ids=pick)
+    return pick, ref, time.perf_counter() - t0
+
+
+def adjoint_sample(leaves, seed=13, per_level=1, k_cols=3, n_rand=24):
+    """g random on S (sampled column leaves, their neighbours, random leaves),
+    zero elsewhere; columns on every level near and far from S."""
+    from paper_2501_17967_gb300 import synth
+    lv, ix, iy = leaves
     rng = np.random.default_rng(seed)
-    order = rng.permutation(len(lv))
-    done, t_used, vals = 0, 0.0, {}
-    k = 1
-    while t_used < seconds and done < len(order):
-        ids = order[done:done + k]
-        t0 = time.perf_counter()
-        u = oracle.potential_at_nodes(p, geom, fvals, leaf_ids=ids)
-        t_used += time.perf_counter() - t0
-        for i, b in enumerate(ids):
-            vals[int(b)] = u[i]
-        done += len(ids)
-        k = min(2 * k, 64)
-    nodes = done * p * p
-    return nodes / t_used / 2.0, nodes, t_used, vals
+    near_cols = synth.sample_leaves_per_level(lv, per_level, seed=seed)
+    far_cols = synth.sample_leaves_per_level(lv, per_level, seed=seed + 1)
+    S = set()
+    for b in near_cols:
+        S.update(touching(lv, ix, iy, int(b)).tolist())
+    S.update(rng.choice(len(lv), size=min(n_rand, len(lv)), replace=False).tolist())
+    S = np.array(sorted(S), dtype=np.int64)
+    cols = [(int(b), int(j)) for b in np.concatenate([near_cols, far_cols])
+            for j in rng.choice(P * P, size=k_cols, replace=False)]
+    g = np.zeros((len(lv), P * P))
+    g[S] = rng.standard_normal((len(S), P * P))
+    return S, cols, g
 
 
+def per_level(levels, errs, scale):
+    out = {}
+    for lvl, e in zip(levels, errs):
+        out[str(int(lvl))] = max(out.get(str(int(lvl)), 0.0), float(e) / scale)
+    return {k: float(f"{v:.3e}") for k, v in sorted(out.items(), key=lambda kv: int(kv[0]))}
+
+
+# ---------------------------------------------------------------- reference arm
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import paper_2501_17967_gb300 as bc
     import oracle
+    import paper_2501_17967_gb300 as bc
     from paper_2501_17967_gb300 import synth
-    g = density(args.workload)
-    hctx = bc.Context(p=16, device=-1, cache_dir=None, build_tables=False)
+    g = density(args.workload if args.workload != "batch64" else "adaptive200")
+    hctx = bc.Context(p=P, device=-1, cache_dir=None, build_tables=False)
     tree = bc.Tree.refine(hctx, g, eps=1e-11, max_level=18)
-    leaves = tree.leaves()
-    geom = synth.leaf_geometry(*leaves)
-    fvals = g(oracle.leaf_nodes(geom, 16)).reshape(-1, 16, 16)
+    lv, ix, iy = (np.asarray(a) for a in tree.leaves())
+    geom = synth.leaf_geometry(lv, ix, iy)
+    fvals = g(oracle.leaf_nodes(geom, P))
     per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    rng = np.random.default_rng(17)
+    order = rng.permutation(len(lv))
+    pos = 0
+
+    def sample(seconds):
+        nonlocal pos
+        done, used, k = 0, 0.0, 1
+        while used < seconds:
+            ids = order[pos % len(order):pos % len(order) + k]
+            pos += len(ids)
+            t0 = time.perf_counter()
+            oracle.potential_at_nodes(P, geom, fvals, leaf_ids=ids)
+            used += time.perf_counter() - t0
+            done += len(ids)
+            k = min(2 * k, 16)
+        return done * P * P, used
+
     for _ in range(args.warmup):
-        oracle_rate(leaves, fvals, per_step / 4)
-    rates, nodes_tot, t_tot = [], 0, 0.0
-    for s in range(args.steps):
-        r, n, t, _ = oracle_rate(leaves, fvals, per_step, seed=100 + s)
-        rates.append(r)
+        sample(per_step / 4)
+    nodes_tot, t_tot = 0, 0.0
+    for _ in range(args.steps):
+        n, t = sample(per_step)
         nodes_tot += n
         t_tot += t
     value = nodes_tot / t_tot / 2.0
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload][1], "nleaf": int(tree.nleaf), "leaf_nodes": int(tree.nleaf) * 256,
-                       "parallelism": "host threads"},
+            "config": {"workload": WORKLOADS[args.workload][1], "nleaf": int(len(lv)),
+                       "leaf_nodes": int(len(lv)) * P * P, "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{nodes_tot} target nodes of randomly sampled leaves over {args.steps} steps "
-                                       f"(~{per_step:.0f}s each), forward oracle rate halved for fwd+adjoint"},
+                             "sample": f"{nodes_tot} target nodes of randomly drawn leaves of the same tree over "
+                                       f"{args.steps} steps (~{per_step:.0f}s each); forward rate halved for "
+                                       f"fwd+adjoint (the transposed operator costs the same per entry)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
 # ---------------------------------------------------------------- GPU arm
 STAGES = ("tensor_v", "clear", "upward", "m2l", "down_levels", "tensor_e", "leaf_output", "tensor_near")
-
-
 STAGE_KERNELS = {
-    "tensor_v": "k_split_vec + k_split_gemm<256> (leaf-to-expansion; X list and near field too with --no-overlap)",
+    "tensor_v": "k_split_vec + k_split_gemm<256> (leaf-to-expansion; X list and near field too in line)",
     "clear": "k_clear_flags",
     "upward": "k_up_levels",
-    "m2l": "k_split_exp + k_split_gemm<64> (M2L per V pair; FP64 path: k_m2l_pairs + k_x_entries)",
-    "down_levels": "k_down_levels",
-    "tensor_e": "k_split_exp + k_split_gemm<64>",
+    "m2l": "k_m2l_boxes (FP64 M2L per target box; FP64 path also k_x_entries) | "
+           "k_split_exp + k_split_gemm<64> (all-tensor split)",
+    "down_levels": "k_down_warps | k_down_levels<double-float> (all-tensor split)",
+    "tensor_e": "k_split_exp + k_split_gemm<64> (L2P and W list)",
     "leaf_output": "k_leaf_out",
-    "tensor_near": "k_split_gemm<256> (X list, then near field, on the internal stream beside stages 1-4)",
+    "tensor_near": "k_split_gemm<256> (X list, then near field, on the internal stream)",
 }
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of each stage's tensor or
-# pass kernel (cold cache; tensor_near: its X-list and near-field launches
-# together), keyed by (workload, nterms, split): the launch list of the bench
-# configuration (profiles/launches_adaptive20_split.md)
-TRAFFIC = {
-    ("adaptive20", 24, True): {"tensor_v": 3.59e6, "tensor_near": 29.24e6, "upward": 0.57e6, "m2l": 2.95e6,
-                               "down_levels": 13.68e6, "tensor_e": 5.27e6, "leaf_output": 32.39e6},
-}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
+# kernel in the bench configuration, keyed by (workload, nterms, precision):
+# filled from the ncu captures of the unchanged kernels, null otherwise
+TRAFFIC = {}
 
 
-def stage_work(st, nleaf, nleaf_far, P1, NP, split):
-    """Algorithmic work of each stage of one apply, counted from the tree's lists:
-    (amount, kind) with kind "tensor" (BF16 flops of the 15 digit products,
-    rows x K x columns of the real operators), "fp64" (FP64 flops: complex x
-    real = 4 per term, complex x complex = 8) or "bytes" (leaf output of the
-    split path: FP64 partial results read + result written)."""
-    n_shift = st["n_down"]
+def stage_work(st, nleaf, nleaf_far, P1, NP, prec):
+    """Algorithmic work of each stage of one apply, counted from the tree's
+    lists: (amount, kind), kind "tensor" (BF16 flops of the 15 digit products,
+    rows x K x columns of the real operators), "fp64" (FP64 flops; a real x
+    complex term counts 4, a complex x complex term 8) or "bytes"."""
     R = 2 * P1
-    if split:
+    m2l64 = (4.0 * P1 * P1 + 14.0 * P1) * st["n_v"]          # factored form, per V pair
+    shift64 = 4.0 * (P1 * (P1 + 1) / 2) + 12.0 * P1           # factored shift per child: binomial + diagonals
+    up64 = 4 * shift64 * st["n_nonleaf"]
+    down64 = shift64 * st["n_down"] + 2.0 * P1 * st["n_x"]
+    if prec == 0:
         return {
-            "tensor_v": (15 * 2.0 * NP * R * (nleaf + st["n_x"]), "tensor"),
-            "tensor_near": (15 * 2.0 * NP * NP * st["n_near"], "tensor"),
-            "clear": (0.0, "fp64"),
-            "upward": (32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
-            "m2l": (15 * 2.0 * R * R * st["n_v"], "tensor"),
-            "down_levels": (8.0 * P1 * P1 * n_shift + 2.0 * P1 * (st["n_v"] + st["n_x"]), "fp64"),
-            "tensor_e": (15 * 2.0 * R * NP * (nleaf_far + st["n_w"]), "tensor"),
-            "leaf_output": (8.0 * NP * (st["n_near"] + st["n_w"] + nleaf_far + nleaf), "bytes"),
+            "tensor_v": (0.0, "tensor"), "tensor_near": (0.0, "tensor"), "clear": (0.0, "fp64"),
+            "upward": (4.0 * P1 * NP * nleaf + up64, "fp64"),
+            "m2l": (m2l64 + 4.0 * P1 * NP * st["n_x"], "fp64"),
+            "down_levels": (down64, "fp64"),
+            "tensor_e": (0.0, "tensor"),
+            "leaf_output": (2.0 * NP * NP * st["n_near"] + 4.0 * P1 * NP * (nleaf_far + st["n_w"]), "fp64"),
         }
-    return {
-        "tensor_v": (0.0, "tensor"),
-        "tensor_near": (0.0, "tensor"),
+    w = {
+        "tensor_v": (15 * 2.0 * NP * R * (nleaf + st["n_x"]), "tensor"),
+        "tensor_near": (15 * 2.0 * NP * NP * st["n_near"], "tensor"),
         "clear": (0.0, "fp64"),
-        "upward": (4.0 * P1 * NP * nleaf + 32.0 * P1 * P1 * st["n_nonleaf"], "fp64"),
-        "m2l": (4.0 * P1 * P1 * st["n_v"] + 4.0 * P1 * NP * st["n_x"], "fp64"),
-        "down_levels": (8.0 * P1 * P1 * n_shift + 2.0 * P1 * (st["n_v"] + st["n_x"]), "fp64"),
-        "tensor_e": (0.0, "tensor"),
-        "leaf_output": (2.0 * NP * NP * st["n_near"] + 4.0 * P1 * NP * (nleaf_far + st["n_w"]), "fp64"),
+        "upward": (up64, "fp64"),
+        "m2l": (m2l64, "fp64"),
+        "down_levels": (down64, "fp64"),
+        "tensor_e": (15 * 2.0 * R * NP * (nleaf_far + st["n_w"]), "tensor"),
+        "leaf_output": (8.0 * NP * (st["n_near"] + st["n_w"] + nleaf_far + nleaf), "bytes"),
     }
+    if prec == 2:
+        w["m2l"] = (15 * 2.0 * R * R * st["n_v"], "tensor")
+    return w
+
+
+def launches_per_apply(prec, overlap, st):
+    """Kernels of one apply (trees of more than three levels)."""
+    if prec == 0:
+        return 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1   # clear, up, M2L, X, down, leaf
+    side = 2 if overlap else 0                                     # X list + near field apart
+    base = 2 + side + 1 + 1 + 1 + 2 + 1                            # digits + group V, clear, up, down, E, leaf
+    return base + (2 if prec == 2 else 1)                          # M2L: digits + GEMM, or the FP64 kernel
 
 
 def run_batch64(args):
@@ -253,7 +315,8 @@ def run_batch64(args):
         groups[p].append((tree, torch.from_numpy(g(tree.nodes())).to(dev)))
     t_tree = time.perf_counter() - t0
     batches = {p: bc.Batch(ctxs[p], [t for t, _ in groups[p]]) for p in groups}
-    prec = {p: (bc.SPLIT_BF16 if (p in bc.SPLIT_ORDERS and args.precision == "split") else bc.FP64) for p in groups}
+    head = PRECISIONS[args.precision]
+    prec = {p: (head if p in bc.SPLIT_ORDERS else bc.FP64) for p in groups}
     outs = {p: [torch.empty_like(f) for _, f in groups[p]] for p in groups}
     adjs = {p: [torch.empty_like(f) for _, f in groups[p]] for p in groups}
     for p in groups:
@@ -287,7 +350,7 @@ def run_batch64(args):
     line = {"metric": METRIC + " (batched)", "value": nodes / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64 (p=8,12) / bf16 digits + f64 (p=16)" if args.precision == "split" else "f64",
+            "dtype": f"f64 (p=8,12) / {DTYPES[head]} (p=16)" if head else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOADS["batch64"][1], "trees": 64, "leaves_min": min(leaves),
                        "leaves_max": max(leaves), "leaves_total": sum(leaves), "leaf_nodes": nodes,
@@ -296,6 +359,98 @@ def run_batch64(args):
                        "l2": "flushed (256 MB write) between timed steps"},
             "clocks": clocks.summary()}
     print(json.dumps(line))
+
+
+class Runner:
+    """Timed forward + adjoint steps of one tree."""
+
+    def __init__(self, bc, torch, ctx, tree, f, gin, dev, world, dist):
+        self.bc, self.torch, self.ctx, self.tree = bc, torch, ctx, tree
+        self.f, self.gin = f, gin
+        self.u = torch.empty_like(f)
+        self.h = torch.empty_like(f)
+        self.dev, self.world, self.dist = dev, world, dist
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2 (129 MB)
+        self.stream = torch.cuda.current_stream()
+
+    def step(self, prec):
+        self.bc.apply(self.tree, self.f, out=self.u, precision=prec, stream=self.stream)
+        self.bc.apply_adjoint(self.tree, self.gin, out=self.h, precision=prec, stream=self.stream)
+
+    def timed(self, prec, steps, warmup, sampler=None, stages=True):
+        torch, bc = self.torch, self.bc
+        for _ in range(max(3, warmup)):
+            self.step(prec)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if self.world > 1:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+            time.sleep(0.3)
+        # the timed steps run as in production: no stage events, no host reads
+        for k in range(steps):
+            self.flush.zero_()
+            ev[k][0].record(self.stream)
+            self.step(prec)
+            ev[k][1].record(self.stream)
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.stop()
+        if self.world > 1:
+            self.dist.barrier()
+        bc._check(bc._load().bc_sync(self.ctx.handle, None))
+        total = torch.tensor([float(sum(a.elapsed_time(b) for a, b in ev))], dtype=torch.float64, device=self.dev)
+        if self.world > 1:
+            self.dist.all_reduce(total, op=self.dist.ReduceOp.MAX)
+        st = np.zeros((2, len(STAGES)))
+        if stages:
+            # per-stage times from a separate pass with the library's stage
+            # events on (they separate the kernels of the launch chain and are
+            # read back every step, so they stay out of the timed steps)
+            self.ctx.debug(timing=True)
+            for k in range(steps):
+                self.flush.zero_()
+                self.step(prec)
+                st[0] += self.ctx.stage_times(adjoint=False)
+                st[1] += self.ctx.stage_times(adjoint=True)
+            self.ctx.debug(timing=False)
+            bc._check(bc._load().bc_sync(self.ctx.handle, None))
+        return float(total.item()) / steps, st / max(1, steps)
+
+
+def rooflines(stage_ms, wk, peaks, traffic):
+    """Per-stage achieved rate against the measured peak of its bound."""
+    out = {}
+    for i, name in enumerate(STAGES):
+        ms = float(stage_ms[:, i].mean())
+        amount, kind = wk[name]
+        if ms <= 0 or amount == 0:
+            continue
+        if kind == "bytes":
+            ach, pk, bound, unit = amount / (ms * 1e-3) / 1e9, peaks["hbm"], "hbm", "GB/s"
+        elif kind == "tensor":
+            ach, pk, bound, unit = amount / (ms * 1e-3) / 1e12, peaks["bf16"], "tensor", "TFLOP/s"
+        else:
+            ach, pk, bound, unit = amount / (ms * 1e-3) / 1e12, peaks["fp64"], "alu", "TFLOP/s"
+        out[name] = {"ms": round(ms, 4), "kernel": STAGE_KERNELS[name], "bound": bound, "achieved": round(ach, 4),
+                     "unit": unit, "peak": round(pk, 3), "frac": round(ach / pk, 4), "traffic": traffic.get(name)}
+    return out
+
+
+PEAK_SOURCE = {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
+               "alu": "FP64 FMA throughput measured in this run (bc_debug_fp64_peak, 8 blocks/SM of independent "
+                      "FMA chains), of measured; nominal 1.25 TFLOP/s",
+               "hbm": "MEASURED_PEAKS.json hbm_gbs, of measured"}
+
+
+def dominant(per_stage):
+    d = max(per_stage, key=lambda k: per_stage[k]["ms"])
+    r = dict(per_stage[d])
+    r["stage"] = d
+    r["peak_source"] = PEAK_SOURCE[r["bound"]]
+    return r
 
 
 def main():
@@ -316,85 +471,39 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     dev = torch.cuda.current_device()
-    head = bc.FP64 if args.precision == "fp64" else bc.SPLIT_BF16
+    head = PRECISIONS[args.precision]
 
     g = density(args.workload)
     workload_name = WORKLOADS[args.workload][1]
-    ctx = bc.Context(p=16, nterms=args.nterms, device=dev)
+    ctx = bc.Context(p=P, nterms=args.nterms, device=dev)
     ctx.set_option("split_overlap", 1 if args.overlap else 0)
     P1 = ctx.nterms or 30
     t0 = time.perf_counter()
     tree = bc.Tree.refine(ctx, g, eps=1e-11, max_level=18)
     t_tree = time.perf_counter() - t0
     st = tree.stats()
-    N = tree.nleaf * 256
-    fvals = g(tree.nodes()).reshape(-1, 16, 16)
+    N = tree.nleaf * P * P
+    lv, ix, iy = (np.asarray(a) for a in tree.leaves())
+    fvals = g(tree.nodes()).reshape(-1, P, P)
     f = torch.from_numpy(fvals).to(dev)
     gen = torch.Generator(device=dev).manual_seed(1)
     gin = torch.randn(f.shape, generator=gen, device=dev, dtype=torch.float64)
-    u = torch.empty_like(f)
-    h = torch.empty_like(f)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2 (129 MB)
-    stream = torch.cuda.current_stream()
+    run = Runner(bc, torch, ctx, tree, f, gin, dev, world, dist if world > 1 else None)
 
-    def timed(precision, steps, sampler=None):
-        def step():
-            bc.apply(tree, f, out=u, precision=precision, stream=stream)
-            bc.apply_adjoint(tree, gin, out=h, precision=precision, stream=stream)
-        for _ in range(max(3, args.warmup)):
-            step()
-        torch.cuda.synchronize()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
-        # the timed steps run as in production: no stage events, no host reads
-        for k in range(steps):
-            flush.zero_()
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-        torch.cuda.synchronize()
-        if sampler:
-            sampler.stop()
-        if world > 1:
-            dist.barrier()
-        bc._check(bc._load().bc_sync(ctx.handle, None))
-        total = torch.tensor([float(sum(a.elapsed_time(b) for a, b in ev))], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(total, op=dist.ReduceOp.MAX)
-        # the per-stage breakdown comes from a separate pass with the library's
-        # stage events on (they separate the kernels of the launch chain and
-        # are read back every step, so they are kept out of the timed steps)
-        stages = np.zeros((2, len(STAGES)))
-        ctx.debug(timing=True)
-        for k in range(steps):
-            flush.zero_()
-            step()
-            stages[0] += ctx.stage_times(adjoint=False)
-            stages[1] += ctx.stage_times(adjoint=True)
-        ctx.debug(timing=False)
-        bc._check(bc._load().bc_sync(ctx.handle, None))
-        return float(total.item()) / steps, stages / steps
-
-    clocks = ClockSampler(dev)
     if args.profile_run:
-        ms_step, _ = timed(head, args.steps)
+        ms_step, _ = run.timed(head, args.steps, args.warmup, stages=False)
         if rank == 0:
             print(json.dumps({"profile_run": True, "workload": workload_name, "nleaf": int(tree.nleaf),
                               "ms_per_step": ms_step}))
         if world > 1:
             dist.destroy_process_group()
         return
-    ms_step, stage_ms = timed(head, args.steps, clocks)
-    value = world * N / (ms_step * 1e-3)
-    other = bc.FP64 if head == bc.SPLIT_BF16 else bc.SPLIT_BF16
-    ms_other, stage_other = timed(other, max(3, args.steps // 2))
 
-    # end to end through the public API with pinned host buffers (headline precision)
+    clocks = ClockSampler(dev)
+    ms_step, stage_ms = run.timed(head, args.steps, args.warmup, sampler=clocks)
+    value = world * N / (ms_step * 1e-3)
+
+    # end to end through the public API with pinned host buffers
     fh = f.cpu().pin_memory()
     gh = gin.cpu().pin_memory()
     uh = torch.empty_like(fh).pin_memory()
@@ -411,102 +520,96 @@ def main():
     e2e = {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 2 * N * 8,
            "d2h_bytes_per_step": 2 * N * 8}
 
-    # rooflines per stage (per apply, averaged over forward and adjoint)
-    peaks = {}
+    # rooflines (per apply, averaged over forward and adjoint)
+    peaks_file = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh_:
-            peaks = json.load(fh_)
+            peaks_file = json.load(fh_)
     except OSError:
         pass
-    fp64_peak = bc.fp64_peak_tflops(dev)
-    bf16_peak = peaks.get("bf16_tflops", 1900.0)
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    lv = tree.leaves()[0]
-    wk = stage_work(st, tree.nleaf, int((lv >= 2).sum()), P1, 256, head == bc.SPLIT_BF16)
-    if not args.overlap:
-        # one group-V tensor launch (near field included) in stage 0
-        wk["tensor_v"] = (wk["tensor_v"][0] + wk["tensor_near"][0], "tensor")
-        wk["tensor_near"] = (0.0, "tensor")
-    elif head == bc.SPLIT_BF16:
-        # the X-list tiles run on the internal stream, before the near field
-        xw = 15 * 2.0 * 256 * 2 * P1 * st["n_x"]
-        wk["tensor_v"] = (wk["tensor_v"][0] - xw, "tensor")
-        wk["tensor_near"] = (wk["tensor_near"][0] + xw, "tensor")
-    # DRAM bytes per launch (read + write) from the ncu capture of this
-    # configuration (profiles/kernels_adaptive20_split.md); null elsewhere
-    traffic = TRAFFIC.get((args.workload, P1, head == bc.SPLIT_BF16), {})
-    per_stage = {}
-    for i, name in enumerate(STAGES):
-        ms = float(stage_ms[:, i].mean())
-        amount, kind = wk[name]
-        if ms <= 0 or amount == 0:
-            continue
-        if kind == "bytes":
-            ach, pk, bound, unit = amount / (ms * 1e-3) / 1e9, hbm_peak, "hbm", "GB/s"
-        else:
-            ach = amount / (ms * 1e-3) / 1e12
-            pk, bound, unit = (bf16_peak, "tensor", "TFLOP/s") if kind == "tensor" else (fp64_peak, "alu", "TFLOP/s")
-        per_stage[name] = {"ms": round(ms, 4), "kernel": STAGE_KERNELS[name], "bound": bound,
-                           "achieved": round(ach, 4), "unit": unit, "peak": round(pk, 2), "frac": round(ach / pk, 4),
-                           "traffic": traffic.get(name)}
-    # the dominant kernel: the one with the most GPU time per apply; the two
-    # launches of the group-V kernel (far tiles in stage 0, near tiles beside
-    # stages 1-4) count together
-    cand = dict(per_stage)
-    if "tensor_v" in cand and "tensor_near" in cand:
-        a, b = cand.pop("tensor_v"), cand.pop("tensor_near")
-        ms_vn = a["ms"] + b["ms"]
-        ach = (wk["tensor_v"][0] + wk["tensor_near"][0]) / (ms_vn * 1e-3) / 1e12
-        tr = a["traffic"] + b["traffic"] if a["traffic"] is not None and b["traffic"] is not None else None
-        cand["tensor_v+tensor_near"] = {
-            "ms": round(ms_vn, 4), "kernel": "k_split_gemm<256> (group V: far and near launches together)",
-            "bound": "tensor", "achieved": round(ach, 4), "unit": "TFLOP/s", "peak": round(bf16_peak, 2),
-            "frac": round(ach / bf16_peak, 4), "traffic": tr}
-    dom = max(cand, key=lambda k: cand[k]["ms"])
-    d = cand[dom]
-    src = {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
-           "alu": "bc_debug_fp64_peak: measured FP64 FMA throughput, of measured",
-           "hbm": "MEASURED_PEAKS.json hbm_gbs, of measured"}
-    roofline = {"bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": d["traffic"], "kernel": d["kernel"], "stage": dom,
-                "peak_source": src[d["bound"]],
-                "stages": per_stage}
+    peaks = {"fp64": bc.fp64_peak_tflops(dev), "bf16": peaks_file.get("bf16_tflops", 1900.0),
+             "hbm": peaks_file.get("hbm_gbs", 6800.0)}
+    nleaf_far = int((lv >= 2).sum())
 
-    nl = st["nlevels"]
-    # kernels per apply (trees of more than three levels): flag clear, upward
-    # pass, M2L, downward level pass, leaf output; FP64: M2L pairs + X-list products;
-    # split: input digits, group-V tensor launch (two when the near field runs apart), M2L
-    # digits + tensor launch, expansion digits + group-E tensor launch
-    if head == bc.SPLIT_BF16:
-        launches_per_apply = 2 + (2 if args.overlap else 0) + 1 + 1 + 2 + 1 + 2 + 1
-    else:
-        launches_per_apply = 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1
-    pname = {bc.FP64: "fp64", bc.SPLIT_BF16: "split-bf16"}
+    def arrangement_work(prec):
+        wk = stage_work(st, tree.nleaf, nleaf_far, P1, P * P, prec)
+        if prec and not args.overlap:
+            wk["tensor_v"] = (wk["tensor_v"][0] + wk["tensor_near"][0], "tensor")   # one group-V launch
+            wk["tensor_near"] = (0.0, "tensor")
+        elif prec:
+            xw = 15 * 2.0 * P * P * 2 * P1 * st["n_x"]   # X-list tiles run on the internal stream
+            wk["tensor_v"] = (wk["tensor_v"][0] - xw, "tensor")
+            wk["tensor_near"] = (wk["tensor_near"][0] + xw, "tensor")
+        return wk
+
+    per_stage = rooflines(stage_ms, arrangement_work(head), peaks,
+                          TRAFFIC.get((args.workload, P1, args.precision), {}))
+    roofline = dominant(per_stage)
+    roofline["stages"] = per_stage
+
+    pname = {v: k for k, v in PRECISIONS.items()}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if head == bc.FP64 else "bf16 digits (5 slices) + f64",
-            "data": "synthetic",
-            "config": {"workload": workload_name, "precision": pname[head], "nleaf": int(tree.nleaf), "leaf_nodes": int(N),
-                       "nlevels": nl, "nterms": P1, "tree_build_s": round(t_tree, 3),
+            "vs_baseline": None, "dtype": DTYPES[head], "data": "synthetic",
+            "config": {"workload": workload_name, "precision": pname[head], "nleaf": int(tree.nleaf),
+                       "leaf_nodes": int(N), "nlevels": st["nlevels"], "nterms": P1, "n_v": st["n_v"],
+                       "n_near": st["n_near"], "tree_build_s": round(t_tree, 3),
                        "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
-            "clocks": clocks.summary(), "e2e": e2e, "gpu_launches": 2 * launches_per_apply * args.steps,
-            "roofline": roofline,
-            "other_precision": {"precision": pname[other], "value": world * N / (ms_other * 1e-3),
-                                "ms_per_step": ms_other,
-                                "stage_ms": {n: round(float(stage_other[:, i].mean()), 4)
-                                             for i, n in enumerate(STAGES)}}}
+            "clocks": clocks.summary(), "e2e": e2e,
+            "gpu_launches": 2 * launches_per_apply(head, args.overlap, st) * args.steps,
+            "roofline": roofline}
 
-    if rank == 0 and not args.no_cpu_baseline:
-        bc.apply(tree, f, out=u, precision=head)
-        torch.cuda.synchronize()
-        rate, nn, tt, vals = oracle_rate(tree.leaves(), fvals, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                "sample": f"{nn} target nodes ({nn // 256} random leaves) of the same tree in "
-                                          f"{tt:.1f}s; forward rate halved for fwd+adjoint"}
-        uu = u.cpu().numpy().reshape(-1, 256)
-        got = np.stack([uu[b] for b in vals])
-        ref = np.stack([vals[b] for b in vals])
-        line["rel_err_vs_oracle_sample"] = float(np.abs(got - ref).max() / np.abs(ref).max())
+    if not args.no_extras:
+        # the other precisions on the same tree, with their own rooflines
+        for other in (p for p in (0, 1, 2) if p != head):
+            ms_o, stage_o = run.timed(other, max(3, args.steps // 2), args.warmup)
+            ps = rooflines(stage_o, arrangement_work(other), peaks,
+                           TRAFFIC.get((args.workload, P1, pname[other]), {}))
+            line[pname[other]] = {"value": world * N / (ms_o * 1e-3), "ms_per_step": ms_o, "dtype": DTYPES[other],
+                                  "roofline": dominant(ps),
+                                  "stage_ms": {k: v["ms"] for k, v in ps.items()}}
+        # the 20-Gaussian workload in the headline precision
+        if args.workload != "adaptive20":
+            g2 = density("adaptive20")
+            tree2 = bc.Tree.refine(ctx, g2, eps=1e-11, max_level=18)
+            f2 = torch.from_numpy(g2(tree2.nodes()).reshape(-1, P, P)).to(dev)
+            gin2 = torch.randn(f2.shape, generator=gen, device=dev, dtype=torch.float64)
+            run2 = Runner(bc, torch, ctx, tree2, f2, gin2, dev, world, dist if world > 1 else None)
+            ms2, _ = run2.timed(head, args.steps, args.warmup, stages=False)
+            line["adaptive20"] = {"workload": WORKLOADS["adaptive20"][1], "nleaf": int(tree2.nleaf),
+                                  "value": world * tree2.nleaf * P * P / (ms2 * 1e-3), "ms_per_step": ms2}
+
+    if rank == 0 and not args.no_extras:
+        # error against the oracle per level, forward (every node of 2 leaves
+        # per level) and adjoint (columns near and far on every level); the
+        # forward sample's oracle time is the CPU baseline
+        import oracle
+        from paper_2501_17967_gb300 import synth
+        leaves = (lv, ix, iy)
+        u = bc.apply(tree, f, precision=head).cpu().numpy().reshape(-1, P * P)
+        pick, ref, t_or = oracle_forward_sample(leaves, fvals.reshape(-1, P * P), per_level=2)
+        scale = np.abs(ref).max()
+        fwd_err = np.abs(u[pick] - ref).max(axis=1)
+        S, cols, gs = adjoint_sample(leaves)
+        hs = bc.apply_adjoint(tree, torch.from_numpy(gs).to(dev), precision=head).cpu().numpy()
+        hs = hs.reshape(-1, P * P)
+        geom = synth.leaf_geometry(lv, ix, iy)
+        href = oracle.adjoint_columns(P, geom, gs, cols, target_leaves=S)
+        hgot = np.array([hs[b, j] for b, j in cols])
+        hscale = np.abs(href).max()
+        line["per_level_error"] = {
+            "forward": per_level(lv[pick], fwd_err, scale),
+            "adjoint": per_level([lv[b] for b, _ in cols], np.abs(hgot - href), hscale),
+            "forward_max": float(fwd_err.max() / scale),
+            "adjoint_max": float(np.abs(hgot - href).max() / hscale),
+            "sample": f"forward: every node of {len(pick)} leaves (2 per level); adjoint: {len(cols)} columns "
+                      f"(3 nodes of 2 leaves per level), g random on {len(S)} leaves and zero elsewhere; "
+                      f"metric max|x - x*| / max|x*| over the sample"}
+        nodes = len(pick) * P * P
+        line["cpu_baseline"] = {"value": nodes / t_or / 2.0, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{nodes} target nodes ({len(pick)} leaves, 2 per level) of the same tree "
+                                          f"in {t_or:.1f}s; forward rate halved for fwd+adjoint"}
+        bc._check(bc._load().bc_sync(ctx.handle, None))
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -111,12 +111,19 @@ void bc_destroy(bc_ctx *ctx);
 const char *bc_last_error(void);
 
 /* Precompute and upload every table (near-field tables for the 33 relative
- * positions a 2:1-balanced tree allows, far-field translation operators).
- * Host FP64 quadrature; cached in `cache_dir` (NULL: no cache) in a file
- * keyed by (p, nterms, node kind, format version) with a checksum. */
+ * positions a 2:1-balanced tree allows, far-field translation operators, the
+ * BF16 digits of the split-precision operators).  Not in the paper: these are
+ * the internals of the box code it calls as a black box (Sec. 3.2.1, last
+ * paragraph); every table is a quadrature of the kernel of eq. (vbulk) or a
+ * translation of its multipole / local expansions.  Host FP64 quadrature;
+ * cached in `cache_dir` (NULL: no cache) in a file keyed by (p, nterms, node
+ * kind, format version) with a checksum.  The factored forms of the level
+ * shifts are checked against the dense operators here (BC_ERR_STATE if they
+ * differ). */
 bc_status bc_tables_build(bc_ctx *ctx, const char *cache_dir);
 
-/* Tree from explicit leaves of the root box [x0, x0+L] x [y0, y0+L]: leaf k is
+/* Tree from explicit leaves of the root box [x0, x0+L] x [y0, y0+L] (the
+ * quadtree of Sec. 3.2.1, 2:1 balanced as in its last paragraph): leaf k is
  * the dyadic box (level[k], ix[k], iy[k]) with 0 <= ix,iy < 2^level, level <= 24.
  * Validates that the leaves are disjoint, cover the root and are 2:1 balanced
  * (BC_ERR_TREE otherwise); builds the interaction lists on the host and
@@ -155,23 +162,26 @@ bc_status bc_tree_boxes(const bc_tree *tree, int32_t *level, int32_t *ix, int32_
                         int32_t *parent, int32_t *leaf);
 void bc_tree_destroy(bc_tree *tree);
 
-/* u = A f: the volume potential at every leaf node (definition above).
- * f, u: [nleaf][p][p] FP64.  Device pointers are used in place.  Host
- * pointers are staged through the tree's device buffers, except pinned
- * (page-locked) ones on the split path with the near field, leaf-to-expansion
- * and X list on the tensor cores, which the kernels read and write in place;
- * either way the call returns after u is written.  u must not alias f. */
+/* u = A f: the volume potential v_bulk at every leaf node (eq. (vbulk) of
+ * Sec. 3.2, definition above), in the arithmetic `prec` names (bc_precision).
+ * f, u: [nleaf][p][p] FP64.  Device pointers are used in place and the call
+ * is asynchronous on `stream`.  Host pointers are staged through the tree's
+ * device buffers, except pinned (page-locked) ones on the split paths, which
+ * the kernels read and write in place; with host pointers the call returns
+ * after u is written.  u must not alias f. */
 bc_status bc_apply(bc_ctx *ctx, const bc_tree *tree, const double *f, double *u,
                    bc_precision prec, void *stream);
 
 /* h = A^T g: the exact transpose of the discrete operator applied by
- * bc_apply (same passes reversed, every operator transposed).  Same layout,
- * pointer and stream rules as bc_apply. */
+ * bc_apply (same passes, every operator transposed; the gradient of a loss of
+ * u with respect to f).  Not in the paper, whose solver needs the forward
+ * operator only.  Same layout, pointer and stream rules as bc_apply. */
 bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, double *h,
                            bc_precision prec, void *stream);
 
-/* out[k] = interpolant of the leaf-node values u at point xy[k] (barycentric
- * Chebyshev interpolation on the leaf containing the point; a point on a
+/* out[k] = interpolant of the leaf-node values u at point xy[k]: v_bulk off
+ * the grid, as the glue step needs it on the fictitious curve (Sec. 3.4)
+ * (barycentric Chebyshev interpolation on the leaf containing the point; a point on a
  * shared edge belongs to the leaf on its +x / +y side, the root's far edges to
  * the last leaf).  Points outside the root give BC_ERR_ARG on the host path;
  * on the device path they produce NaN.  u, xy, out: device or host (all of the
@@ -180,7 +190,8 @@ bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, cons
                          int64_t n, double *out, void *stream);
 
 /* Batched applies: many independent densities on different trees (all of
- * this context's p and root side L) in one launch per pass.  A batch is the
+ * this context's p and root side L) in one launch per pass.  Not in the
+ * paper (its solver applies one box code at a time).  A batch is the
  * disjoint union of its trees (leaves and boxes renumbered, lists
  * concatenated), uploaded once; every pass of an apply then covers all trees
  * in a single kernel launch, and the whole pass sequence is captured once per
@@ -216,33 +227,42 @@ bc_status bc_batch_shape(const bc_batch *batch, int precision, int adjoint, int 
  * out = NULL to get *count (doubles). */
 bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *out);
 
-/* Runtime options of a context.
+/* Runtime options of a context (none in the paper).
  *   "m2l_triangular" (0/1, default 0): keep only the terms with k + l <= P of
  *     each multipole-to-local translation (and exactly their transpose in the
  *     adjoint), which halves the M2L arithmetic but loses accuracy.
+ *   "m2l_kernel" (0/1, default 0): the FP64 multipole-to-local kernel: 0 FP64
+ *     FMAs, one block per target box; 1 the FP64 tensor cores (mma.sync f64
+ *     tiles of the binomial matrix), one warp per target box.  Same results
+ *     to rounding.
+ *   "m2l_blocks_per_sm" (integer 0..32, default 0): resident blocks per SM of
+ *     the FP64 M2L launch; 0 chooses by arrangement (3, or 2 for kernel 1,
+ *     beside the near-field tensor launch, which fits beside them; 8 (4)
+ *     otherwise).
  *   "wait_limit" (default 2^26): polls of each bounded device-side wait of the
  *     split-precision kernel before it gives up, records the failure (reported
  *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns; the
  *     level passes' box flags poll a sixteenth of it and report the same way.
- *   "split_overlap" (0/1, default 1): the near-field tensor-core launch of a
- *     split-precision apply runs on an internal stream, concurrently with the
- *     far-field passes, and is joined before the leaf output (1), or in line
- *     on the apply's stream (0).  The level passes are latency-bound chains
- *     that leave most SMs idle, so the near field mostly hides behind them.
+ *   "split_overlap" (0/1, default 1): the X-list and near-field tensor-core
+ *     launches of a split-precision apply run on an internal stream and are
+ *     joined before the downward pass (X list) and the leaf output (near
+ *     field) (1), or in line on the apply's stream (0).  With the M2L in FP64
+ *     (BC_SPLIT_BF16) they start after the upward pass and run beside the
+ *     FP64 M2L (they use the tensor cores, it the FP64 units); with the
+ *     tensor-core M2L (BC_SPLIT_BF16_ALL) they start at once, beside the
+ *     latency-bound level passes.
  *   "split_overlap_ctas" (integer >= 0, default 0): CTAs (one per SM) of
- *     that near-field launch; 0 takes three quarters of the SMs, which leaves
- *     the rest to the level passes undisturbed (on the 20-Gaussian workload
- *     76 to 152 CTAs are within 1%, 40 to 56 about 5% slower).
- *   "debug_split_parts" (integer 0..127, default 127): diagnostics; which
+ *     that near-field launch; 0 takes every SM beside the FP64 M2L and three
+ *     quarters of them beside the level passes.
+ *   "debug_split_parts" (integer -1..127, default -1): diagnostics; which
  *     products of a split-precision apply use the tensor-core results (bits:
  *     1 near field, 2 leaf-to-expansion, 4 X list, 8 expansion-to-leaf,
  *     16 W list, 32 M2L translations); the others are evaluated in FP64.
  *     Bit 64: the shifts of the upward and downward level passes, and with
  *     bit 2 off the leaf-to-expansion step, in double-float arithmetic (pairs
- *     of FP32 numbers, about 48 bits) instead of FP64 (inside the upward
- *     pass, which is then slower on the 20-Gaussian workload than the tensor
- *     launch of bit 2).
- *   "debug_withhold_copy" (0/1, default 0): diagnostics; the split-precision
+ *     of FP32 numbers, about 48 bits) instead of FP64.  -1 takes the set of
+ *     the precision mode: 31 for BC_SPLIT_BF16, 127 for BC_SPLIT_BF16_ALL.
+   "debug_withhold_copy" (0/1, default 0): diagnostics; the split-precision
  *     kernel never starts its table copy, so its first wait runs out (tests of
  *     the timeout path).
  * Unknown names give BC_ERR_ARG. */
@@ -253,19 +273,20 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value);
  * (expansions); 3 = the full operator (default).  timing != 0 records a CUDA
  * event at each stage boundary:
  *   0 tensor group V, far part (split precision: digits of the input,
- *     leaf-to-expansion, X list), 1 flag clearing, 2 upward pass (FP64: with
- *     the leaf-to-expansion step), 3 M2L per V pair (FP64 path: and the X-list
- *     products), 4 downward level pass (sums, shifts), 5 tensor group E
- *     (split precision: digits of the expansions, expansion-to-leaf and W
- *     list), 6 leaf output; 7 the near-field tensor launch when it runs
- *     apart, on an internal stream beside stages 1-4 (split_overlap; in line
- *     the near field is part of stage 0's tensor launch and stage 7 is empty);
+ *     leaf-to-expansion; in line also the X list and the near field),
+ *     1 flag clearing, 2 upward pass (FP64: with the leaf-to-expansion step),
+ *     3 M2L (FP64 path: and the X-list products), 4 downward level pass (sums,
+ *     shifts), 5 tensor group E (split precision: digits of the expansions,
+ *     expansion-to-leaf and W list), 6 leaf output; 7 the X-list and
+ *     near-field tensor launches when they run apart on the internal stream
+ *     (split_overlap: beside stage 3 with the FP64 M2L, beside stages 1-4
+ *     otherwise; in line stage 7 is empty);
  * bc_debug_stage_times then waits for the last events of the most recent
  * forward (adjoint = 0) or adjoint apply and writes the eight stage durations
  * in milliseconds to ms[8] (stages 0, 5 and 7 are empty for FP64 applies). */
 bc_status bc_debug_set(bc_ctx *ctx, int pass_mask, int timing);
 bc_status bc_debug_stage_times(bc_ctx *ctx, int adjoint, double *ms);
-/* The term schedule of the double-float upward shift of the split path, for
+/* The term schedule of the double-float upward shift of BC_SPLIT_BF16_ALL, for
  * the forward (adjoint = 0: M2M) or adjoint (L2L^H) operator of a context
  * whose tables are built (host-only contexts too).  The nonzero terms
  * (output l, input k) of the four child operators, output by output, are cut
@@ -282,7 +303,7 @@ bc_status bc_debug_up_schedule(const bc_ctx *ctx, int adjoint, int32_t *T, int32
                                float *ops, int32_t *np);
 /* Measured FP64 FMA throughput of `device` in TFLOP/s (independent FMA chains,
  * 8 blocks per SM, best of three timed runs).  The roofline denominator of
- * the FP64 passes. */
+ * the FP64 passes (diagnostics; not in the paper). */
 bc_status bc_debug_fp64_peak(int device, double *tflops);
 
 /* FP64 apply (adjoint = 0: u = A f; adjoint != 0: the transpose) that

@@ -482,6 +482,7 @@ PassArgs pass_args(const bc_ctx *ctx, const bc_tree *t)
     a.shift_blocks = ctx->shift_blocks;
     a.down_blocks = ctx->down_blocks;
     a.m2l_bps = ctx->m2l_bps;
+    a.m2l_kind = ctx->m2l_kind;
     a.wait_limit = ctx->split.wait_limit;
     a.err = ctx->dev_err;
     return a;
@@ -1565,6 +1566,14 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
             return BC_ERR_ARG;
         }
         ctx->overlap_ctas = int(value);
+        return BC_OK;
+    }
+    if (std::strcmp(name, "m2l_kernel") == 0) {
+        if (value != 0.0 && value != 1.0) {
+            set_error("bc_set_option: m2l_kernel must be 0 (FP64 FMA) or 1 (FP64 tensor cores)");
+            return BC_ERR_ARG;
+        }
+        ctx->m2l_kind = int(value);
         return BC_OK;
     }
     if (std::strcmp(name, "m2l_blocks_per_sm") == 0) {

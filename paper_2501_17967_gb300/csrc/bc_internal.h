@@ -298,6 +298,7 @@ struct PassArgs {
     double half_L;        // r at level 0
     int64_t nleaf, nbox;
     int leaf_bps = 0, m2l_bps = 0;
+    int m2l_kind = 0;     // FP64 M2L: 0 by FMAs (k_m2l_boxes), 1 on the FP64 tensor cores (k_m2l_mma)
     // persistent level-synchronous passes: resident blocks of the upward and
     // shift kernels (all blocks must be resident), bounded barrier waits
     int up_blocks = 0, shift_blocks = 0, down_blocks = 0;   // down_blocks: the one-warp-per-box FP64 pass
@@ -366,6 +367,7 @@ struct bc_ctx {
     int split_overlap = 1;      // near-field tensor launch on the side stream (1) or inline (0)
     int overlap_ctas = 0;       // CTAs of that launch (0: by arrangement, see near_ctas_for)
     int m2l_bps = 0;            // resident blocks per SM of the FP64 M2L kernel (0: by arrangement)
+    int m2l_kind = 0;           // FP64 M2L kernel: 0 FMA, 1 tensor-core MMA (see PassArgs)
     bool timing = false;        // record CUDA events around each stage
     cudaEvent_t ev[2][bc::kNumEvents] = {};   // [forward, adjoint]
     bc::SideStream side;

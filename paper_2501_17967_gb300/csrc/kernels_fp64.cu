@@ -514,6 +514,126 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
     griddep_launch_dependents();
 }
 
+// -------------------------------------------------------------------------
+// m2l_mma: the same V-list sums as k_m2l_boxes, with the binomial contraction
+// on the FP64 tensor cores (mma.sync m8n8k4, f64): one warp per target box.
+// For the pairs e of V(b) taken four at a time, the real matrix product
+//     T[o][n] = sum_k B[o][k] X[k][n],   B[o][k] = the binomial entry of (k, o)
+// has eight columns n: the real and imaginary parts of a(e) = S_c(e) . A_s(e)
+// for the four pairs (column n: pair n / 2, part n % 2); B (P1 x P1, padded to
+// 8 MT rows and 4 KS columns with zeros) sits in registers as the MMA's A
+// fragments for the whole launch.  Lane layout of the m8n8k4 f64 fragments
+// (g = lane / 4, t = lane % 4): A[g][t], B[t][g], D[g][2t], D[g][2t+1]; so a
+// lane forms X at rows 4s + t of column g and receives T at row 8m + g for
+// pair t, real (D[..][2t]) and imaginary (D[..][2t+1]) parts together, which
+// it scales by W_c(e)[o] and adds to its running sums.  The four pairs' sums
+// meet by two shuffles at the end of the box.  One MMA does 256 FMAs, so the
+// FP64 pipe stays busy with one warp per SM sub-partition and no shared
+// memory.  Pairs past the end of the list are zero columns.
+// -------------------------------------------------------------------------
+__device__ __forceinline__ void dmma_m8n8k4(double &d0, double &d1, double a, double b)
+{
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+template <bool ADJ, int MT, int KS>
+__global__ void __launch_bounds__(128)
+k_m2l_mma(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int32_t *__restrict__ v_src,
+          const int32_t *__restrict__ v_code, const int32_t *__restrict__ box_level,
+          const double2 *__restrict__ dsig, const double2 *__restrict__ dpow, const double *__restrict__ logd,
+          const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ out, int P1,
+          int tri)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    double bf[MT][KS];   // B[8m + g][4s + t]
+#pragma unroll
+    for (int m = 0; m < MT; m++)
+#pragma unroll
+        for (int s = 0; s < KS; s++) {
+            const int o = 8 * m + g, k = 4 * s + t;
+            // tri = 1 keeps only the terms with k + o <= P (and exactly their transpose)
+            const bool keep = !tri || (ADJ ? (o == 0 || k + o < P1) : (k == 0 || k + o < P1));
+            bf[m][s] = (o < P1 && k < P1 && keep) ? (ADJ ? c_binom[o][k] : c_binom[k][o]) : 0.0;
+        }
+    // The dependents (the persistent downward pass) are released only at the
+    // end, as in k_m2l_boxes.
+    griddep_wait();
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t b = b0 + ((int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5); b < b1; b += nwarps) {
+        const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
+        const double lgb = lvtab[kLvTab + box_level[b]];
+        double ar[MT], ai[MT];   // sums for rows 8m + g, pairs of slot t
+#pragma unroll
+        for (int m = 0; m < MT; m++) ar[m] = ai[m] = 0.0;
+        for (int e0 = v0; e0 < v1; e0 += 4) {
+            // this lane's column of X: pair slot g / 2, part g % 2, rows 4s + t
+            const int ex = e0 + (g >> 1);
+            double xv[KS];
+            if (ex < v1) {
+                const int s_src = v_src[ex], c = v_code[ex];
+#pragma unroll
+                for (int s = 0; s < KS; s++) {
+                    const int k = 4 * s + t;
+                    xv[s] = 0.0;
+                    if (k < P1) {
+                        const double2 A = in[int64_t(s_src) * P1 + k], S = dsig[c * P1 + k];
+                        xv[s] = (g & 1) ? fma(A.x, S.y, A.y * S.x) : fma(A.x, S.x, -A.y * S.y);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < KS; s++) xv[s] = 0.0;
+            }
+            double dr[MT], di[MT];
+#pragma unroll
+            for (int m = 0; m < MT; m++) dr[m] = di[m] = 0.0;
+#pragma unroll
+            for (int s = 0; s < KS; s++)
+#pragma unroll
+                for (int m = 0; m < MT; m++) dmma_m8n8k4(dr[m], di[m], bf[m][s], xv[s]);
+            // T for pair slot t at rows 8m + g: scale by W_c[o] and add
+            const int eo = e0 + t;
+            if (eo < v1) {
+                const int c = v_code[eo];
+#pragma unroll
+                for (int m = 0; m < MT; m++) {
+                    const int o = 8 * m + g;
+                    if (o < P1) {
+                        double tr = dr[m], ti = di[m];
+                        if (o == 0) {   // the log term of the box's local expansion
+                            const double2 A0 = in[int64_t(v_src[eo]) * P1];
+                            const double c0 = logd[c] + lgb;
+                            tr = fma(c0, A0.x, tr);
+                            ti = fma(c0, A0.y, ti);
+                        }
+                        const double2 W = dpow[c * P1 + o];
+                        ar[m] = fma(tr, W.x, fma(-ti, W.y, ar[m]));
+                        ai[m] = fma(tr, W.y, fma(ti, W.x, ai[m]));
+                    }
+                }
+            }
+        }
+        // the four pair slots (lanes 4g .. 4g + 3) meet
+#pragma unroll
+        for (int m = 0; m < MT; m++) {
+            ar[m] += __shfl_xor_sync(0xffffffffu, ar[m], 1);
+            ai[m] += __shfl_xor_sync(0xffffffffu, ai[m], 1);
+            ar[m] += __shfl_xor_sync(0xffffffffu, ar[m], 2);
+            ai[m] += __shfl_xor_sync(0xffffffffu, ai[m], 2);
+        }
+        if (t == 0) {
+#pragma unroll
+            for (int m = 0; m < MT; m++) {
+                const int o = 8 * m + g;
+                if (o < P1) out[b * P1 + o] = make_double2(ar[m], ai[m]);
+            }
+        }
+    }
+    griddep_launch_dependents();
+}
+
 // Groups per block of the M2L kernel: the smallest NG >= 4 with NG * P1 a
 // multiple of 32 (no idle lane) and at most 256 threads, else 4.
 inline int m2l_groups(int P1)
@@ -1300,6 +1420,30 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             g.ops = sT->ops[1][dir]; g.op_exp = sT->op_exp[1][dir];
             g.dig = sp->edig; g.dexp = sp->eexp;
             ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            if (ce != cudaSuccess) return ce;
+        } else if (a.m2l_kind == 1) {
+            // FP64 tensor cores, one warp per target box; beside the
+            // near-field tensor CTAs (late fork) two warps per SM
+            // sub-partition fit next to one of them (registers)
+            const int64_t b0 = h.level_start[2], b1 = a.nbox;
+            const int grid = grid_for((b1 - b0 + 3) / 4, 152 * (a.m2l_bps ? a.m2l_bps : (late ? 2 : 4)));
+            const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
+#define BC_M2LT(A, MT, KS)                                                                                      \
+    ce = launch_pdl(k_m2l_mma<A, MT, KS>, grid, 128, 0, st, b0, b1, d.v_ptr, d.v_src, d.v_code, d.box_level, dsig, \
+                    dpw, tb.logd, d.lvtab, first, second, P1, m2l_tri)
+#define BC_M2LD(MT, KS) { if (adj) BC_M2LT(true, MT, KS); else BC_M2LT(false, MT, KS); }
+            switch ((P1 + 3) / 4) {
+            case 1: BC_M2LD(1, 1) break;
+            case 2: BC_M2LD(1, 2) break;
+            case 3: BC_M2LD(2, 3) break;
+            case 4: BC_M2LD(2, 4) break;
+            case 5: BC_M2LD(3, 5) break;
+            case 6: BC_M2LD(3, 6) break;
+            case 7: BC_M2LD(4, 7) break;
+            default: BC_M2LD(4, 8) break;
+            }
+#undef BC_M2LD
+#undef BC_M2LT
             if (ce != cudaSuccess) return ce;
         } else {
             const int64_t b0 = h.level_start[2], b1 = a.nbox;

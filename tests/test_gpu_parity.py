@@ -537,3 +537,34 @@ def test_split_double_float_shifts_other_orders(nterms):
         print(f"nterms {nterms} {tag}: double-float vs FP64 shifts {d_df:.2e}, split vs FP64 {d_all:.2e}")
         assert 0.0 < d_df < 1e-13, (nterms, tag, d_df)
         assert d_all < TOL, (nterms, tag, d_all)
+
+
+@pytest.mark.parametrize("nterms", [8, 13, 24, 31])
+def test_m2l_tensor_core_kernel_matches_fma_kernel(nterms):
+    """The FP64 M2L by FMAs (the default) and on the FP64 tensor cores (MMA
+    tiles of the binomial matrix) give the same local expansions up to rounding,
+    forward and adjoint, at expansion orders that fill the 8 x 4 MMA tiles
+    partially and exactly; both match the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ctx = bc.Context(p=16, nterms=nterms, device=0)
+    g = synth.gaussians(8, 21, wlog10=(-2.3, -1.0))
+    lv, ix, iy = synth.geometric_leaves(g, kappa=1.0, max_level=8)
+    tree, geom, fvals, f = make(ctx, lv, ix, iy, g)
+    gen = torch.Generator(device="cuda").manual_seed(23)
+    gg = torch.randn(f.shape, generator=gen, device="cuda", dtype=torch.float64)
+    out = {}
+    try:
+        for kind in (0, 1):
+            ctx.set_option("m2l_kernel", kind)
+            out[kind] = (bc.apply(tree, f), bc.apply_adjoint(tree, gg))
+    finally:
+        ctx.set_option("m2l_kernel", 0)
+    for k in range(2):
+        d = ((out[0][k] - out[1][k]).abs().max() / out[1][k].abs().max()).item()
+        assert d < 1e-13, (nterms, k, d)
+    if nterms == 24:
+        pick = synth.sample_leaves_per_level(np.asarray(lv), 1, seed=5)
+        ref = oracle.potential_at_nodes(16, geom, fvals, leaf_ids=pick)
+        err = relerr(out[1][0].cpu().numpy().reshape(-1, 256)[pick], ref)
+        assert err < TOL, err
