@@ -806,6 +806,7 @@ bc_status build_split_tree(bc_tree *t)
             cl.push_back(c);
         }
         E.add(T.e_op[dir], cl);
+        s.ntL[dir] = int(E.tiles.size());
         for (auto &v : by_code) v.clear();
         for (int64_t k = 0; k < nw; k++) {
             SplitCol c;

@@ -240,6 +240,7 @@ struct SplitTree {
     SplitCol *cV[2] = {}, *cN[2] = {}, *cVN[2] = {}, *cE[2] = {}, *cM[2] = {};
     int ntV[2] = {}, ntN[2] = {}, ntVN[2] = {}, ntE[2] = {}, ntM[2] = {};
     int ntA[2] = {};   // the first ntA tiles of tV: leaf-to-expansion (the rest: X list)
+    int ntL[2] = {};   // the first ntL tiles of tE: expansion-to-leaf (the rest: W list)
     double *Pnear = nullptr;      // [n_near][256] near-field result per entry (scale included)
     double *PX = nullptr;         // [n_x][64] X-list result per entry
     double *PE = nullptr;         // [nleaf][256] L2P (adjoint P2M^H) result per leaf

@@ -1322,6 +1322,21 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
         if (e != cudaSuccess) return e;
         if ((e = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return e;
+        if (late) {
+            // the W list needs the multipoles only: their digits and the W
+            // tiles here too, beside the FP64 M2L (the downward pass's group E
+            // keeps the expansion-to-leaf tiles)
+            const int64_t f0 = adj ? a.nbox : 0;
+            e = launch_split_digits_exp(f0, f0 + a.nbox, a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0,
+                                        sT->escale[dir], sp->edig, sp->eexp, sd->side);
+            if (e != cudaSuccess) return e;
+            SplitGemm gw;
+            gw.tiles = sp->tE[dir] + sp->ntL[dir]; gw.cols = sp->cE[dir]; gw.ntiles = sp->ntE[dir] - sp->ntL[dir];
+            gw.ops = sT->ops[1][dir]; gw.op_exp = sT->op_exp[1][dir];
+            gw.dig = sp->edig; gw.dexp = sp->eexp;
+            e = launch_split_gemm(gw, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+            if (e != cudaSuccess) return e;
+        }
         g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
         g.max_ctas = split->near_ctas;
         e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
@@ -1501,14 +1516,16 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (ev) cudaEventRecord(ev[5], st);
     if (split && far) {
         // tensor group E: digits of both expansion arrays (times alpha0 in the
-        // adjoint; those of `first` already taken for the M2L), then L2P
-        // (P2M^H) of `second` into PE and the W list of `first` into PW
-        const int64_t s0 = first_digits ? (adj ? 0 : a.nbox) : 0, s1 = first_digits ? s0 + a.nbox : 2 * a.nbox;
+        // adjoint; those of `first` already taken for the M2L or, late fork,
+        // on the internal stream), then L2P (P2M^H) of `second` into PE and
+        // the W list of `first` into PW (late fork: L2P only)
+        const bool first_done = first_digits || late;
+        const int64_t s0 = first_done ? (adj ? 0 : a.nbox) : 0, s1 = first_done ? s0 + a.nbox : 2 * a.nbox;
         ce = launch_split_digits_exp(s0, s1, a.nbox, d.expA, d.expB, P1, adj ? alpha0 : 1.0, sT->escale[dir],
                                      sp->edig, sp->eexp, st);
         if (ce != cudaSuccess) return ce;
         SplitGemm g;
-        g.tiles = sp->tE[dir]; g.cols = sp->cE[dir]; g.ntiles = sp->ntE[dir];
+        g.tiles = sp->tE[dir]; g.cols = sp->cE[dir]; g.ntiles = late ? sp->ntL[dir] : sp->ntE[dir];
         g.ops = sT->ops[1][dir]; g.op_exp = sT->op_exp[1][dir];
         g.dig = sp->edig; g.dexp = sp->eexp;
         ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
