@@ -288,8 +288,10 @@ cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,
                                     int P1, double scale, const double *escale, uint16_t *dig, int32_t *dexp,
                                     cudaStream_t st);
+// intcvt: the epilogue converts its integer sums to FP64 with integer
+// operations only (same bits), for launches that run beside FP64 kernels.
 cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int32_t *err, long long wait_limit,
-                              int withhold, cudaStream_t st);
+                              int withhold, cudaStream_t st, bool intcvt = false);
 
 // Launch parameters common to the passes.  leaf_bps / m2l_bps: resident
 // blocks per SM used to size the grids of the leaf kernels and of the M2L

@@ -1319,7 +1319,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         }
         SplitGemm g = gv;
         g.tiles = sp->tV[dir] + sp->ntA[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
-        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
         if (e != cudaSuccess) return e;
         if ((e = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return e;
         if (late) {
@@ -1334,12 +1334,13 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             gw.tiles = sp->tE[dir] + sp->ntL[dir]; gw.cols = sp->cE[dir]; gw.ntiles = sp->ntE[dir] - sp->ntL[dir];
             gw.ops = sT->ops[1][dir]; gw.op_exp = sT->op_exp[1][dir];
             gw.dig = sp->edig; gw.dexp = sp->eexp;
-            e = launch_split_gemm(gw, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+            e = launch_split_gemm(gw, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side,
+                                  true);
             if (e != cudaSuccess) return e;
         }
         g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
         g.max_ctas = split->near_ctas;
-        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side);
+        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
         if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[9], sd->side);
         return cudaEventRecord(sd->join, sd->side);

@@ -265,6 +265,28 @@ __device__ __forceinline__ double i64_scaled(long long S, int ex)
     return (S == 0 || e <= 0) ? 0.0 : __longlong_as_double(b + ((long long)ex << 52));
 }
 
+// The same value with integer operations only (bit for bit: S rounded to 53
+// bits, nearest with ties to even).  The tensor launches that run beside the
+// FP64 kernels use it, since the hardware conversion occupies the FP64 pipe,
+// a small fraction of the FP32 rate on this GPU.  The magnitude is
+// normalised so that its leading one is bit 63; its top 53 bits, rounded by
+// the 11 below them, are the significand, whose leading one (and a carry from
+// rounding up to 2^53) adds into the exponent field.
+__device__ __forceinline__ double i64_scaled_int(long long S, int ex)
+{
+    if (S == 0) return 0.0;
+    const unsigned long long sgn = static_cast<unsigned long long>(S) & 0x8000000000000000ull;
+    unsigned long long m = S < 0 ? 0ull - static_cast<unsigned long long>(S) : static_cast<unsigned long long>(S);
+    const int lz = __clzll(static_cast<long long>(m));
+    m <<= lz;
+    const unsigned long long rem = m & 0x7FFull, mant = m >> 11;
+    const unsigned long long up = (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) ? 1ull : 0ull;
+    const int e = 63 - lz + ex + 1023;   // biased exponent of the leading one
+    if (e <= 0) return 0.0;
+    return __longlong_as_double(
+        static_cast<long long>((sgn | (static_cast<unsigned long long>(e - 1) << 52)) + mant + up));
+}
+
 // Five balanced base-256 digits (BF16 bit patterns) of round(x * 2^(40 - E)),
 // |x| < 2^(E-1), from the FP64 bit pattern by integer operations; written to
 // out[0], out[stride], ... (most significant first).
@@ -415,7 +437,7 @@ struct GemmBars {
 // leave room, in each SM sub-partition's register file, for the FP64 M2L
 // blocks that run beside a near-field CTA.  Two CTAs never share an SM (shared
 // memory allows one).
-template <int KD>
+template <int KD, bool ICVT>
 __global__ void __launch_bounds__(kGemmThreads, 2)
 k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__restrict__ err, long long wait_limit,
              int withhold)
@@ -707,7 +729,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
 #pragma unroll
                         for (int g = 0; g < kS; g++)
                             S += (long long)__float2int_rn(__uint_as_float(d[g][q])) << (8 * (kS - 1 - g));
-                        double val = i64_scaled(S, ea + M[c].exp);
+                        double val = ICVT ? i64_scaled_int(S, ea + M[c].exp) : i64_scaled(S, ea + M[c].exp);
                         if (M[c].flag) val *= inv_alpha0;
                         M[c].out[row] = val;
                     }
@@ -741,10 +763,12 @@ size_t split_smem_bytes(int kd) { return kd == 256 ? GemmShape<256>::kSmem : Gem
 
 cudaError_t split_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_split_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(GemmShape<256>::kSmem));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_split_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64);
+    cudaError_t e = cudaSuccess;
+    for (const void *k : {(const void *)k_split_gemm<256, false>, (const void *)k_split_gemm<256, true>})
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GemmShape<256>::kSmem));
+    for (const void *k : {(const void *)k_split_gemm<64, false>, (const void *)k_split_gemm<64, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64);
     // the digit kernels run before and beside the tensor launches: the
     // largest shared-memory carveout (see fp64_prepare)
     if (e == cudaSuccess)
@@ -779,7 +803,7 @@ cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const 
 }
 
 cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int32_t *err, long long wait_limit,
-                              int withhold, cudaStream_t st)
+                              int withhold, cudaStream_t st, bool intcvt)
 {
     if (g.ntiles <= 0) return cudaSuccess;
     const int sms = g_sms > 0 ? g_sms : 152;
@@ -787,10 +811,10 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
     int ie = 0;
     const int inv_alpha_exp = std::frexp(inv_alpha0, &ie) == 0.5 ? ie - 1 : kNoExp;
     if (kd == 256)
-        return launch_pdl(k_split_gemm<256>, grid, kGemmThreads, GemmShape<256>::kSmem, st, g, inv_alpha0,
-                          inv_alpha_exp, err, wait_limit, withhold);
-    return launch_pdl(k_split_gemm<64>, grid, kGemmThreads, size_t(kSmem64), st, g, inv_alpha0, inv_alpha_exp, err,
-                      wait_limit, withhold);
+        return launch_pdl(intcvt ? k_split_gemm<256, true> : k_split_gemm<256, false>, grid, kGemmThreads,
+                          GemmShape<256>::kSmem, st, g, inv_alpha0, inv_alpha_exp, err, wait_limit, withhold);
+    return launch_pdl(intcvt ? k_split_gemm<64, true> : k_split_gemm<64, false>, grid, kGemmThreads, size_t(kSmem64),
+                      st, g, inv_alpha0, inv_alpha_exp, err, wait_limit, withhold);
 }
 
 }  // namespace bc
