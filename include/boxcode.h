@@ -143,6 +143,31 @@ typedef void (*bc_density_fn)(const double *xy, int64_t n, double *out, void *us
 bc_status bc_tree_refine(bc_ctx *ctx, double x0, double y0, double L, bc_density_fn fn,
                          void *user, double eps, int max_level, bc_tree **out);
 
+/* Truncated adaptive tree (paper Alg. 2 with both criteria, Sec. 3.2.1): the
+ * domain Omega is bounded by the closed polygon gamma (n_gamma vertices
+ * [x, y], the last joined to the first), the bulk region Omega_B by the
+ * closed polygon gamma_b (inside Omega); the strip is Omega \ Omega_B.  f is
+ * evaluated at the nodes inside Omega only and extended by zero outside it.
+ * A box is split (below max_level) if it lies inside Omega and its
+ * coefficients are not resolved to eps (as in bc_tree_refine); if it meets
+ * both Omega_B and the outside of Omega; or if it meets the strip and its
+ * diagonal exceeds half the local strip width s, s the distance between the
+ * vertices of gamma and of gamma_b nearest to the box centre.  Then 2:1
+ * balance.  Leaves outside Omega are discarded: they are no source and their
+ * output is zero (bc_apply / bc_apply_adjoint); leaves cut by gamma keep the
+ * zero-extended f (the paper's remark on cut boxes).  The density passed to
+ * the applies should be the zero extension (bc_tree_node_mask).  Both curves
+ * are simple polygons; gamma lies in the root box; BC_ERR_ARG otherwise. */
+bc_status bc_tree_refine_truncated(bc_ctx *ctx, double x0, double y0, double L, bc_density_fn fn, void *user,
+                                   double eps, int max_level, const double *gamma, int64_t n_gamma,
+                                   const double *gamma_b, int64_t n_gamma_b, bc_tree **out);
+/* Leaf classes (host array of nleaf): 0 outside the domain (discarded), 1 cut
+ * by its boundary, 2 inside (every leaf of a tree without truncation). */
+bc_status bc_tree_leaf_class(const bc_tree *tree, int8_t *cls);
+/* Node mask of the zero extension (host array [nleaf][p*p]): 1 where the
+ * node lies inside the domain (every node of a tree without truncation). */
+bc_status bc_tree_node_mask(const bc_tree *tree, uint8_t *mask);
+
 int64_t bc_tree_nleaf(const bc_tree *tree);
 /* Leaves in caller order (host arrays of nleaf entries). */
 bc_status bc_tree_leaves(const bc_tree *tree, int32_t *level, int32_t *ix, int32_t *iy);

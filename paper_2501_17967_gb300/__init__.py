@@ -68,6 +68,11 @@ SIGNATURES = [
                                       _I32P, ctypes.POINTER(_VP)]),
     ("bc_tree_refine", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, DENSITY_FN, _VP,
                                       ctypes.c_double, ctypes.c_int, ctypes.POINTER(_VP)]),
+    ("bc_tree_refine_truncated", ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_double, ctypes.c_double, DENSITY_FN,
+                                                _VP, ctypes.c_double, ctypes.c_int, _DP, _I64, _DP, _I64,
+                                                ctypes.POINTER(_VP)]),
+    ("bc_tree_leaf_class", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int8)]),
+    ("bc_tree_node_mask", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint8)]),
     ("bc_tree_nleaf", _I64, [_VP]),
     ("bc_tree_leaves", ctypes.c_int, [_VP, _I32P, _I32P, _I32P]),
     ("bc_tree_nodes", ctypes.c_int, [_VP, _DP]),
@@ -232,6 +237,47 @@ class Tree:
             raise err[0]
         _check(st)
         return cls(ctx, None, None, None, x0, y0, L, _handle=h)
+
+    @classmethod
+    def refine_truncated(cls, ctx: Context, density, gamma, gamma_b, eps: float = 1e-11, max_level: int = 20,
+                         x0=-1.0, y0=-1.0, L=2.0):
+        """Truncated adaptive tree (Alg. 2 with both criteria, 2:1 balance): the domain
+        bounded by the closed polygon gamma [n, 2], the bulk region by gamma_b [m, 2];
+        density(xy[n,2]) -> f[n] is called at nodes inside the domain only."""
+        lib = _load()
+        err = []
+
+        def cb(xy, n, out, user):
+            try:
+                pts = np.ctypeslib.as_array(xy, shape=(n, 2))
+                vals = np.asarray(density(pts), dtype=np.float64).reshape(n)
+                np.ctypeslib.as_array(out, shape=(n,))[:] = vals
+            except Exception as exc:  # report after the call
+                err.append(exc)
+                np.ctypeslib.as_array(out, shape=(n,))[:] = np.nan
+
+        g = np.ascontiguousarray(gamma, dtype=np.float64).reshape(-1, 2)
+        gb = np.ascontiguousarray(gamma_b, dtype=np.float64).reshape(-1, 2)
+        cfn = DENSITY_FN(cb)
+        h = _VP()
+        st = lib.bc_tree_refine_truncated(ctx.handle, x0, y0, L, cfn, None, eps, max_level, g.ctypes.data_as(_DP),
+                                          g.shape[0], gb.ctypes.data_as(_DP), gb.shape[0], ctypes.byref(h))
+        if err:
+            raise err[0]
+        _check(st)
+        return cls(ctx, None, None, None, x0, y0, L, _handle=h)
+
+    def leaf_class(self) -> np.ndarray:
+        """0 outside the domain (discarded), 1 cut by its boundary, 2 inside."""
+        out = np.empty(self.nleaf, np.int8)
+        _check(_load().bc_tree_leaf_class(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))))
+        return out
+
+    def node_mask(self) -> np.ndarray:
+        """[nleaf, p*p]: 1 where the node lies inside the domain (the zero extension of f)."""
+        out = np.empty((self.nleaf, self.ctx.p * self.ctx.p), np.uint8)
+        _check(_load().bc_tree_node_mask(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+        return out
 
     @property
     def handle(self):

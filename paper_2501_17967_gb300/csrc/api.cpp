@@ -420,6 +420,14 @@ bc_status upload_tree(bc_tree *t)
 #undef UPV
     e = dev_upload<int32_t>(d.allocs, &d.zero_ptr, nullptr, size_t(h.nleaf) + 1);
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    if (!h.leaf_class.empty()) {
+        std::vector<uint8_t> act(h.nleaf);
+        for (int64_t k = 0; k < h.nleaf; k++) act[k] = h.leaf_class[k] != 0;
+        uint8_t *pa = nullptr;
+        e = dev_upload(d.allocs, &pa, act.data(), act.size());
+        if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+        d.leaf_active = pa;
+    }
     // r^2 and log r per level, r = (L/2) 2^-lv
     std::vector<double> lt(2 * kLvTab, 0.0);
     for (int lv = 0; lv < kLvTab; lv++) {
@@ -1196,6 +1204,83 @@ bc_status bc_tree_refine(bc_ctx *ctx, double x0, double y0, double L, bc_density
     bc_status s = refine_leaves(ctx->p, x0, y0, L, fn, user, eps, max_level, lv, ix, iy);
     if (s != BC_OK) return s;
     return bc_tree_create(ctx, x0, y0, L, int64_t(lv.size()), lv.data(), ix.data(), iy.data(), out);
+}
+
+bc_status bc_tree_refine_truncated(bc_ctx *ctx, double x0, double y0, double L, bc_density_fn fn, void *user,
+                                   double eps, int max_level, const double *gamma, int64_t n_gamma,
+                                   const double *gamma_b, int64_t n_gamma_b, bc_tree **out)
+{
+    if (!ctx || !out || !gamma || !gamma_b) { set_error("bc_tree_refine_truncated: NULL argument"); return BC_ERR_ARG; }
+    *out = nullptr;
+    if (n_gamma < 3 || n_gamma_b < 3 || n_gamma > (int64_t(1) << 24) || n_gamma_b > (int64_t(1) << 24)) {
+        set_error("bc_tree_refine_truncated: each curve needs 3 .. 2^24 vertices");
+        return BC_ERR_ARG;
+    }
+    for (int64_t i = 0; i < 2 * n_gamma; i++)
+        if (!std::isfinite(gamma[i])) { set_error("bc_tree_refine_truncated: non-finite vertex"); return BC_ERR_ARG; }
+    for (int64_t i = 0; i < 2 * n_gamma_b; i++)
+        if (!std::isfinite(gamma_b[i])) { set_error("bc_tree_refine_truncated: non-finite vertex"); return BC_ERR_ARG; }
+    Truncation tr;
+    tr.gamma = Polygon{gamma, n_gamma};
+    tr.gamma_b = Polygon{gamma_b, n_gamma_b};
+    for (int64_t i = 0; i < n_gamma_b; i++)
+        if (!polygon_contains(tr.gamma, gamma_b[2 * i], gamma_b[2 * i + 1])) {
+            set_error("bc_tree_refine_truncated: vertex %lld of the bulk curve lies outside the domain",
+                      (long long)i);
+            return BC_ERR_ARG;
+        }
+    for (int64_t i = 0; i < n_gamma; i++)
+        if (!(gamma[2 * i] >= x0 && gamma[2 * i] <= x0 + L && gamma[2 * i + 1] >= y0 && gamma[2 * i + 1] <= y0 + L)) {
+            set_error("bc_tree_refine_truncated: the domain must lie in the root box");
+            return BC_ERR_ARG;
+        }
+    std::vector<int32_t> lv, ix, iy;
+    bc_status s = refine_leaves(ctx->p, x0, y0, L, fn, user, eps, max_level, lv, ix, iy, &tr);
+    if (s != BC_OK) return s;
+    bc_tree *t = new bc_tree;
+    t->ctx = ctx;
+    s = build_host_tree(t->h, x0, y0, L, ctx->p, int64_t(lv.size()), lv.data(), ix.data(), iy.data());
+    if (s != BC_OK) { delete t; return s; }
+    // each leaf's class; leaves outside the domain are discarded (Alg. 2)
+    HostTree &h = t->h;
+    h.gamma.assign(gamma, gamma + 2 * n_gamma);
+    h.leaf_class.resize(h.nleaf);
+    std::vector<uint8_t> act(h.nleaf);
+    for (int64_t k = 0; k < h.nleaf; k++) {
+        const double r = 0.5 * L / double(int64_t(1) << h.leaf_level[k]);
+        const double cx = x0 + (2.0 * h.leaf_ix[k] + 1.0) * r, cy = y0 + (2.0 * h.leaf_iy[k] + 1.0) * r;
+        const BoxSide sd = box_side(tr.gamma, cx - r, cx + r, cy - r, cy + r);
+        h.leaf_class[k] = sd == BoxSide::Outside ? 0 : sd == BoxSide::Cut ? 1 : 2;
+        act[k] = h.leaf_class[k] != 0;
+    }
+    drop_inactive(h, act);
+    return finish_tree(ctx, out, t);
+}
+
+bc_status bc_tree_leaf_class(const bc_tree *tree, int8_t *cls)
+{
+    if (!tree || !cls) { set_error("bc_tree_leaf_class: NULL argument"); return BC_ERR_ARG; }
+    for (int64_t k = 0; k < tree->h.nleaf; k++) cls[k] = tree->h.leaf_class.empty() ? 2 : tree->h.leaf_class[k];
+    return BC_OK;
+}
+
+bc_status bc_tree_node_mask(const bc_tree *tree, uint8_t *mask)
+{
+    if (!tree || !mask) { set_error("bc_tree_node_mask: NULL argument"); return BC_ERR_ARG; }
+    const HostTree &h = tree->h;
+    const int p = h.p, NP = p * p;
+    std::vector<double> xy(size_t(h.nleaf) * NP * 2);
+    bc_status s = bc_tree_nodes(tree, xy.data());
+    if (s != BC_OK) return s;
+    const Polygon G{h.gamma.data(), int64_t(h.gamma.size() / 2)};
+    for (int64_t k = 0; k < h.nleaf; k++) {
+        const int c = h.leaf_class.empty() ? 2 : h.leaf_class[k];
+        for (int j = 0; j < NP; j++) {
+            const size_t i = size_t(k) * NP + j;
+            mask[i] = c == 2 ? 1 : c == 0 ? 0 : uint8_t(polygon_contains(G, xy[2 * i], xy[2 * i + 1]));
+        }
+    }
+    return BC_OK;
 }
 
 int64_t bc_tree_nleaf(const bc_tree *tree) { return tree ? tree->h.nleaf : 0; }

@@ -43,17 +43,40 @@ struct HostTree {
     std::vector<int32_t> w_ptr, w_src, w_code;            // per leaf: source box, W code
     std::vector<int32_t> x_ptr, x_src, x_code;            // per box: source leaf, X code
     int64_t n_nonleaf = 0, n_down = 0;
+    // truncated trees (Alg. 2 with a domain): the domain's boundary polygon
+    // and each leaf's class, 0 outside the domain (discarded: no source, zero
+    // output), 1 cut by its boundary, 2 inside (empty: no truncation)
+    std::vector<double> gamma;
+    std::vector<int8_t> leaf_class;
 };
+void drop_inactive(HostTree &t, const std::vector<uint8_t> &active);
 
 // Builds boxes and lists from explicit leaves; returns BC_OK or BC_ERR_TREE /
 // BC_ERR_ARG with the message set.
 bc_status build_host_tree(HostTree &t, double x0, double y0, double L, int p, int64_t nleaf,
                           const int32_t *level, const int32_t *ix, const int32_t *iy);
-// Alg. 2 (function-resolution criterion) followed by 2:1 balancing; fills the
-// leaf arrays (level/ix/iy) only.
+// A closed polygon (vertices xy[2n], the last joined to the first).
+struct Polygon {
+    const double *xy = nullptr;
+    int64_t n = 0;
+};
+// The truncation of Alg. 2: the domain Omega bounded by gamma, the bulk region
+// Omega_B bounded by gamma_b (inside Omega); the strip is Omega \ Omega_B.
+struct Truncation {
+    Polygon gamma, gamma_b;
+};
+enum class BoxSide { Inside, Outside, Cut };
+BoxSide box_side(const Polygon &P, double x0, double x1, double y0, double y1);
+bool polygon_contains(const Polygon &P, double x, double y);
+bool truncation_split(const Truncation &tr, double cx, double cy, double r);
+// Alg. 2 followed by 2:1 balancing; fills the leaf arrays (level/ix/iy)
+// only.  Without a truncation only the function-resolution criterion
+// applies; with one, f is extended by zero outside Omega, the resolution
+// criterion applies to boxes inside Omega and the separation criterion to
+// every box.
 bc_status refine_leaves(int p, double x0, double y0, double L, bc_density_fn fn, void *user,
                         double eps, int max_level, std::vector<int32_t> &lv,
-                        std::vector<int32_t> &ix, std::vector<int32_t> &iy);
+                        std::vector<int32_t> &ix, std::vector<int32_t> &iy, const Truncation *tr = nullptr);
 
 // ---------------------------------------------------------------------------
 // Tables
@@ -170,6 +193,7 @@ struct DevTree {
     int32_t *flag = nullptr;                   // [nbox] completion flags of the persistent level passes
     float4 *exdf = nullptr;                    // [nbox][P1] double-float upward expansions of the climb
     double *stage_in = nullptr, *stage_out = nullptr; // host-pointer staging [nleaf*NP]
+    const uint8_t *leaf_active = nullptr;      // [nleaf] truncated trees: 0 = discarded leaf (zero output); null: all
     std::vector<void *> allocs;
 };
 
@@ -282,7 +306,7 @@ struct SplitLaunch {
 // Digits of the leaf vectors (times scale), of the two expansion arrays
 // (times scale), and the tensor-core operator products of one group.
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
-                                    cudaStream_t st);
+                                    cudaStream_t st, const uint8_t *active = nullptr);
 // Expansion digits of vectors [i0, i1) of the pair (expA: 0..nbox-1, expB:
 // nbox..2 nbox-1).
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,

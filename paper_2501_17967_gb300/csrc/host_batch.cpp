@@ -84,10 +84,13 @@ bc_status merge_host_trees(const std::vector<const HostTree *> &trees, HostTree 
     for (int l = 1; l <= nlevels; l++) out.level_start[l] = std::max(out.level_start[l], out.level_start[l - 1]);
     out.near_ptr.assign(nleaf + 1, 0);
     out.w_ptr.assign(nleaf + 1, 0);
+    bool any_class = false;   // truncated trees keep their leaf classes (discarded leaves: zero output)
+    for (size_t k = 0; k < n; k++) any_class = any_class || !trees[k]->leaf_class.empty();
     for (size_t k = 0; k < n; k++) {
         const HostTree &t = *trees[k];
         for (int64_t l = 0; l < t.nleaf; l++) {
             const int64_t gl = leaf_offset[k] + l;
+            if (any_class) out.leaf_class.push_back(t.leaf_class.empty() ? int8_t(2) : t.leaf_class[l]);
             out.leaf_level.push_back(t.leaf_level[l]);
             out.leaf_ix.push_back(t.leaf_ix[l]);
             out.leaf_iy.push_back(t.leaf_iy[l]);

@@ -300,9 +300,121 @@ bc_status build_host_tree(HostTree &t, double x0, double y0, double L, int p, in
 // ---------------------------------------------------------------------------
 // Alg. 2 (function-resolution criterion) + 2:1 balance.
 // ---------------------------------------------------------------------------
+// Drops from the lists what a zero density or a discarded target makes void:
+// near entries whose target or source is inactive, W entries of inactive
+// targets, X entries of inactive sources (leaf-indexed active flags).
+void drop_inactive(HostTree &t, const std::vector<uint8_t> &active)
+{
+    auto filter = [](std::vector<int32_t> &ptr, std::vector<int32_t> &src, std::vector<int32_t> &code,
+                     auto keep) {
+        std::vector<int32_t> nsrc, ncode;
+        nsrc.reserve(src.size());
+        ncode.reserve(code.size());
+        int32_t w = 0;
+        for (size_t r = 0; r + 1 < ptr.size(); r++) {
+            const int32_t a = ptr[r], b = ptr[r + 1];
+            ptr[r] = w;
+            for (int32_t k = a; k < b; k++)
+                if (keep(int64_t(r), src[k])) {
+                    nsrc.push_back(src[k]);
+                    ncode.push_back(code[k]);
+                    w++;
+                }
+        }
+        ptr.back() = w;
+        src.swap(nsrc);
+        code.swap(ncode);
+    };
+    filter(t.near_ptr, t.near_src, t.near_tab, [&](int64_t o, int32_t s) { return active[o] && active[s]; });
+    filter(t.w_ptr, t.w_src, t.w_code, [&](int64_t o, int32_t) { return bool(active[o]); });
+    filter(t.x_ptr, t.x_src, t.x_code, [&](int64_t, int32_t s) { return bool(active[s]); });
+}
+
+// ---------------------------------------------------------------------------
+// Polygon geometry for the truncated tree (Alg. 2, separation criterion).
+// A curve is a closed polygon: vertices v_0 .. v_{n-1}, edge v_{n-1} -> v_0.
+// ---------------------------------------------------------------------------
+namespace {
+
+// even-odd crossing rule
+bool point_in_polygon(const Polygon &P, double x, double y)
+{
+    bool in = false;
+    for (int64_t i = 0, j = P.n - 1; i < P.n; j = i++) {
+        const double xi = P.xy[2 * i], yi = P.xy[2 * i + 1], xj = P.xy[2 * j], yj = P.xy[2 * j + 1];
+        if ((yi > y) != (yj > y) && x < (xj - xi) * (y - yi) / (yj - yi) + xi) in = !in;
+    }
+    return in;
+}
+
+// does the segment (ax,ay)-(bx,by) meet the closed box [x0,x1] x [y0,y1]?
+// (Liang-Barsky clipping of the segment's parameter interval)
+bool segment_meets_box(double ax, double ay, double bx, double by, double x0, double x1, double y0, double y1)
+{
+    double t0 = 0.0, t1 = 1.0;
+    const double dx = bx - ax, dy = by - ay;
+    const double pq[4][2] = {{-dx, ax - x0}, {dx, x1 - ax}, {-dy, ay - y0}, {dy, y1 - ay}};
+    for (const auto &e : pq) {
+        if (e[0] == 0.0) {
+            if (e[1] < 0.0) return false;
+        } else {
+            const double t = e[1] / e[0];
+            if (e[0] < 0.0) t0 = std::max(t0, t);
+            else t1 = std::min(t1, t);
+            if (t0 > t1) return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+// Where a box lies relative to a polygon: the curve meets the box (cut), or
+// the box lies wholly inside or wholly outside the region it bounds.
+BoxSide box_side(const Polygon &P, double x0, double x1, double y0, double y1)
+{
+    for (int64_t i = 0, j = P.n - 1; i < P.n; j = i++)
+        if (segment_meets_box(P.xy[2 * j], P.xy[2 * j + 1], P.xy[2 * i], P.xy[2 * i + 1], x0, x1, y0, y1))
+            return BoxSide::Cut;
+    // the curve misses the box: the box is on one side (its centre tells)
+    return point_in_polygon(P, 0.5 * (x0 + x1), 0.5 * (y0 + y1)) ? BoxSide::Inside : BoxSide::Outside;
+}
+
+bool polygon_contains(const Polygon &P, double x, double y) { return point_in_polygon(P, x, y); }
+
+// Distance from (x, y) to the nearest vertex of P, and that vertex.
+static int64_t nearest_vertex(const Polygon &P, double x, double y)
+{
+    int64_t best = 0;
+    double bd = 1e300;
+    for (int64_t i = 0; i < P.n; i++) {
+        const double d = (P.xy[2 * i] - x) * (P.xy[2 * i] - x) + (P.xy[2 * i + 1] - y) * (P.xy[2 * i + 1] - y);
+        if (d < bd) { bd = d; best = i; }
+    }
+    return best;
+}
+
+// Alg. 2's separation criterion for box B (half side r, centre c): B must be
+// split if it meets the bulk region and the outside of the domain, or if it
+// meets the strip and its diagonal exceeds half the local strip width s, s
+// the distance between the vertices of Gamma and of Gamma_b nearest to c.
+bool truncation_split(const Truncation &tr, double cx, double cy, double r)
+{
+    const double x0 = cx - r, x1 = cx + r, y0 = cy - r, y1 = cy + r;
+    const BoxSide so = box_side(tr.gamma, x0, x1, y0, y1), sb = box_side(tr.gamma_b, x0, x1, y0, y1);
+    if (sb != BoxSide::Outside && so != BoxSide::Inside) return true;   // meets Omega_B and R^2 \ Omega
+    if (so != BoxSide::Outside && sb != BoxSide::Inside) {              // meets the strip Omega \ Omega_B
+        const int64_t a = nearest_vertex(tr.gamma, cx, cy), b = nearest_vertex(tr.gamma_b, cx, cy);
+        const double s = std::hypot(tr.gamma.xy[2 * a] - tr.gamma_b.xy[2 * b],
+                                    tr.gamma.xy[2 * a + 1] - tr.gamma_b.xy[2 * b + 1]);
+        if (2.0 * std::sqrt(2.0) * r > 0.5 * s) return true;
+    }
+    return false;
+}
+
 bc_status refine_leaves(int p, double x0, double y0, double L, bc_density_fn fn, void *user,
                         double eps, int max_level, std::vector<int32_t> &lv_out,
-                        std::vector<int32_t> &ix_out, std::vector<int32_t> &iy_out)
+                        std::vector<int32_t> &ix_out, std::vector<int32_t> &iy_out, const Truncation *tr)
 {
     if (!fn || !(eps > 0.0) || max_level < 0 || max_level > kMaxLevel || !(L > 0.0)) {
         set_error("refine: need a callback, eps > 0, 0 <= max_level <= %d, L > 0", kMaxLevel);
@@ -340,7 +452,33 @@ bc_status refine_leaves(int p, double x0, double y0, double L, bc_density_fn fn,
                     xy[(k * NP + jy * p + jx) * 2 + 1] = cy + r * xn[jy];
                 }
         }
-        fn(xy.data(), int64_t(nb * NP), fv.data(), user);
+        // with a truncation, f is evaluated at the nodes inside the domain
+        // only and extended by zero outside it (Alg. 2; on cut boxes its
+        // coefficients are kept, Sec. 3.2.1, remark on cut boxes)
+        std::vector<BoxSide> side(nb, BoxSide::Inside);
+        if (!tr) {
+            fn(xy.data(), int64_t(nb * NP), fv.data(), user);
+        } else {
+            std::vector<double> xin;
+            std::vector<int64_t> where;
+            for (size_t k = 0; k < nb; k++) {
+                const double r = 0.5 * L / double(int64_t(1) << cur[k].lv);
+                const double cx = x0 + (2.0 * cur[k].ix + 1.0) * r, cy = y0 + (2.0 * cur[k].iy + 1.0) * r;
+                side[k] = box_side(tr->gamma, cx - r, cx + r, cy - r, cy + r);
+                if (side[k] == BoxSide::Outside) continue;
+                for (int j = 0; j < NP; j++) {
+                    const double px = xy[(k * NP + j) * 2], py = xy[(k * NP + j) * 2 + 1];
+                    if (side[k] == BoxSide::Inside || point_in_polygon(tr->gamma, px, py)) {
+                        xin.push_back(px);
+                        xin.push_back(py);
+                        where.push_back(int64_t(k * NP + j));
+                    }
+                }
+            }
+            std::vector<double> fin(where.size());
+            if (!where.empty()) fn(xin.data(), int64_t(where.size()), fin.data(), user);
+            for (size_t i = 0; i < where.size(); i++) fv[where[i]] = fin[i];
+        }
         for (double v : fv)
             if (!std::isfinite(v)) { set_error("refine: density callback returned a non-finite value"); return BC_ERR_ARG; }
         if (cur.size() == 1 && cur[0].lv == 0) {
@@ -366,7 +504,12 @@ bc_status refine_leaves(int p, double x0, double y0, double L, bc_density_fn fn,
                     for (int n = 0; n < p; n++) s += tmp[n * p + a] * Tm[n * p + b];
                     tail = std::max(tail, std::fabs(s * (b == 0 ? 1.0 : 2.0) / p));
                 }
-            if (tail > eps * vscale && cur[k].lv < max_level) {
+            bool split = tail > eps * vscale && side[k] == BoxSide::Inside;   // function resolution
+            if (tr && !split) {
+                const double r = 0.5 * L / double(int64_t(1) << cur[k].lv);
+                split = truncation_split(*tr, x0 + (2.0 * cur[k].ix + 1.0) * r, y0 + (2.0 * cur[k].iy + 1.0) * r, r);
+            }
+            if (split && cur[k].lv < max_level) {
                 for (int q = 0; q < 4; q++)
                     next.push_back({cur[k].lv + 1, 2 * cur[k].ix + (q & 1), 2 * cur[k].iy + (q >> 1)});
             } else {

@@ -185,9 +185,9 @@ __global__ void __launch_bounds__(128)
 k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
             const int32_t *__restrict__ leaf_level, const int64_t *__restrict__ level_start, int nlevels,
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
-            const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, DfSched us, ShiftFac uf, double2 *ex, float4 *exdf, int NP, int P1, const double *__restrict__ lvtab,
-            bool climb, int32_t *flag,
-            long long limit, int32_t *err)
+            const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, DfSched us, ShiftFac uf, double2 *ex,
+            float4 *exdf, int NP, int P1, const double *__restrict__ lvtab, bool climb, int32_t *flag,
+            const uint8_t *__restrict__ active, long long limit, int32_t *err)
 {
     extern __shared__ double2 shu[];
     double2 *sc = shu;                                       // 4 * P1 children
@@ -230,6 +230,8 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         const int leaf = order[li];
         const int b = leaf_box[leaf];
         const double s = ADJ ? 1.0 : lvtab[leaf_level[leaf]];   // r^2
+        // a discarded leaf of a truncated tree is no source: its expansion is zero
+        const bool skip = active && !active[leaf];
         __syncthreads();
         if constexpr (DF) {
             // double-float: the leaf values as {hi, lo} pairs, OpA as pairs
@@ -288,7 +290,8 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         for (int l = threadIdx.x; l < P1; l += blockDim.x) {
             const double2 a0 = part[l], a1 = part[P1 + l], a2 = part[2 * P1 + l], a3 = part[3 * P1 + l];
             ex[int64_t(b) * P1 + l] =
-                make_double2(s * ((a0.x + a1.x) + (a2.x + a3.x)), s * ((a0.y + a1.y) + (a2.y + a3.y)));
+                skip ? make_double2(0.0, 0.0)
+                     : make_double2(s * ((a0.x + a1.x) + (a2.x + a3.x)), s * ((a0.y + a1.y) + (a2.y + a3.y)));
         }
         flag_publish(&flag[b], 1);
     }
@@ -1106,7 +1109,7 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const double2 *__restrict__ aux, const double *__restrict__ vnear,
                            double *__restrict__ vout, int NP, int P1, const double *__restrict__ lvtab, bool far,
                            const double *__restrict__ Pnear, const double *__restrict__ PE,
-                           const double *__restrict__ PW)
+                           const double *__restrict__ PW, const uint8_t *__restrict__ active)
 {
     griddep_wait();
     griddep_launch_dependents();
@@ -1117,6 +1120,10 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
     const int lane = threadIdx.x & 31;
     for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
         const int o = order[li];
+        if (active && !active[o]) {   // a discarded leaf of a truncated tree (uniform over the block)
+            vout[int64_t(o) * NP + threadIdx.x] = 0.0;
+            continue;
+        }
         const int lvo = leaf_level[o];
         const double r2o = lvtab[lvo], lgo = lvtab[kLvTab + lvo];
         const int j = threadIdx.x;   // blockDim.x == NP
@@ -1314,7 +1321,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             return e;
         if (ev) cudaEventRecord(ev[8], sd->side);
         if (!leaf_tc) {
-            e = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side);
+            e = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side, d.leaf_active);
             if (e != cudaSuccess) return e;
         }
         SplitGemm g = gv;
@@ -1353,7 +1360,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (!sd) {
             // one launch: the near-field tiles (two jobs each) first, then the
             // leaf-to-expansion and X-list tiles
-            ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
+            ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active);
             if (ce != cudaSuccess) return ce;
             SplitGemm g = gv;
             g.tiles = sp->tVN[dir]; g.cols = sp->cVN[dir]; g.ntiles = sp->ntVN[dir];
@@ -1369,7 +1376,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             // double-float inside the upward pass, and then the digits run on
             // the internal stream too.
             if (leaf_tc) {
-                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st);
+                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active);
                 if (ce != cudaSuccess) return ce;
             }
             if (!late && (ce = side_launches()) != cudaSuccess) return ce;
@@ -1408,7 +1415,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
                d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up_s, op.up_f, first, d.exdf, NP, \
-               P1, d.lvtab, climb, d.flag, glimit, a.err)
+               P1, d.lvtab, climb, d.flag, d.leaf_active, glimit, a.err)
         if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
         else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
 #undef BC_UP
@@ -1543,11 +1550,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (adj)
         ce = launch_pdl(k_leaf_out<true>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                         wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW);
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active);
     else
         ce = launch_pdl(k_leaf_out<false>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                         wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW);
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active);
     if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[7], st);
     return cudaGetLastError();

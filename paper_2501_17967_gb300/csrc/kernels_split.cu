@@ -315,14 +315,17 @@ __device__ __forceinline__ void digits_of(long long bits, int E, uint16_t *out, 
 // max |scale v| < 2^(E-1).  One block of 256 threads per leaf.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *__restrict__ v, double scale,
-                                                   uint16_t *__restrict__ dig, int32_t *__restrict__ dexp)
+                                                   uint16_t *__restrict__ dig, int32_t *__restrict__ dexp,
+                                                   const uint8_t *__restrict__ active)
 {
     griddep_wait();
     griddep_launch_dependents();
     __shared__ int wmax[8];
     const int k = threadIdx.x;
     for (int64_t leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
-        const long long bits = __double_as_longlong(scale * v[leaf * 256 + k]);
+        // a discarded leaf of a truncated tree is no source: zero digits
+        const double x = (active && !active[leaf]) ? 0.0 : v[leaf * 256 + k];
+        const long long bits = __double_as_longlong(scale * x);
         int m = int((bits >> 52) & 0x7FF);
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((k & 31) == 0) wmax[k >> 5] = m;
@@ -786,10 +789,11 @@ cudaError_t split_prepare()
 int split_sm_count() { return g_sms > 0 ? g_sms : 152; }
 
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
-                                    cudaStream_t st)
+                                    cudaStream_t st, const uint8_t *active)
 {
     if (nleaf <= 0) return cudaSuccess;
-    return launch_pdl(k_split_vec, int(std::min<int64_t>(nleaf, 152 * 16)), 256, 0, st, nleaf, v, scale, dig, dexp);
+    return launch_pdl(k_split_vec, int(std::min<int64_t>(nleaf, 152 * 16)), 256, 0, st, nleaf, v, scale, dig, dexp,
+                      active);
 }
 
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,

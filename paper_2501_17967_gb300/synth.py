@@ -186,3 +186,17 @@ def sample_leaves_per_level(levels: np.ndarray, k: int, seed: int = 7) -> np.nda
 def mass_hint(g: GaussianSum) -> float:
     """Untruncated total mass sum_k 2 pi a_k w_k^2 (for sanity checks only)."""
     return float(np.sum(2.0 * math.pi * g.a * g.w ** 2))
+
+
+def star_domain(n: int = 600, r0: float = 0.8, amp: float = 0.1, k: int = 5, strip: float = 0.08):
+    """A smooth star-shaped domain and its bulk region, as closed polygons of n
+    vertices each (counterclockwise): the domain boundary r(t) = r0 + amp cos(k t)
+    and the fictitious curve r(t) - strip, a radial inward offset (the paper's
+    geometries are not available; Sec. 3.1 builds its curve by an inward offset
+    of the boundary).  Returns (gamma, gamma_b), each [n, 2]."""
+    t = 2.0 * math.pi * np.arange(n) / n
+    r = r0 + amp * np.cos(k * t)
+    gamma = np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
+    rb = r - strip
+    gamma_b = np.stack([rb * np.cos(t), rb * np.sin(t)], axis=1)
+    return gamma, gamma_b
