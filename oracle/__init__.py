@@ -54,6 +54,9 @@ def _load():
         lib.oracle_potential.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp,
                                          i64p, i64p, dp, ctypes.c_int]
         lib.oracle_potential.restype = ctypes.c_int
+        lib.oracle_gradient.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp,
+                                        i64p, i64p, dp, ctypes.c_int]
+        lib.oracle_gradient.restype = ctypes.c_int
         lib.oracle_nodes.argtypes = [ctypes.c_int, dp]
         lib.oracle_nodes.restype = None
         lib.oracle_s_rule.argtypes = [ctypes.c_int, dp, dp, dp]
@@ -124,6 +127,26 @@ def potential(p: int, geom: np.ndarray, f: np.ndarray, targets: np.ndarray,
                                   pp, ip, _dp(out), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_potential failed ({rc})")
+    return out
+
+
+def gradient(p: int, geom: np.ndarray, f: np.ndarray, targets: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """grad u at ``targets`` [n, 2] -> [n, 2]: (1/2pi) sum_B int_B (x - y)/|x - y|^2 f_B(y) dy,
+    the derivative of eq. (vbulk) (the glue step of Sec. 3.4 needs the normal
+    derivative of v_bulk on the fictitious curve).  Direct quadrature as in
+    ``potential``: tensor Gauss-Legendre on admissible rectangles, Duffy rays
+    from targets inside a leaf (the 1/r singularity cancels the ray Jacobian).
+    Pinned by the rectangle and Gaussian closed forms and by central
+    differences of ``potential``.
+    """
+    geom = np.ascontiguousarray(geom, dtype=np.float64)
+    f = np.ascontiguousarray(f, dtype=np.float64).reshape(geom.shape[0], p * p)
+    t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 2)
+    out = np.empty((t.shape[0], 2), dtype=np.float64)
+    rc = _load().oracle_gradient(p, geom.shape[0], _dp(geom), _dp(f), t.shape[0], _dp(t), None, None,
+                                 _dp(out), int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"oracle_gradient failed ({rc})")
     return out
 
 

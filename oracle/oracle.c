@@ -397,6 +397,145 @@ static double ref_integral(const leaf_poly *L, double xi, double eta, int ns)
 }
 
 /* ------------------------------------------------------------------ */
+/* Gradient kernel: int (xi - eta)/|xi - eta|^2 f(eta) d eta.          */
+/* ------------------------------------------------------------------ */
+
+/* the same on a rectangle by the 16x16 tensor GL rule (admissible) */
+static void rect_gl_grad(const leaf_poly *L, double xi, double eta, double x0, double x1, double y0, double y1,
+                         double *gx, double *gy)
+{
+    int p = L->p;
+    double hx = 0.5 * (x1 - x0), hy = 0.5 * (y1 - y0);
+    double u[OR_NQ], v[OR_NQ];
+    double Tu[OR_NQ][OR_MAXP], Tv[OR_NQ][OR_MAXP];
+    for (int q = 0; q < OR_NQ; q++) {
+        u[q] = x0 + hx * (g_q[q] + 1.0);
+        v[q] = y0 + hy * (g_q[q] + 1.0);
+        cheb_T(p, u[q], Tu[q]);
+        cheb_T(p, v[q], Tv[q]);
+    }
+    double sx = 0.0, sy = 0.0;
+    for (int r = 0; r < OR_NQ; r++) {
+        double row[OR_MAXP];
+        for (int a = 0; a < p; a++) {
+            double s = 0.0;
+            for (int b = 0; b < p; b++) s += L->c[b * p + a] * Tv[r][b];
+            row[a] = s;
+        }
+        double dy = eta - v[r];
+        double ax = 0.0, ay = 0.0;
+        for (int q = 0; q < OR_NQ; q++) {
+            double fv = 0.0;
+            for (int a = 0; a < p; a++) fv += row[a] * Tu[q][a];
+            double dx = xi - u[q], d2 = dx * dx + dy * dy;
+            ax += g_wq[q] * dx / d2 * fv;
+            ay += g_wq[q] * dy / d2 * fv;
+        }
+        sx += g_wq[r] * ax;
+        sy += g_wq[r] * ay;
+    }
+    *gx = sx * hx * hy;
+    *gy = sy * hx * hy;
+}
+
+static void subdiv_grad(const leaf_poly *L, double xi, double eta, double x0, double x1, double y0, double y1,
+                        double *gx, double *gy)
+{
+    double diam = hypot(x1 - x0, y1 - y0);
+    double dist = rect_dist(xi, eta, x0, x1, y0, y1);
+    if (dist >= diam) { rect_gl_grad(L, xi, eta, x0, x1, y0, y1, gx, gy); return; }
+    *gx = *gy = 0.0;
+    if (diam < 1e-14) return; /* |contribution| <= max|f| diam */
+    double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1), ax, ay;
+    subdiv_grad(L, xi, eta, x0, xm, y0, ym, &ax, &ay); *gx += ax; *gy += ay;
+    subdiv_grad(L, xi, eta, xm, x1, y0, ym, &ax, &ay); *gx += ax; *gy += ay;
+    subdiv_grad(L, xi, eta, x0, xm, ym, y1, &ax, &ay); *gx += ax; *gy += ay;
+    subdiv_grad(L, xi, eta, xm, x1, ym, y1, &ax, &ay); *gx += ax; *gy += ay;
+}
+
+/* Target inside the closed square: the four Duffy triangles with apex xi.
+ * On the ray eta = xi + s (e(t) - xi) the kernel is -(e - xi) / (s |e - xi|^2)
+ * and the Jacobian twoA * s, so the s-integral of f is regular (plain
+ * Gauss-Legendre on ns nodes, exact for the degree 2(p-1) of f along the ray)
+ * and the t-integral of -(e - xi)/|e - xi|^2 is graded toward the foot of the
+ * perpendicular from xi. */
+static void duffy_square_grad(const leaf_poly *L, double xi, double eta, int ns, double *gx, double *gy)
+{
+    static const double vx[5] = {-1.0, 1.0, 1.0, -1.0, -1.0};
+    static const double vy[5] = {-1.0, -1.0, 1.0, 1.0, -1.0};
+    int p = L->p;
+    double sn[OR_MAXS], sw[OR_MAXS];
+    gl_rule(ns, sn, sw);
+    for (int m = 0; m < ns; m++) { sn[m] = 0.5 * (sn[m] + 1.0); sw[m] *= 0.5; }
+    double tx = 0.0, ty = 0.0;
+    for (int e = 0; e < 4; e++) {
+        double ax = vx[e], ay = vy[e], bx = vx[e + 1], by = vy[e + 1];
+        double ex = bx - ax, ey = by - ay;
+        double le = hypot(ex, ey);
+        double twoA = fabs((ax - xi) * ey - (ay - eta) * ex);
+        if (twoA < 1e-300) continue;
+        double d = twoA / le;
+        double tf = ((xi - ax) * ex + (eta - ay) * ey) / (le * le);
+        double br[2 * OR_MAXPANEL];
+        int nb = t_panels(tf, d / le, br);
+        int horizontal = (ey == 0.0);
+        for (int k = 0; k + 1 < nb; k++) {
+            double t0 = br[k], t1 = br[k + 1], h = 0.5 * (t1 - t0);
+            for (int q = 0; q < OR_NT; q++) {
+                double t = t0 + h * (g_t[q] + 1.0), wt = h * g_wt[q];
+                double px = ax + t * ex - xi, py = ay + t * ey - eta, d2 = px * px + py * py;
+                /* int_0^1 f(xi + s (e(t) - xi)) ds */
+                double fs = 0.0;
+                for (int m = 0; m < ns; m++) {
+                    double s = sn[m];
+                    double X = xi + s * px, Y = eta + s * py;
+                    double TX[OR_MAXP], TY[OR_MAXP];
+                    cheb_T(p, X, TX);
+                    cheb_T(p, Y, TY);
+                    double fv = 0.0;
+                    for (int b = 0; b < p; b++) {
+                        double acc = 0.0;
+                        for (int a = 0; a < p; a++) acc += L->c[b * p + a] * TX[a];
+                        fv += acc * TY[b];
+                    }
+                    fs += sw[m] * fv;
+                }
+                (void)horizontal;
+                tx -= wt * twoA * px / d2 * fs;
+                ty -= wt * twoA * py / d2 * fs;
+            }
+        }
+    }
+    *gx = tx;
+    *gy = ty;
+}
+
+/* int_{[-1,1]^2} (xi - eta)/|xi - eta|^2 f(eta) d eta for the leaf polynomial. */
+static void ref_integral_grad(const leaf_poly *L, double xi, double eta, int ns, double *gx, double *gy)
+{
+    if (fabs(xi) <= 1.0 && fabs(eta) <= 1.0) { duffy_square_grad(L, xi, eta, ns, gx, gy); return; }
+    double dist = rect_dist(xi, eta, -1.0, 1.0, -1.0, 1.0);
+    if (dist >= 2.0 * sqrt(2.0)) {
+        double sx = 0.0, sy = 0.0;
+        for (int qx = 0; qx < OR_NQ; qx++) {
+            double dx = xi - g_q[qx], ax = 0.0, ay = 0.0;
+            for (int qy = 0; qy < OR_NQ; qy++) {
+                double dy = eta - g_q[qy], d2 = dx * dx + dy * dy;
+                double w = g_wq[qy] * L->fgrid[qx * OR_NQ + qy] / d2;
+                ax += w * dx;
+                ay += w * dy;
+            }
+            sx += g_wq[qx] * ax;
+            sy += g_wq[qx] * ay;
+        }
+        *gx = sx;
+        *gy = sy;
+        return;
+    }
+    subdiv_grad(L, xi, eta, -1.0, 1.0, -1.0, 1.0, gx, gy);
+}
+
+/* ------------------------------------------------------------------ */
 /* Driver.                                                             */
 /* ------------------------------------------------------------------ */
 typedef struct {
@@ -408,11 +547,36 @@ typedef struct {
     const int64_t *src_ptr, *src_idx;
     double *out;
     int64_t t0, t1;
+    int grad;                  /* 1: out[2i], out[2i+1] = the gradient */
 } or_job;
 
 static void *or_worker(void *arg)
 {
     or_job *J = (or_job *)arg;
+    if (J->grad) {
+        for (int64_t i = J->t0; i < J->t1; i++) {
+            double X = J->txy[2 * i], Y = J->txy[2 * i + 1];
+            double sx = 0.0, cx_ = 0.0, sy = 0.0, cy_ = 0.0;
+            int64_t k0 = 0, k1 = J->nleaf;
+            if (J->src_ptr) { k0 = J->src_ptr[i]; k1 = J->src_ptr[i + 1]; }
+            for (int64_t k = k0; k < k1; k++) {
+                int64_t b = J->src_ptr ? J->src_idx[k] : k;
+                double cx = J->leaf[3 * b], cy = J->leaf[3 * b + 1], r = J->leaf[3 * b + 2];
+                double gx, gy;
+                ref_integral_grad(&J->poly[b], (X - cx) / r, (Y - cy) / r, J->ns, &gx, &gy);
+                double vx = r * gx, vy = r * gy;
+                double t = sx + vx;   /* Neumaier summation, per component */
+                if (fabs(sx) >= fabs(vx)) cx_ += (sx - t) + vx; else cx_ += (vx - t) + sx;
+                sx = t;
+                t = sy + vy;
+                if (fabs(sy) >= fabs(vy)) cy_ += (sy - t) + vy; else cy_ += (vy - t) + sy;
+                sy = t;
+            }
+            J->out[2 * i] = (sx + cx_) / (2.0 * OR_PI);
+            J->out[2 * i + 1] = (sy + cy_) / (2.0 * OR_PI);
+        }
+        return NULL;
+    }
     for (int64_t i = J->t0; i < J->t1; i++) {
         double X = J->txy[2 * i], Y = J->txy[2 * i + 1];
         double sum = 0.0, comp = 0.0;
@@ -481,9 +645,34 @@ static void *or_rr_worker(void *arg)
  *          means every leaf.
  * Returns 0, or -1 on bad arguments / allocation failure.
  */
+static int oracle_run(int p, int64_t nleaf, const double *leaf, const double *f, int64_t ntarget,
+                      const double *txy, const int64_t *src_ptr, const int64_t *src_idx, double *out,
+                      int nthreads, int grad);
+
 int oracle_potential(int p, int64_t nleaf, const double *leaf, const double *f, int64_t ntarget,
                      const double *txy, const int64_t *src_ptr, const int64_t *src_idx, double *out,
                      int nthreads)
+{
+    return oracle_run(p, nleaf, leaf, f, ntarget, txy, src_ptr, src_idx, out, nthreads, 0);
+}
+
+/*
+ * The gradient of the same potential at the targets:
+ *   out[2i], out[2i+1] = (1/2pi) sum_{B in S(i)} int_B (x_i - y)/|x_i - y|^2 f_B(y) dy,
+ * the derivative of eq. (vbulk) that the glue step needs on the fictitious
+ * curve (normal derivative of v_bulk, Sec. 3.4).  Same arguments as
+ * oracle_potential; out has 2 ntarget entries.
+ */
+int oracle_gradient(int p, int64_t nleaf, const double *leaf, const double *f, int64_t ntarget,
+                    const double *txy, const int64_t *src_ptr, const int64_t *src_idx, double *out,
+                    int nthreads)
+{
+    return oracle_run(p, nleaf, leaf, f, ntarget, txy, src_ptr, src_idx, out, nthreads, 1);
+}
+
+static int oracle_run(int p, int64_t nleaf, const double *leaf, const double *f, int64_t ntarget,
+                      const double *txy, const int64_t *src_ptr, const int64_t *src_idx, double *out,
+                      int nthreads, int grad)
 {
     if (p < 2 || p > OR_MAXP || nleaf < 0 || ntarget < 0) return -1;
     if (ntarget == 0) return 0;
@@ -526,7 +715,7 @@ int oracle_potential(int p, int64_t nleaf, const double *leaf, const double *f, 
         or_job *J = &jobs[c];
         J->p = p; J->ns = ns; J->nleaf = nleaf; J->ntarget = ntarget;
         J->leaf = leaf; J->poly = poly; J->txy = txy;
-        J->src_ptr = src_ptr; J->src_idx = src_idx; J->out = out;
+        J->src_ptr = src_ptr; J->src_idx = src_idx; J->out = out; J->grad = grad;
         J->t0 = c * chunk;
         J->t1 = (c + 1) * chunk < ntarget ? (c + 1) * chunk : ntarget;
     }

@@ -347,3 +347,77 @@ def test_adjoint_column_against_scipy(oracle_mod):
     xi, eta = x[i % p], x[i // p]
     ref = _dblquad_leaf(lambda a, b: _lagrange_1d(p, jx, a) * _lagrange_1d(p, jy, b), xi, eta) / (2 * math.pi)
     assert abs(got - ref) <= 1e-13 * max(1.0, abs(ref)), (got, ref)
+
+
+def _Fa(a, b):
+    """d/da of _F: int_0^b (1/2) log(a^2 + t^2) dt (closed form, signed b)."""
+    if b == 0.0:
+        return 0.0
+    if a == 0.0:
+        return 0.5 * (b * math.log(b * b) - 2.0 * b)
+    return 0.5 * (b * math.log(a * a + b * b) - 2.0 * b + 2.0 * a * math.atan(b / a))
+
+
+def rect_gradient(x, y, x0, x1, y0, y1):
+    """Gradient of rect_potential (closed form): d/dx and d/dy of
+    (1/2pi) [F(x1-x, y1-y) - F(x0-x, y1-y) - F(x1-x, y0-y) + F(x0-x, y0-y)]."""
+    gx = (-_Fa(x1 - x, y1 - y) + _Fa(x0 - x, y1 - y) + _Fa(x1 - x, y0 - y) - _Fa(x0 - x, y0 - y))
+    gy = (-_Fa(y1 - y, x1 - x) + _Fa(y1 - y, x0 - x) + _Fa(y0 - y, x1 - x) - _Fa(y0 - y, x0 - x))
+    return np.array([gx, gy]) / (2.0 * math.pi)
+
+
+def test_gradient_constant_density_closed_form(oracle_mod):
+    """The oracle's gradient of the potential of f = 1 on a 2:1-refined tree
+    against the closed form, at targets inside leaves (at a node, near an edge,
+    near a corner), on a shared edge, and outside the root."""
+    p = 8
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: r > 0.9 or (cx > 0 and cy > 0 and r > 0.3), 3)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    f = np.ones((len(lv), p, p))
+    x = oracle_mod.cheb_nodes(p)
+    pts = np.array([[-0.5 + 0.5 * x[3], -0.5 + 0.5 * x[5]], [0.2, 0.999], [0.999, -0.998], [0.0, 0.37],
+                    [0.75, 0.26], [1.6, -0.3], [-2.5, 1.8]])
+    g = oracle_mod.gradient(p, geom, f, pts)
+    ref = np.array([rect_gradient(a, b, -1.0, 1.0, -1.0, 1.0) for a, b in pts])
+    assert np.abs(g - ref).max() < 1e-13 * np.abs(ref).max(), np.abs(g - ref).max()
+
+
+def test_gradient_gaussian_closed_form(oracle_mod):
+    """Radial Gaussian a exp(-r^2/(2 s^2)): grad u = u'(r) (x - c)/r with
+    u'(r) = a s^2 (1 - exp(-r^2/(2 s^2)))/r (derivative of the E1 form)."""
+    p = 16
+    a, s, c0 = 1.7, 0.04, np.array([0.1, -0.2])
+    lv, ix, iy = refine_leaves(
+        lambda cx, cy, r: (math.hypot(cx - c0[0], cy - c0[1]) < 10 * s + 1.5 * r) and r > 0.6 * s, 9)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    nodes = oracle_mod.leaf_nodes(geom, p)
+    fvals = a * np.exp(-((nodes[..., 0] - c0[0]) ** 2 + (nodes[..., 1] - c0[1]) ** 2) / (2 * s * s))
+    pts = np.array([c0 + [0.013, 0.0], c0 + [0.05, -0.07], c0 + [-0.021, 0.033], c0 + [0.3, 0.41], [0.9, 0.9]])
+    g = oracle_mod.gradient(p, geom, fvals.reshape(len(lv), p, p), pts)
+    d = pts - c0
+    r = np.hypot(d[:, 0], d[:, 1])
+    up = a * s * s * (1.0 - np.exp(-r ** 2 / (2 * s * s))) / r
+    ref = up[:, None] * d / r[:, None]
+    assert np.abs(g - ref).max() < 1e-12 * np.abs(ref).max(), np.abs(g - ref).max()
+
+
+def test_gradient_matches_differences_of_the_potential(oracle_mod):
+    """Central differences of the pinned potential (step 1e-4, O(h^2)) agree
+    with the gradient for a random polynomial density on a 2:1 tree, at targets
+    inside leaves and away from them.  (The density jumps across leaf edges, so
+    u is only C^1 there and differences across an edge are O(h); targets on
+    edges are pinned by the closed form above.)"""
+    p = 8
+    lv, ix, iy = refine_leaves(lambda cx, cy, r: r > 0.9 or (cx < 0 and cy > 0 and r > 0.3), 3)
+    geom = oracle_mod.leaf_geometry(lv, ix, iy)
+    rng = np.random.default_rng(4)
+    f = rng.standard_normal((len(lv), p, p))
+    pts = np.array([[-0.3, 0.41], [0.52, -0.77], [0.07, 0.123], [-0.63, 0.62], [1.4, 0.2]])
+    h = 1e-4
+    fd = np.zeros_like(pts)
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        fd[:, k] = (oracle_mod.potential(p, geom, f, pts + e) - oracle_mod.potential(p, geom, f, pts - e)) / (2 * h)
+    g = oracle_mod.gradient(p, geom, f, pts)
+    assert np.abs(g - fd).max() < 1e-6 * np.abs(g).max(), np.abs(g - fd).max()
