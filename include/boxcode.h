@@ -214,6 +214,17 @@ bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, do
 bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy,
                          int64_t n, double *out, void *stream);
 
+/* Value and gradient at points: val[k] as in bc_eval_points and
+ * grad[2k], grad[2k+1] = the x and y derivatives of the same leaf
+ * interpolant at xy[k] (barycentric differentiation, free of cancellation as
+ * a point nears a node).  The glue step of Sec. 3.4 needs v_bulk and its
+ * normal derivative n . grad v_bulk on the fictitious curve (the jumps tau
+ * and sigma of Alg. 1).  u, xy, val, grad: device or host (all of the same
+ * kind); points outside the root: BC_ERR_ARG on the host path, NaN on the
+ * device path. */
+bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy, int64_t n,
+                              double *val, double *grad, void *stream);
+
 /* Batched applies: many independent densities on different trees (all of
  * this context's p and root side L) in one launch per pass.  Not in the
  * paper (its solver applies one box code at a time).  A batch is the

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "SPLIT_BF16_ALL", "apply",
-           "apply_adjoint", "eval_points", "BoxCodeApply", "lib_path"]
+           "apply_adjoint", "eval_points", "eval_points_grad", "BoxCodeApply", "lib_path"]
 
 # precision modes (bc_precision): FP64 everywhere; BF16 digit products for the
 # fixed-operator contractions (near field, P2M, L2P, W and X lists) with the
@@ -83,6 +83,7 @@ SIGNATURES = [
     ("bc_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_eval_points", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP]),
+    ("bc_eval_points_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     ("bc_batch_create", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
     ("bc_batch_destroy", None, [_VP]),
     ("bc_batch_nleaf", _I64, [_VP]),
@@ -389,6 +390,22 @@ def eval_points(tree: Tree, u, xy, out=None, stream=None):
                                   ctypes.c_void_p(xy.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
                                   _stream_ptr(stream) if xy.is_cuda else None))
     return out
+
+
+def eval_points_grad(tree: Tree, u, xy, stream=None):
+    """Value and gradient of the leaf interpolant of u at points xy[n, 2]
+    (device tensors): returns (val[n], grad[n, 2])."""
+    import torch
+    _check_tensor(u, tree, "u")
+    xy = xy.contiguous()
+    n = xy.shape[0]
+    val = torch.empty(n, dtype=torch.float64, device=xy.device)
+    grad = torch.empty((n, 2), dtype=torch.float64, device=xy.device)
+    _check(_load().bc_eval_points_grad(tree.ctx.handle, tree.handle, ctypes.c_void_p(u.data_ptr()),
+                                       ctypes.c_void_p(xy.data_ptr()), n, ctypes.c_void_p(val.data_ptr()),
+                                       ctypes.c_void_p(grad.data_ptr()),
+                                       _stream_ptr(stream) if xy.is_cuda else None))
+    return val, grad
 
 
 class Batch:

@@ -1384,6 +1384,54 @@ bc_status bc_apply_adjoint(bc_ctx *ctx, const bc_tree *tree, const double *g, do
     return apply_impl(ctx, tree, g, h, prec, stream, true);
 }
 
+bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy, int64_t n,
+                              double *val, double *grad, void *stream)
+{
+    if (!ctx || !tree || (n > 0 && (!u || !xy || !val || !grad)) || n < 0) {
+        set_error("bc_eval_points_grad: bad argument");
+        return BC_ERR_ARG;
+    }
+    if (tree->ctx != ctx) { set_error("bc_eval_points_grad: tree belongs to another context"); return BC_ERR_ARG; }
+    if (ctx->device < 0) { set_error("bc_eval_points_grad: host-only context (device -1)"); return BC_ERR_STATE; }
+    if (n == 0) return BC_OK;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    PassArgs a = pass_args(ctx, tree);
+    const HostTree &h = tree->h;
+    const bool du = is_device_ptr(u), dx = is_device_ptr(xy), dv = is_device_ptr(val), dg = is_device_ptr(grad);
+    if (du && dx && dv && dg) {
+        e = launch_eval_points_grad(a, tree->d, u, xy, n, val, grad, h.x0, h.y0, h.L, st);
+        return e == cudaSuccess ? BC_OK : cuda_fail(e, "eval launch");
+    }
+    if (du || dx || dv || dg) {
+        set_error("bc_eval_points_grad: u, xy, val and grad must all be device or all host memory");
+        return BC_ERR_ARG;
+    }
+    for (int64_t k = 0; k < n; k++) {
+        const double x = xy[2 * k], y = xy[2 * k + 1];
+        if (!(x >= h.x0 && x <= h.x0 + h.L && y >= h.y0 && y <= h.y0 + h.L)) {
+            set_error("bc_eval_points_grad: point %lld outside the root box", (long long)k);
+            return BC_ERR_ARG;
+        }
+    }
+    const size_t nu = size_t(h.nleaf) * ctx->NP;
+    double *du_ = nullptr, *dxy = nullptr, *dval = nullptr, *dgrad = nullptr;
+    std::vector<void *> tmp;
+    if ((e = dev_upload(tmp, &du_, u, nu)) != cudaSuccess || (e = dev_upload(tmp, &dxy, xy, size_t(2 * n))) != cudaSuccess ||
+        (e = dev_upload<double>(tmp, &dval, nullptr, size_t(n))) != cudaSuccess ||
+        (e = dev_upload<double>(tmp, &dgrad, nullptr, size_t(2 * n))) != cudaSuccess) {
+        free_all(tmp);
+        return cuda_fail(e, "eval staging");
+    }
+    e = launch_eval_points_grad(a, tree->d, du_, dxy, n, dval, dgrad, h.x0, h.y0, h.L, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(val, dval, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad, dgrad, size_t(2 * n) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    free_all(tmp);
+    return e == cudaSuccess ? BC_OK : cuda_fail(e, "eval");
+}
+
 bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy, int64_t n,
                          double *out, void *stream)
 {

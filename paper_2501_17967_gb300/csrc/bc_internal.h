@@ -377,6 +377,9 @@ struct BatchPtrs {
     int n;
 };
 cudaError_t launch_batch_copy(const BatchPtrs &bp, bool gather, double *union_buf, int NP, cudaStream_t st);
+cudaError_t launch_eval_points_grad(const PassArgs &a, const DevTree &d, const double *u, const double *xy,
+                                    int64_t n, double *val, double *grad, double x0, double y0, double L,
+                                    cudaStream_t stream);
 cudaError_t launch_eval_points(const PassArgs &a, const DevTree &d, const double *u, const double *xy,
                                int64_t n, double *out, double x0, double y0, double L,
                                cudaStream_t stream);

@@ -1259,6 +1259,102 @@ __global__ void k_eval_points(int64_t n, const double *__restrict__ xy, const do
     }
 }
 
+// -------------------------------------------------------------------------
+// Value and gradient of the leaf interpolant at points (v_bulk and its
+// gradient off the grid, as the glue step needs them on the fictitious curve):
+// the point's leaf is found as in k_eval_points; with xi its reference
+// coordinate, l_j the barycentric Lagrange basis (weights lam_j) and
+// w_j = lam_j / (xi - x_j), S = sum w_j, T = sum w_j / (xi - x_j):
+//     l_j = w_j / S,   l'_j = l_j (T/S - 1/(xi - x_j))   (j not the nearest node m)
+//     l'_m = l_m sum_{k != m} lam_k (x_k - x_m) / (xi - x_k)^2 / (lam_m + d sum_{k != m} w_k),
+// d = xi - x_m, which is the same quantity without the cancellation of
+// T/S - 1/d as the point nears x_m; at a node the differentiation matrix
+// D_mj = (lam_j / lam_m) / (x_m - x_j), D_mm = -sum_{j != m} D_mj.
+// grad u = (1/r) (sum l_jy sum l'_jx u, sum l'_jy sum l_jx u).
+// -------------------------------------------------------------------------
+__device__ void bary_with_derivative(int p, double xi, double *l, double *dl)
+{
+    const double pi = 3.14159265358979323846;
+    double xn[kMaxP], lam[kMaxP];
+    int m = 0;
+    for (int k = 0; k < p; k++) {
+        const double th = (2.0 * k + 1.0) * pi / (2.0 * p);
+        xn[k] = -cos(th);
+        lam[k] = ((k & 1) ? -1.0 : 1.0) * sin(th);
+        if (fabs(xi - xn[k]) < fabs(xi - xn[m])) m = k;
+    }
+    const double d = xi - xn[m];
+    if (fabs(d) < 1e-250) {   // at the node (closer than any w_k could be formed without overflow)
+        double dmm = 0.0;
+        for (int j = 0; j < p; j++) {
+            l[j] = j == m ? 1.0 : 0.0;
+            if (j == m) continue;
+            dl[j] = (lam[j] / lam[m]) / (xn[m] - xn[j]);
+            dmm -= dl[j];
+        }
+        dl[m] = dmm;
+        return;
+    }
+    double S = 0.0, T = 0.0, Sr = 0.0, Q = 0.0;   // Sr = sum_{k != m} w_k, Q = sum_{k != m} lam_k (x_k - x_m)/(xi - x_k)^2
+    for (int k = 0; k < p; k++) {
+        const double e = xi - xn[k], w = lam[k] / e;
+        S += w;
+        T += w / e;
+        if (k != m) {
+            Sr += w;
+            Q += lam[k] * (xn[k] - xn[m]) / (e * e);
+        }
+    }
+    for (int j = 0; j < p; j++) {
+        l[j] = (lam[j] / (xi - xn[j])) / S;
+        dl[j] = j == m ? l[j] * Q / (lam[m] + d * Sr) : l[j] * (T / S - 1.0 / (xi - xn[j]));
+    }
+}
+
+__global__ void k_eval_points_grad(int64_t n, const double *__restrict__ xy, const double *__restrict__ u,
+                                   const int32_t *__restrict__ child0, const int32_t *__restrict__ box_leaf,
+                                   const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_ix,
+                                   const int32_t *__restrict__ box_iy, double x0, double y0, double L, int p,
+                                   double *__restrict__ val, double *__restrict__ grad)
+{
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < n; k += int64_t(gridDim.x) * blockDim.x) {
+        const double x = xy[2 * k], y = xy[2 * k + 1];
+        if (!(x >= x0 && x <= x0 + L && y >= y0 && y <= y0 + L)) {
+            val[k] = grad[2 * k] = grad[2 * k + 1] = nan("");
+            continue;
+        }
+        int b = 0;
+        while (box_leaf[b] < 0) {
+            const int lv = box_level[b];
+            const double h = ldexp(L, -lv);
+            const double mx = x0 + (box_ix[b] + 0.5) * h, my = y0 + (box_iy[b] + 0.5) * h;
+            b = child0[b] + (x >= mx ? 1 : 0) + (y >= my ? 2 : 0);
+        }
+        const int lv = box_level[b];
+        const double h = ldexp(L, -lv), r = 0.5 * h;
+        const double xi = (x - (x0 + (box_ix[b] + 0.5) * h)) / r, eta = (y - (y0 + (box_iy[b] + 0.5) * h)) / r;
+        double lx[kMaxP], ly[kMaxP], dlx[kMaxP], dly[kMaxP];
+        bary_with_derivative(p, xi, lx, dlx);
+        bary_with_derivative(p, eta, ly, dly);
+        const double *ub = u + int64_t(box_leaf[b]) * p * p;
+        double v = 0.0, gx = 0.0, gy = 0.0;
+        for (int jy = 0; jy < p; jy++) {
+            double row = 0.0, drow = 0.0;
+            for (int jx = 0; jx < p; jx++) {
+                const double uv = ub[jy * p + jx];
+                row = fma(lx[jx], uv, row);
+                drow = fma(dlx[jx], uv, drow);
+            }
+            v = fma(ly[jy], row, v);
+            gx = fma(ly[jy], drow, gx);
+            gy = fma(dly[jy], row, gy);
+        }
+        val[k] = v;
+        grad[2 * k] = gx / r;
+        grad[2 * k + 1] = gy / r;
+    }
+}
+
 inline int grid_for(int64_t n, int cap = 152 * 16)
 {
     return int(n < cap ? (n > 0 ? n : 1) : cap);
@@ -1638,6 +1734,16 @@ cudaError_t launch_batch_copy(const BatchPtrs &bp, bool gather, double *union_bu
     if (total <= 0) return cudaSuccess;
     const int grid = int(std::min<int64_t>((total + 255) / 256, 152 * 8));
     k_batch_copy<<<grid, 256, 0, st>>>(bp, gather, union_buf, NP);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_points_grad(const PassArgs &a, const DevTree &d, const double *u, const double *xy, int64_t n,
+                                    double *val, double *grad, double x0, double y0, double L, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int grid = int(std::min<int64_t>((n + 127) / 128, 152 * 8));
+    k_eval_points_grad<<<grid, 128, 0, st>>>(n, xy, u, d.box_child0, d.box_leaf, d.box_level, d.box_ix, d.box_iy,
+                                             x0, y0, L, a.p, val, grad);
     return cudaGetLastError();
 }
 
