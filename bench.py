@@ -298,6 +298,11 @@ def launches_per_apply(prec, overlap, st):
 
 
 def run_batch64(args):
+    import torch
+    print(json.dumps(batch64_line(args, torch.cuda.current_device())))
+
+
+def batch64_line(args, dev):
     """64 independent Gaussian-sum densities on their own adaptive trees, p in
     {8, 12, 16} round-robin; one batch (union of trees, CUDA graph, autotuned
     launch shapes) per order.  A step = forward + adjoint of all 64."""
@@ -305,7 +310,6 @@ def run_batch64(args):
 
     import paper_2501_17967_gb300 as bc
     from paper_2501_17967_gb300 import synth
-    dev = torch.cuda.current_device()
     ctxs = {p: bc.Context(p=p, nterms=args.nterms, device=dev) for p in (8, 12, 16)}
     groups = {8: [], 12: [], 16: []}
     t0 = time.perf_counter()
@@ -358,7 +362,7 @@ def run_batch64(args):
                        "launch_shapes": {str(p): batches[p].shape(prec[p], 0) for p in groups},
                        "l2": "flushed (256 MB write) between timed steps"},
             "clocks": clocks.summary()}
-    print(json.dumps(line))
+    return line
 
 
 class Runner:
@@ -439,9 +443,13 @@ def rooflines(stage_ms, wk, peaks, traffic):
     return out
 
 
+# FP64 pipe: 1.25 TFLOP/s nominal over 152 SMs at 2070 MHz is 4 flop per clock
+# per SM (one 32-lane DFMA warp instruction per 16 clocks per SM)
+FP64_FLOP_PER_CLK_SM = 4.0
 PEAK_SOURCE = {"tensor": "MEASURED_PEAKS.json bf16_tflops (burst), of measured",
-               "alu": "FP64 FMA throughput measured in this run (bc_debug_fp64_peak, 8 blocks/SM of independent "
-                      "FMA chains), of measured; nominal 1.25 TFLOP/s",
+               "alu": "FP64 pipe derived from unit rate and clock: SMs x 4 flop/clk/SM x max SM clock "
+                      "(1.259 TFLOP/s at 152 SMs, 2070 MHz; nominal 1.25), of derived; the FMA probe of this "
+                      "run is fp64_probe_tflops",
                "hbm": "MEASURED_PEAKS.json hbm_gbs, of measured"}
 
 
@@ -527,7 +535,10 @@ def main():
             peaks_file = json.load(fh_)
     except OSError:
         pass
-    peaks = {"fp64": bc.fp64_peak_tflops(dev), "bf16": peaks_file.get("bf16_tflops", 1900.0),
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = clocks.summary().get("sm_max_mhz") or 2070.0
+    fp64_probe = bc.fp64_peak_tflops(dev)
+    peaks = {"fp64": FP64_FLOP_PER_CLK_SM * sms * sm_max * 1e6 / 1e12, "bf16": peaks_file.get("bf16_tflops", 1900.0),
              "hbm": peaks_file.get("hbm_gbs", 6800.0)}
     nleaf_far = int((lv >= 2).sum())
 
@@ -545,6 +556,7 @@ def main():
     per_stage = rooflines(stage_ms, arrangement_work(head), peaks,
                           TRAFFIC.get((args.workload, P1, args.precision), {}))
     roofline = dominant(per_stage)
+    roofline["fp64_probe_tflops"] = round(fp64_probe, 4)
     roofline["stages"] = per_stage
 
     pname = {v: k for k, v in PRECISIONS.items()}
@@ -578,6 +590,10 @@ def main():
             ms2, _ = run2.timed(head, args.steps, args.warmup, stages=False)
             line["adaptive20"] = {"workload": WORKLOADS["adaptive20"][1], "nleaf": int(tree2.nleaf),
                                   "value": world * tree2.nleaf * P * P / (ms2 * 1e-3), "ms_per_step": ms2}
+        # the 64-tree batch (p = 8, 12, 16) in the headline precision
+        b64 = batch64_line(args, dev)
+        line["batch64"] = {k: b64[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "clocks")}
+        line["batch64"]["value"] *= world
 
     if rank == 0 and not args.no_extras:
         # error against the oracle per level, forward (every node of 2 leaves

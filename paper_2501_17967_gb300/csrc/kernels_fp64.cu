@@ -424,7 +424,9 @@ __constant__ double c_binom[32][32];
 // (adjoint, the conjugate transpose of the reversed pair) S_c[k] =
 // (-1)^k conj(d)^-k, W_c[o] = conj(d)^-o, B = c_binom transposed.  The log
 // r_b term is the level term of the box's own local expansion (r-scaled A_0
-// of each source times log r_b).  Boxes without V entries get 0.
+// of each source times log r_b).  Boxes without V entries get 0.  Since
+// S_c[k] = (-1)^k W_c[k], the kernel reads the W table only and carries the
+// sign (-1)^k in its binomial column.
 // The block is NG groups of P1 threads: thread (g, o) owns output o of the
 // pairs v0 + g, v0 + g + NG, ...; per pair the group first forms a(e) in
 // shared memory (thread o its coefficient o), then every thread contracts it
@@ -452,7 +454,8 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
     for (int k = 0; k < PMAX; k++) {
         // tri = 1 keeps only the terms with k + o <= P (and exactly their transpose)
         const bool keep = !tri || (ADJ ? (o == 0 || k + o < P1) : (k == 0 || k + o < P1));
-        bcol[k] = (act && k < P1 && keep) ? (ADJ ? c_binom[o][k] : c_binom[k][o]) : 0.0;
+        const double sg = (k & 1) ? -1.0 : 1.0;   // (-1)^k of S_c[k]
+        bcol[k] = (act && k < P1 && keep) ? sg * (ADJ ? c_binom[o][k] : c_binom[k][o]) : 0.0;
     }
     // The dependents (the persistent downward pass) are released only at the
     // end: released early, their resident blocks would take the SM space that
@@ -470,7 +473,9 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
             __syncthreads();   // the previous pair's a(e) has been read
             if (live) {
                 c = v_code[e];
-                const double2 A = in[int64_t(v_src[e]) * P1 + o], S = dsig[c * P1 + o];
+                // S_c[k] = (-1)^k W_c[k]: the sign is in bcol, so one table
+                // serves both scalings
+                const double2 A = in[int64_t(v_src[e]) * P1 + o], S = dpow[c * P1 + o];
                 arow[o] = make_double2(fma(A.x, S.x, -A.y * S.y), fma(A.x, S.y, A.y * S.x));
             }
             __syncthreads();

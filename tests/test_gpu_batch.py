@@ -65,6 +65,43 @@ def test_batch_autotune_and_oracle(batch_setup):
         assert np.abs(got - ref).max() / np.abs(ref).max() < 1e-10
 
 
+@pytest.mark.parametrize("p", [8, 12, 16])
+def test_batch_oracle_sample_per_order(batch_setup, p):
+    """Batched forward and adjoint of one tree of each order against the
+    oracle: every node of 8 random leaves (forward), and 8 adjoint columns
+    with g random on 6 leaves and zero elsewhere; FP64, and split where the
+    order provides it.  Bar 1e-10 relative max-norm (Sec. 4)."""
+    ctxs, per_p = batch_setup
+    items = per_p[p]
+    batch = bc.Batch(ctxs[p], [t for t, _, _ in items])
+    k = int(np.argmax([t.nleaf for t, _, _ in items]))   # the largest tree of this order
+    t, g, f = items[k]
+    lv, ix, iy = t.leaves()
+    geom = synth.leaf_geometry(lv, ix, iy)
+    pick = synth.sample_leaves(t.nleaf, 8, seed=p)
+    ref = oracle.potential_at_nodes(p, geom, f.cpu().numpy().reshape(-1, p, p), leaf_ids=pick)
+    rng = np.random.default_rng(p)
+    S = np.sort(rng.choice(t.nleaf, 6, replace=False))
+    gl = [torch.zeros_like(ff) for _, _, ff in items]
+    gv = np.zeros((t.nleaf, p * p))
+    gv[S] = rng.standard_normal((6, p * p))
+    gl[k] = torch.from_numpy(gv.reshape(-1)).cuda().reshape(gl[k].shape)
+    cols = [(int(b), int(j)) for b, j in zip(np.r_[S[:4], rng.choice(t.nleaf, 4)], rng.integers(0, p * p, 8))]
+    href = oracle.adjoint_columns(p, geom, gv, cols, target_leaves=S)
+    precs = [bc.FP64] + ([bc.SPLIT_BF16] if p in bc.SPLIT_ORDERS else [])
+    for prec in precs:
+        outs = [torch.empty_like(ff) for _, _, ff in items]
+        batch.run([ff for _, _, ff in items], outs, precision=prec)
+        got = outs[k].cpu().numpy().reshape(-1, p * p)[pick]
+        ef = np.abs(got - ref).max() / np.abs(ref).max()
+        adj = [torch.empty_like(ff) for _, _, ff in items]
+        batch.run(gl, adj, precision=prec, adjoint=True)
+        h = adj[k].cpu().numpy().reshape(-1, p * p)
+        ea = np.abs(np.array([h[b, j] for b, j in cols]) - href).max() / np.abs(href).max()
+        print(f"batch p={p} precision {prec} ({t.nleaf} leaves): forward {ef:.2e}, adjoint {ea:.2e}")
+        assert ef < 1e-10 and ea < 1e-10, (ef, ea)
+
+
 def test_batch_rejects_mixed_contexts(batch_setup):
     ctxs, per_p = batch_setup
     with pytest.raises(bc.BoxCodeError):
