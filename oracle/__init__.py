@@ -10,7 +10,8 @@ It evaluates (paper Sec. 3.2, eq. (vbulk); Phi as in Sec. 2)
     u(x) = (1/2pi) * sum_B int_B log|x - y| f_B(y) dy
 
 by direct singular quadrature per (target, leaf); see ``oracle.c`` for the
-method.  Nodes are first-kind Chebyshev points, ascending; leaf values are
+method.  It also evaluates the glue layer potential S[sigma] - D[tau] of
+Sec. 3.4 on a discretised curve by direct summation (``layer``).  Nodes are first-kind Chebyshev points, ascending; leaf values are
 stored [leaf][jy][jx].
 
 Parity status of each function is stated in its docstring; every one is
@@ -57,6 +58,8 @@ def _load():
         lib.oracle_gradient.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp, ctypes.c_int64, dp,
                                         i64p, i64p, dp, ctypes.c_int]
         lib.oracle_gradient.restype = ctypes.c_int
+        lib.oracle_layer.argtypes = [ctypes.c_int64, dp, dp, dp, ctypes.c_int64, dp, dp, ctypes.c_int]
+        lib.oracle_layer.restype = ctypes.c_int
         lib.oracle_nodes.argtypes = [ctypes.c_int, dp]
         lib.oracle_nodes.restype = None
         lib.oracle_s_rule.argtypes = [ctypes.c_int, dp, dp, dp]
@@ -147,6 +150,26 @@ def gradient(p: int, geom: np.ndarray, f: np.ndarray, targets: np.ndarray, nthre
                                  _dp(out), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_gradient failed ({rc})")
+    return out
+
+
+def layer(src: np.ndarray, q: np.ndarray, m: np.ndarray, targets: np.ndarray, nthreads: int = 0) -> np.ndarray:
+    """The glue potential S[sigma] - D[tau] of Sec. 3.4 discretised on curve
+    nodes src[n, 2] with q_j = w_j sigma_j and dipoles m[n, 2] = w_j tau_j n_j:
+    -(1/2pi) sum_j [q_j log|x - y_j| + m_j . (x - y_j)/|x - y_j|^2] at targets
+    [nt, 2] (direct sum; coincident pairs skipped).  Pinned by the circle's
+    closed forms (single layer -R log R inside, -R log|x| outside; double
+    layer: Gauss's identity, 1 inside and 0 outside)."""
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 2)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    m = np.ascontiguousarray(m, dtype=np.float64).reshape(-1, 2)
+    t = np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 2)
+    if q.shape[0] != src.shape[0] or m.shape[0] != src.shape[0]:
+        raise ValueError("q, m and src differ in length")
+    out = np.empty(t.shape[0], dtype=np.float64)
+    if _load().oracle_layer(src.shape[0], _dp(src), _dp(q), _dp(m), t.shape[0], _dp(t), _dp(out),
+                            int(nthreads)) != 0:
+        raise RuntimeError("oracle_layer failed")
     return out
 
 

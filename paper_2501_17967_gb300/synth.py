@@ -80,6 +80,32 @@ def batch_density(k: int) -> tuple[GaussianSum, int, float]:
     return gaussians(n, 1000 + k, wlog10=(wmin, -0.9)), p, max(1e-11, 10.0 ** (-p))
 
 
+def fictitious_curve_sources(n_panels: int = 256, q: int = 16, r0: float = 0.8, amp: float = 0.1, k: int = 5,
+                             strip: float = 0.08):
+    """Quadrature nodes of the fictitious curve of ``star_domain`` (the smooth
+    curve r(t) = r0 + amp cos(k t) - strip, counterclockwise): n_panels equal
+    panels in t, q Gauss-Legendre nodes each (the paper discretises its
+    curves by Gauss-Legendre panels, Sec. 3.1).  Returns (xy[n, 2], w[n]
+    arc-length weights, normal[n, 2] outward unit normals, t[n])."""
+    g, gw = np.polynomial.legendre.leggauss(q)
+    h = 2.0 * math.pi / n_panels
+    t = ((np.arange(n_panels)[:, None] + 0.5) * h + 0.5 * h * g[None, :]).reshape(-1)
+    wt = np.tile(0.5 * h * gw, n_panels)
+    r = r0 + amp * np.cos(k * t) - strip
+    dr = -amp * k * np.sin(k * t)
+    xy = np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
+    d = np.stack([dr * np.cos(t) - r * np.sin(t), dr * np.sin(t) + r * np.cos(t)], axis=1)
+    speed = np.linalg.norm(d, axis=1)
+    normal = np.stack([d[:, 1], -d[:, 0]], axis=1) / speed[:, None]
+    return xy, wt * speed, normal, t
+
+
+def glue_densities(t: np.ndarray):
+    """Smooth synthetic jump densities on the curve parameter t: sigma (the
+    normal-derivative jump) and tau (the value jump) of Sec. 3.4."""
+    return np.cos(3 * t) + 0.5 * np.sin(5 * t), np.sin(2 * t) + 0.3 * np.cos(7 * t)
+
+
 def random_targets(n: int, seed: int = 101) -> np.ndarray:
     """n points uniform in [-1,1]^2."""
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=(n, 2))

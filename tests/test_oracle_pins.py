@@ -421,3 +421,69 @@ def test_gradient_matches_differences_of_the_potential(oracle_mod):
         fd[:, k] = (oracle_mod.potential(p, geom, f, pts + e) - oracle_mod.potential(p, geom, f, pts - e)) / (2 * h)
     g = oracle_mod.gradient(p, geom, f, pts)
     assert np.abs(g - fd).max() < 1e-6 * np.abs(g).max(), np.abs(g - fd).max()
+
+
+# ---------------------------------------------------------------------------
+# Glue layer potential (Sec. 3.4): closed forms on a circle and Gauss's
+# identity on the star-shaped fictitious curve.
+# ---------------------------------------------------------------------------
+def _circle(n, R, c):
+    th = 2 * np.pi * np.arange(n) / n
+    nrm = np.stack([np.cos(th), np.sin(th)], 1)
+    return np.asarray(c) + R * nrm, np.full(n, 2 * np.pi * R / n), nrm
+
+
+def test_layer_single_layer_circle_closed_form(oracle_mod):
+    """S[1] on a circle of radius R: -R log R inside, -R log|x - c| outside
+    (trapezoid rule, geometrically convergent away from the curve)."""
+    R, c = 0.7, np.array([0.1, -0.05])
+    src, w, nrm = _circle(400, R, c)
+    rng = np.random.default_rng(1)
+    ang = rng.uniform(0, 2 * np.pi, 20)
+    rad_in, rad_out = rng.uniform(0, 0.5 * R, 20), rng.uniform(1.6 * R, 4 * R, 20)
+    pin = c + rad_in[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1)
+    pout = c + rad_out[:, None] * np.stack([np.cos(ang), np.sin(ang)], 1)
+    zero = np.zeros_like(src)
+    uin = oracle_mod.layer(src, w, zero, pin)
+    uout = oracle_mod.layer(src, w, zero, pout)
+    assert np.allclose(uin, -R * np.log(R), rtol=0, atol=1e-13)
+    assert np.allclose(uout, -R * np.log(rad_out), rtol=0, atol=1e-13)
+
+
+def test_layer_double_layer_gauss_identity(oracle_mod):
+    """-D[1] = 1 inside a closed curve and 0 outside (Gauss), on a circle and
+    on the Gauss-Legendre panels of the star-shaped fictitious curve; with
+    a sign flip of the normals the interior value flips too."""
+    R, c = 0.6, np.array([-0.2, 0.15])
+    src, w, nrm = _circle(300, R, c)
+    m = w[:, None] * nrm
+    pts = np.array([c, c + [0.2, 0.1], c + [1.5, 0.0], c + [-0.9, 0.7]])
+    u = oracle_mod.layer(src, np.zeros(len(w)), m, pts)
+    assert np.allclose(u, [1, 1, 0, 0], rtol=0, atol=1e-13)
+    assert np.allclose(oracle_mod.layer(src, np.zeros(len(w)), -m, pts[:2]), [-1, -1], atol=1e-13)
+    # Gauss-Legendre panels on r(t) = 0.72 + 0.1 cos 5t (counterclockwise)
+    g, gw = np.polynomial.legendre.leggauss(16)
+    h = 2 * np.pi / 128
+    t = ((np.arange(128)[:, None] + 0.5) * h + 0.5 * h * g[None, :]).ravel()
+    r, dr = 0.72 + 0.1 * np.cos(5 * t), -0.5 * np.sin(5 * t)
+    xy = np.stack([r * np.cos(t), r * np.sin(t)], 1)
+    d = np.stack([dr * np.cos(t) - r * np.sin(t), dr * np.sin(t) + r * np.cos(t)], 1)
+    sp = np.linalg.norm(d, axis=1)
+    ws, ns = np.tile(0.5 * h * gw, 128) * sp, np.stack([d[:, 1], -d[:, 0]], 1) / sp[:, None]
+    pts = np.array([[0.0, 0.0], [0.3, -0.2], [1.2, 0.4], [-0.95, -0.9]])
+    u = oracle_mod.layer(xy, np.zeros(len(ws)), ws[:, None] * ns, pts)
+    assert np.allclose(u, [1, 1, 0, 0], rtol=0, atol=1e-12)
+
+
+def test_layer_linearity_and_coincident_source(oracle_mod):
+    """Charges and dipoles add; a target on a source node skips that pair
+    only (the rest of the sum is unchanged)."""
+    rng = np.random.default_rng(4)
+    src = rng.uniform(-1, 1, (30, 2))
+    q, m = rng.standard_normal(30), rng.standard_normal((30, 2))
+    t = np.vstack([rng.uniform(-1, 1, (5, 2)), src[7:8]])
+    both = oracle_mod.layer(src, q, m, t)
+    sep = oracle_mod.layer(src, q, 0 * m, t) + oracle_mod.layer(src, 0 * q, m, t)
+    assert np.allclose(both, sep, rtol=1e-14, atol=1e-14)
+    keep = np.arange(30) != 7
+    assert np.isclose(both[-1], oracle_mod.layer(src[keep], q[keep], m[keep], t[-1:])[0], rtol=1e-14)
