@@ -225,6 +225,37 @@ bc_status bc_eval_points(bc_ctx *ctx, const bc_tree *tree, const double *u, cons
 bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u, const double *xy, int64_t n,
                               double *val, double *grad, void *stream);
 
+/* Glue layer potential (Sec. 3.4): v_glue = S[sigma] - D[tau] on the
+ * fictitious curve, with S[s](x) = int Phi(x,y) s(y) dy, D[t](x) = int
+ * dPhi(x,y)/dn_y t(y) dy and Phi = (1/2pi) log(1/|x-y|), evaluated by the
+ * fast multipole method at every leaf node of a tree (the step that, with the
+ * box code, gives the particular solution at the nodes; Sec. 4.1 times it).
+ * The curve is discretised by quadrature nodes y_j (weights w_j, unit normals
+ * n_j); with q_j = w_j sigma(y_j) and m_j = w_j tau(y_j) n_j (a vector):
+ *
+ *     u(x_i) = -(1/2pi) sum_j [ q_j log|x_i - y_j| + m_j . (x_i - y_j) / |x_i - y_j|^2 ]
+ *
+ * at every leaf node x_i ([nleaf][p][p], as the applies).  A source that
+ * coincides with a node contributes nothing there.  FP64; the far field uses
+ * the tree's expansions and lists (error of the expansion order, as the
+ * volume apply), the near field is summed directly.
+ *
+ * bc_layer_create: the sources xy[n][2] (host, read during the call), inside
+ * the root box (else BC_ERR_ARG), are sorted into the tree's leaves, and the
+ * tree's lists are kept only where the source side holds sources.  The layer
+ * keeps the tree (destroy the layer first) and shares its workspaces: an
+ * apply of any kind on the same tree must not overlap a layer apply.
+ * bc_layer_apply: q[n], m[n][2] in the order of xy, u[nleaf*p*p]; device
+ * pointers (ordered on `stream`) or host pointers (staged, synchronous), all
+ * of one kind.
+ * bc_layer_info: counts[6] = sources, V pairs, W pairs, X entries,
+ * (target leaf, near source) pairs, leaves holding sources. */
+typedef struct bc_layer bc_layer;
+bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer **out);
+bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const double *m, double *u, void *stream);
+bc_status bc_layer_info(const bc_layer *layer, int64_t *counts);
+void bc_layer_destroy(bc_layer *layer);
+
 /* Batched applies: many independent densities on different trees (all of
  * this context's p and root side L) in one launch per pass.  Not in the
  * paper (its solver applies one box code at a time).  A batch is the

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "SPLIT_BF16_ALL", "apply",
-           "apply_adjoint", "eval_points", "eval_points_grad", "BoxCodeApply", "lib_path"]
+           "apply_adjoint", "eval_points", "eval_points_grad", "Layer", "BoxCodeApply", "lib_path"]
 
 # precision modes (bc_precision): FP64 everywhere; BF16 digit products for the
 # fixed-operator contractions (near field, P2M, L2P, W and X lists) with the
@@ -84,6 +84,10 @@ SIGNATURES = [
     ("bc_apply_adjoint", ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_eval_points", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP]),
     ("bc_eval_points_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
+    ("bc_layer_create", ctypes.c_int, [_VP, _DP, _I64, ctypes.POINTER(_VP)]),
+    ("bc_layer_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("bc_layer_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    ("bc_layer_destroy", None, [_VP]),
     ("bc_batch_create", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
     ("bc_batch_destroy", None, [_VP]),
     ("bc_batch_nleaf", _I64, [_VP]),
@@ -406,6 +410,54 @@ def eval_points_grad(tree: Tree, u, xy, stream=None):
                                        ctypes.c_void_p(grad.data_ptr()),
                                        _stream_ptr(stream) if xy.is_cuda else None))
     return val, grad
+
+
+class Layer:
+    """Point sources on a curve (the fictitious curve of Sec. 3.4) in the
+    leaves of a tree, for the FMM evaluation of the glue potential
+    S[sigma] - D[tau] at every leaf node: u = -(1/2pi) sum_j [q_j log|x - y_j|
+    + m_j.(x - y_j)/|x - y_j|^2] with q_j = w_j sigma_j, m_j = w_j tau_j n_j.
+    The layer keeps the tree alive and shares its workspaces."""
+
+    def __init__(self, tree: Tree, xy):
+        self.tree = tree
+        pts = np.ascontiguousarray(xy, dtype=np.float64).reshape(-1, 2)
+        self.n = pts.shape[0]
+        h = _VP()
+        _check(_load().bc_layer_create(tree.handle, pts.ctypes.data_as(_DP), self.n, ctypes.byref(h)))
+        self._h = h
+
+    def info(self) -> dict:
+        c = (ctypes.c_int64 * 6)()
+        _check(_load().bc_layer_info(self._h, c))
+        return dict(zip(("sources", "n_v", "n_w", "n_x", "near_pairs", "leaves_with_sources"), (int(v) for v in c)))
+
+    def apply(self, q, m, out=None, stream=None):
+        """u at every leaf node ([nleaf * p * p]) from charges q[n] and dipoles
+        m[n, 2]; device tensors (on `stream`) or host tensors."""
+        import torch
+        q = q.contiguous()
+        m = m.contiguous()
+        if q.dtype != torch.float64 or m.dtype != torch.float64 or q.numel() != self.n or m.numel() != 2 * self.n:
+            raise ValueError("q must be float64 [n] and m float64 [n, 2]")
+        NP = self.tree.ctx.p ** 2
+        if out is None:
+            out = torch.empty(self.tree.nleaf * NP, dtype=torch.float64, device=q.device)
+        _check(_load().bc_layer_apply(self.tree.ctx.handle, self._h, ctypes.c_void_p(q.data_ptr()),
+                                      ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      _stream_ptr(stream) if q.is_cuda else None))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _load().bc_layer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

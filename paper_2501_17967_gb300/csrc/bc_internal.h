@@ -368,6 +368,39 @@ struct SideStream {
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaEvent_t xdone = nullptr;   // the X-list tiles (first on the side stream) are done
 };
+// Far-field passes for point sources on a tree (the glue layer potential):
+// the caller has written every leaf box's multipole into d.expA and the X-list
+// rows into fl.PX; this clears the flags, climbs (M2M), runs the M2L over the
+// given V lists into d.expB and the downward pass (L2L + X rows) in place.
+// FP64, forward only.
+struct FarLists {
+    const int32_t *v_ptr = nullptr, *v_src = nullptr, *v_code = nullptr;   // per box
+    const int32_t *x_ptr = nullptr, *x_src = nullptr;                        // per box
+    const double2 *PX = nullptr;                                             // [n_x][P1]
+};
+cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
+                              const FarLists &fl, cudaStream_t stream);
+// Point sources of the glue layer potential on a tree (device side): the
+// sources sorted by leaf, their permutation, the scaled strengths, and the
+// tree's lists kept only where the source side holds sources (V: source box
+// with sources in its subtree; W: the same; X: source leaf with sources; near:
+// leaves with sources).
+struct LayerDev {
+    int64_t n = 0, nx = 0;
+    const int32_t *src_ptr = nullptr;   // [nleaf + 1] caller-leaf CSR into the sorted sources
+    const int32_t *perm = nullptr;      // [n] sorted -> caller order
+    const double2 *sxy = nullptr;       // [n]
+    double *cq = nullptr;               // [n] -q / (2 pi), sorted
+    double2 *cm = nullptr;              // [n] -m / (2 pi), sorted
+    const int32_t *v_ptr = nullptr, *v_src = nullptr, *v_code = nullptr;
+    const int32_t *x_ptr = nullptr, *x_src = nullptr, *x_box = nullptr;
+    const int32_t *w_ptr = nullptr, *w_src = nullptr, *w_code = nullptr;
+    const int32_t *n_ptr = nullptr, *n_src = nullptr;
+    double2 *PX = nullptr;              // [nx][P1]
+};
+// u at every leaf node (device pointers: q [n], m [n][2] caller order, u [nleaf][NP]).
+cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
+                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t stream);
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
 struct BatchPtrs {

@@ -1661,6 +1661,46 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     return cudaGetLastError();
 }
 
+cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
+                              const FarLists &fl, cudaStream_t st)
+{
+    const int P1 = a.P1, NP = a.NP;
+    const OpSet &op = tb.fwd;
+    cudaError_t ce;
+    const int64_t nf = int64_t(h.box_level.size());
+    ce = launch_pdl(k_clear_flags, grid_for((nf + 255) / 256, 152), 256, 0, st, d.flag, nf);
+    if (ce != cudaSuccess) return ce;
+    if (h.nlevels <= 2) return cudaSuccess;
+    const long long glimit = std::max(1ll, a.wait_limit / 16);
+    if (h.nlevels > 3) {
+        // climb only: the leaf expansions were written by the caller
+        const size_t shU = up_smem_bytes_f64(NP, P1, op.up_f.T, op.up_f.maxp);
+        ce = launch_pdl(k_up_levels<false, false>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
+                        d.leaf_level, d.level_start, h.nlevels, d.box_child0, (const double *)nullptr,
+                        (const double2 *)nullptr, op.leafA_df, op.up_s, op.up_f, d.expA, d.exdf, NP, P1, d.lvtab,
+                        true, d.flag, (const uint8_t *)nullptr, glimit, a.err);
+        if (ce != cudaSuccess) return ce;
+    }
+    {
+        const int64_t b0 = h.level_start[2], b1 = a.nbox;
+        const int ng = m2l_groups(P1), nth = m2l_threads(P1);
+        const size_t shM = sizeof(double2) * ng * (P1 + 1);
+        const int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : 8));
+#define BC_M2LP(PM)                                                                                             \
+    ce = launch_pdl(k_m2l_boxes<false, PM>, grid, nth, shM, st, b0, b1, fl.v_ptr, fl.v_src, fl.v_code,          \
+                    d.box_level, (const double2 *)nullptr, tb.dpow_f, tb.logd, d.lvtab, d.expA, d.expB, P1, ng, 0)
+        if (P1 <= 16) BC_M2LP(16);
+        else if (P1 <= 24) BC_M2LP(24);
+        else BC_M2LP(32);
+#undef BC_M2LP
+        if (ce != cudaSuccess) return ce;
+    }
+    return launch_pdl(k_down_warps, a.down_blocks, 128, down_warps_smem_bytes(P1, op.par_f.T, op.par_f.maxp, 4), st,
+                      d.level_start, h.nlevels, fl.v_ptr, d.Pv, fl.x_ptr, fl.x_src, fl.PX, P1, d.leaf_box, d.expA,
+                      d.box_parent, d.box_ix, d.box_iy, op.par_f, d.expB, P1, d.lvtab, (const int32_t *)nullptr,
+                      fl.v_code, tb.logd, true, d.flag, glimit, a.err);
+}
+
 cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int f_T, int f_maxp, int up_per_sm, int down_per_sm,
                          int *up_blocks, int *shift_blocks, int *down_blocks)
 {

@@ -1,0 +1,262 @@
+// FMM evaluation of the glue layer potential at every leaf node of a tree.
+//
+// The glue step of the solver (Sec. 3.4) patches the bulk and strip
+// solutions together with v_glue = S[sigma] - D[tau] on the fictitious curve,
+// a single-layer and a double-layer Laplace potential with Phi = (1/2pi)
+// log(1/|x - y|); discretised on the curve's quadrature nodes y_j (weights
+// w_j, unit normals n_j) with q_j = w_j sigma_j and m_j = w_j tau_j n_j:
+//
+//   u(x) = -(1/2pi) sum_j [ q_j log|x - y_j| + Re(m_j / (x - y_j)) ]
+//
+// (points as complex numbers; Re(m / (x - y)) = m.(x - y)/|x - y|^2).  The
+// sources are point charges and dipoles; the far field runs through the same
+// expansions, lists and level passes as the volume potential (multipoles in
+// the scaled form of the leaf-to-expansion step, M2M, M2L, L2L), with these
+// point-source steps around them:
+//   P2M  (leaf box of centre c, half-side r, eta = (y - c)/r):
+//        M_0 = sum c_q,  M_k = sum [ -c_q eta^k / k + (c_m / r) eta^(k-1) ]
+//   P2L  (X list: source leaf c, target box b one level finer, e = (c_b - c_c)/r_c,
+//        w = e - eta, the target's own coordinate rho = (x - c_b)/r_b):
+//        L_0 = sum [ c_q log|w| + (c_m / r_c) / w ]     (c_q log r_c: downward pass)
+//        L_l = sum (-1)^l (2w)^-l [ -c_q / l + (c_m / r_c) / w ]
+//   M2P  (W list) and L2P as for the volume potential, near field direct;
+// with c_q = -q / (2 pi), c_m = -m / (2 pi).  A source that coincides with a
+// target node contributes nothing.  FP64 throughout.
+#include <cuda_runtime.h>
+
+#include "bc_internal.h"
+
+namespace bc {
+namespace {
+
+constexpr double kInvTwoPi = 0.159154943091895335768883763372514362;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cinv(double2 a)
+{
+    const double d = 1.0 / fma(a.x, a.x, a.y * a.y);
+    return make_double2(a.x * d, -a.y * d);
+}
+// a^n (n >= 0) by binary powering
+__device__ __forceinline__ double2 cpow(double2 a, int n)
+{
+    double2 r = make_double2(1.0, 0.0);
+    while (n > 0) {
+        if (n & 1) r = cmul(r, a);
+        a = cmul(a, a);
+        n >>= 1;
+    }
+    return r;
+}
+
+struct BoxGeom {
+    double cx, cy, r;
+};
+__device__ __forceinline__ BoxGeom box_geom(int b, const int32_t *box_level, const int32_t *box_ix,
+                                            const int32_t *box_iy, double x0, double y0, double L)
+{
+    const double h = ldexp(L, -box_level[b]);
+    return {x0 + (box_ix[b] + 0.5) * h, y0 + (box_iy[b] + 0.5) * h, 0.5 * h};
+}
+
+// the strengths in sorted order, scaled by -1/(2 pi)
+__global__ void k_layer_gather(int64_t n, const int32_t *__restrict__ perm, const double *__restrict__ q,
+                               const double *__restrict__ m, double *__restrict__ cq, double2 *__restrict__ cm)
+{
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        const int64_t j = perm[i];
+        cq[i] = -kInvTwoPi * q[j];
+        cm[i] = make_double2(-kInvTwoPi * m[2 * j], -kInvTwoPi * m[2 * j + 1]);
+    }
+}
+
+// P2M: one warp per leaf, lane k its coefficient; every leaf box is written
+// (zero without sources: the climb reads all children)
+__global__ void k_layer_p2m(int64_t nleaf, const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy,
+                            const double *__restrict__ cq, const double2 *__restrict__ cm,
+                            const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_level,
+                            const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy, double x0,
+                            double y0, double L, int P1, double2 *__restrict__ ex)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t leaf = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); leaf < nleaf; leaf += nw) {
+        const int b = leaf_box[leaf];
+        const BoxGeom g = box_geom(b, box_level, box_ix, box_iy, x0, y0, L);
+        const double ir = 1.0 / g.r;
+        double2 acc = make_double2(0.0, 0.0);
+        const int k = lane;
+        for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
+            const double2 y = sxy[j];
+            const double2 eta = make_double2((y.x - g.cx) * ir, (y.y - g.cy) * ir);
+            const double c = cq[j];
+            if (k == 0) {
+                acc.x += c;
+            } else if (k < P1) {
+                const double2 e1 = cpow(eta, k - 1), ek = cmul(e1, eta);
+                const double2 d = cmul(make_double2(cm[j].x * ir, cm[j].y * ir), e1);
+                acc.x += fma(-c / k, ek.x, d.x);
+                acc.y += fma(-c / k, ek.y, d.y);
+            }
+        }
+        if (k < P1) ex[int64_t(b) * P1 + k] = acc;
+    }
+}
+
+// P2L of the X list: one warp per entry, lane l its coefficient
+__global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__restrict__ x_src,
+                            const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy,
+                            const double *__restrict__ cq, const double2 *__restrict__ cm,
+                            const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_level,
+                            const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy, double x0,
+                            double y0, double L, int P1, double2 *__restrict__ PX)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t x = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); x < nx; x += nw) {
+        const int leaf = x_src[x];
+        const BoxGeom gc = box_geom(leaf_box[leaf], box_level, box_ix, box_iy, x0, y0, L);
+        const BoxGeom gb = box_geom(x_box[x], box_level, box_ix, box_iy, x0, y0, L);
+        const double ir = 1.0 / gc.r;
+        const double2 e = make_double2((gb.cx - gc.cx) * ir, (gb.cy - gc.cy) * ir);
+        const int l = lane;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
+            const double2 y = sxy[j];
+            const double2 w = make_double2(e.x - (y.x - gc.cx) * ir, e.y - (y.y - gc.cy) * ir);
+            const double2 iw = cinv(w);
+            const double2 dm = cmul(make_double2(cm[j].x * ir, cm[j].y * ir), iw);   // (c_m / r_c) / w
+            const double c = cq[j];
+            if (l == 0) {
+                acc.x += fma(c, 0.5 * log(fma(w.x, w.x, w.y * w.y)), dm.x);
+                acc.y += dm.y;
+            } else if (l < P1) {
+                double2 t = cpow(make_double2(0.5 * iw.x, 0.5 * iw.y), l);   // (2w)^-l
+                if (l & 1) t = make_double2(-t.x, -t.y);
+                const double2 s = make_double2(dm.x - c / l, dm.y);
+                const double2 v = cmul(t, s);
+                acc.x += v.x;
+                acc.y += v.y;
+            }
+        }
+        if (l < P1) PX[x * P1 + l] = acc;
+    }
+}
+
+// Leaf output: one block of NP threads per target leaf, thread j its node.
+// u = L2P of the leaf's local expansion (levels >= 2) + the W list's
+// multipoles at the nodes (M2P, with the log r term of the target level) +
+// the direct sum over the sources of the leaf's near leaves.
+constexpr int kSrcChunk = 128;
+__global__ void __launch_bounds__(256)
+k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__restrict__ leaf_box,
+            const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_ix,
+            const int32_t *__restrict__ box_iy, double x0, double y0, double L, const int32_t *__restrict__ w_ptr,
+            const int32_t *__restrict__ w_src, const int32_t *__restrict__ w_code,
+            const int32_t *__restrict__ n_ptr, const int32_t *__restrict__ n_src,
+            const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy, const double *__restrict__ cq,
+            const double2 *__restrict__ cm, const double2 *__restrict__ OpE, const double2 *__restrict__ OpW,
+            const double2 *__restrict__ loc, const double2 *__restrict__ mul, const double *__restrict__ lvtab,
+            int p, int P1, double *__restrict__ u)
+{
+    const int NP = p * p, j = threadIdx.x;
+    __shared__ double2 se[32];
+    __shared__ double2 s_xy[kSrcChunk], s_m[kSrcChunk];
+    __shared__ double s_q[kSrcChunk];
+    const double pi = 3.14159265358979323846;
+    const double xj = -cos((2.0 * (j % p) + 1.0) * pi / (2.0 * p)), yj = -cos((2.0 * (j / p) + 1.0) * pi / (2.0 * p));
+    for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
+        const int o = order[li];
+        const int b = leaf_box[o];
+        const int lvo = box_level[b];
+        const BoxGeom g = box_geom(b, box_level, box_ix, box_iy, x0, y0, L);
+        const double zx = g.cx + g.r * xj, zy = g.cy + g.r * yj;
+        double acc = 0.0;
+        if (lvo >= 2) {
+            __syncthreads();
+            for (int i = j; i < P1; i += blockDim.x) se[i] = loc[int64_t(b) * P1 + i];
+            __syncthreads();
+            for (int l = 0; l < P1; l++) {
+                const double2 op = OpE[l * NP + j], c = se[l];
+                acc = fma(op.x, c.x, fma(-op.y, c.y, acc));
+            }
+        }
+        double lw = 0.0;
+        for (int e = w_ptr[o]; e < w_ptr[o + 1]; e++) {
+            const double2 *op = OpW + size_t(w_code[e]) * P1 * NP;
+            __syncthreads();
+            for (int i = j; i < P1; i += blockDim.x) se[i] = mul[int64_t(w_src[e]) * P1 + i];
+            __syncthreads();
+            for (int k = 0; k < P1; k++) {
+                const double2 opk = op[k * NP + j], c = se[k];
+                acc = fma(opk.x, c.x, fma(-opk.y, c.y, acc));
+            }
+            lw += se[0].x;
+        }
+        acc = fma(lvtab[kLvTab + lvo], lw, acc);
+        // near field, sources staged in chunks
+        double near = 0.0;
+        for (int e = n_ptr[o]; e < n_ptr[o + 1]; e++) {
+            const int s = n_src[e];
+            for (int c0 = src_ptr[s]; c0 < src_ptr[s + 1]; c0 += kSrcChunk) {
+                const int cnt = min(kSrcChunk, src_ptr[s + 1] - c0);
+                __syncthreads();
+                for (int i = j; i < cnt; i += blockDim.x) {
+                    s_xy[i] = sxy[c0 + i];
+                    s_q[i] = cq[c0 + i];
+                    s_m[i] = cm[c0 + i];
+                }
+                __syncthreads();
+                for (int i = 0; i < cnt; i++) {
+                    const double dx = zx - s_xy[i].x, dy = zy - s_xy[i].y;
+                    const double r2 = fma(dx, dx, dy * dy);
+                    if (r2 > 0.0) {
+                        const double ir2 = 1.0 / r2;
+                        near = fma(s_q[i], 0.5 * log(r2), near);
+                        near = fma(fma(s_m[i].x, dx, s_m[i].y * dy), ir2, near);
+                    }
+                }
+            }
+        }
+        u[int64_t(o) * NP + j] = acc + near;
+    }
+}
+
+inline int grid_cap(int64_t n, int cap) { return int(n < cap ? (n > 0 ? n : 1) : cap); }
+
+}  // namespace
+
+cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
+                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t st)
+{
+    cudaError_t e;
+    const int P1 = a.P1;
+    if (ly.n > 0) {
+        k_layer_gather<<<grid_cap((ly.n + 255) / 256, 152 * 8), 256, 0, st>>>(ly.n, ly.perm, q, m, ly.cq, ly.cm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_layer_p2m<<<grid_cap((a.nleaf + 3) / 4, 152 * 8), 128, 0, st>>>(
+        a.nleaf, ly.src_ptr, ly.sxy, ly.cq, ly.cm, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, P1,
+        d.expA);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ly.nx > 0) {
+        k_layer_p2l<<<grid_cap((ly.nx + 3) / 4, 152 * 8), 128, 0, st>>>(
+            ly.nx, ly.x_box, ly.x_src, ly.src_ptr, ly.sxy, ly.cq, ly.cm, d.leaf_box, d.box_level, d.box_ix, d.box_iy,
+            h.x0, h.y0, h.L, P1, ly.PX);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    FarLists fl;
+    fl.v_ptr = ly.v_ptr; fl.v_src = ly.v_src; fl.v_code = ly.v_code;
+    fl.x_ptr = ly.x_ptr; fl.x_src = ly.x_src; fl.PX = ly.PX;
+    if ((e = launch_far_points(a, h, d, tb, fl, st)) != cudaSuccess) return e;
+    k_layer_out<<<grid_cap(a.nleaf, 152 * 8), a.NP, 0, st>>>(
+        a.nleaf, d.leaf_order, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, ly.w_ptr, ly.w_src,
+        ly.w_code, ly.n_ptr, ly.n_src, ly.src_ptr, ly.sxy, ly.cq, ly.cm, tb.fwd.e, tb.fwd.w, d.expB, d.expA, d.lvtab,
+        a.p, P1, u);
+    return cudaGetLastError();
+}
+
+}  // namespace bc

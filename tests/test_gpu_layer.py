@@ -1,0 +1,145 @@
+"""The glue layer potential S[sigma] - D[tau] (Sec. 3.4) by the FMM at every
+leaf node, against the oracle's direct sum and against closed forms.
+
+Cases: the star-shaped domain's truncated tree with Gauss-Legendre sources on
+its fictitious curve and smooth jump densities (W and X lists present,
+sources in leaves of several levels); a circle of sources in an adaptive tree
+(single layer -R log R inside, -R log|x - c| outside; double layer 1 inside
+and 0 outside, at nodes away from the circle); host arrays against device
+arrays; no sources; a source on a node and on leaf edges.
+
+Bar: the near field is summed exactly and the far field carries the
+truncation error of the expansions.  Point sources anywhere in a box,
+corners included, converge like (sqrt 2 / (4 - sqrt 2))^P ~ 0.55^P across
+the V list (smooth volume densities converge much faster): nterms 24 gave
+6e-11..1.5e-10 here, so the layer runs with nterms 30 (the library
+default), a further 0.55^6 ~ 0.03.  The bar is 1e-10 of max |u| over the
+sample (Sec. 4's tolerance); the closed forms hold to the trapezoid rule's
+error (below 1e-14 at the selected nodes) plus the truncation, so the bar
+there is 1e-11 absolute."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import paper_2501_17967_gb300 as bc  # noqa: E402
+from paper_2501_17967_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+P = 16
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return bc.Context(p=P, nterms=30, device=0)
+
+
+@pytest.fixture(scope="module")
+def star(ctx):
+    gamma, gamma_b = synth.star_domain()
+    tree = bc.Tree.refine_truncated(ctx, synth.config_density(2), gamma, gamma_b, eps=1e-11, max_level=18)
+    xy, w, nrm, t = synth.fictitious_curve_sources(256, 16)
+    sig, tau = synth.glue_densities(t)
+    q, m = w * sig, (w * tau)[:, None] * nrm
+    return tree, xy, q, m
+
+
+def _nodes(tree):
+    lv, ix, iy = (np.asarray(a) for a in tree.leaves())
+    geom = synth.leaf_geometry(lv, ix, iy)
+    return lv, geom, oracle.leaf_nodes(geom, P)
+
+
+def _leaves_holding(geom, pts):
+    inside = ((np.abs(pts[:, None, 0] - geom[None, :, 0]) <= geom[None, :, 2])
+              & (np.abs(pts[:, None, 1] - geom[None, :, 1]) <= geom[None, :, 2]))
+    return np.unique(np.nonzero(inside)[1])
+
+
+def test_layer_against_oracle(ctx, star):
+    tree, xy, q, m = star
+    layer = bc.Layer(tree, xy)
+    info = layer.info()
+    assert info["sources"] == len(q) and info["n_w"] > 0 and info["n_v"] > 0
+    u = layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda()).cpu().numpy().reshape(-1, P * P)
+    lv, geom, nodes = _nodes(tree)
+    hold = _leaves_holding(geom, xy)
+    rng = np.random.default_rng(2)
+    pick = np.unique(np.concatenate([rng.choice(hold, 12, replace=False),
+                                     synth.sample_leaves_per_level(lv, 2, seed=5)]))
+    ref = oracle.layer(xy, q, m, nodes[pick].reshape(-1, 2)).reshape(len(pick), P * P)
+    err = np.abs(u[pick] - ref).max() / np.abs(ref).max()
+    print(f"layer: {len(q)} sources, {tree.nleaf} leaves, {info}; sample {len(pick)} leaves: {err:.2e}")
+    assert err < TOL, err
+    # host arrays give the device result bit for bit
+    uh = layer.apply(torch.from_numpy(q), torch.from_numpy(m)).numpy().reshape(-1, P * P)
+    assert np.array_equal(uh, u)
+
+
+def test_layer_scattered_sources_against_oracle(ctx):
+    """Charges and dipoles scattered over the whole root box of an adaptive
+    tree, so that every list kind carries sources (X entries included)."""
+    tree = bc.Tree.refine(ctx, synth.config_density(2), eps=1e-11, max_level=18)
+    rng = np.random.default_rng(12)
+    src = rng.uniform(-1, 1, (3000, 2))
+    q, m = rng.standard_normal(3000), rng.standard_normal((3000, 2))
+    layer = bc.Layer(tree, src)
+    info = layer.info()
+    assert info["n_x"] > 0 and info["n_w"] > 0
+    u = layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda()).cpu().numpy().reshape(-1, P * P)
+    lv, geom, nodes = _nodes(tree)
+    pick = synth.sample_leaves_per_level(lv, 2, seed=9)
+    ref = oracle.layer(src, q, m, nodes[pick].reshape(-1, 2)).reshape(len(pick), P * P)
+    err = np.abs(u[pick] - ref).max() / np.abs(ref).max()
+    print(f"scattered: {info}; {len(pick)} leaves: {err:.2e}")
+    assert err < TOL, err
+
+
+def test_layer_circle_closed_forms(ctx):
+    # an adaptive tree refined toward a circle, sources on the circle
+    R, c = 0.55, np.array([0.07, -0.11])
+    g = synth.gaussians(3, 7, wlog10=(-1.6, -1.2))
+    tree = bc.Tree.refine(ctx, g, eps=1e-9, max_level=10)
+    n = 1024
+    th = 2 * np.pi * np.arange(n) / n
+    nrm = np.stack([np.cos(th), np.sin(th)], 1)
+    src, w = c + R * nrm, np.full(n, 2 * np.pi * R / n)
+    layer = bc.Layer(tree, src)
+    lv, geom, nodes = _nodes(tree)
+    x = nodes.reshape(-1, 2)
+    d = np.linalg.norm(x - c, axis=1)
+    inner, outer = d < 0.8 * R, d > 1.25 * R
+    zero = torch.zeros(n, dtype=torch.float64, device="cuda")
+    us = layer.apply(torch.from_numpy(w).cuda(), torch.zeros((n, 2), dtype=torch.float64, device="cuda"))
+    ud = layer.apply(zero, torch.from_numpy(w[:, None] * nrm).cuda())
+    us, ud = us.cpu().numpy(), ud.cpu().numpy()
+    es = max(np.abs(us[inner] + R * np.log(R)).max(), np.abs(us[outer] + R * np.log(d[outer])).max())
+    ed = max(np.abs(ud[inner] - 1.0).max(), np.abs(ud[outer]).max())
+    print(f"circle: single layer {es:.2e}, double layer {ed:.2e}")
+    assert es < 1e-11 and ed < 1e-11, (es, ed)
+
+
+def test_layer_edge_cases(ctx):
+    tree = bc.Tree(ctx, *synth.uniform_leaves(3))
+    lv, geom, nodes = _nodes(tree)
+    # no sources
+    empty = bc.Layer(tree, np.zeros((0, 2)))
+    z = empty.apply(torch.zeros(0, dtype=torch.float64, device="cuda"),
+                    torch.zeros((0, 2), dtype=torch.float64, device="cuda"))
+    assert torch.count_nonzero(z).item() == 0
+    # a source on a node, sources on leaf edges and corners, one on the root's edge
+    src = np.array([nodes[5, 17], [0.0, 0.0], [0.25, 0.1], [-0.5, -0.75], [1.0, 0.3], [0.3, -1.0]])
+    rng = np.random.default_rng(8)
+    q, m = rng.standard_normal(len(src)), rng.standard_normal((len(src), 2))
+    u = bc.Layer(tree, src).apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda()).cpu().numpy()
+    ref = oracle.layer(src, q, m, nodes.reshape(-1, 2))
+    err = np.abs(u - ref).max() / np.abs(ref).max()
+    print(f"edge cases: {err:.2e}")
+    assert err < TOL and np.all(np.isfinite(u))
+    with pytest.raises(bc.BoxCodeError):
+        bc.Layer(tree, np.array([[1.5, 0.0]]))
