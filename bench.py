@@ -365,6 +365,54 @@ def batch64_line(args, dev):
     return line
 
 
+def layer_line(args, dev, steps):
+    """The glue layer potential (S[sigma] - D[tau] on the fictitious curve,
+    Sec. 3.4) by the FMM at every leaf node of the star-shaped domain's
+    truncated tree of the 200-Gaussian density: 256 Gauss-Legendre panels of
+    16 nodes, nterms 30 (point sources converge like 0.55^P).  Device
+    arrays, L2 flushed between timed applies; error against the oracle's
+    direct sum at every node of sampled leaves."""
+    import torch
+
+    import oracle
+    import paper_2501_17967_gb300 as bc
+    from paper_2501_17967_gb300 import synth
+    ctx = bc.Context(p=P, nterms=30, device=dev)
+    gamma, gamma_b = synth.star_domain()
+    tree = bc.Tree.refine_truncated(ctx, synth.config_density(3), gamma, gamma_b, eps=1e-11, max_level=18)
+    xy, w, nrm, t = synth.fictitious_curve_sources(256, 16)
+    sig, tau = synth.glue_densities(t)
+    qh, mh = w * sig, (w * tau)[:, None] * nrm
+    layer = bc.Layer(tree, xy)
+    q, m = torch.from_numpy(qh).to(dev), torch.from_numpy(mh).to(dev)
+    u = torch.empty(tree.nleaf * P * P, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        layer.apply(q, m, out=u, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        layer.apply(q, m, out=u, stream=stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    un = u.cpu().numpy().reshape(-1, P * P)
+    lv, ix, iy = (np.asarray(a) for a in tree.leaves())
+    geom = synth.leaf_geometry(lv, ix, iy)
+    pick = synth.sample_leaves_per_level(lv, 1, seed=4)
+    ref = oracle.layer(xy, qh, mh, oracle.leaf_nodes(geom, P)[pick].reshape(-1, 2)).reshape(len(pick), P * P)
+    return {"value": tree.nleaf * P * P / (ms * 1e-3), "unit": "leaf nodes/s (layer potential at every node)",
+            "ms": ms, "workload": "star-shaped domain, truncated 200-Gaussian tree; 4096 curve nodes "
+                                  "(256 Gauss-Legendre panels x 16); nterms 30",
+            "nleaf": int(tree.nleaf), "lists": layer.info(),
+            "rel_err_vs_oracle": float(np.abs(un[pick] - ref).max() / np.abs(ref).max()),
+            "sample": f"every node of {len(pick)} leaves (1 per level)", "l2": "flushed between applies",
+            "dtype": "f64"}
+
+
 class Runner:
     """Timed forward + adjoint steps of one tree."""
 
@@ -594,6 +642,9 @@ def main():
         b64 = batch64_line(args, dev)
         line["batch64"] = {k: b64[k] for k in ("value", "unit", "ms_per_step", "dtype", "config", "clocks")}
         line["batch64"]["value"] *= world
+        # the glue layer potential at every node (FMM, point sources)
+        if rank == 0:
+            line["layer"] = layer_line(args, dev, args.steps)
 
     if rank == 0 and not args.no_extras:
         # error against the oracle per level, forward (every node of 2 leaves

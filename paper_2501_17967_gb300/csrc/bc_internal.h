@@ -387,6 +387,7 @@ cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTre
 // leaves with sources).
 struct LayerDev {
     int64_t n = 0, nx = 0;
+    const int32_t *order = nullptr;     // [nleaf] leaf output order (heaviest near work first)
     const int32_t *src_ptr = nullptr;   // [nleaf + 1] caller-leaf CSR into the sorted sources
     const int32_t *perm = nullptr;      // [n] sorted -> caller order
     const double2 *sxy = nullptr;       // [n]

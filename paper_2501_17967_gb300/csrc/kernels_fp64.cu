@@ -414,6 +414,9 @@ __device__ __forceinline__ int lv_of(const int64_t *__restrict__ level_start, in
 // Constant memory: in the unrolled loops below each entry is a DFMA operand.
 // -------------------------------------------------------------------------
 __constant__ double c_binom[32][32];
+// its transpose, so that the adjoint kernels also read a row with the lanes
+// (consecutive o) on consecutive addresses
+__constant__ double c_binomT[32][32];
 
 // -------------------------------------------------------------------------
 // m2l_boxes: the whole V-list sum of one target box b per block, in FP64,
@@ -455,7 +458,7 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
         // tri = 1 keeps only the terms with k + o <= P (and exactly their transpose)
         const bool keep = !tri || (ADJ ? (o == 0 || k + o < P1) : (k == 0 || k + o < P1));
         const double sg = (k & 1) ? -1.0 : 1.0;   // (-1)^k of S_c[k]
-        bcol[k] = (act && k < P1 && keep) ? sg * (ADJ ? c_binom[o][k] : c_binom[k][o]) : 0.0;
+        bcol[k] = (act && k < P1 && keep) ? sg * (ADJ ? c_binomT[k][o] : c_binom[k][o]) : 0.0;
     }
     // The dependents (the persistent downward pass) are released only at the
     // end: released early, their resident blocks would take the SM space that
@@ -1718,7 +1721,11 @@ cudaError_t fp64_prepare(int NP, int P1, int df_T, int df_maxp, int f_T, int f_m
                 for (int t = 1; t <= m; t++) c = c * (n - m + t) / t;
                 tab[k][o] = double(c);
             }
+        double tabT[32][32];
+        for (int k = 0; k < 32; k++)
+            for (int o = 0; o < 32; o++) tabT[k][o] = tab[o][k];
         cudaError_t e = cudaMemcpyToSymbol(c_binom, tab, sizeof(tab));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_binomT, tabT, sizeof(tabT));
         if (e != cudaSuccess) return e;
     }
     int dev = 0, sms = 0, bu0 = 0, bu1 = 0, bs = 0;

@@ -89,6 +89,7 @@ __global__ void k_layer_p2m(int64_t nleaf, const int32_t *__restrict__ src_ptr, 
         const double ir = 1.0 / g.r;
         double2 acc = make_double2(0.0, 0.0);
         const int k = lane;
+        const double ik = k > 0 ? 1.0 / k : 0.0;
         for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
             const double2 y = sxy[j];
             const double2 eta = make_double2((y.x - g.cx) * ir, (y.y - g.cy) * ir);
@@ -98,8 +99,8 @@ __global__ void k_layer_p2m(int64_t nleaf, const int32_t *__restrict__ src_ptr, 
             } else if (k < P1) {
                 const double2 e1 = cpow(eta, k - 1), ek = cmul(e1, eta);
                 const double2 d = cmul(make_double2(cm[j].x * ir, cm[j].y * ir), e1);
-                acc.x += fma(-c / k, ek.x, d.x);
-                acc.y += fma(-c / k, ek.y, d.y);
+                acc.x += fma(-c * ik, ek.x, d.x);
+                acc.y += fma(-c * ik, ek.y, d.y);
             }
         }
         if (k < P1) ex[int64_t(b) * P1 + k] = acc;
@@ -123,6 +124,7 @@ __global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const
         const double ir = 1.0 / gc.r;
         const double2 e = make_double2((gb.cx - gc.cx) * ir, (gb.cy - gc.cy) * ir);
         const int l = lane;
+        const double il = l > 0 ? 1.0 / l : 0.0;
         double2 acc = make_double2(0.0, 0.0);
         for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
             const double2 y = sxy[j];
@@ -136,7 +138,7 @@ __global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const
             } else if (l < P1) {
                 double2 t = cpow(make_double2(0.5 * iw.x, 0.5 * iw.y), l);   // (2w)^-l
                 if (l & 1) t = make_double2(-t.x, -t.y);
-                const double2 s = make_double2(dm.x - c / l, dm.y);
+                const double2 s = make_double2(dm.x - c * il, dm.y);
                 const double2 v = cmul(t, s);
                 acc.x += v.x;
                 acc.y += v.y;
@@ -179,10 +181,18 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             __syncthreads();
             for (int i = j; i < P1; i += blockDim.x) se[i] = loc[int64_t(b) * P1 + i];
             __syncthreads();
-            for (int l = 0; l < P1; l++) {
+            double a1 = 0.0;
+            int l = 0;
+            for (; l + 1 < P1; l += 2) {
+                const double2 op0 = OpE[l * NP + j], c0 = se[l], op1 = OpE[(l + 1) * NP + j], c1 = se[l + 1];
+                acc = fma(op0.x, c0.x, fma(-op0.y, c0.y, acc));
+                a1 = fma(op1.x, c1.x, fma(-op1.y, c1.y, a1));
+            }
+            if (l < P1) {
                 const double2 op = OpE[l * NP + j], c = se[l];
                 acc = fma(op.x, c.x, fma(-op.y, c.y, acc));
             }
+            acc += a1;
         }
         double lw = 0.0;
         for (int e = w_ptr[o]; e < w_ptr[o + 1]; e++) {
@@ -253,7 +263,7 @@ cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d,
     fl.x_ptr = ly.x_ptr; fl.x_src = ly.x_src; fl.PX = ly.PX;
     if ((e = launch_far_points(a, h, d, tb, fl, st)) != cudaSuccess) return e;
     k_layer_out<<<grid_cap(a.nleaf, 152 * 8), a.NP, 0, st>>>(
-        a.nleaf, d.leaf_order, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, ly.w_ptr, ly.w_src,
+        a.nleaf, ly.order, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, ly.w_ptr, ly.w_src,
         ly.w_code, ly.n_ptr, ly.n_src, ly.src_ptr, ly.sxy, ly.cq, ly.cm, tb.fwd.e, tb.fwd.w, d.expB, d.expA, d.lvtab,
         a.p, P1, u);
     return cudaGetLastError();

@@ -139,6 +139,15 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
         }
         n_ptr[o + 1] = int32_t(n_src.size());
     }
+    // output order: target leaves by descending near work (near sources x
+    // nodes), the heavy ones first, so that the grid-stride loop of the leaf
+    // output spreads them over every block
+    std::vector<int64_t> work(static_cast<size_t>(nleaf), 0);
+    for (int64_t o = 0; o < nleaf; o++)
+        for (int e = n_ptr[o]; e < n_ptr[o + 1]; e++) work[o] += src_ptr[n_src[e] + 1] - src_ptr[n_src[e]];
+    std::vector<int32_t> out_order(static_cast<size_t>(nleaf));
+    for (int64_t o = 0; o < nleaf; o++) out_order[o] = int32_t(o);
+    std::stable_sort(out_order.begin(), out_order.end(), [&](int32_t a, int32_t b) { return work[a] > work[b]; });
     bc_layer *L = new bc_layer;
     L->tree = tree;
     L->n = n;
@@ -152,9 +161,10 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
     LayerDev &d = L->d;
     d.n = n;
     d.nx = int64_t(x_src.size());
-    int32_t *p_src_ptr, *p_perm, *p_v_ptr, *p_v_src, *p_v_code, *p_x_ptr, *p_x_src, *p_x_box, *p_w_ptr, *p_w_src,
+    int32_t *p_order, *p_src_ptr, *p_perm, *p_v_ptr, *p_v_src, *p_v_code, *p_x_ptr, *p_x_src, *p_x_box, *p_w_ptr, *p_w_src,
         *p_w_code, *p_n_ptr, *p_n_src;
     double2 *p_sxy;
+    if (e == cudaSuccess) e = upload(L->allocs, &p_order, out_order.data(), out_order.size());
     if (e == cudaSuccess) e = upload(L->allocs, &p_src_ptr, src_ptr.data(), src_ptr.size());
     if (e == cudaSuccess) e = upload(L->allocs, &p_perm, perm.data(), perm.size());
     if (e == cudaSuccess) e = upload(L->allocs, &p_sxy, sxy.data(), sxy.size());
@@ -177,7 +187,7 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
         delete L;
         return fail(e, "bc_layer_create");
     }
-    d.src_ptr = p_src_ptr; d.perm = p_perm; d.sxy = p_sxy;
+    d.order = p_order; d.src_ptr = p_src_ptr; d.perm = p_perm; d.sxy = p_sxy;
     d.v_ptr = p_v_ptr; d.v_src = p_v_src; d.v_code = p_v_code;
     d.x_ptr = p_x_ptr; d.x_src = p_x_src; d.x_box = p_x_box;
     d.w_ptr = p_w_ptr; d.w_src = p_w_src; d.w_code = p_w_code;
