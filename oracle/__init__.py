@@ -225,3 +225,32 @@ def interp(p: int, fvals: np.ndarray, pts: np.ndarray) -> np.ndarray:
     if _load().oracle_interp(p, _dp(fvals), pts.shape[0], _dp(pts), _dp(out)) != 0:
         raise ValueError("bad p")
     return out
+
+
+def strip_assemble(A: np.ndarray, B: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """The strip system of Sec. 3.3 as one dense matrix: N element blocks on a
+    closed strip, block row k coupling x_(k-1), x_k and x_(k+1) (indices mod
+    N) through C[k], A[k] and B[k] ([N, m, m] each); with N = 1 or 2 the
+    blocks that land on the same position add up."""
+    A, B, C = (np.asarray(t, dtype=np.float64) for t in (A, B, C))
+    N, m = A.shape[0], A.shape[1]
+    M = np.zeros((N * m, N * m))
+    for k in range(N):
+        r = slice(k * m, (k + 1) * m)
+        M[r, k * m:(k + 1) * m] += A[k]
+        kp, km = (k + 1) % N, (k - 1) % N
+        M[r, kp * m:(kp + 1) * m] += B[k]
+        M[r, km * m:(km + 1) * m] += C[k]
+    return M
+
+
+def strip_solve(A: np.ndarray, B: np.ndarray, C: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """x with sum over the block row of (C[k] x_(k-1) + A[k] x_k + B[k] x_(k+1)) = b[k]
+    (Sec. 3.3's block-tridiagonal strip system with its periodic corners), by
+    a dense solve of the assembled matrix.  b: [N, m, r] -> x: [N, m, r].
+    Pinned by block-circulant systems solved through the block DFT and by
+    the scalar periodic second-difference closed form."""
+    b = np.asarray(b, dtype=np.float64)
+    N, m, r = b.shape
+    x = np.linalg.solve(strip_assemble(A, B, C), b.reshape(N * m, r))
+    return x.reshape(N, m, r)

@@ -487,3 +487,36 @@ def test_layer_linearity_and_coincident_source(oracle_mod):
     assert np.allclose(both, sep, rtol=1e-14, atol=1e-14)
     keep = np.arange(30) != 7
     assert np.isclose(both[-1], oracle_mod.layer(src[keep], q[keep], m[keep], t[-1:])[0], rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Strip solve (Sec. 3.3): block-tridiagonal system with periodic corners.
+# ---------------------------------------------------------------------------
+def test_strip_block_circulant_by_dft(oracle_mod):
+    """Identical blocks (A, B, C) on every element: the system is block
+    circulant, so the block DFT diagonalises it: x_hat_j = (A + B w^j +
+    C w^-j)^-1 b_hat_j with w = exp(2 pi i / N).  Fails on a swapped B/C or a
+    corner placed on the wrong side."""
+    rng = np.random.default_rng(21)
+    for N, m in ((7, 3), (2, 4), (1, 2), (16, 5)):
+        A0 = rng.standard_normal((m, m)) + 4 * m * np.eye(m)
+        B0, C0 = rng.standard_normal((m, m)), 0.5 * rng.standard_normal((m, m))
+        b = rng.standard_normal((N, m, 2))
+        x = oracle_mod.strip_solve(np.tile(A0, (N, 1, 1)), np.tile(B0, (N, 1, 1)), np.tile(C0, (N, 1, 1)), b)
+        bh = np.fft.fft(b, axis=0)
+        w = np.exp(2j * np.pi * np.arange(N) / N)
+        xh = np.stack([np.linalg.solve(A0 + B0 * w[j] + C0 / w[j], bh[j]) for j in range(N)])
+        assert np.allclose(x, np.fft.ifft(xh, axis=0).real, rtol=0, atol=1e-12), (N, m)
+
+
+def test_strip_periodic_second_difference(oracle_mod):
+    """m = 1, A = 2 + h^2, B = C = -1: the periodic discretisation of
+    -u'' + u = f on N points; for f = cos(2 pi s / N) the exact discrete
+    solution is f / (2 - 2 cos(2 pi / N) + h^2)."""
+    N, h = 40, 0.1
+    s = np.arange(N)
+    f = np.cos(2 * np.pi * s / N)[:, None, None]
+    one = np.ones((N, 1, 1))
+    x = oracle_mod.strip_solve((2 + h * h) * one, -one, -one, f)
+    exact = f / (2 - 2 * np.cos(2 * np.pi / N) + h * h)
+    assert np.abs(x - exact).max() <= 1e-13 * np.abs(exact).max()
