@@ -256,6 +256,28 @@ bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const do
 bc_status bc_layer_info(const bc_layer *layer, int64_t *counts);
 void bc_layer_destroy(bc_layer *layer);
 
+/* Strip solve (Sec. 3.3): the spectral-collocation system of the strip
+ * couples each element only to its two neighbours around the closed strip,
+ * so it is block tridiagonal with two corner blocks from the periodicity:
+ *
+ *     C[k] x[k-1] + A[k] x[k] + B[k] x[k+1] = b[k],   k = 0..N-1, indices mod N
+ *
+ * (with N = 1 or 2 the blocks meeting at one position add).  Solved as the
+ * paper does: block LU of the tridiagonal part, then the Woodbury identity
+ * for the corner blocks C[0] and B[N-1] (O(m^3 N) per system).  Batched over
+ * nsys independent systems, one warp each.  Layout, all FP64 row-major
+ * device arrays: A, B, C [nsys][N][m][m]; b, x [nsys][N][m][r].  Shapes:
+ * N >= 1, 1 <= m <= 32, 1 <= r <= 32.  work: device scratch of
+ * bc_strip_workspace() bytes, owned by the caller.  status: NULL or device
+ * int32 [nsys], set to 1 where a pivot of the block LU (every diagonal block
+ * D_k and the 2m x 2m capacitance matrix are factored with partial pivoting)
+ * was zero or not finite, else 0; no pivoting across blocks, so the systems
+ * should be block diagonally dominant, as collocation strips with their
+ * continuity rows are.  Host pointers: BC_ERR_ARG.  Stream-ordered. */
+bc_status bc_strip_workspace(int64_t nsys, int64_t N, int m, int r, int64_t *bytes);
+bc_status bc_strip_solve(int64_t nsys, int64_t N, int m, int r, const double *A, const double *B, const double *C,
+                         const double *b, double *x, void *work, int32_t *status, void *stream);
+
 /* Batched applies: many independent densities on different trees (all of
  * this context's p and root side L) in one launch per pass.  Not in the
  * paper (its solver applies one box code at a time).  A batch is the

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "SPLIT_BF16_ALL", "apply",
-           "apply_adjoint", "eval_points", "eval_points_grad", "Layer", "BoxCodeApply", "lib_path"]
+           "apply_adjoint", "eval_points", "eval_points_grad", "Layer", "strip_solve", "BoxCodeApply", "lib_path"]
 
 # precision modes (bc_precision): FP64 everywhere; BF16 digit products for the
 # fixed-operator contractions (near field, P2M, L2P, W and X lists) with the
@@ -88,6 +88,9 @@ SIGNATURES = [
     ("bc_layer_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     ("bc_layer_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     ("bc_layer_destroy", None, [_VP]),
+    ("bc_strip_workspace", ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    ("bc_strip_solve", ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                      _VP]),
     ("bc_batch_create", ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(_VP)]),
     ("bc_batch_destroy", None, [_VP]),
     ("bc_batch_nleaf", _I64, [_VP]),
@@ -458,6 +461,30 @@ class Layer:
             self.close()
         except Exception:
             pass
+
+
+def strip_solve(A, B, C, b, stream=None, return_status=False):
+    """Batched strip systems of Sec. 3.3 (block tridiagonal with periodic
+    corners): C[k] x[k-1] + A[k] x[k] + B[k] x[k+1] = b[k], indices mod N.
+    A, B, C: float64 device tensors [nsys, N, m, m]; b: [nsys, N, m, r].
+    Returns x (and the per-system status if asked: 1 = zero pivot)."""
+    import torch
+    A, B, C, b = (t.contiguous() for t in (A, B, C, b))
+    if b.dim() != 4 or A.shape != B.shape or A.shape != C.shape or A.shape[:3] != b.shape[:3] \
+            or A.shape[2] != A.shape[3] or any(t.dtype != torch.float64 for t in (A, B, C, b)):
+        raise ValueError("A, B, C must be float64 [nsys, N, m, m] and b float64 [nsys, N, m, r]")
+    nsys, N, m, r = (int(v) for v in b.shape)
+    lib = _load()
+    nbytes = ctypes.c_int64()
+    _check(lib.bc_strip_workspace(nsys, N, m, r, ctypes.byref(nbytes)))
+    work = torch.empty(max(1, nbytes.value // 8), dtype=torch.float64, device=b.device)
+    x = torch.empty_like(b)
+    status = torch.zeros(max(1, nsys), dtype=torch.int32, device=b.device)
+    _check(lib.bc_strip_solve(nsys, N, m, r, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
+                              ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                              ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                              ctypes.c_void_p(status.data_ptr()), _stream_ptr(stream)))
+    return (x, status[:nsys]) if return_status else x
 
 
 class Batch:

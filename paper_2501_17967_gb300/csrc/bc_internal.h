@@ -402,6 +402,12 @@ struct LayerDev {
 // u at every leaf node (device pointers: q [n], m [n][2] caller order, u [nleaf][NP]).
 cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t stream);
+// Strip solve (kernels_strip.cu): nsys block-cyclic-tridiagonal systems,
+// one warp each; workspace strip_work_doubles(N, m, r) per system.
+size_t strip_work_doubles(int64_t N, int m, int r);
+size_t strip_smem_bytes(int m, int r);
+cudaError_t launch_strip(int64_t nsys, int64_t N, int m, int r, const double *A, const double *B, const double *C,
+                         const double *b, double *x, double *work, int32_t *status, cudaStream_t stream);
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
 struct BatchPtrs {
