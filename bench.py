@@ -46,6 +46,8 @@ WORKLOADS = {
     "adaptive200": (3, "adaptive 200-Gaussian quadtree (widths 1e-4..1e-1), p=16, eps=1e-11"),
     "adaptive20": (2, "adaptive 20-Gaussian quadtree (widths 1e-3..1e-1), p=16, eps=1e-11"),
     "batch64": (None, "64 adaptive trees (about 2e2..2e4 leaves, log-uniform), p in {8,12,16}, batched"),
+    "layer": (None, "glue layer potential at every node of the star-shaped domain's truncated 200-Gaussian tree"),
+    "strip": (None, "strip solve: batched block-tridiagonal systems with periodic corners"),
 }
 PRECISIONS = {"fp64": 0, "split": 1, "split_all": 2}
 DTYPES = {
@@ -365,7 +367,7 @@ def batch64_line(args, dev):
     return line
 
 
-def layer_line(args, dev, steps):
+def layer_line(args, dev, steps, check=True):
     """The glue layer potential (S[sigma] - D[tau] on the fictitious curve,
     Sec. 3.4) by the FMM at every leaf node of the star-shaped domain's
     truncated tree of the 200-Gaussian density: 256 Gauss-Legendre panels of
@@ -399,6 +401,8 @@ def layer_line(args, dev, steps):
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    if not check:
+        return {"value": tree.nleaf * P * P / (ms * 1e-3), "ms": ms, "profile_run": True}
     un = u.cpu().numpy().reshape(-1, P * P)
     lv, ix, iy = (np.asarray(a) for a in tree.leaves())
     geom = synth.leaf_geometry(lv, ix, iy)
@@ -411,6 +415,75 @@ def layer_line(args, dev, steps):
             "rel_err_vs_oracle": float(np.abs(un[pick] - ref).max() / np.abs(ref).max()),
             "sample": f"every node of {len(pick)} leaves (1 per level)", "l2": "flushed between applies",
             "dtype": "f64"}
+
+
+def strip_line(args, dev, steps, peak_fp64, check=True):
+    """The strip solve of Sec. 3.3 at the paper's size: 56 elements of 16 x 24
+    nodes (N = 56 blocks of m = 384, one right-hand side), block LU of the
+    tridiagonal part plus the Woodbury corner correction, random block
+    diagonally dominant blocks; and the batched small-block case (608
+    systems of N = 256, m = 17, one warp each).  Algorithmic FP64 work per
+    system N m^2 (14 m / 3 + 6 R), R = r + 2m."""
+    import torch
+
+    import oracle
+    import paper_2501_17967_gb300 as bc
+
+    def make(nsys, N, m, r, seed):
+        rng = np.random.default_rng(seed)
+        A = rng.standard_normal((nsys, N, m, m)) + 3.0 * m * np.eye(m)
+        B, C = rng.standard_normal((nsys, N, m, m)), rng.standard_normal((nsys, N, m, m))
+        b = rng.standard_normal((nsys, N, m, r))
+        return A, B, C, b
+
+    def timed(arrs, nsteps):
+        stream = torch.cuda.current_stream()
+        t = [torch.from_numpy(a).to(dev) for a in arrs]
+        for _ in range(2):
+            x = bc.strip_solve(*t, stream=stream)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        for k in range(nsteps):
+            ev[k][0].record(stream)
+            x = bc.strip_solve(*t, stream=stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(c) for a, c in ev) / nsteps, x
+
+    def work(nsys, N, m, r):
+        return nsys * N * m * m * (14.0 * m / 3.0 + 6.0 * (r + 2 * m))
+
+    big = make(1, 56, 384, 1, 5)
+    ms, x = timed(big, max(3, steps // 2))
+    ach = work(1, 56, 384, 1) / (ms * 1e-3) / 1e12
+    line = {"value": 1.0 / (ms * 1e-3), "unit": "strip solves/s", "ms": ms,
+            "workload": "the paper's strip size: N = 56 elements of 16 x 24 nodes (m = 384), one right-hand side; "
+                        "block LU + Woodbury, blocked LU per element over the whole GPU",
+            "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(peak_fp64, 3), "unit": "TFLOP/s",
+                         "frac": round(ach / peak_fp64, 4), "traffic": None,
+                         "work": "N m^2 (14 m / 3 + 6 R) FP64 flop per system, R = r + 2m"},
+            "dtype": "f64"}
+    if check:
+        A, B, C, b = big
+        xs = x.cpu().numpy()[0]
+        N = 56
+        res = max(float(np.abs(A[0, k] @ xs[k] + B[0, k] @ xs[(k + 1) % N] + C[0, k] @ xs[(k - 1) % N]
+                               - b[0, k]).max()) for k in range(N))
+        rows = max(float((np.abs(A[0, k]).sum(1) + np.abs(B[0, k]).sum(1) + np.abs(C[0, k]).sum(1)).max())
+                   for k in range(N))
+        line["backward_error"] = res / (rows * float(np.abs(xs).max()))
+    small = make(608, 256, 17, 1, 6)
+    ms2, x2 = timed(small, steps)
+    ach2 = work(608, 256, 17, 1) / (ms2 * 1e-3) / 1e12
+    line["batched_small"] = {"value": 608 / (ms2 * 1e-3), "unit": "strip systems/s", "ms": ms2,
+                             "workload": "608 systems, N = 256, m = 17, r = 1, one warp each",
+                             "roofline_frac": round(ach2 / peak_fp64, 4)}
+    if check:
+        A, B, C, b = small
+        ref = oracle.strip_solve(A[0], B[0], C[0], b[0])
+        line["batched_small"]["rel_err_vs_oracle"] = float(np.abs(x2[0].cpu().numpy() - ref).max()
+                                                           / np.abs(ref).max())
+    return line
 
 
 class Runner:
@@ -515,6 +588,18 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload in ("layer", "strip"):
+        # one extra workload alone (profiler captures: --profile-run keeps the
+        # oracle check out)
+        import torch
+        dev = torch.cuda.current_device()
+        if args.workload == "layer":
+            line = layer_line(args, dev, args.steps, check=not args.profile_run)
+        else:
+            line = strip_line(args, dev, args.steps, FP64_FLOP_PER_CLK_SM * 152 * 2070e6 / 1e12,
+                              check=not args.profile_run)
+        print(json.dumps(line))
+        return
     import torch
     import torch.distributed as dist
 
@@ -645,6 +730,7 @@ def main():
         # the glue layer potential at every node (FMM, point sources)
         if rank == 0:
             line["layer"] = layer_line(args, dev, args.steps)
+            line["strip"] = strip_line(args, dev, args.steps, peaks["fp64"])
 
     if rank == 0 and not args.no_extras:
         # error against the oracle per level, forward (every node of 2 leaves

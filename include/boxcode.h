@@ -265,9 +265,12 @@ void bc_layer_destroy(bc_layer *layer);
  * (with N = 1 or 2 the blocks meeting at one position add).  Solved as the
  * paper does: block LU of the tridiagonal part, then the Woodbury identity
  * for the corner blocks C[0] and B[N-1] (O(m^3 N) per system).  Batched over
- * nsys independent systems, one warp each.  Layout, all FP64 row-major
- * device arrays: A, B, C [nsys][N][m][m]; b, x [nsys][N][m][r].  Shapes:
- * N >= 1, 1 <= m <= 32, 1 <= r <= 32.  work: device scratch of
+ * nsys independent systems: blocks up to 32 x 32 one warp per system, all
+ * systems at once; larger blocks (the paper's elements, 16 x 24 = 384 nodes)
+ * one system after another, each step a blocked LU over the whole GPU (rank
+ * updates as cuBLAS DGEMMs).  Layout, all FP64 row-major device arrays: A, B,
+ * C [nsys][N][m][m]; b, x [nsys][N][m][r].  Shapes: N >= 1, 1 <= m <= 448,
+ * 1 <= r <= 32.  work: device scratch of
  * bc_strip_workspace() bytes, owned by the caller.  status: NULL or device
  * int32 [nsys], set to 1 where a pivot of the block LU (every diagonal block
  * D_k and the 2m x 2m capacitance matrix are factored with partial pivoting)

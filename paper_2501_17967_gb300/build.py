@@ -20,6 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", f"-I{INCLUDE}"]
+LIBS = ["-lcublas"]   # plain DGEMMs of the large-block strip solve
 
 
 def _nvcc() -> str:
@@ -41,7 +42,7 @@ def _digest() -> str:
             h.update(name.encode())
             with open(path, "rb") as fh:
                 h.update(fh.read())
-    h.update(" ".join(ARCH + COMMON).encode())
+    h.update(" ".join(ARCH + COMMON + LIBS).encode())
     return h.hexdigest()
 
 
@@ -73,7 +74,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + ["-o", tmp, "-lpthread"]
+    cmd = [nvcc, "-shared", "-cudart", "shared"] + ARCH + objs + ["-o", tmp, "-lpthread"] + LIBS
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

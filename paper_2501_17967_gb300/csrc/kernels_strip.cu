@@ -16,10 +16,14 @@
 // X_{N-1} = g_{N-1}, X_k = g_k - H_k X_{k+1}.  Every D_k and the capacitance
 // matrix I + V^T Z (2m x 2m) are factored by LU with partial pivoting.
 //
-// One warp per system (the batched small-dense-LU workload: many strips or
-// many right-hand-side sets at once); the blocks of the current step live in
-// shared memory, H_k and g_k / X_k in a global workspace.  FP64.
+// Blocks up to 32 x 32 (interface-sized blocks): one warp per system, the
+// batched small-dense-LU workload (many strips or right-hand-side sets at
+// once); the blocks of the current step live in shared memory, H_k and g_k /
+// X_k in a global workspace.  Larger blocks (the paper's elements of 16 x 24
+// nodes): one system at a time on the whole GPU, below.  FP64.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "bc_internal.h"
 
@@ -191,7 +195,220 @@ __global__ void k_strip_solve(int64_t nsys, int64_t N, int m, int r, const doubl
     if (status && lane == 0) status[s] = ok ? 0 : 1;
 }
 
+// ---------------------------------------------------------------------------
+// Large blocks (m > 32, the element blocks of the paper's strip: 16 x 24 =
+// 384 nodes): one system at a time on the whole GPU.  The host loops over
+// the elements; each step factors the augmented block [D_k | B_k | rhs_k]
+// (row-major, Wc = m + m + R columns) by right-looking blocked LU with
+// partial pivoting (panels of kPanel columns: k_strip_panel factors a panel
+// in shared memory in one CTA, k_strip_swap and k_strip_trsm_l carry its row
+// exchanges and L11^-1 to the columns on its right, a DGEMM updates the
+// trailing block), then back-substitutes the right-hand columns
+// (k_strip_trsm_u per diagonal block, DGEMM for the rows above).
+// ---------------------------------------------------------------------------
+constexpr int kPanel = 32;
+constexpr int kPanelThreads = 512;
+
+// step k's augmented block: [A_k | B_k (k < N-1) | b_k | C_0 (k = 0) | B_{N-1} (k = N-1)]
+__global__ void k_strip_aug(int64_t N, int m, int r, int64_t k, const double *__restrict__ A,
+                            const double *__restrict__ B, const double *__restrict__ C,
+                            const double *__restrict__ b, double *__restrict__ aug, int Wc)
+{
+    const size_t mm = size_t(m) * m;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < int64_t(m) * Wc;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(idx / Wc), c = int(idx % Wc);
+        double v = 0.0;
+        if (c < m) v = A[k * mm + size_t(i) * m + c];
+        else if (c < 2 * m) v = k < N - 1 ? B[k * mm + size_t(i) * m + (c - m)] : 0.0;
+        else if (c < 2 * m + r) v = b[(k * m + i) * r + (c - 2 * m)];
+        else if (c < 3 * m + r) v = k == 0 ? C[size_t(i) * m + (c - 2 * m - r)] : 0.0;
+        else v = k == N - 1 ? B[(N - 1) * mm + size_t(i) * m + (c - 3 * m - r)] : 0.0;
+        aug[idx] = v;
+    }
+}
+
+// LU with partial pivoting of the panel: rows [j0, n), columns [j0, j0 + jb)
+// of M (row-major, leading dimension ld), staged in shared memory; the pivot
+// rows go to piv[j] (absolute); a zero or non-finite pivot sets *status.
+__global__ void __launch_bounds__(kPanelThreads)
+k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__restrict__ piv,
+              int32_t *__restrict__ status)
+{
+    extern __shared__ double sp[];   // [n - j0][jb]
+    __shared__ double s_best[kPanelThreads / 32];
+    __shared__ int s_row[kPanelThreads / 32];
+    __shared__ int s_piv;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x;
+    const int rows = n - j0;
+    for (int idx = t; idx < rows * jb; idx += nt) sp[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
+    __syncthreads();
+    for (int jj = 0; jj < jb; jj++) {
+        double best = -1.0;
+        int bi = jj;
+        for (int i = jj + t; i < rows; i += nt) {
+            const double v = fabs(sp[i * jb + jj]);
+            if (v > best) { best = v; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_best[w] = best; s_row[w] = bi; }
+        __syncthreads();
+        if (t == 0) {
+            double bb = s_best[0];
+            int br = s_row[0];
+            for (int q = 1; q < nt / 32; q++)
+                if (s_best[q] > bb || (s_best[q] == bb && s_row[q] < br)) { bb = s_best[q]; br = s_row[q]; }
+            s_piv = br;
+            piv[j0 + jj] = j0 + br;
+            if (!(bb > 0.0) || !isfinite(bb)) *status = 1;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != jj)
+            for (int c = t; c < jb; c += nt) {
+                const double x = sp[jj * jb + c];
+                sp[jj * jb + c] = sp[p * jb + c];
+                sp[p * jb + c] = x;
+            }
+        __syncthreads();
+        const double d = sp[jj * jb + jj];
+        const double inv = (d != 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
+        for (int i = jj + 1 + t; i < rows; i += nt) sp[i * jb + jj] *= inv;
+        __syncthreads();
+        const int wc = jb - jj - 1;
+        for (int idx = t; idx < (rows - jj - 1) * wc; idx += nt) {
+            const int i = jj + 1 + idx / wc, c = jj + 1 + idx % wc;
+            sp[i * jb + c] = fma(-sp[i * jb + jj], sp[jj * jb + c], sp[i * jb + c]);
+        }
+        __syncthreads();
+    }
+    for (int idx = t; idx < rows * jb; idx += nt) M[size_t(j0 + idx / jb) * ld + j0 + idx % jb] = sp[idx];
+}
+
+// the panel's row exchanges on columns [c0, c1)
+__global__ void k_strip_swap(double *__restrict__ M, int ld, int j0, int jb, const int32_t *__restrict__ piv,
+                             int c0, int c1)
+{
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    for (int j = j0; j < j0 + jb; j++) {
+        const int p = piv[j];
+        if (p != j) {
+            const double x = M[size_t(j) * ld + c];
+            M[size_t(j) * ld + c] = M[size_t(p) * ld + c];
+            M[size_t(p) * ld + c] = x;
+        }
+    }
+}
+
+// U12 = L11^-1 A12 (L11 unit lower, the panel's top jb x jb) on columns [c0, c1)
+__global__ void k_strip_trsm_l(double *__restrict__ M, int ld, int j0, int jb, int c0, int c1)
+{
+    __shared__ double sl[kPanel * kPanel];
+    for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x)
+        sl[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
+    __syncthreads();
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    double x[kPanel];
+#pragma unroll
+    for (int i = 0; i < kPanel; i++) x[i] = i < jb ? M[size_t(j0 + i) * ld + c] : 0.0;
+#pragma unroll
+    for (int i = 1; i < kPanel; i++) {
+        double s = x[i];
+#pragma unroll
+        for (int q = 0; q < kPanel; q++)
+            if (q < i) s = fma(-sl[i * jb + q], x[q], s);
+        x[i] = s;
+    }
+#pragma unroll
+    for (int i = 0; i < kPanel; i++)
+        if (i < jb) M[size_t(j0 + i) * ld + c] = x[i];
+}
+
+// X = U11^-1 Y (U11 the jb x jb diagonal block at j0) on columns [c0, c1)
+__global__ void k_strip_trsm_u(double *__restrict__ M, int ld, int j0, int jb, int c0, int c1)
+{
+    __shared__ double su[kPanel * kPanel];
+    for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x)
+        su[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
+    __syncthreads();
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    double x[kPanel];
+#pragma unroll
+    for (int i = 0; i < kPanel; i++) x[i] = i < jb ? M[size_t(j0 + i) * ld + c] : 0.0;
+#pragma unroll
+    for (int i = kPanel - 1; i >= 0; i--) {
+        if (i >= jb) continue;
+        double s = x[i];
+#pragma unroll
+        for (int q = 0; q < kPanel; q++)
+            if (q > i && q < jb) s = fma(-su[i * jb + q], x[q], s);
+        const double d = su[i * jb + i];
+        x[i] = d != 0.0 ? s / d : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < kPanel; i++)
+        if (i < jb) M[size_t(j0 + i) * ld + c] = x[i];
+}
+
+// capacitance system of the Woodbury correction: [I + [Z_{N-1}; Z_0] | y_{N-1}; y_0]
+__global__ void k_strip_cap(const double *__restrict__ G, int64_t N, int m, int r, int R, double *__restrict__ K)
+{
+    const int n2 = 2 * m, ldk = n2 + r;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < int64_t(n2) * ldk;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(idx / ldk), c = int(idx % ldk);
+        const int64_t blk = i < m ? N - 1 : 0;
+        const double *row = G + (blk * m + (i % m)) * R;
+        K[idx] = c < n2 ? row[r + c] + (c == i ? 1.0 : 0.0) : row[c - n2];
+    }
+}
+
 }  // namespace
+
+int strip_panel_width() { return kPanel; }
+
+cudaError_t launch_strip_aug(int64_t N, int m, int r, int64_t k, const double *A, const double *B, const double *C,
+                             const double *b, double *aug, int Wc, cudaStream_t st)
+{
+    const int64_t n = int64_t(m) * Wc;
+    k_strip_aug<<<int(std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(N, m, r, k, A, B, C, b, aug, Wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_panel(double *M, int n, int ld, int j0, int jb, int32_t *piv, int32_t *status,
+                               cudaStream_t st)
+{
+    const size_t sm = sizeof(double) * size_t(n - j0) * jb;
+    cudaError_t e = cudaFuncSetAttribute(k_strip_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
+    if (e != cudaSuccess) return e;
+    k_strip_panel<<<1, kPanelThreads, sm, st>>>(M, n, ld, j0, jb, piv, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_cols(int which, double *M, int ld, int j0, int jb, const int32_t *piv, int c0, int c1,
+                              cudaStream_t st)
+{
+    if (c1 <= c0) return cudaSuccess;
+    const int grid = (c1 - c0 + 127) / 128;
+    if (which == 0) k_strip_swap<<<grid, 128, 0, st>>>(M, ld, j0, jb, piv, c0, c1);
+    else if (which == 1) k_strip_trsm_l<<<grid, 128, 0, st>>>(M, ld, j0, jb, c0, c1);
+    else k_strip_trsm_u<<<grid, 128, 0, st>>>(M, ld, j0, jb, c0, c1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_cap(const double *G, int64_t N, int m, int r, int R, double *K, cudaStream_t st)
+{
+    const int64_t n = int64_t(2 * m) * (2 * m + r);
+    k_strip_cap<<<int(std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(G, N, m, r, R, K);
+    return cudaGetLastError();
+}
 
 size_t strip_smem_bytes(int m, int r)
 {

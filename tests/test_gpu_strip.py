@@ -6,7 +6,9 @@ continuity rows is), random per system; shapes cover N = 1 and 2 (blocks
 that meet at one position add), odd N, the paper's element count and block
 size (N = 256 panels, m = p + 1 = 17 interface nodes), m = 1 and the largest
 m = 32, several right-hand sides, and a batch wider than the SM count.  A
-singular diagonal block is reported in the status array.  Bar: the backward
+singular diagonal block is reported in the status array.  Blocks above 32
+take the whole-GPU blocked-LU path (checked up to the paper's 384 against the
+oracle, and at the paper's 56 x 384 by the backward error).  Bar: the backward
 error of a stable elimination, 1e-12 relative max-norm for these
 well-conditioned systems."""
 import numpy as np
@@ -52,6 +54,41 @@ def test_strip_against_oracle(gpu, nsys, N, m, r):
     assert worst < 1e-12, worst
 
 
+@pytest.mark.parametrize("nsys,N,m,r", [(2, 3, 40, 2), (1, 1, 64, 1), (1, 2, 100, 3), (2, 10, 65, 1),
+                                        (1, 12, 384, 1)])
+def test_strip_large_blocks_against_oracle(gpu, nsys, N, m, r):
+    """Blocks above 32 (blocked LU over the whole GPU per element), up to the
+    paper's element size 16 x 24 = 384."""
+    A, B, C, b = _systems(nsys, N, m, r, seed=N * 1000 + m)
+    x, status = bc.strip_solve(*(torch.from_numpy(t).to(gpu) for t in (A, B, C, b)), return_status=True)
+    x = x.cpu().numpy()
+    assert int(status.sum().item()) == 0
+    worst = 0.0
+    for s in range(nsys):
+        ref = oracle.strip_solve(A[s], B[s], C[s], b[s])
+        worst = max(worst, float(np.abs(x[s] - ref).max() / np.abs(ref).max()))
+    print(f"strip (large) nsys={nsys} N={N} m={m} r={r}: {worst:.2e}")
+    assert worst < 1e-12, worst
+
+
+def test_strip_paper_size_residual(gpu):
+    """The paper's strip (56 elements of 16 x 24 nodes: N = 56, m = 384): the
+    dense oracle is too large to run here, so the check is the normwise
+    backward error max|M x - b| / (max row sum |M| * max|x|), which a stable
+    elimination keeps at a small multiple of the unit roundoff (bar 1e-14)."""
+    N, m = 56, 384
+    A, B, C, b = _systems(1, N, m, 1, seed=77)
+    x = bc.strip_solve(*(torch.from_numpy(t).to(gpu) for t in (A, B, C, b))).cpu().numpy()[0]
+    res = np.zeros((N, m, 1))
+    for k in range(N):
+        res[k] = A[0, k] @ x[k] + B[0, k] @ x[(k + 1) % N] + C[0, k] @ x[(k - 1) % N] - b[0, k]
+    rowsum = max(float((np.abs(A[0, k]).sum(1) + np.abs(B[0, k]).sum(1) + np.abs(C[0, k]).sum(1)).max())
+                 for k in range(N))
+    berr = float(np.abs(res).max() / (rowsum * np.abs(x).max()))
+    print(f"strip N=56 m=384: backward error {berr:.2e}")
+    assert berr < 1e-14, berr
+
+
 def test_strip_singular_block_flagged(gpu):
     A, B, C, b = _systems(3, 5, 4, 1, seed=3)
     A[1, 2] = 0.0
@@ -59,12 +96,17 @@ def test_strip_singular_block_flagged(gpu):
     C[1, 2] = 0.0   # D_2 = A_2 - C_2 H_1 = 0
     _, status = bc.strip_solve(*(torch.from_numpy(t).to(gpu) for t in (A, B, C, b)), return_status=True)
     assert status.cpu().tolist() == [0, 1, 0]
+    A, B, C, b = _systems(2, 4, 40, 1, seed=4)
+    A[0, 3] = 0.0
+    C[0, 3] = 0.0
+    _, status = bc.strip_solve(*(torch.from_numpy(t).to(gpu) for t in (A, B, C, b)), return_status=True)
+    assert status.cpu().tolist() == [1, 0]
 
 
 def test_strip_rejects_bad_shapes(gpu):
-    z = torch.zeros((1, 2, 33, 33), dtype=torch.float64, device=gpu)
+    z = torch.zeros((1, 2, 449, 449), dtype=torch.float64, device=gpu)
     with pytest.raises(bc.BoxCodeError):
-        bc.strip_solve(z, z, z, torch.zeros((1, 2, 33, 1), dtype=torch.float64, device=gpu))
+        bc.strip_solve(z, z, z, torch.zeros((1, 2, 449, 1), dtype=torch.float64, device=gpu))
     h = torch.zeros((1, 2, 3, 3), dtype=torch.float64)
     with pytest.raises(bc.BoxCodeError):
         bc.strip_solve(h, h, h, torch.zeros((1, 2, 3, 1), dtype=torch.float64))
