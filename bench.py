@@ -439,13 +439,17 @@ def strip_line(args, dev, steps, peak_fp64, check=True):
     def timed(arrs, nsteps):
         stream = torch.cuda.current_stream()
         t = [torch.from_numpy(a).to(dev) for a in arrs]
+        nsys, N, m, r = arrs[3].shape
+        x = torch.empty_like(t[3])
+        bufs = {"out": x, "work": bc.strip_workspace(nsys, N, m, r, t[3].device),
+                "status": torch.zeros(nsys, dtype=torch.int32, device=t[3].device)}
         for _ in range(2):
-            x = bc.strip_solve(*t, stream=stream)
+            bc.strip_solve(*t, stream=stream, **bufs)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
         for k in range(nsteps):
             ev[k][0].record(stream)
-            x = bc.strip_solve(*t, stream=stream)
+            bc.strip_solve(*t, stream=stream, **bufs)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         return sum(a.elapsed_time(c) for a, c in ev) / nsteps, x

@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build_mod
 
 __all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_BF16", "SPLIT_BF16_ALL", "apply",
-           "apply_adjoint", "eval_points", "eval_points_grad", "Layer", "strip_solve", "BoxCodeApply", "lib_path"]
+           "apply_adjoint", "eval_points", "eval_points_grad", "Layer", "strip_solve", "strip_workspace", "BoxCodeApply", "lib_path"]
 
 # precision modes (bc_precision): FP64 everywhere; BF16 digit products for the
 # fixed-operator contractions (near field, P2M, L2P, W and X lists) with the
@@ -463,11 +463,21 @@ class Layer:
             pass
 
 
-def strip_solve(A, B, C, b, stream=None, return_status=False):
+def strip_workspace(nsys: int, N: int, m: int, r: int, device=None):
+    """A scratch tensor large enough for strip_solve of these shapes."""
+    import torch
+    nbytes = ctypes.c_int64()
+    _check(_load().bc_strip_workspace(nsys, N, m, r, ctypes.byref(nbytes)))
+    return torch.empty(max(1, (nbytes.value + 7) // 8), dtype=torch.float64, device=device)
+
+
+def strip_solve(A, B, C, b, stream=None, return_status=False, out=None, work=None, status=None):
     """Batched strip systems of Sec. 3.3 (block tridiagonal with periodic
     corners): C[k] x[k-1] + A[k] x[k] + B[k] x[k+1] = b[k], indices mod N.
     A, B, C: float64 device tensors [nsys, N, m, m]; b: [nsys, N, m, r].
-    Returns x (and the per-system status if asked: 1 = zero pivot)."""
+    Returns x (and the per-system status if asked: 1 = zero pivot).  With
+    the same tensors (out, work and status passed in too) a large-block
+    solve replays its captured launch graph."""
     import torch
     A, B, C, b = (t.contiguous() for t in (A, B, C, b))
     if b.dim() != 4 or A.shape != B.shape or A.shape != C.shape or A.shape[:3] != b.shape[:3] \
@@ -475,11 +485,11 @@ def strip_solve(A, B, C, b, stream=None, return_status=False):
         raise ValueError("A, B, C must be float64 [nsys, N, m, m] and b float64 [nsys, N, m, r]")
     nsys, N, m, r = (int(v) for v in b.shape)
     lib = _load()
-    nbytes = ctypes.c_int64()
-    _check(lib.bc_strip_workspace(nsys, N, m, r, ctypes.byref(nbytes)))
-    work = torch.empty(max(1, nbytes.value // 8), dtype=torch.float64, device=b.device)
-    x = torch.empty_like(b)
-    status = torch.zeros(max(1, nsys), dtype=torch.int32, device=b.device)
+    if work is None:
+        work = strip_workspace(nsys, N, m, r, b.device)
+    x = torch.empty_like(b) if out is None else out
+    if status is None:
+        status = torch.zeros(max(1, nsys), dtype=torch.int32, device=b.device)
     _check(lib.bc_strip_solve(nsys, N, m, r, ctypes.c_void_p(A.data_ptr()), ctypes.c_void_p(B.data_ptr()),
                               ctypes.c_void_p(C.data_ptr()), ctypes.c_void_p(b.data_ptr()),
                               ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(work.data_ptr()),

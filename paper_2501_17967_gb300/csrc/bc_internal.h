@@ -410,14 +410,20 @@ cudaError_t launch_strip(int64_t nsys, int64_t N, int m, int r, const double *A,
                          const double *b, double *x, double *work, int32_t *status, cudaStream_t stream);
 // large blocks (m > 32): the pieces of the blocked LU, launched by strip.cpp
 int strip_panel_width();
+// shared-memory limit of the panel kernel for panels of up to nmax rows (before any capture)
+cudaError_t strip_prepare(int nmax);
 cudaError_t launch_strip_aug(int64_t N, int m, int r, int64_t k, const double *A, const double *B, const double *C,
                              const double *b, double *aug, int Wc, cudaStream_t stream);
 cudaError_t launch_strip_panel(double *M, int n, int ld, int j0, int jb, int32_t *piv, int32_t *status,
                                cudaStream_t stream);
-// which: 0 row exchanges, 1 L11^-1 (unit lower), 2 U11^-1, on columns [c0, c1)
-cudaError_t launch_strip_cols(int which, double *M, int ld, int j0, int jb, const int32_t *piv, int c0, int c1,
+// the row exchanges of the panel at j0 on columns [c0, c1)
+cudaError_t launch_strip_swap(double *M, int ld, int j0, int jb, const int32_t *piv, int c0, int c1,
                               cudaStream_t stream);
-cudaError_t launch_strip_cap(const double *G, int64_t N, int m, int r, int R, double *K, cudaStream_t stream);
+cudaError_t launch_strip_border(int64_t N, int m, int r, const double *A, const double *B, const double *C,
+                                const double *b, double *S, cudaStream_t stream);
+// rows [j0, j0 + jb) of columns [c0, c1) := L11^-1 (unit lower, upper = false)
+// or U11^-1 (upper = true) times themselves
+cudaError_t launch_strip_trsm(double *M, int ld, int j0, int jb, bool upper, int c0, int c1, cudaStream_t stream);
 // Batched applies: copy the per-tree arrays into / out of the union's vectors.
 constexpr int kBatchChunk = 96;   // trees per gather/scatter launch (pointer tables go by value)
 struct BatchPtrs {

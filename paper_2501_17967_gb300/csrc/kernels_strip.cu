@@ -201,15 +201,25 @@ __global__ void k_strip_solve(int64_t nsys, int64_t N, int m, int r, const doubl
 // the elements; each step factors the augmented block [D_k | B_k | rhs_k]
 // (row-major, Wc = m + m + R columns) by right-looking blocked LU with
 // partial pivoting (panels of kPanel columns: k_strip_panel factors a panel
-// in shared memory in one CTA, k_strip_swap and k_strip_trsm_l carry its row
-// exchanges and L11^-1 to the columns on its right, a DGEMM updates the
-// trailing block), then back-substitutes the right-hand columns
-// (k_strip_trsm_u per diagonal block, DGEMM for the rows above).
+// in shared memory in one CTA, k_strip_swap carries its row exchanges to the
+// columns on its right, k_strip_trsm applies L11^-1 to them (one thread per
+// column, so the many columns spread over the SMs), and a DGEMM updates the
+// trailing block), then back-substitutes the right-hand columns (k_strip_trsm
+// with U11 per diagonal block, DGEMM for the rows above).  Narrow panels keep
+// the single-CTA FP64 work of each panel small: one SM's FP64 pipe does 4
+// flop per clock.
 // ---------------------------------------------------------------------------
-constexpr int kPanel = 32;
+constexpr int kPanel = 16;
 constexpr int kPanelThreads = 512;
 
-// step k's augmented block: [A_k | B_k (k < N-1) | b_k | C_0 (k = 0) | B_{N-1} (k = N-1)]
+// Large blocks take the corners as a border: x_{N-1} is eliminated last.  The
+// first N - 1 block rows form a tridiagonal T' whose right-hand side also
+// carries the border column E (C_0 in row 0, B_{N-2} in row N-2: they couple
+// to x_{N-1}), so only m extra columns ride through the sweep; then the
+// Schur complement S = A_{N-1} - F T'^-1 E (F: B_{N-1} at column 0, C_{N-1}
+// at column N-2) gives x_{N-1}, and x_k = Y_k - Z_k x_{N-1}.  This is the
+// rank-m form of the corner correction.
+// Step k's augmented block (k < N - 1): [A_k | B_k (k < N-2) | b_k | E_k].
 __global__ void k_strip_aug(int64_t N, int m, int r, int64_t k, const double *__restrict__ A,
                             const double *__restrict__ B, const double *__restrict__ C,
                             const double *__restrict__ b, double *__restrict__ aug, int Wc)
@@ -220,11 +230,36 @@ __global__ void k_strip_aug(int64_t N, int m, int r, int64_t k, const double *__
         const int i = int(idx / Wc), c = int(idx % Wc);
         double v = 0.0;
         if (c < m) v = A[k * mm + size_t(i) * m + c];
-        else if (c < 2 * m) v = k < N - 1 ? B[k * mm + size_t(i) * m + (c - m)] : 0.0;
+        else if (c < 2 * m) v = k < N - 2 ? B[k * mm + size_t(i) * m + (c - m)] : 0.0;
         else if (c < 2 * m + r) v = b[(k * m + i) * r + (c - 2 * m)];
-        else if (c < 3 * m + r) v = k == 0 ? C[size_t(i) * m + (c - 2 * m - r)] : 0.0;
-        else v = k == N - 1 ? B[(N - 1) * mm + size_t(i) * m + (c - 3 * m - r)] : 0.0;
+        else {
+            const int q = c - 2 * m - r;
+            if (k == 0) v += C[size_t(i) * m + q];
+            if (k == N - 2) v += B[k * mm + size_t(i) * m + q];
+        }
         aug[idx] = v;
+    }
+}
+
+// the border system [A_{N-1} | b_{N-1}] (N = 1: [A_0 + B_0 + C_0 | b_0]),
+// before the products with T'^-1 [b | E] are taken off
+__global__ void k_strip_border(int64_t N, int m, int r, const double *__restrict__ A, const double *__restrict__ B,
+                               const double *__restrict__ C, const double *__restrict__ b, double *__restrict__ S)
+{
+    const size_t mm = size_t(m) * m;
+    const int ld = m + r;
+    const int64_t k = N - 1;
+    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < int64_t(m) * ld;
+         idx += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(idx / ld), c = int(idx % ld);
+        double v;
+        if (c < m) {
+            v = A[k * mm + size_t(i) * m + c];
+            if (N == 1) v += B[size_t(i) * m + c] + C[size_t(i) * m + c];
+        } else {
+            v = b[(k * m + i) * r + (c - m)];
+        }
+        S[idx] = v;
     }
 }
 
@@ -305,69 +340,40 @@ __global__ void k_strip_swap(double *__restrict__ M, int ld, int j0, int jb, con
     }
 }
 
-// U12 = L11^-1 A12 (L11 unit lower, the panel's top jb x jb) on columns [c0, c1)
-__global__ void k_strip_trsm_l(double *__restrict__ M, int ld, int j0, int jb, int c0, int c1)
+// Triangular solve with the jb x jb diagonal block at j0, in place on rows
+// [j0, j0 + jb) of the columns [c0, c1), one thread per column (jb <= kPanel):
+// upper = false: the unit lower block (L11^-1 A12); upper = true: the upper
+// block (U11^-1 Y).  A zero diagonal gives zero (the panel flagged it).
+__global__ void k_strip_trsm(double *__restrict__ M, int ld, int j0, int jb, bool upper, int c0, int c1)
 {
-    __shared__ double sl[kPanel * kPanel];
+    __shared__ double sa[kPanel * kPanel];
     for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x)
-        sl[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
+        sa[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
     __syncthreads();
     const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= c1) return;
     double x[kPanel];
 #pragma unroll
     for (int i = 0; i < kPanel; i++) x[i] = i < jb ? M[size_t(j0 + i) * ld + c] : 0.0;
+    if (!upper) {
 #pragma unroll
-    for (int i = 1; i < kPanel; i++) {
-        double s = x[i];
+        for (int i = 1; i < kPanel; i++)
 #pragma unroll
-        for (int q = 0; q < kPanel; q++)
-            if (q < i) s = fma(-sl[i * jb + q], x[q], s);
-        x[i] = s;
+            for (int q = 0; q < i; q++) x[i] = fma(-sa[i * jb + q], x[q], x[i]);   // x[q] = 0 past jb
+    } else {
+#pragma unroll
+        for (int i = kPanel - 1; i >= 0; i--) {
+            if (i >= jb) continue;
+#pragma unroll
+            for (int q = i + 1; q < kPanel; q++)
+                if (q < jb) x[i] = fma(-sa[i * jb + q], x[q], x[i]);
+            const double d = sa[i * jb + i];
+            x[i] = d != 0.0 ? x[i] / d : 0.0;
+        }
     }
 #pragma unroll
     for (int i = 0; i < kPanel; i++)
         if (i < jb) M[size_t(j0 + i) * ld + c] = x[i];
-}
-
-// X = U11^-1 Y (U11 the jb x jb diagonal block at j0) on columns [c0, c1)
-__global__ void k_strip_trsm_u(double *__restrict__ M, int ld, int j0, int jb, int c0, int c1)
-{
-    __shared__ double su[kPanel * kPanel];
-    for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x)
-        su[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
-    __syncthreads();
-    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= c1) return;
-    double x[kPanel];
-#pragma unroll
-    for (int i = 0; i < kPanel; i++) x[i] = i < jb ? M[size_t(j0 + i) * ld + c] : 0.0;
-#pragma unroll
-    for (int i = kPanel - 1; i >= 0; i--) {
-        if (i >= jb) continue;
-        double s = x[i];
-#pragma unroll
-        for (int q = 0; q < kPanel; q++)
-            if (q > i && q < jb) s = fma(-su[i * jb + q], x[q], s);
-        const double d = su[i * jb + i];
-        x[i] = d != 0.0 ? s / d : 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < kPanel; i++)
-        if (i < jb) M[size_t(j0 + i) * ld + c] = x[i];
-}
-
-// capacitance system of the Woodbury correction: [I + [Z_{N-1}; Z_0] | y_{N-1}; y_0]
-__global__ void k_strip_cap(const double *__restrict__ G, int64_t N, int m, int r, int R, double *__restrict__ K)
-{
-    const int n2 = 2 * m, ldk = n2 + r;
-    for (int64_t idx = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; idx < int64_t(n2) * ldk;
-         idx += int64_t(gridDim.x) * blockDim.x) {
-        const int i = int(idx / ldk), c = int(idx % ldk);
-        const int64_t blk = i < m ? N - 1 : 0;
-        const double *row = G + (blk * m + (i % m)) * R;
-        K[idx] = c < n2 ? row[r + c] + (c == i ? 1.0 : 0.0) : row[c - n2];
-    }
 }
 
 }  // namespace
@@ -382,31 +388,39 @@ cudaError_t launch_strip_aug(int64_t N, int m, int r, int64_t k, const double *A
     return cudaGetLastError();
 }
 
+cudaError_t strip_prepare(int nmax)
+{
+    return cudaFuncSetAttribute(k_strip_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(sizeof(double) * size_t(nmax) * kPanel));
+}
+
 cudaError_t launch_strip_panel(double *M, int n, int ld, int j0, int jb, int32_t *piv, int32_t *status,
                                cudaStream_t st)
 {
     const size_t sm = sizeof(double) * size_t(n - j0) * jb;
-    cudaError_t e = cudaFuncSetAttribute(k_strip_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm));
-    if (e != cudaSuccess) return e;
     k_strip_panel<<<1, kPanelThreads, sm, st>>>(M, n, ld, j0, jb, piv, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_strip_cols(int which, double *M, int ld, int j0, int jb, const int32_t *piv, int c0, int c1,
-                              cudaStream_t st)
+cudaError_t launch_strip_swap(double *M, int ld, int j0, int jb, const int32_t *piv, int c0, int c1, cudaStream_t st)
 {
     if (c1 <= c0) return cudaSuccess;
-    const int grid = (c1 - c0 + 127) / 128;
-    if (which == 0) k_strip_swap<<<grid, 128, 0, st>>>(M, ld, j0, jb, piv, c0, c1);
-    else if (which == 1) k_strip_trsm_l<<<grid, 128, 0, st>>>(M, ld, j0, jb, c0, c1);
-    else k_strip_trsm_u<<<grid, 128, 0, st>>>(M, ld, j0, jb, c0, c1);
+    k_strip_swap<<<(c1 - c0 + 127) / 128, 128, 0, st>>>(M, ld, j0, jb, piv, c0, c1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_strip_cap(const double *G, int64_t N, int m, int r, int R, double *K, cudaStream_t st)
+cudaError_t launch_strip_trsm(double *M, int ld, int j0, int jb, bool upper, int c0, int c1, cudaStream_t st)
 {
-    const int64_t n = int64_t(2 * m) * (2 * m + r);
-    k_strip_cap<<<int(std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(G, N, m, r, R, K);
+    if (c1 <= c0) return cudaSuccess;
+    k_strip_trsm<<<(c1 - c0 + 31) / 32, 32, 0, st>>>(M, ld, j0, jb, upper, c0, c1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_strip_border(int64_t N, int m, int r, const double *A, const double *B, const double *C,
+                                const double *b, double *S, cudaStream_t st)
+{
+    const int64_t n = int64_t(m) * (m + r);
+    k_strip_border<<<int(std::min<int64_t>((n + 255) / 256, 152 * 8)), 256, 0, st>>>(N, m, r, A, B, C, b, S);
     return cudaGetLastError();
 }
 

@@ -32,13 +32,20 @@ bool strip_shape_ok(int64_t nsys, int64_t N, int m, int r)
            (m <= kSmallM || N * int64_t(m) <= INT32_MAX / 4);
 }
 
+// large blocks, one system: H and G for the N - 1 blocks of T' (R = r + m),
+// the augmented block (2m + R columns) and the border system (m + r columns)
+size_t large_work_doubles(int64_t N, int m, int r)
+{
+    const size_t nt = size_t(std::max<int64_t>(N - 1, 1)), R = size_t(r) + m;
+    return nt * (size_t(m) * m + size_t(m) * R) + size_t(m) * (2 * m + R) + size_t(m) * (m + r);
+}
+
 // doubles of scratch: small blocks, per system; large blocks, one system's
-// H, G, the augmented block, the capacitance system, pivots and a status word
+// arrays, the pivots and a status word
 size_t strip_scratch_doubles(int64_t nsys, int64_t N, int m, int r)
 {
     if (m <= kSmallM) return size_t(nsys) * strip_work_doubles(N, m, r);
-    const size_t R = size_t(r) + 2 * m, Wc = 2 * size_t(m) + R;
-    return strip_work_doubles(N, m, r) + size_t(m) * Wc + size_t(2 * m) * (2 * m + r) + size_t(2 * m) + 2;
+    return large_work_doubles(N, m, r) + size_t(m) + 2;
 }
 
 // Row-major DGEMM: C (rows x cols, ldc) = alpha A (rows x k, lda) B (k x cols, ldb) + beta C
@@ -48,20 +55,49 @@ cublasStatus_t gemm_rm(cublasHandle_t h, int rows, int cols, int k, double alpha
     return cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, cols, rows, k, &alpha, B, ldb, A, lda, &beta, C, ldc);
 }
 
+// Per thread and device: a cuBLAS handle with its own workspace (so that its
+// calls can be captured into a graph), a private capture stream, and the
+// graph of the last large-block solve with its arguments.
+struct StripKey {
+    const void *p[7] = {};
+    int64_t nsys = 0, N = 0;
+    int m = 0, r = 0;
+    bool operator==(const StripKey &o) const
+    {
+        for (int i = 0; i < 7; i++)
+            if (p[i] != o.p[i]) return false;
+        return nsys == o.nsys && N == o.N && m == o.m && r == o.r;
+    }
+};
 struct Blas {
     cublasHandle_t h = nullptr;
     int device = -1;
+    void *ws = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    StripKey key;
 };
 thread_local Blas t_blas;
+constexpr size_t kBlasWorkspace = size_t(32) << 20;
 
-cublasHandle_t blas_for(int device)
+Blas *blas_for(int device)
 {
-    if (t_blas.h && t_blas.device == device) return t_blas.h;
+    if (t_blas.h && t_blas.device == device) return &t_blas;
+    if (t_blas.exec) cudaGraphExecDestroy(t_blas.exec);
     if (t_blas.h) cublasDestroy(t_blas.h);
-    t_blas.h = nullptr;
-    if (cublasCreate(&t_blas.h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+    if (t_blas.ws) cudaFree(t_blas.ws);
+    if (t_blas.cap) cudaStreamDestroy(t_blas.cap);
+    t_blas = Blas();
+    if (cublasCreate(&t_blas.h) != CUBLAS_STATUS_SUCCESS) { t_blas.h = nullptr; return nullptr; }
+    if (cudaMalloc(&t_blas.ws, kBlasWorkspace) != cudaSuccess ||
+        cublasSetWorkspace(t_blas.h, t_blas.ws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS ||
+        cudaStreamCreateWithFlags(&t_blas.cap, cudaStreamNonBlocking) != cudaSuccess ||
+        strip_prepare(2 * 448) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     t_blas.device = device;
-    return t_blas.h;
+    return &t_blas;
 }
 
 // LU with partial pivoting of M[:, 0:n] (row-major, ld), carried to the
@@ -75,8 +111,8 @@ bool lu_solve(cublasHandle_t h, double *M, int n, int ld, int c_rhs, int c_end, 
         const int jb = std::min(nb, n - j0), c0 = j0 + jb;
         if (launch_strip_panel(M, n, ld, j0, jb, piv, status, st) != cudaSuccess) return false;
         if (c0 < c_end) {
-            if (launch_strip_cols(0, M, ld, j0, jb, piv, c0, c_end, st) != cudaSuccess) return false;
-            if (launch_strip_cols(1, M, ld, j0, jb, piv, c0, c_end, st) != cudaSuccess) return false;
+            if (launch_strip_swap(M, ld, j0, jb, piv, c0, c_end, st) != cudaSuccess) return false;
+            if (launch_strip_trsm(M, ld, j0, jb, false, c0, c_end, st) != cudaSuccess) return false;
             if (c0 < n &&
                 gemm_rm(h, n - c0, c_end - c0, jb, -1.0, M + size_t(c0) * ld + j0, ld, M + size_t(j0) * ld + c0, ld,
                         1.0, M + size_t(c0) * ld + c0, ld) != CUBLAS_STATUS_SUCCESS)
@@ -86,7 +122,7 @@ bool lu_solve(cublasHandle_t h, double *M, int n, int ld, int c_rhs, int c_end, 
     const int last = ((n - 1) / nb) * nb;
     for (int j0 = last; j0 >= 0; j0 -= nb) {
         const int jb = std::min(nb, n - j0);
-        if (launch_strip_cols(2, M, ld, j0, jb, piv, c_rhs, c_end, st) != cudaSuccess) return false;
+        if (launch_strip_trsm(M, ld, j0, jb, true, c_rhs, c_end, st) != cudaSuccess) return false;
         if (j0 > 0 && gemm_rm(h, j0, c_end - c_rhs, jb, -1.0, M + j0, ld, M + size_t(j0) * ld + c_rhs, ld, 1.0,
                               M + c_rhs, ld) != CUBLAS_STATUS_SUCCESS)
             return false;
@@ -94,43 +130,60 @@ bool lu_solve(cublasHandle_t h, double *M, int n, int ld, int c_rhs, int c_end, 
     return true;
 }
 
-// One system with m > 32, on `st`; returns a CUDA/cuBLAS failure as false.
+// One system with m > 32, on `st` (the bordered form of the corner
+// correction, kernels_strip.cu); returns a CUDA/cuBLAS failure as false.
 bool solve_large(cublasHandle_t h, int64_t N, int m, int r, const double *A, const double *B, const double *C,
                  const double *b, double *x, double *work, int32_t *status, cudaStream_t st)
 {
-    const int R = r + 2 * m, Wc = 2 * m + R, n2 = 2 * m, ldk = n2 + r;
+    const int R = r + m, Wc = 2 * m + R, ldS = m + r;
     const size_t mm = size_t(m) * m;
-    double *H = work, *G = H + size_t(N) * mm, *aug = G + size_t(N) * m * R, *K = aug + size_t(m) * Wc;
-    int32_t *piv = reinterpret_cast<int32_t *>(K + size_t(n2) * ldk);
-    for (int64_t k = 0; k < N; k++) {
+    const int64_t Nt = N - 1;   // blocks of T'
+    double *H = work, *G = H + size_t(std::max<int64_t>(Nt, 1)) * mm;
+    double *aug = G + size_t(std::max<int64_t>(Nt, 1)) * m * R, *S = aug + size_t(m) * Wc;
+    int32_t *piv = reinterpret_cast<int32_t *>(S + size_t(m) * ldS);
+    for (int64_t k = 0; k < Nt; k++) {
         if (launch_strip_aug(N, m, r, k, A, B, C, b, aug, Wc, st) != cudaSuccess) return false;
         if (k > 0) {
-            // D_k = A_k - C_k H_{k-1};  rhs_k -= C_k g_{k-1}
+            // D_k = A_k - C_k H_{k-1};  [b_k | E_k] -= C_k [Y_{k-1} | Z_{k-1}]
             if (gemm_rm(h, m, m, m, -1.0, C + k * mm, m, H + (k - 1) * mm, m, 1.0, aug, Wc) != CUBLAS_STATUS_SUCCESS ||
                 gemm_rm(h, m, R, m, -1.0, C + k * mm, m, G + (k - 1) * size_t(m) * R, R, 1.0, aug + 2 * m, Wc) !=
                     CUBLAS_STATUS_SUCCESS)
                 return false;
         }
         if (!lu_solve(h, aug, m, Wc, m, Wc, piv, status, st)) return false;
-        if (k < N - 1 && cudaMemcpy2DAsync(H + k * mm, sizeof(double) * m, aug + m, sizeof(double) * Wc,
-                                           sizeof(double) * m, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        if (k < Nt - 1 && cudaMemcpy2DAsync(H + k * mm, sizeof(double) * m, aug + m, sizeof(double) * Wc,
+                                            sizeof(double) * m, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return false;
         if (cudaMemcpy2DAsync(G + k * size_t(m) * R, sizeof(double) * R, aug + 2 * m, sizeof(double) * Wc,
                               sizeof(double) * R, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return false;
     }
-    // X_k = g_k - H_k X_{k+1}
-    for (int64_t k = N - 2; k >= 0; k--)
+    // T'^-1 [b | E]: X_k = g_k - H_k X_{k+1}
+    for (int64_t k = Nt - 2; k >= 0; k--)
         if (gemm_rm(h, m, R, m, -1.0, H + k * mm, m, G + (k + 1) * size_t(m) * R, R, 1.0, G + k * size_t(m) * R, R) !=
             CUBLAS_STATUS_SUCCESS)
             return false;
-    // Woodbury: w = (I + [Z_{N-1}; Z_0])^-1 [y_{N-1}; y_0];  x = y - Z w
-    if (launch_strip_cap(G, N, m, r, R, K, st) != cudaSuccess) return false;
-    if (!lu_solve(h, K, n2, ldk, n2, ldk, piv, status, st)) return false;
-    if (cudaMemcpy2DAsync(x, sizeof(double) * r, G, sizeof(double) * R, sizeof(double) * r, size_t(N) * m,
+    // border: [S | s] = [A_{N-1} | b_{N-1}] - B_{N-1} [Z_0 | Y_0] - C_{N-1} [Z_{N-2} | Y_{N-2}]
+    if (launch_strip_border(N, m, r, A, B, C, b, S, st) != cudaSuccess) return false;
+    if (Nt > 0) {
+        const double *Bl = B + (N - 1) * mm, *Cl = C + (N - 1) * mm;
+        const double *G0 = G, *Gl = G + (Nt - 1) * size_t(m) * R;
+        if (gemm_rm(h, m, m, m, -1.0, Bl, m, G0 + r, R, 1.0, S, ldS) != CUBLAS_STATUS_SUCCESS ||
+            gemm_rm(h, m, r, m, -1.0, Bl, m, G0, R, 1.0, S + m, ldS) != CUBLAS_STATUS_SUCCESS ||
+            gemm_rm(h, m, m, m, -1.0, Cl, m, Gl + r, R, 1.0, S, ldS) != CUBLAS_STATUS_SUCCESS ||
+            gemm_rm(h, m, r, m, -1.0, Cl, m, Gl, R, 1.0, S + m, ldS) != CUBLAS_STATUS_SUCCESS)
+            return false;
+    }
+    if (!lu_solve(h, S, m, ldS, m, ldS, piv, status, st)) return false;
+    // x_{N-1} from the border, x_k = Y_k - Z_k x_{N-1}
+    if (cudaMemcpy2DAsync(x + size_t(Nt) * m * r, sizeof(double) * r, S + m, sizeof(double) * ldS,
+                          sizeof(double) * r, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return false;
+    if (Nt == 0) return true;
+    if (cudaMemcpy2DAsync(x, sizeof(double) * r, G, sizeof(double) * R, sizeof(double) * r, size_t(Nt) * m,
                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return false;
-    return gemm_rm(h, int(N * m), r, n2, -1.0, G + r, R, K + n2, ldk, 1.0, x, r) == CUBLAS_STATUS_SUCCESS;
+    return gemm_rm(h, int(Nt * m), r, m, -1.0, G + r, R, S + m, ldS, 1.0, x, r) == CUBLAS_STATUS_SUCCESS;
 }
 
 }  // namespace
@@ -172,25 +225,60 @@ bc_status bc_strip_solve(int64_t nsys, int64_t N, int m, int r, const double *A,
     }
     int dev = 0;
     cudaGetDevice(&dev);
-    cublasHandle_t h = blas_for(dev);
-    if (!h || cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS) {
+    Blas *bl = blas_for(dev);
+    if (!bl) {
         set_error("bc_strip_solve: cuBLAS handle unavailable");
         return BC_ERR_CUDA;
     }
+    cublasHandle_t h = bl->h;
+    // The sequence (some 10^4 launches for the paper's strip) is captured
+    // once into a CUDA graph on a private stream and replayed on `stream`
+    // while the arguments stay the same.
+    StripKey key;
+    const void *ptrs[7] = {A, B, C, b, x, work, status};
+    for (int i = 0; i < 7; i++) key.p[i] = ptrs[i];
+    key.nsys = nsys; key.N = N; key.m = m; key.r = r;
+    if (bl->exec && bl->key == key) {
+        const cudaError_t e = cudaGraphLaunch(bl->exec, st);
+        if (e == cudaSuccess) return BC_OK;
+        set_error("bc_strip_solve: %s", cudaGetErrorString(e));
+        return BC_ERR_CUDA;
+    }
+    if (bl->exec) {
+        cudaGraphExecDestroy(bl->exec);
+        bl->exec = nullptr;
+    }
+    cudaStream_t cs = bl->cap;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess ||
+        cublasSetStream(h, cs) != CUBLAS_STATUS_SUCCESS) {
+        set_error("bc_strip_solve: cannot capture");
+        return BC_ERR_CUDA;
+    }
     double *wk = static_cast<double *>(work);
-    const size_t per = strip_work_doubles(N, m, r) + size_t(m) * (2 * size_t(m) + r + 2 * m) +
-                       size_t(2 * m) * (2 * m + r);
-    int32_t *scratch_status = reinterpret_cast<int32_t *>(wk + per + size_t(2 * m) / 2 + 1);
+    int32_t *scratch_status = reinterpret_cast<int32_t *>(wk + large_work_doubles(N, m, r) + size_t(m) / 2 + 1);
     const size_t mm = size_t(m) * m;
-    for (int64_t s = 0; s < nsys; s++) {
+    bool ok = true;
+    for (int64_t s = 0; s < nsys && ok; s++) {
         int32_t *st_s = status ? status + s : scratch_status;
-        if (cudaMemsetAsync(st_s, 0, sizeof(int32_t), st) != cudaSuccess ||
-            !solve_large(h, N, m, r, A + s * N * mm, B + s * N * mm, C + s * N * mm, b + s * N * m * r,
-                         x + s * N * m * r, wk, st_s, st)) {
-            const cudaError_t e = cudaGetLastError();
-            set_error("bc_strip_solve: %s", e != cudaSuccess ? cudaGetErrorString(e) : "cuBLAS call failed");
-            return BC_ERR_CUDA;
-        }
+        ok = cudaMemsetAsync(st_s, 0, sizeof(int32_t), cs) == cudaSuccess &&
+             solve_large(h, N, m, r, A + s * N * mm, B + s * N * mm, C + s * N * mm, b + s * N * m * r,
+                         x + s * N * m * r, wk, st_s, cs);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+    cudaError_t e = ok ? ec : cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bl->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e == cudaSuccess) {
+        bl->key = key;
+        e = cudaGraphLaunch(bl->exec, st);
+    } else {
+        bl->exec = nullptr;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("bc_strip_solve: %s", ok ? cudaGetErrorString(e) : "a CUDA or cuBLAS call failed");
+        return BC_ERR_CUDA;
     }
     return BC_OK;
 }
