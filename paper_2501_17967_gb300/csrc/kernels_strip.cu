@@ -210,7 +210,7 @@ __global__ void k_strip_solve(int64_t nsys, int64_t N, int m, int r, const doubl
 // flop per clock.
 // ---------------------------------------------------------------------------
 constexpr int kPanel = 16;
-constexpr int kPanelThreads = 512;
+constexpr int kPanelThreads = 256;
 
 // Large blocks take the corners as a border: x_{N-1} is eliminated last.  The
 // first N - 1 block rows form a tridiagonal T' whose right-hand side also
@@ -266,6 +266,9 @@ __global__ void k_strip_border(int64_t N, int m, int r, const double *__restrict
 // LU with partial pivoting of the panel: rows [j0, n), columns [j0, j0 + jb)
 // of M (row-major, leading dimension ld), staged in shared memory; the pivot
 // rows go to piv[j] (absolute); a zero or non-finite pivot sets *status.
+// Thread t owns the rows t, t + nt, ...: it searches them for the pivot and
+// applies the rank-1 update to them, so a column step needs three barriers
+// (pivot found, pivot row in place, and the next step's search).
 __global__ void __launch_bounds__(kPanelThreads)
 k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__restrict__ piv,
               int32_t *__restrict__ status)
@@ -274,16 +277,16 @@ k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__
     __shared__ double s_best[kPanelThreads / 32];
     __shared__ int s_row[kPanelThreads / 32];
     __shared__ int s_piv;
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x, nw = nt >> 5;
     const int rows = n - j0;
     for (int idx = t; idx < rows * jb; idx += nt) sp[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
     __syncthreads();
     for (int jj = 0; jj < jb; jj++) {
         double best = -1.0;
         int bi = jj;
-        for (int i = jj + t; i < rows; i += nt) {
+        for (int i = jj + ((t - jj) % nt + nt) % nt; i < rows; i += nt) {   // owned rows >= jj
             const double v = fabs(sp[i * jb + jj]);
-            if (v > best) { best = v; bi = i; }
+            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -292,14 +295,19 @@ k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__
         }
         if (lane == 0) { s_best[w] = best; s_row[w] = bi; }
         __syncthreads();
-        if (t == 0) {
-            double bb = s_best[0];
-            int br = s_row[0];
-            for (int q = 1; q < nt / 32; q++)
-                if (s_best[q] > bb || (s_best[q] == bb && s_row[q] < br)) { bb = s_best[q]; br = s_row[q]; }
-            s_piv = br;
-            piv[j0 + jj] = j0 + br;
-            if (!(bb > 0.0) || !isfinite(bb)) *status = 1;
+        if (w == 0) {
+            best = lane < nw ? s_best[lane] : -1.0;
+            bi = lane < nw ? s_row[lane] : rows;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            }
+            if (lane == 0) {
+                s_piv = bi;
+                piv[j0 + jj] = j0 + bi;
+                if (!(best > 0.0) || !isfinite(best)) *status = 1;
+            }
         }
         __syncthreads();
         const int p = s_piv;
@@ -312,15 +320,13 @@ k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__
         __syncthreads();
         const double d = sp[jj * jb + jj];
         const double inv = (d != 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
-        for (int i = jj + 1 + t; i < rows; i += nt) sp[i * jb + jj] *= inv;
-        __syncthreads();
-        const int wc = jb - jj - 1;
-        for (int idx = t; idx < (rows - jj - 1) * wc; idx += nt) {
-            const int i = jj + 1 + idx / wc, c = jj + 1 + idx % wc;
-            sp[i * jb + c] = fma(-sp[i * jb + jj], sp[jj * jb + c], sp[i * jb + c]);
+        for (int i = jj + 1 + ((t - jj - 1) % nt + nt) % nt; i < rows; i += nt) {   // owned rows > jj
+            const double l = sp[i * jb + jj] * inv;
+            sp[i * jb + jj] = l;
+            for (int c = jj + 1; c < jb; c++) sp[i * jb + c] = fma(-l, sp[jj * jb + c], sp[i * jb + c]);
         }
-        __syncthreads();
     }
+    __syncthreads();
     for (int idx = t; idx < rows * jb; idx += nt) M[size_t(j0 + idx / jb) * ld + j0 + idx % jb] = sp[idx];
 }
 
@@ -347,8 +353,14 @@ __global__ void k_strip_swap(double *__restrict__ M, int ld, int j0, int jb, con
 __global__ void k_strip_trsm(double *__restrict__ M, int ld, int j0, int jb, bool upper, int c0, int c1)
 {
     __shared__ double sa[kPanel * kPanel];
+    __shared__ double sr[kPanel];   // reciprocals of the diagonal (upper)
     for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x)
         sa[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
+    __syncthreads();
+    if (upper && threadIdx.x < jb) {
+        const double d = sa[threadIdx.x * jb + threadIdx.x];
+        sr[threadIdx.x] = d != 0.0 ? 1.0 / d : 0.0;
+    }
     __syncthreads();
     const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= c1) return;
@@ -367,8 +379,7 @@ __global__ void k_strip_trsm(double *__restrict__ M, int ld, int j0, int jb, boo
 #pragma unroll
             for (int q = i + 1; q < kPanel; q++)
                 if (q < jb) x[i] = fma(-sa[i * jb + q], x[q], x[i]);
-            const double d = sa[i * jb + i];
-            x[i] = d != 0.0 ? x[i] / d : 0.0;
+            x[i] *= sr[i];
         }
     }
 #pragma unroll
