@@ -490,6 +490,22 @@ def strip_line(args, dev, steps, peak_fp64, check=True):
     return line
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest x over the ranks of the process group (x itself without
+    one): the whole-job time of replicas that ran side by side."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_units(units_per_rank: float, world: int) -> float:
+    """Units processed by the whole job: every replica does the same work."""
+    return float(units_per_rank) * world
+
+
 class Runner:
     """Timed forward + adjoint steps of one tree."""
 
@@ -530,9 +546,8 @@ class Runner:
         if self.world > 1:
             self.dist.barrier()
         bc._check(bc._load().bc_sync(self.ctx.handle, None))
-        total = torch.tensor([float(sum(a.elapsed_time(b) for a, b in ev))], dtype=torch.float64, device=self.dev)
-        if self.world > 1:
-            self.dist.all_reduce(total, op=self.dist.ReduceOp.MAX)
+        total = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), self.dist if self.world > 1 else None,
+                               self.dev)
         st = np.zeros((2, len(STAGES)))
         if stages:
             # per-stage times from a separate pass with the library's stage
@@ -546,7 +561,7 @@ class Runner:
                 st[1] += self.ctx.stage_times(adjoint=True)
             self.ctx.debug(timing=False)
             bc._check(bc._load().bc_sync(self.ctx.handle, None))
-        return float(total.item()) / steps, st / max(1, steps)
+        return total / steps, st / max(1, steps)
 
 
 def rooflines(stage_ms, wk, peaks, traffic):
@@ -646,7 +661,7 @@ def main():
 
     clocks = ClockSampler(dev)
     ms_step, stage_ms = run.timed(head, args.steps, args.warmup, sampler=clocks)
-    value = world * N / (ms_step * 1e-3)
+    value = replica_units(N, world) / (ms_step * 1e-3)
 
     # end to end through the public API with pinned host buffers
     fh = f.cpu().pin_memory()
