@@ -253,7 +253,8 @@ STAGE_KERNELS = {
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of each stage's
 # kernel in the bench configuration, keyed by (workload, nterms, precision):
 # filled from the ncu captures of the unchanged kernels, null otherwise
-TRAFFIC = {}
+# (the FP64 M2L: mean of one forward and one adjoint launch)
+TRAFFIC = {("adaptive200", 24, "split"): {"m2l": 10090752}}
 
 
 def stage_work(st, nleaf, nleaf_far, P1, NP, prec):
