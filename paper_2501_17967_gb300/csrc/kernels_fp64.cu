@@ -1576,9 +1576,10 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             const int64_t b0 = h.level_start[2], b1 = a.nbox;
             const int ng = m2l_groups(P1), nth = m2l_threads(P1);
             const size_t shM = sizeof(double2) * ng * (P1 + 1);
-            // beside the near-field tensor CTAs (late fork): 3 blocks per SM
-            // fit next to one of them (registers and shared memory)
-            const int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : (late ? 3 : 8)));
+            // beside the near-field tensor CTAs (late fork): 4 blocks per SM
+            // fit next to one of them (registers per sub-partition, and the
+            // shared memory the two-buffer tensor launch leaves)
+            const int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : (late ? 4 : 8)));
             const double2 *dsig = adj ? tb.dsig_a : tb.dsig_f, *dpw = adj ? tb.dpow_a : tb.dpow_f;
 #define BC_M2L(A, PM)                                                                                           \
     ce = launch_pdl(k_m2l_boxes<A, PM>, grid, nth, shM, st, b0, b1, d.v_ptr, d.v_src, d.v_code, d.box_level, dsig, \

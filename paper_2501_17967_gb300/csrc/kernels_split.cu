@@ -388,7 +388,7 @@ __device__ __forceinline__ int chunk_digit(int p, bool interleave)
     return interleave ? ((0x23140 >> (4 * p)) & 0xF) : p;
 }
 
-template <int KD>
+template <int KD, int NB = kNBuf>
 struct GemmShape {
     static constexpr int KC = KD < kSplitKC ? KD : kSplitKC;   // K columns per operator chunk
     static constexpr int NKC = KD / KC;
@@ -401,7 +401,7 @@ struct GemmShape {
     // MMAs run), one for K = 256 (120 KB)
     static constexpr int kBBuf = KD <= 64 ? 2 : 1;
     static constexpr int kBTile = kS * kBSlice;         // bytes of one tile's B
-    static constexpr size_t kSmem = size_t(kBBuf) * kBTile + size_t(kNBuf) * kChunk + 2 * kN * sizeof(ColMeta) +
+    static constexpr size_t kSmem = size_t(kBBuf) * kBTile + size_t(NB) * kChunk + 2 * kN * sizeof(ColMeta) +
                                     64 * sizeof(uint64_t);
 };
 
@@ -445,11 +445,14 @@ __global__ void __launch_bounds__(kGemmThreads, 2)
 k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__restrict__ err, long long wait_limit,
              int withhold)
 {
-    using Sh = GemmShape<KD>;
+    // the K = 256 launches beside the FP64 M2L (ICVT) keep two operator
+    // buffers: 32 KB less shared memory makes room for a fourth M2L block
+    constexpr int NB = (KD == 256 && ICVT) ? 2 : kNBuf;
+    using Sh = GemmShape<KD, NB>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t *Bs = smem;                                                      // kBBuf x kS x kBSlice
-    uint8_t *As = smem + Sh::kBBuf * Sh::kBTile;                             // kNBuf x kChunk
-    ColMeta *meta = reinterpret_cast<ColMeta *>(As + kNBuf * Sh::kChunk);    // [2][kN]
+    uint8_t *As = smem + Sh::kBBuf * Sh::kBTile;                             // NB x kChunk
+    ColMeta *meta = reinterpret_cast<ColMeta *>(As + NB * Sh::kChunk);       // [2][kN]
     GemmBars *bars = reinterpret_cast<GemmBars *>(meta + 2 * kN);
     volatile int *fail = &bars->fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -461,7 +464,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < kNBuf; i++) {
+        for (int i = 0; i < NB; i++) {
             mbar_init(&bars->lbar[i], 1);
             mbar_init(&bars->mbar[i], 1);
         }
@@ -504,8 +507,8 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                 }
                 tc_fence_after();
                 for (int g = 0; g < Sh::kChunksPerJob; g++, G++) {
-                    const int buf = int(G % kNBuf);
-                    if (!wait_bar(&bars->lbar[buf], uint32_t((G / kNBuf) & 1), wait_limit, fail)) {
+                    const int buf = int(G % NB);
+                    if (!wait_bar(&bars->lbar[buf], uint32_t((G / NB) & 1), wait_limit, fail)) {
                         failed = true;
                         break;
                     }
@@ -544,7 +547,7 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
             *fail = 1;
             int dummy = 0;   // bounded wait, without the failure shortcut
             if (last_commit >= 0)
-                wait_bar(&bars->mbar[int(last_commit % kNBuf)], uint32_t((last_commit / kNBuf) & 1), wait_limit,
+                wait_bar(&bars->mbar[int(last_commit % NB)], uint32_t((last_commit / NB) & 1), wait_limit,
                          &dummy);
         }
     } else if (warp == 1) {
@@ -556,10 +559,10 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
             const int mh = tl.rows > 128 ? 2 : 1;
             for (int h = 0; h < mh && !failed; h++)
                 for (int g = 0; g < Sh::kChunksPerJob; g++, n++) {
-                    const int buf = int(n % kNBuf);
-                    // buffer free once the MMAs of chunk n - kNBuf have completed
-                    if (n >= kNBuf &&
-                        !wait_bar(&bars->mbar[buf], uint32_t(((n - kNBuf) / kNBuf) & 1), wait_limit, fail)) {
+                    const int buf = int(n % NB);
+                    // buffer free once the MMAs of chunk n - NB have completed
+                    if (n >= NB &&
+                        !wait_bar(&bars->mbar[buf], uint32_t(((n - NB) / NB) & 1), wait_limit, fail)) {
                         failed = true;
                         break;
                     }
@@ -583,10 +586,10 @@ k_split_gemm(SplitGemm gm, double inv_alpha0, int inv_alpha_exp, int32_t *__rest
                 }
         }
         if (failed && !withhold) {
-            // copies still in flight: at most the last kNBuf issued
+            // copies still in flight: at most the last NB issued
             int dummy = 0;
-            for (long long q = n > kNBuf ? n - kNBuf : 0; q < n; q++)
-                wait_bar(&bars->lbar[int(q % kNBuf)], uint32_t((q / kNBuf) & 1), wait_limit, &dummy);
+            for (long long q = n > NB ? n - NB : 0; q < n; q++)
+                wait_bar(&bars->lbar[int(q % NB)], uint32_t((q / NB) & 1), wait_limit, &dummy);
         }
     } else if (warp < kEpiWarp0) {
         // ---------------- column metadata and B gather ----------------
@@ -767,9 +770,12 @@ size_t split_smem_bytes(int kd) { return kd == 256 ? GemmShape<256>::kSmem : Gem
 cudaError_t split_prepare()
 {
     cudaError_t e = cudaSuccess;
-    for (const void *k : {(const void *)k_split_gemm<256, false>, (const void *)k_split_gemm<256, true>})
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(GemmShape<256>::kSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(GemmShape<256>::kSmem));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_split_gemm<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(GemmShape<256, 2>::kSmem));
     for (const void *k : {(const void *)k_split_gemm<64, false>, (const void *)k_split_gemm<64, true>})
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem64);
     // the digit kernels run before and beside the tensor launches: the
@@ -816,7 +822,8 @@ cudaError_t launch_split_gemm(const SplitGemm &g, int kd, double inv_alpha0, int
     const int inv_alpha_exp = std::frexp(inv_alpha0, &ie) == 0.5 ? ie - 1 : kNoExp;
     if (kd == 256)
         return launch_pdl(intcvt ? k_split_gemm<256, true> : k_split_gemm<256, false>, grid, kGemmThreads,
-                          GemmShape<256>::kSmem, st, g, inv_alpha0, inv_alpha_exp, err, wait_limit, withhold);
+                          intcvt ? GemmShape<256, 2>::kSmem : GemmShape<256>::kSmem, st, g, inv_alpha0, inv_alpha_exp,
+                          err, wait_limit, withhold);
     return launch_pdl(intcvt ? k_split_gemm<64, true> : k_split_gemm<64, false>, grid, kGemmThreads, size_t(kSmem64),
                       st, g, inv_alpha0, inv_alpha_exp, err, wait_limit, withhold);
 }
