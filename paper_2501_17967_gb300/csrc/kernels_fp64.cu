@@ -434,7 +434,9 @@ __constant__ double c_binomT[32][32];
 // pairs v0 + g, v0 + g + NG, ...; per pair the group first forms a(e) in
 // shared memory (thread o its coefficient o), then every thread contracts it
 // with its column of B, held in registers (constant-memory reads with a
-// different index per lane would serialise).  The sums stay in registers
+// different index per lane would serialise).  The rows are double-buffered,
+// so one barrier per pair suffices (3.2 KB of shared memory per block: four
+// blocks still fit beside a two-buffer near-field CTA).  The sums stay in registers
 // until the groups meet in shared memory at the end of the box.  Nearly every
 // instruction is an FP64 FMA: 2 P1 per pair and thread, plus 8 for the two
 // diagonal scalings; NG P1 is a multiple of 32 wherever possible so that no
@@ -448,7 +450,7 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
             const double *__restrict__ lvtab, const double2 *__restrict__ in, double2 *__restrict__ out, int P1,
             int NG, int tri)
 {
-    extern __shared__ double2 sm2l[];   // [NG][P1 + 1]: a(e) of each group's pair, then the group sums
+    extern __shared__ double2 sm2l[];   // [NG][2][P1 + 1]: a(e) of each group's pair, then the group sums
     const int t = threadIdx.x, g = t / P1, o = t - g * P1;
     const bool act = g < NG;
     const int ld = P1 + 1;   // padded row: the groups' rows start in different banks
@@ -464,16 +466,19 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
     // end: released early, their resident blocks would take the SM space that
     // a near-field tensor CTA on the internal stream needs beside this kernel.
     griddep_wait();
-    double2 *arow = sm2l + (act ? g : 0) * ld;
+    // two rows per group (double buffer): a pair's row is written while
+    // other groups may still read the previous one, so one barrier per pair
+    double2 *arow0 = sm2l + 2 * (act ? g : 0) * ld;
     for (int64_t b = b0 + blockIdx.x; b < b1; b += gridDim.x) {
         const int v0 = v_ptr[b], v1 = v_ptr[b + 1];
         const double lgb = lvtab[kLvTab + box_level[b]];
         double accr = 0.0, acci = 0.0;
+        int buf = 0;
         for (int e0 = v0; e0 < v1; e0 += NG) {
             const int e = e0 + g;
             const bool live = act && e < v1;
+            double2 *arow = arow0 + buf * ld;
             int c = 0;
-            __syncthreads();   // the previous pair's a(e) has been read
             if (live) {
                 c = v_code[e];
                 // S_c[k] = (-1)^k W_c[k]: the sign is in bcol, so one table
@@ -483,33 +488,28 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
             }
             __syncthreads();
             if (live) {
-                double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
+                const double2 W = dpow[c * P1 + o];
+                double sr = 0.0, si = 0.0;
 #pragma unroll
-                for (int k = 0; k < PMAX; k += 2) {
+                for (int k = 0; k < PMAX; k++) {
                     if (k < P1) {
                         const double2 a = arow[k];
-                        sr0 = fma(bcol[k], a.x, sr0);
-                        si0 = fma(bcol[k], a.y, si0);
-                    }
-                    if (k + 1 < P1) {
-                        const double2 a = arow[k + 1];
-                        sr1 = fma(bcol[k + 1], a.x, sr1);
-                        si1 = fma(bcol[k + 1], a.y, si1);
+                        sr = fma(bcol[k], a.x, sr);
+                        si = fma(bcol[k], a.y, si);
                     }
                 }
-                double sr = sr0 + sr1, si = si0 + si1;
                 if (o == 0) {
                     const double c0 = logd[c] + lgb;
                     const double2 a = arow[0];
                     sr = fma(c0, a.x, sr);
                     si = fma(c0, a.y, si);
                 }
-                const double2 W = dpow[c * P1 + o];
                 accr = fma(sr, W.x, fma(-si, W.y, accr));
                 acci = fma(sr, W.y, fma(si, W.x, acci));
             }
+            buf ^= 1;
         }
-        __syncthreads();   // last a(e) read
+        __syncthreads();   // last rows read
         if (act) sm2l[g * ld + o] = make_double2(accr, acci);
         __syncthreads();
         if (t < P1) {
@@ -521,6 +521,7 @@ k_m2l_boxes(int64_t b0, int64_t b1, const int32_t *__restrict__ v_ptr, const int
             }
             out[b * P1 + t] = s;
         }
+        __syncthreads();   // group sums read before the next box's rows
     }
     griddep_launch_dependents();
 }
@@ -1575,7 +1576,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         } else {
             const int64_t b0 = h.level_start[2], b1 = a.nbox;
             const int ng = m2l_groups(P1), nth = m2l_threads(P1);
-            const size_t shM = sizeof(double2) * ng * (P1 + 1);
+            const size_t shM = sizeof(double2) * 2 * ng * (P1 + 1);
             // beside the near-field tensor CTAs (late fork): 4 blocks per SM
             // fit next to one of them (registers per sub-partition, and the
             // shared memory the two-buffer tensor launch leaves)
@@ -1688,7 +1689,7 @@ cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTre
     {
         const int64_t b0 = h.level_start[2], b1 = a.nbox;
         const int ng = m2l_groups(P1), nth = m2l_threads(P1);
-        const size_t shM = sizeof(double2) * ng * (P1 + 1);
+        const size_t shM = sizeof(double2) * 2 * ng * (P1 + 1);
         const int grid = grid_for(b1 - b0, 152 * (a.m2l_bps ? a.m2l_bps : 8));
 #define BC_M2LP(PM)                                                                                             \
     ce = launch_pdl(k_m2l_boxes<false, PM>, grid, nth, shM, st, b0, b1, fl.v_ptr, fl.v_src, fl.v_code,          \
