@@ -254,7 +254,7 @@ STAGE_KERNELS = {
 # kernel in the bench configuration, keyed by (workload, nterms, precision):
 # filled from the ncu captures of the unchanged kernels, null otherwise
 # (the FP64 M2L: mean of one forward and one adjoint launch)
-TRAFFIC = {("adaptive200", 24, "split"): {"m2l": 10090752}}
+TRAFFIC = {("adaptive200", 24, "split"): {"m2l": 10043776}}
 
 
 def stage_work(st, nleaf, nleaf_far, P1, NP, prec):
