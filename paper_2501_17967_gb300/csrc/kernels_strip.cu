@@ -274,39 +274,48 @@ k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__
               int32_t *__restrict__ status)
 {
     extern __shared__ double sp[];   // [n - j0][jb]
-    __shared__ double s_best[kPanelThreads / 32];
+    __shared__ unsigned long long s_key[kPanelThreads / 32];
     __shared__ int s_row[kPanelThreads / 32];
     __shared__ int s_piv;
+    __shared__ double s_inv;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5, nt = blockDim.x, nw = nt >> 5;
     const int rows = n - j0;
     for (int idx = t; idx < rows * jb; idx += nt) sp[idx] = M[size_t(j0 + idx / jb) * ld + j0 + idx % jb];
     __syncthreads();
+    // |x| compared through its bit pattern (sign cleared): an integer order
+    // that matches the order of the magnitudes, so the search leaves the FP64
+    // pipe to the updates (a NaN sorts above every number and is flagged)
+    constexpr unsigned long long kMag = 0x7FFFFFFFFFFFFFFFull;
     for (int jj = 0; jj < jb; jj++) {
-        double best = -1.0;
-        int bi = jj;
+        unsigned long long key = 0;
+        int bi = rows;
         for (int i = jj + ((t - jj) % nt + nt) % nt; i < rows; i += nt) {   // owned rows >= jj
-            const double v = fabs(sp[i * jb + jj]);
-            if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+            const unsigned long long v = static_cast<unsigned long long>(__double_as_longlong(sp[i * jb + jj])) & kMag;
+            if (bi == rows || v > key) { key = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            if (oi < rows && (bi == rows || ok > key || (ok == key && oi < bi))) { key = ok; bi = oi; }
         }
-        if (lane == 0) { s_best[w] = best; s_row[w] = bi; }
+        if (lane == 0) { s_key[w] = key; s_row[w] = bi; }
         __syncthreads();
         if (w == 0) {
-            best = lane < nw ? s_best[lane] : -1.0;
+            key = lane < nw ? s_key[lane] : 0ull;
             bi = lane < nw ? s_row[lane] : rows;
             for (int o = 16; o > 0; o >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+                if (oi < rows && (bi == rows || ok > key || (ok == key && oi < bi))) { key = ok; bi = oi; }
             }
             if (lane == 0) {
-                s_piv = bi;
-                piv[j0 + jj] = j0 + bi;
-                if (!(best > 0.0) || !isfinite(best)) *status = 1;
+                const int p = bi < rows ? bi : jj;
+                const double d = sp[p * jb + jj];
+                const bool good = d != 0.0 && isfinite(d);
+                s_piv = p;
+                s_inv = good ? 1.0 / d : 0.0;
+                piv[j0 + jj] = j0 + p;
+                if (!good) *status = 1;
             }
         }
         __syncthreads();
@@ -318,8 +327,7 @@ k_strip_panel(double *__restrict__ M, int n, int ld, int j0, int jb, int32_t *__
                 sp[p * jb + c] = x;
             }
         __syncthreads();
-        const double d = sp[jj * jb + jj];
-        const double inv = (d != 0.0 && isfinite(d)) ? 1.0 / d : 0.0;
+        const double inv = s_inv;
         for (int i = jj + 1 + ((t - jj - 1) % nt + nt) % nt; i < rows; i += nt) {   // owned rows > jj
             const double l = sp[i * jb + jj] * inv;
             sp[i * jb + jj] = l;
