@@ -69,11 +69,13 @@ struct StripKey {
         return nsys == o.nsys && N == o.N && m == o.m && r == o.r;
     }
 };
+constexpr int kMaxPanels = 64;   // panels of one LU: up to 448 rows / 16, with room
 struct Blas {
-    cublasHandle_t h = nullptr;
+    cublasHandle_t h = nullptr, h2 = nullptr;   // one per capture stream (own workspaces)
     int device = -1;
-    void *ws = nullptr;
-    cudaStream_t cap = nullptr;
+    void *ws = nullptr, *ws2 = nullptr;
+    cudaStream_t cap = nullptr, cap2 = nullptr;
+    cudaEvent_t evA[kMaxPanels] = {}, evB[kMaxPanels] = {};
     cudaGraphExec_t exec = nullptr;
     StripKey key;
 };
@@ -85,14 +87,29 @@ Blas *blas_for(int device)
     if (t_blas.h && t_blas.device == device) return &t_blas;
     if (t_blas.exec) cudaGraphExecDestroy(t_blas.exec);
     if (t_blas.h) cublasDestroy(t_blas.h);
+    if (t_blas.h2) cublasDestroy(t_blas.h2);
     if (t_blas.ws) cudaFree(t_blas.ws);
+    if (t_blas.ws2) cudaFree(t_blas.ws2);
     if (t_blas.cap) cudaStreamDestroy(t_blas.cap);
+    if (t_blas.cap2) cudaStreamDestroy(t_blas.cap2);
+    for (int i = 0; i < kMaxPanels; i++) {
+        if (t_blas.evA[i]) cudaEventDestroy(t_blas.evA[i]);
+        if (t_blas.evB[i]) cudaEventDestroy(t_blas.evB[i]);
+    }
     t_blas = Blas();
     if (cublasCreate(&t_blas.h) != CUBLAS_STATUS_SUCCESS) { t_blas.h = nullptr; return nullptr; }
-    if (cudaMalloc(&t_blas.ws, kBlasWorkspace) != cudaSuccess ||
-        cublasSetWorkspace(t_blas.h, t_blas.ws, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS ||
-        cudaStreamCreateWithFlags(&t_blas.cap, cudaStreamNonBlocking) != cudaSuccess ||
-        strip_prepare(2 * 448) != cudaSuccess) {
+    if (cublasCreate(&t_blas.h2) != CUBLAS_STATUS_SUCCESS) { t_blas.h2 = nullptr; return nullptr; }
+    bool ok = cudaMalloc(&t_blas.ws, kBlasWorkspace) == cudaSuccess &&
+              cudaMalloc(&t_blas.ws2, kBlasWorkspace) == cudaSuccess &&
+              cublasSetWorkspace(t_blas.h, t_blas.ws, kBlasWorkspace) == CUBLAS_STATUS_SUCCESS &&
+              cublasSetWorkspace(t_blas.h2, t_blas.ws2, kBlasWorkspace) == CUBLAS_STATUS_SUCCESS &&
+              cudaStreamCreateWithFlags(&t_blas.cap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&t_blas.cap2, cudaStreamNonBlocking) == cudaSuccess &&
+              strip_prepare(2 * 448) == cudaSuccess;
+    for (int i = 0; ok && i < kMaxPanels; i++)
+        ok = cudaEventCreateWithFlags(&t_blas.evA[i], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&t_blas.evB[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
         return nullptr;
     }
@@ -103,27 +120,51 @@ Blas *blas_for(int device)
 // LU with partial pivoting of M[:, 0:n] (row-major, ld), carried to the
 // columns [n, c_end), then back substitution on the columns [c_rhs, c_end):
 // those columns end as M[:, 0:n]^-1 times their input.
-bool lu_solve(cublasHandle_t h, double *M, int n, int ld, int c_rhs, int c_end, int32_t *piv, int32_t *status,
-              cudaStream_t st)
+// The panels' updates of the columns right of the next panel run on a second
+// captured stream (look-ahead): while they run, the first stream updates the
+// next panel's columns alone and factors that panel, which is the critical
+// path.  A column block gets its row exchanges and updates in panel order:
+// the next panel's columns wait for the second stream's previous update.
+bool lu_solve(const Blas &bl, double *M, int n, int ld, int c_rhs, int c_end, int32_t *piv, int32_t *status,
+              cudaStream_t A)
 {
-    const int nb = strip_panel_width();
-    for (int j0 = 0; j0 < n; j0 += nb) {
-        const int jb = std::min(nb, n - j0), c0 = j0 + jb;
-        if (launch_strip_panel(M, n, ld, j0, jb, piv, status, st) != cudaSuccess) return false;
-        if (c0 < c_end) {
-            if (launch_strip_swap(M, ld, j0, jb, piv, c0, c_end, st) != cudaSuccess) return false;
-            if (launch_strip_trsm(M, ld, j0, jb, false, c0, c_end, st) != cudaSuccess) return false;
-            if (c0 < n &&
-                gemm_rm(h, n - c0, c_end - c0, jb, -1.0, M + size_t(c0) * ld + j0, ld, M + size_t(j0) * ld + c0, ld,
-                        1.0, M + size_t(c0) * ld + c0, ld) != CUBLAS_STATUS_SUCCESS)
+    const int nb = strip_panel_width(), np = (n + nb - 1) / nb;
+    cudaStream_t B = bl.cap2;
+    if (np > kMaxPanels || cublasSetStream(bl.h2, B) != CUBLAS_STATUS_SUCCESS) return false;
+    if (cudaEventRecord(bl.evA[0], A) != cudaSuccess || cudaStreamWaitEvent(B, bl.evA[0], 0) != cudaSuccess)
+        return false;
+    if (launch_strip_panel(M, n, ld, 0, std::min(nb, n), piv, status, A) != cudaSuccess) return false;
+    for (int p = 0; p < np; p++) {
+        const int j0 = p * nb, jb = std::min(nb, n - j0), c0 = j0 + jb;
+        const int nx1 = c0 < n ? std::min(c0 + nb, n) : c0;   // end of the next panel's columns
+        if (cudaEventRecord(bl.evA[p], A) != cudaSuccess) return false;   // panel p factored
+        if (c0 < n) {
+            if (p > 0 && cudaStreamWaitEvent(A, bl.evB[p - 1], 0) != cudaSuccess) return false;
+            if (launch_strip_swap(M, ld, j0, jb, piv, c0, nx1, A) != cudaSuccess ||
+                launch_strip_trsm(M, ld, j0, jb, false, c0, nx1, A) != cudaSuccess ||
+                gemm_rm(bl.h, n - c0, nx1 - c0, jb, -1.0, M + size_t(c0) * ld + j0, ld, M + size_t(j0) * ld + c0,
+                        ld, 1.0, M + size_t(c0) * ld + c0, ld) != CUBLAS_STATUS_SUCCESS ||
+                launch_strip_panel(M, n, ld, c0, nx1 - c0, piv, status, A) != cudaSuccess)
                 return false;
         }
+        if (nx1 < c_end) {
+            if (cudaStreamWaitEvent(B, bl.evA[p], 0) != cudaSuccess ||
+                launch_strip_swap(M, ld, j0, jb, piv, nx1, c_end, B) != cudaSuccess ||
+                launch_strip_trsm(M, ld, j0, jb, false, nx1, c_end, B) != cudaSuccess)
+                return false;
+            if (c0 < n && gemm_rm(bl.h2, n - c0, c_end - nx1, jb, -1.0, M + size_t(c0) * ld + j0, ld,
+                                  M + size_t(j0) * ld + nx1, ld, 1.0, M + size_t(c0) * ld + nx1, ld) !=
+                              CUBLAS_STATUS_SUCCESS)
+                return false;
+        }
+        if (cudaEventRecord(bl.evB[p], B) != cudaSuccess) return false;
     }
+    if (cudaStreamWaitEvent(A, bl.evB[np - 1], 0) != cudaSuccess) return false;
     const int last = ((n - 1) / nb) * nb;
     for (int j0 = last; j0 >= 0; j0 -= nb) {
         const int jb = std::min(nb, n - j0);
-        if (launch_strip_trsm(M, ld, j0, jb, true, c_rhs, c_end, st) != cudaSuccess) return false;
-        if (j0 > 0 && gemm_rm(h, j0, c_end - c_rhs, jb, -1.0, M + j0, ld, M + size_t(j0) * ld + c_rhs, ld, 1.0,
+        if (launch_strip_trsm(M, ld, j0, jb, true, c_rhs, c_end, A) != cudaSuccess) return false;
+        if (j0 > 0 && gemm_rm(bl.h, j0, c_end - c_rhs, jb, -1.0, M + j0, ld, M + size_t(j0) * ld + c_rhs, ld, 1.0,
                               M + c_rhs, ld) != CUBLAS_STATUS_SUCCESS)
             return false;
     }
@@ -132,9 +173,10 @@ bool lu_solve(cublasHandle_t h, double *M, int n, int ld, int c_rhs, int c_end, 
 
 // One system with m > 32, on `st` (the bordered form of the corner
 // correction, kernels_strip.cu); returns a CUDA/cuBLAS failure as false.
-bool solve_large(cublasHandle_t h, int64_t N, int m, int r, const double *A, const double *B, const double *C,
+bool solve_large(const Blas &bl, int64_t N, int m, int r, const double *A, const double *B, const double *C,
                  const double *b, double *x, double *work, int32_t *status, cudaStream_t st)
 {
+    cublasHandle_t h = bl.h;
     const int R = r + m, Wc = 2 * m + R, ldS = m + r;
     const size_t mm = size_t(m) * m;
     const int64_t Nt = N - 1;   // blocks of T'
@@ -150,7 +192,7 @@ bool solve_large(cublasHandle_t h, int64_t N, int m, int r, const double *A, con
                     CUBLAS_STATUS_SUCCESS)
                 return false;
         }
-        if (!lu_solve(h, aug, m, Wc, m, Wc, piv, status, st)) return false;
+        if (!lu_solve(bl, aug, m, Wc, m, Wc, piv, status, st)) return false;
         if (k < Nt - 1 && cudaMemcpy2DAsync(H + k * mm, sizeof(double) * m, aug + m, sizeof(double) * Wc,
                                             sizeof(double) * m, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return false;
@@ -174,7 +216,7 @@ bool solve_large(cublasHandle_t h, int64_t N, int m, int r, const double *A, con
             gemm_rm(h, m, r, m, -1.0, Cl, m, Gl, R, 1.0, S + m, ldS) != CUBLAS_STATUS_SUCCESS)
             return false;
     }
-    if (!lu_solve(h, S, m, ldS, m, ldS, piv, status, st)) return false;
+    if (!lu_solve(bl, S, m, ldS, m, ldS, piv, status, st)) return false;
     // x_{N-1} from the border, x_k = Y_k - Z_k x_{N-1}
     if (cudaMemcpy2DAsync(x + size_t(Nt) * m * r, sizeof(double) * r, S + m, sizeof(double) * ldS,
                           sizeof(double) * r, m, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -261,7 +303,7 @@ bc_status bc_strip_solve(int64_t nsys, int64_t N, int m, int r, const double *A,
     for (int64_t s = 0; s < nsys && ok; s++) {
         int32_t *st_s = status ? status + s : scratch_status;
         ok = cudaMemsetAsync(st_s, 0, sizeof(int32_t), cs) == cudaSuccess &&
-             solve_large(h, N, m, r, A + s * N * mm, B + s * N * mm, C + s * N * mm, b + s * N * m * r,
+             solve_large(*bl, N, m, r, A + s * N * mm, B + s * N * mm, C + s * N * mm, b + s * N * m * r,
                          x + s * N * m * r, wk, st_s, cs);
     }
     cudaGraph_t graph = nullptr;
