@@ -420,6 +420,8 @@ bc_status upload_tree(bc_tree *t)
 #undef UPV
     e = dev_upload<int32_t>(d.allocs, &d.zero_ptr, nullptr, size_t(h.nleaf) + 1);
     if (e != cudaSuccess) return cuda_fail(e, "tree upload");
+    e = dev_upload<double2>(d.allocs, &d.leaf_logs, nullptr, size_t(h.nleaf));
+    if (e != cudaSuccess) return cuda_fail(e, "tree upload");
     if (!h.leaf_class.empty()) {
         std::vector<uint8_t> act(h.nleaf);
         for (int64_t k = 0; k < h.nleaf; k++) act[k] = h.leaf_class[k] != 0;

@@ -188,6 +188,7 @@ struct DevTree {
     double2 *PX = nullptr;                             // [n_x][P1] X-list product of each entry (FP64 path)
     double2 *expA = nullptr, *expB = nullptr;  // [nbox][P1] workspaces
     int32_t *zero_ptr = nullptr;               // [nleaf+1] zeros: empty lists (diagnostic pass masks)
+    double2 *leaf_logs = nullptr;              // [nleaf] the W and near lists' log-term sums of each target leaf
     double *lvtab = nullptr;                   // [2][kLvTab]: r^2 and log r per level
     int64_t *level_start = nullptr;            // [nlevels + 1] first box of each level
     int32_t *flag = nullptr;                   // [nbox] completion flags of the persistent level passes

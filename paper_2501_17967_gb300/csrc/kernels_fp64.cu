@@ -1106,6 +1106,38 @@ inline size_t down_warps_smem_bytes(int P1, int T, int maxp, int nwarps)
 // first warp sums them over the W and near lists, one entry per lane, so the
 // products of the lists are plain streams of independent loads.
 // -------------------------------------------------------------------------
+// The log-term sums of each target leaf's W and near lists (one warp per
+// leaf, one entry per lane), computed before the leaf output so that its
+// blocks stream the partial rows without waiting on this gather:
+//   logs[o].x = sum_W A_0(w),  logs[o].y = sum_near log(r_s) A_0(s)  (forward)
+//                                          sum_near B_0(s)           (adjoint)
+template <bool ADJ>
+__global__ void __launch_bounds__(256)
+k_leaf_logs(int64_t nleaf, const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ leaf_level,
+            const int32_t *__restrict__ w_ptr, const int32_t *__restrict__ w_src, const int32_t *__restrict__ n_ptr,
+            const int32_t *__restrict__ n_src, const double2 *__restrict__ src, const double2 *__restrict__ aux,
+            const double *__restrict__ lvtab, int P1, double2 *__restrict__ logs)
+{
+    griddep_wait();
+    griddep_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t o = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); o < nleaf; o += nw) {
+        double lw = 0.0, ln = 0.0;
+        for (int e = w_ptr[o] + lane; e < w_ptr[o + 1]; e += 32) lw += src[int64_t(w_src[e]) * P1].x;
+        for (int e = n_ptr[o] + lane; e < n_ptr[o + 1]; e += 32) {
+            const int s = n_src[e];
+            const double a0 = aux[int64_t(leaf_box[s]) * P1].x;
+            ln += ADJ ? a0 : lvtab[kLvTab + leaf_level[s]] * a0;
+        }
+        for (int m = 16; m > 0; m >>= 1) {
+            lw += __shfl_xor_sync(0xffffffffu, lw, m);
+            ln += __shfl_xor_sync(0xffffffffu, ln, m);
+        }
+        if (lane == 0) logs[o] = make_double2(lw, ln);
+    }
+}
+
 template <bool ADJ>
 __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ leaf_level,
@@ -1118,7 +1150,8 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                            const double2 *__restrict__ aux, const double *__restrict__ vnear,
                            double *__restrict__ vout, int NP, int P1, const double *__restrict__ lvtab, bool far,
                            const double *__restrict__ Pnear, const double *__restrict__ PE,
-                           const double *__restrict__ PW, const uint8_t *__restrict__ active)
+                           const double *__restrict__ PW, const uint8_t *__restrict__ active,
+                           const double2 *__restrict__ logs)
 {
     griddep_wait();
     griddep_launch_dependents();
@@ -1140,8 +1173,8 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
         // adjoint log term of a target leaf o: r_o^2 log(r_o) w_j / (2 pi)
         const double cO = ADJ ? r2o * lgo * wj * kInvTwoPi : lgo;
         const int w0 = w_ptr[o], w1 = w_ptr[o + 1], n0 = n_ptr[o], n1 = n_ptr[o + 1];
-        __syncthreads();   // s_log of the previous leaf has been read
-        if (threadIdx.x < 32) {
+        if (!logs) __syncthreads();   // s_log of the previous leaf has been read
+        if (!logs && threadIdx.x < 32) {
             // The log terms of the W and near sources, gathered by the first
             // warp (one entry per lane) while the others start on the products:
             //   lw = sum_W A_0(w)              (times cO below)
@@ -1210,9 +1243,18 @@ __global__ void k_leaf_out(int64_t nleaf, const int32_t *__restrict__ order,
                 acc = fma(ADJ ? r2o : lvtab[leaf_level[s]], t, acc);
             }
         }
-        __syncthreads();   // s_log written
-        acc = fma(cO, s_log[0], acc);
-        acc = ADJ ? fma(cO, s_log[1], acc) : acc + s_log[1];
+        double l0, l1;
+        if (logs) {
+            const double2 lg = logs[o];
+            l0 = lg.x;
+            l1 = lg.y;
+        } else {
+            __syncthreads();   // s_log written
+            l0 = s_log[0];
+            l1 = s_log[1];
+        }
+        acc = fma(cO, l0, acc);
+        acc = ADJ ? fma(cO, l1, acc) : acc + l1;
         vout[int64_t(o) * NP + j] = acc;
     }
 }
@@ -1645,6 +1687,17 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         ce = launch_split_gemm(g, kSplitKE, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
         if (ce != cudaSuccess) return ce;
     }
+    // the log-term sums of every leaf's W and near lists (they read `first`
+    // only), before the join: they run while the near field finishes
+    {
+        const int32_t *wl = far ? d.w_ptr : d.zero_ptr, *nl = near ? d.near_ptr : d.zero_ptr;
+        const int lgrid = grid_for((a.nleaf + 7) / 8, 152 * 8);
+        ce = adj ? launch_pdl(k_leaf_logs<true>, lgrid, 256, 0, st, a.nleaf, d.leaf_box, d.leaf_level, wl, d.w_src,
+                              nl, d.near_src, first, first, d.lvtab, P1, d.leaf_logs)
+                 : launch_pdl(k_leaf_logs<false>, lgrid, 256, 0, st, a.nleaf, d.leaf_box, d.leaf_level, wl, d.w_src,
+                              nl, d.near_src, first, first, d.lvtab, P1, d.leaf_logs);
+        if (ce != cudaSuccess) return ce;
+    }
     if (ev) cudaEventRecord(ev[6], st);
     if (split && split->side && (ce = cudaStreamWaitEvent(st, split->side->join, 0)) != cudaSuccess) return ce;
     // leafB: own expansion = second (local / adjoint multipole), W sources and
@@ -1656,11 +1709,11 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
     if (adj)
         ce = launch_pdl(k_leaf_out<true>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                         wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active);
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active, d.leaf_logs);
     else
         ce = launch_pdl(k_leaf_out<false>, grid_leaf, NP, shD, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level,
                         wp, d.w_src, d.w_code, np_, d.near_src, d.near_tab, op.e, op.w, op.t, tb.wvec, second, first,
-                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active);
+                        first, vin, vout, NP, P1, d.lvtab, far, Pnear, PE, PW, d.leaf_active, d.leaf_logs);
     if (ce != cudaSuccess) return ce;
     if (ev) cudaEventRecord(ev[7], st);
     return cudaGetLastError();
