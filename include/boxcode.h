@@ -335,10 +335,11 @@ bc_status bc_table_export(const bc_ctx *ctx, int which, int64_t *count, double *
  *     split-precision kernel before it gives up, records the failure (reported
  *     by bc_sync as BC_ERR_TIMEOUT), frees its tensor memory and returns; the
  *     level passes' box flags poll a sixteenth of it and report the same way.
- *   "split_overlap" (0/1, default 1): the X-list and near-field tensor-core
+ *   "split_overlap" (0..3, default 1): the X-list and near-field tensor-core
  *     launches of a split-precision apply run on an internal stream and are
  *     joined before the downward pass (X list) and the leaf output (near
- *     field) (1), or in line on the apply's stream (0).  With the M2L in FP64
+ *     field) (1; 2 in the forward apply only, 3 in the adjoint only), or in
+ *     line on the apply's stream (0).  With the M2L in FP64
  *     (BC_SPLIT_BF16) they start after the upward pass and run beside the
  *     FP64 M2L (they use the tensor cores, it the FP64 units); with the
  *     tensor-core M2L (BC_SPLIT_BF16_ALL) they start at once, beside the

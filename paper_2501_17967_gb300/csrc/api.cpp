@@ -921,8 +921,11 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     bool din = is_device_ptr(vin), dout = is_device_ptr(vout);
     if (din != dout) { set_error("apply: input and output must both be device or both host memory"); return BC_ERR_ARG; }
     const int parts = split_parts_for(int(prec), ctx->split_parts);
-    SplitLaunch sl{&ctx->split, nullptr, parts, ctx->split_overlap ? &ctx->side : nullptr,
-                   near_ctas_for(ctx, parts)};
+    // split_overlap: 1 both directions beside the far field, 2 the forward
+    // apply only, 3 the adjoint only, 0 neither
+    const int ov = ctx->split_overlap;
+    const bool side = ov == 1 || (ov == 2 && !adj) || (ov == 3 && adj);
+    SplitLaunch sl{&ctx->split, nullptr, parts, side ? &ctx->side : nullptr, near_ctas_for(ctx, parts)};
     const SplitLaunch *split = nullptr;
     bc_tree *tw = const_cast<bc_tree *>(tree);
     if (is_split(prec)) {
@@ -1019,8 +1022,9 @@ bc_status batch_capture(bc_batch *b, int prec, int adj, int leaf_bps, int m2l_bp
     a.leaf_bps = leaf_bps;
     if (m2l_bps) a.m2l_bps = m2l_bps;
     const int parts = split_parts_for(prec, ctx->split_parts);
-    SplitLaunch sl{&ctx->split, &b->u->sp, parts, ctx->split_overlap ? &ctx->side : nullptr,
-                   near_ctas_for(ctx, parts)};
+    const int ov = ctx->split_overlap;
+    const bool side = ov == 1 || (ov == 2 && !adj) || (ov == 3 && adj);
+    SplitLaunch sl{&ctx->split, &b->u->sp, parts, side ? &ctx->side : nullptr, near_ctas_for(ctx, parts)};
     if (is_split(prec) && (parts & 32)) {   // before the capture: it allocates
         bc_status s = build_split_m2l(b->u);
         if (s != BC_OK) return s;
@@ -1693,7 +1697,11 @@ bc_status bc_set_option(bc_ctx *ctx, const char *name, double value)
         return BC_OK;
     }
     if (std::strcmp(name, "split_overlap") == 0) {
-        ctx->split_overlap = value != 0.0;
+        if (!(value >= 0.0 && value <= 3.0) || value != std::floor(value)) {
+            set_error("bc_set_option: split_overlap must be 0, 1, 2 or 3");
+            return BC_ERR_ARG;
+        }
+        ctx->split_overlap = int(value);
         return BC_OK;
     }
     if (std::strcmp(name, "split_overlap_ctas") == 0) {

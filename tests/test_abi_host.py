@@ -64,13 +64,14 @@ def test_set_option_validation(hctx):
     give BC_ERR_ARG; valid values are accepted."""
     for name, bad in (("debug_split_parts", 128), ("debug_split_parts", -2), ("debug_split_parts", 2.5),
                       ("wait_limit", 0), ("split_overlap_ctas", -1), ("split_overlap_ctas", 2.5),
-                      ("no_such_option", 1)):
+                      ("split_overlap", 4), ("split_overlap", 0.5), ("no_such_option", 1)):
         with pytest.raises(bc.BoxCodeError) as e:
             hctx.set_option(name, bad)
         assert e.value.status == -1, (name, bad)
     for name, good in (("debug_split_parts", 0), ("debug_split_parts", 127), ("debug_split_parts", -1),
                        ("wait_limit", 2 ** 26),
-                       ("m2l_triangular", 0), ("split_overlap_ctas", 76), ("split_overlap_ctas", 0)):
+                       ("m2l_triangular", 0), ("split_overlap_ctas", 76), ("split_overlap_ctas", 0),
+                       ("split_overlap", 2), ("split_overlap", 1)):
         hctx.set_option(name, good)
 
 
