@@ -29,7 +29,8 @@
 //              tile; the next tile's slices are gathered as the current tile's
 //              last job stops reading them;
 //   A operand: the operator's digits, 128 rows x 128 columns per chunk (32 KB),
-//              brought in by bulk asynchronous copies through three buffers;
+//              brought in by bulk asynchronous copies through three buffers
+//              (two in the K = 256 launches beside the FP64 M2L);
 //              a tile's first row-half job takes the operator digits in the
 //              order 0, 4, 1, 3, 2 (long and short chunks alternate, so copies
 //              keep up), its last job in the order 0..4 (B slices are freed
