@@ -695,9 +695,10 @@ def main():
              "hbm": peaks_file.get("hbm_gbs", 6800.0)}
     nleaf_far = int((lv >= 2).sum())
 
-    def arrangement_work(prec):
+    def arrangement_work(prec, overlap=None):
+        overlap = args.overlap if overlap is None else overlap
         wk = stage_work(st, tree.nleaf, nleaf_far, P1, P * P, prec)
-        if prec and not args.overlap:
+        if prec and not overlap:
             wk["tensor_v"] = (wk["tensor_v"][0] + wk["tensor_near"][0], "tensor")   # one group-V launch
             wk["tensor_near"] = (0.0, "tensor")
         elif prec:
@@ -725,6 +726,19 @@ def main():
             "roofline": roofline}
 
     if not args.no_extras:
+        # the same precision with the tensor launches in line (nothing beside
+        # them): each kernel's rate alone
+        if head and args.overlap:
+            ctx.set_option("split_overlap", 0)
+            ms_i, stage_i = run.timed(head, max(3, args.steps // 2), args.warmup)
+            ctx.set_option("split_overlap", 1)
+            ps_i = rooflines(stage_i, arrangement_work(head, overlap=False), peaks, {})
+            line["inline"] = {"value": world * N / (ms_i * 1e-3), "ms_per_step": ms_i,
+                              "note": "tensor launches in line on the apply's stream (option split_overlap 0): "
+                                      "each stage alone; tensor_v = digits + the one group-V launch (near field, "
+                                      "P2M, X list)",
+                              "stages": {k: {kk: v[kk] for kk in ("ms", "achieved", "unit", "peak", "frac")}
+                                         for k, v in ps_i.items()}}
         # the other precisions on the same tree, with their own rooflines
         for other in (p for p in (0, 1, 2) if p != head):
             ms_o, stage_o = run.timed(other, max(3, args.steps // 2), args.warmup)
