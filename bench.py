@@ -292,12 +292,17 @@ def stage_work(st, nleaf, nleaf_far, P1, NP, prec):
 
 
 def launches_per_apply(prec, overlap, st):
-    """Kernels of one apply (trees of more than three levels)."""
+    """Kernels of one apply (trees of more than three levels), as the launch
+    list of the profiles shows them."""
     if prec == 0:
-        return 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 1   # clear, up, M2L, X, down, leaf
-    side = 2 if overlap else 0                                     # X list + near field apart
-    base = 2 + side + 1 + 1 + 1 + 2 + 1                            # digits + group V, clear, up, down, E, leaf
-    return base + (2 if prec == 2 else 1)                          # M2L: digits + GEMM, or the FP64 kernel
+        return 1 + 1 + 1 + (1 if st["n_x"] > 0 else 0) + 1 + 2   # clear, up, M2L, X, down, leaf logs + leaf
+    if prec == 1:
+        # digits + P2M tiles, clear, up, FP64 M2L, down, L2P digits + tiles, logs + leaf; beside the M2L:
+        # X tiles, multipole digits + W tiles, near field
+        return 2 + 1 + 1 + 1 + 1 + 2 + 2 + (4 if overlap else 0)
+    # all-tensor: digits + group V, clear, up, M2L digits + tiles, down, E digits + tiles, logs + leaf;
+    # X tiles and near field on the internal stream
+    return 2 + 1 + 1 + 2 + 1 + 2 + 2 + (2 if overlap else 0)
 
 
 def run_batch64(args):
