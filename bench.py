@@ -396,31 +396,42 @@ def layer_line(args, dev, steps, check=True):
     u = torch.empty(tree.nleaf * P * P, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    for _ in range(3):
-        layer.apply(q, m, out=u, stream=stream)
-    torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    for k in range(steps):
-        flush.zero_()
-        ev[k][0].record(stream)
-        layer.apply(q, m, out=u, stream=stream)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+
+    def timed(prec):
+        for _ in range(3):
+            layer.apply(q, m, out=u, stream=stream, precision=prec)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            layer.apply(q, m, out=u, stream=stream, precision=prec)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, u.cpu().numpy().reshape(-1, P * P)
+
+    # split: the L2P at every leaf on the tensor cores; FP64: all of it in FP64
+    ms, un = timed(bc.SPLIT_BF16)
     if not check:
         return {"value": tree.nleaf * P * P / (ms * 1e-3), "ms": ms, "profile_run": True}
-    un = u.cpu().numpy().reshape(-1, P * P)
+    ms64, un64 = timed(bc.FP64)
     lv, ix, iy = (np.asarray(a) for a in tree.leaves())
     geom = synth.leaf_geometry(lv, ix, iy)
     pick = synth.sample_leaves_per_level(lv, 1, seed=4)
     ref = oracle.layer(xy, qh, mh, oracle.leaf_nodes(geom, P)[pick].reshape(-1, 2)).reshape(len(pick), P * P)
+
+    def err(x):
+        return float(np.abs(x[pick] - ref).max() / np.abs(ref).max())
     return {"value": tree.nleaf * P * P / (ms * 1e-3), "unit": "leaf nodes/s (layer potential at every node)",
             "ms": ms, "workload": "star-shaped domain, truncated 200-Gaussian tree; 4096 curve nodes "
                                   "(256 Gauss-Legendre panels x 16); nterms 30",
-            "nleaf": int(tree.nleaf), "lists": layer.info(),
-            "rel_err_vs_oracle": float(np.abs(un[pick] - ref).max() / np.abs(ref).max()),
+            "precision": "split: L2P at every leaf on the BF16 tensor cores (exact digit products); near sums, "
+                         "W list, far field in FP64",
+            "nleaf": int(tree.nleaf), "lists": layer.info(), "rel_err_vs_oracle": err(un),
+            "fp64": {"value": tree.nleaf * P * P / (ms64 * 1e-3), "ms": ms64, "rel_err_vs_oracle": err(un64),
+                     "split_vs_fp64_all_nodes": float(np.abs(un - un64).max() / np.abs(un64).max())},
             "sample": f"every node of {len(pick)} leaves (1 per level)", "l2": "flushed between applies",
-            "dtype": "f64"}
+            "dtype": "f64 + bf16 digit products"}
 
 
 def strip_line(args, dev, steps, peak_fp64, check=True):

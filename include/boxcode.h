@@ -236,9 +236,13 @@ bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u,
  *     u(x_i) = -(1/2pi) sum_j [ q_j log|x_i - y_j| + m_j . (x_i - y_j) / |x_i - y_j|^2 ]
  *
  * at every leaf node x_i ([nleaf][p][p], as the applies).  A source that
- * coincides with a node contributes nothing there.  FP64; the far field uses
- * the tree's expansions and lists (error of the expansion order, as the
- * volume apply), the near field is summed directly.
+ * coincides with a node contributes nothing there.  The far field uses the
+ * tree's expansions and lists (error of the expansion order, as the volume
+ * apply), the near field is summed directly, in FP64.  precision BC_FP64: all
+ * of it in FP64; BC_SPLIT_BF16 (p = 16, nterms <= 32, else
+ * BC_ERR_UNSUPPORTED): the local-to-node evaluation (L2P) at every leaf runs
+ * on the BF16 tensor cores as exact digit products (the volume apply's
+ * split-precision L2P), the rest in FP64; other values BC_ERR_ARG.
  *
  * bc_layer_create: the sources xy[n][2] (host, read during the call), inside
  * the root box (else BC_ERR_ARG), are sorted into the tree's leaves, and the
@@ -252,7 +256,8 @@ bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u,
  * (target leaf, near source) pairs, leaves holding sources. */
 typedef struct bc_layer bc_layer;
 bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer **out);
-bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const double *m, double *u, void *stream);
+bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const double *m, double *u,
+                         bc_precision precision, void *stream);
 bc_status bc_layer_info(const bc_layer *layer, int64_t *counts);
 void bc_layer_destroy(bc_layer *layer);
 

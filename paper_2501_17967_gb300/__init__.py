@@ -85,7 +85,7 @@ SIGNATURES = [
     ("bc_eval_points", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP]),
     ("bc_eval_points_grad", ctypes.c_int, [_VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP]),
     ("bc_layer_create", ctypes.c_int, [_VP, _DP, _I64, ctypes.POINTER(_VP)]),
-    ("bc_layer_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
+    ("bc_layer_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_layer_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     ("bc_layer_destroy", None, [_VP]),
     ("bc_strip_workspace", ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
@@ -435,9 +435,10 @@ class Layer:
         _check(_load().bc_layer_info(self._h, c))
         return dict(zip(("sources", "n_v", "n_w", "n_x", "near_pairs", "leaves_with_sources"), (int(v) for v in c)))
 
-    def apply(self, q, m, out=None, stream=None):
+    def apply(self, q, m, out=None, stream=None, precision: int = 0):
         """u at every leaf node ([nleaf * p * p]) from charges q[n] and dipoles
-        m[n, 2]; device tensors (on `stream`) or host tensors."""
+        m[n, 2]; device tensors (on `stream`) or host tensors.  precision FP64,
+        or SPLIT_BF16: the L2P at every leaf on the tensor cores (p = 16)."""
         import torch
         q = q.contiguous()
         m = m.contiguous()
@@ -448,7 +449,7 @@ class Layer:
             out = torch.empty(self.tree.nleaf * NP, dtype=torch.float64, device=q.device)
         _check(_load().bc_layer_apply(self.tree.ctx.handle, self._h, ctypes.c_void_p(q.data_ptr()),
                                       ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                                      _stream_ptr(stream) if q.is_cuda else None))
+                                      int(precision), _stream_ptr(stream) if q.is_cuda else None))
         return out
 
     def close(self):

@@ -981,6 +981,8 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
 
 }  // namespace
 
+bc_status prepare_split_tree(bc_tree *t) { return build_split_tree(t); }
+
 void set_error(const char *fmt, ...)
 {
     va_list ap;

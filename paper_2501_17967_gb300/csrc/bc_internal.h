@@ -401,8 +401,14 @@ struct LayerDev {
     double2 *PX = nullptr;              // [nx][P1]
 };
 // u at every leaf node (device pointers: q [n], m [n][2] caller order, u [nleaf][NP]).
+// With split (tables and the tree's tiles), the L2P at every leaf runs as the
+// forward group-E tiles of the volume apply (expansion digits of the locals,
+// then the tensor products into the tree's PE rows); otherwise in FP64.
 cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
-                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t stream);
+                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t stream,
+                         const struct SplitLaunch *split = nullptr);
+// The split path's tiles of a tree (built on first use; api.cpp).
+bc_status prepare_split_tree(struct bc_tree *t);
 // Strip solve (kernels_strip.cu): nsys block-cyclic-tridiagonal systems,
 // one warp each; workspace strip_work_doubles(N, m, r) per system.
 size_t strip_work_doubles(int64_t N, int m, int r);

@@ -149,7 +149,8 @@ __global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const
 }
 
 // Leaf output: one block of NP threads per target leaf, thread j its node.
-// u = L2P of the leaf's local expansion (levels >= 2) + the W list's
+// u = L2P of the leaf's local expansion (levels >= 2; PE: its row from the
+// tensor-core tiles, else in FP64 here) + the W list's
 // multipoles at the nodes (M2P, with the log r term of the target level) +
 // the direct sum over the sources of the leaf's near leaves.
 constexpr int kSrcChunk = 128;
@@ -162,7 +163,7 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy, const double *__restrict__ cq,
             const double2 *__restrict__ cm, const double2 *__restrict__ OpE, const double2 *__restrict__ OpW,
             const double2 *__restrict__ loc, const double2 *__restrict__ mul, const double *__restrict__ lvtab,
-            int p, int P1, double *__restrict__ u)
+            int p, int P1, double *__restrict__ u, const double *__restrict__ PE)
 {
     const int NP = p * p, j = threadIdx.x;
     __shared__ double2 se[32];
@@ -177,7 +178,9 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         const BoxGeom g = box_geom(b, box_level, box_ix, box_iy, x0, y0, L);
         const double zx = g.cx + g.r * xj, zy = g.cy + g.r * yj;
         double acc = 0.0;
-        if (lvo >= 2) {
+        if (lvo >= 2 && PE) {
+            acc = PE[int64_t(o) * NP + j];   // the L2P from the tensor cores
+        } else if (lvo >= 2) {
             __syncthreads();
             for (int i = j; i < P1; i += blockDim.x) se[i] = loc[int64_t(b) * P1 + i];
             __syncthreads();
@@ -240,7 +243,8 @@ inline int grid_cap(int64_t n, int cap) { return int(n < cap ? (n > 0 ? n : 1) :
 }  // namespace
 
 cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
-                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t st)
+                         const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t st,
+                         const SplitLaunch *split)
 {
     cudaError_t e;
     const int P1 = a.P1;
@@ -262,10 +266,30 @@ cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d,
     fl.v_ptr = ly.v_ptr; fl.v_src = ly.v_src; fl.v_code = ly.v_code;
     fl.x_ptr = ly.x_ptr; fl.x_src = ly.x_src; fl.PX = ly.PX;
     if ((e = launch_far_points(a, h, d, tb, fl, st)) != cudaSuccess) return e;
+    const double *PE = nullptr;
+    if (split) {
+        // L2P of every leaf at level >= 2 on the tensor cores: digits of the
+        // locals (expB, the forward apply's second array), then the forward
+        // group-E tiles that evaluate them at the leaf nodes, into PE
+        const SplitTables *sT = split->tables;
+        const SplitTree *sp = split->tree;
+        const int64_t nbox = a.nbox;
+        e = launch_split_digits_exp(nbox, 2 * nbox, nbox, d.expA, d.expB, P1, 1.0, sT->escale[0], sp->edig,
+                                    sp->eexp, st);
+        if (e != cudaSuccess) return e;
+        SplitGemm g;
+        g.tiles = sp->tE[0]; g.cols = sp->cE[0]; g.ntiles = sp->ntL[0];
+        g.ops = sT->ops[1][0]; g.op_exp = sT->op_exp[1][0];
+        g.dig = sp->edig; g.dexp = sp->eexp;
+        e = launch_split_gemm(g, kSplitKE, 1.0 / (a.half_L * a.half_L), sp->err, sT->wait_limit, sT->withhold_copy,
+                              st);
+        if (e != cudaSuccess) return e;
+        PE = sp->PE;
+    }
     k_layer_out<<<grid_cap(a.nleaf, 152 * 8), a.NP, 0, st>>>(
         a.nleaf, ly.order, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, ly.w_ptr, ly.w_src,
         ly.w_code, ly.n_ptr, ly.n_src, ly.src_ptr, ly.sxy, ly.cq, ly.cm, tb.fwd.e, tb.fwd.w, d.expB, d.expA, d.lvtab,
-        a.p, P1, u);
+        a.p, P1, u, PE);
     return cudaGetLastError();
 }
 

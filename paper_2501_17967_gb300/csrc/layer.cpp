@@ -203,22 +203,39 @@ bc_status bc_layer_info(const bc_layer *layer, int64_t *counts)
     return BC_OK;
 }
 
-bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const double *m, double *u, void *stream)
+bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const double *m, double *u,
+                         bc_precision prec, void *stream)
 {
     if (!ctx || !layer || !u || (layer->n > 0 && (!q || !m))) {
         set_error("bc_layer_apply: bad argument");
         return BC_ERR_ARG;
     }
     if (layer->tree->ctx != ctx) { set_error("bc_layer_apply: layer belongs to another context"); return BC_ERR_ARG; }
+    if (prec != BC_FP64 && prec != BC_SPLIT_BF16) {
+        set_error("bc_layer_apply: precision must be BC_FP64 or BC_SPLIT_BF16");
+        return BC_ERR_ARG;
+    }
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bc_tree *tree = layer->tree;
+    bc_tree *tree = layer->tree;
     const PassArgs a = pass_args(ctx, tree);
+    SplitLaunch sl{&ctx->split, nullptr};
+    const SplitLaunch *split = nullptr;
+    if (prec == BC_SPLIT_BF16) {
+        if (!ctx->split_ready) {
+            set_error("bc_layer_apply: split precision is provided for p = 16 with nterms <= 32 only");
+            return BC_ERR_UNSUPPORTED;
+        }
+        const bc_status bs = prepare_split_tree(tree);
+        if (bs != BC_OK) return bs;
+        sl.tree = &tree->sp;
+        split = &sl;
+    }
     const size_t nu = size_t(tree->h.nleaf) * ctx->NP, n = size_t(layer->n);
     const bool dq = n == 0 || on_device(q), dm = n == 0 || on_device(m), du = on_device(u);
     if (dq && dm && du) {
-        e = launch_layer(a, tree->h, tree->d, ctx->dt, layer->d, q, m, u, st);
+        e = launch_layer(a, tree->h, tree->d, ctx->dt, layer->d, q, m, u, st, split);
         return e == cudaSuccess ? BC_OK : fail(e, "bc_layer_apply");
     }
     if ((n > 0 && (on_device(q) || on_device(m))) || du) {
@@ -237,7 +254,8 @@ bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const do
         if (e == cudaSuccess) e = cudaMemcpyAsync(layer->stage_m, m, 2 * n * sizeof(double), cudaMemcpyHostToDevice, st);
     }
     if (e == cudaSuccess)
-        e = launch_layer(a, tree->h, tree->d, ctx->dt, layer->d, layer->stage_q, layer->stage_m, layer->stage_u, st);
+        e = launch_layer(a, tree->h, tree->d, ctx->dt, layer->d, layer->stage_q, layer->stage_m, layer->stage_u, st,
+                         split);
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, layer->stage_u, nu * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? BC_OK : fail(e, "bc_layer_apply");

@@ -61,12 +61,17 @@ def _leaves_holding(geom, pts):
     return np.unique(np.nonzero(inside)[1])
 
 
-def test_layer_against_oracle(ctx, star):
+@pytest.mark.parametrize("prec", [bc.FP64, bc.SPLIT_BF16])
+def test_layer_against_oracle(ctx, star, prec):
+    """FP64, and split precision (the L2P at every leaf on the tensor cores:
+    its digit products are exact and the rounding of the 40-bit operands and
+    locals adds about 1e-12 of max |u|, well inside the bar)."""
     tree, xy, q, m = star
     layer = bc.Layer(tree, xy)
     info = layer.info()
     assert info["sources"] == len(q) and info["n_w"] > 0 and info["n_v"] > 0
-    u = layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda()).cpu().numpy().reshape(-1, P * P)
+    u = layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda(),
+                    precision=prec).cpu().numpy().reshape(-1, P * P)
     lv, geom, nodes = _nodes(tree)
     hold = _leaves_holding(geom, xy)
     rng = np.random.default_rng(2)
@@ -74,11 +79,19 @@ def test_layer_against_oracle(ctx, star):
                                      synth.sample_leaves_per_level(lv, 2, seed=5)]))
     ref = oracle.layer(xy, q, m, nodes[pick].reshape(-1, 2)).reshape(len(pick), P * P)
     err = np.abs(u[pick] - ref).max() / np.abs(ref).max()
-    print(f"layer: {len(q)} sources, {tree.nleaf} leaves, {info}; sample {len(pick)} leaves: {err:.2e}")
+    print(f"layer ({prec}): {len(q)} sources, {tree.nleaf} leaves, {info}; sample {len(pick)} leaves: {err:.2e}")
     assert err < TOL, err
     # host arrays give the device result bit for bit
-    uh = layer.apply(torch.from_numpy(q), torch.from_numpy(m)).numpy().reshape(-1, P * P)
+    uh = layer.apply(torch.from_numpy(q), torch.from_numpy(m), precision=prec).numpy().reshape(-1, P * P)
     assert np.array_equal(uh, u)
+    if prec == bc.SPLIT_BF16:
+        # the split L2P against the FP64 one over every node of the tree
+        u64 = layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda()).cpu().numpy().reshape(-1, P * P)
+        d = np.abs(u - u64).max() / np.abs(u64).max()
+        print(f"split vs FP64 L2P, all {tree.nleaf} leaves: {d:.2e}")
+        assert d < 1e-11, d
+        with pytest.raises(bc.BoxCodeError):
+            layer.apply(torch.from_numpy(q).cuda(), torch.from_numpy(m).cuda(), precision=bc.SPLIT_BF16_ALL)
 
 
 def test_layer_scattered_sources_against_oracle(ctx):
