@@ -362,7 +362,7 @@ def batch64_line(args, dev):
     line = {"metric": METRIC + " (batched)", "value": nodes / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": f"f64 (p=8,12) / {DTYPES[head]} (p=16)" if head else "f64",
+            "dtype": f"{DTYPES[head]} (p=8,12,16)" if head else "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOADS["batch64"][1], "trees": 64, "leaves_min": min(leaves),
                        "leaves_max": max(leaves), "leaves_total": sum(leaves), "leaf_nodes": nodes,

@@ -71,14 +71,15 @@ typedef enum {
                               for the multipole-to-local translations, the
                               M2M and L2L shifts, every log-kernel scaling
                               term and every sum of partial results
-                              (p = 16 only) */
+                              (p = 8, 12 and 16, nterms <= 32; other orders
+                              BC_ERR_UNSUPPORTED) */
     BC_SPLIT_BF16_ALL = 2  /* BC_SPLIT_BF16 plus the multipole-to-local
                               translations on BF16 digits (their log terms
                               stay FP64) and the M2M / L2L shifts in
                               double-float arithmetic (pairs of FP32 numbers,
                               about 48 bits, on the FP32 units); the V- and
                               X-list sums and the local expansions handed to
-                              later steps stay FP64 (p = 16 only) */
+                              later steps stay FP64 (p = 8, 12, 16) */
 } bc_precision;
 
 typedef struct {
@@ -239,7 +240,7 @@ bc_status bc_eval_points_grad(bc_ctx *ctx, const bc_tree *tree, const double *u,
  * coincides with a node contributes nothing there.  The far field uses the
  * tree's expansions and lists (error of the expansion order, as the volume
  * apply), the near field is summed directly, in FP64.  precision BC_FP64: all
- * of it in FP64; BC_SPLIT_BF16 (p = 16, nterms <= 32, else
+ * of it in FP64; BC_SPLIT_BF16 (p = 8, 12, 16, nterms <= 32, else
  * BC_ERR_UNSUPPORTED): the local-to-node evaluation (L2P) at every leaf runs
  * on the BF16 tensor cores as exact digit products (the volume apply's
  * split-precision L2P), the rest in FP64; other values BC_ERR_ARG.

@@ -29,7 +29,7 @@ __all__ = ["build", "Context", "Tree", "Batch", "BoxCodeError", "FP64", "SPLIT_B
 FP64 = 0
 SPLIT_BF16 = 1
 SPLIT_BF16_ALL = 2
-SPLIT_ORDERS = (16,)    # orders p with a split-precision path
+SPLIT_ORDERS = (8, 12, 16)    # orders p with a split-precision path
 _STATUS = {0: "BC_OK", -1: "BC_ERR_ARG", -2: "BC_ERR_TREE", -3: "BC_ERR_CUDA", -4: "BC_ERR_OOM",
            -5: "BC_ERR_TIMEOUT", -6: "BC_ERR_UNSUPPORTED", -7: "BC_ERR_STATE"}
 _DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "tables")
@@ -438,7 +438,7 @@ class Layer:
     def apply(self, q, m, out=None, stream=None, precision: int = 0):
         """u at every leaf node ([nleaf * p * p]) from charges q[n] and dipoles
         m[n, 2]; device tensors (on `stream`) or host tensors.  precision FP64,
-        or SPLIT_BF16: the L2P at every leaf on the tensor cores (p = 16)."""
+        or SPLIT_BF16: the L2P at every leaf on the tensor cores (p = 8, 12, 16)."""
         import torch
         q = q.contiguous()
         m = m.contiguous()

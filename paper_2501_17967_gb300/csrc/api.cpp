@@ -565,51 +565,55 @@ SplitOp add_split_op(std::vector<uint16_t> &dig, std::vector<int32_t> &ex, const
 }
 
 // Real operators of the split path, direction dir (0 forward, 1 adjoint):
-//   group V, K = p^2 = 256: near tables (256 rows), leafA (2 P1 rows: P2M /
+//   group V, K = KV (the p^2 leaf nodes, zero columns up to 64 for p = 8 and
+//     to 256 for p = 12, 16): near tables (p^2 rows), leafA (2 P1 rows: P2M /
 //     L2P^H), X list per code (2 P1 rows: P2L / M2P^H); output rows 2l, 2l+1 =
 //     Re, Im of coefficient l;
 //   group E, K = 64 (coefficient l at columns 2l, 2l+1 = Re, Im): L2P / P2M^H
-//     and the W list per code (M2P / P2L^H), 256 rows, output = real part.
+//     and the W list per code (M2P / P2L^H), p^2 rows, output = real part.
 bc_status build_split_tables(bc_ctx *ctx)
 {
-    if (ctx->p != 16 || ctx->device < 0 || 2 * ctx->P1 > kSplitKE) return BC_OK;   // split path: p = 16, P1 <= 32
+    // split path: p = 8, 12 or 16, P1 <= 32
+    if ((ctx->p != 8 && ctx->p != 12 && ctx->p != 16) || ctx->device < 0 || 2 * ctx->P1 > kSplitKE) return BC_OK;
     const HostTables &ht = ctx->ht;
-    const int NP = 256, P1 = ctx->P1, R = 2 * P1, KE = kSplitKE;
+    const int NP = ctx->NP, KV = NP <= 64 ? 64 : 256, P1 = ctx->P1, R = 2 * P1, KE = kSplitKE;
     SplitTables &T = ctx->split;
+    T.np = NP;
+    T.kv = KV;
     for (int dir = 0; dir < 2; dir++) {
         std::vector<uint16_t> dv, de;
         std::vector<int32_t> xv, xe;
         std::vector<double> m;
         // group V
         T.near_op[dir].assign(kNumNear, SplitOp());
-        m.assign(size_t(NP) * NP, 0.0);
+        m.assign(size_t(NP) * KV, 0.0);
         for (int tab = 0; tab < kNumNear; tab++) {
             NearGeom g = near_table_geometry(tab);
             if (!g.valid) continue;
             for (int i = 0; i < NP; i++)
                 for (int k = 0; k < NP; k++)
-                    m[size_t(i) * NP + k] = dir == 0 ? ht.T[(size_t(tab) * NP + i) * NP + k]
+                    m[size_t(i) * KV + k] = dir == 0 ? ht.T[(size_t(tab) * NP + i) * NP + k]
                                                      : ht.T[(size_t(g.rev) * NP + k) * NP + i];
-            T.near_op[dir][tab] = add_split_op(dv, xv, m, NP, NP);
+            T.near_op[dir][tab] = add_split_op(dv, xv, m, NP, KV);
         }
-        m.assign(size_t(R) * NP, 0.0);
+        m.assign(size_t(R) * KV, 0.0);
         for (int l = 0; l < P1; l++)
             for (int j = 0; j < NP; j++) {
                 cplx z = dir == 0 ? at2(ht.Q, size_t(l) * NP + j) : std::conj(at2(ht.E, size_t(j) * P1 + l));
-                m[size_t(2 * l) * NP + j] = z.real();
-                m[size_t(2 * l + 1) * NP + j] = z.imag();
+                m[size_t(2 * l) * KV + j] = z.real();
+                m[size_t(2 * l + 1) * KV + j] = z.imag();
             }
-        T.leafA_op[dir] = add_split_op(dv, xv, m, R, NP);
+        T.leafA_op[dir] = add_split_op(dv, xv, m, R, KV);
         T.x_op[dir].assign(kNumWX, SplitOp());
         for (int c = 0; c < kNumWX; c++) {
             for (int l = 0; l < P1; l++)
                 for (int j = 0; j < NP; j++) {
                     cplx z = dir == 0 ? at2(ht.P2L, (size_t(c) * P1 + l) * NP + j)
                                       : std::conj(at2(ht.M2P, (size_t(c) * NP + j) * P1 + l));
-                    m[size_t(2 * l) * NP + j] = z.real();
-                    m[size_t(2 * l + 1) * NP + j] = z.imag();
+                    m[size_t(2 * l) * KV + j] = z.real();
+                    m[size_t(2 * l + 1) * KV + j] = z.imag();
                 }
-            T.x_op[dir][c] = add_split_op(dv, xv, m, R, NP);
+            T.x_op[dir][c] = add_split_op(dv, xv, m, R, KV);
         }
         // group E: out_j = Re(sum_l Op(j,l) b_l) = sum_l Re Op(j,l) Re b_l - Im Op(j,l) Im b_l;
         // columns rescaled by powers of two (the expansion digits carry the inverse scale)
@@ -748,11 +752,12 @@ bc_status build_split_tree(bc_tree *t)
     SplitTree &s = t->sp;
     std::vector<void *> &al = t->d.allocs;
     cudaError_t e;
-    if ((e = dev_upload<double>(al, &s.Pnear, nullptr, size_t(nn) * 256)) != cudaSuccess ||
+    const size_t NP = size_t(T.np), KV = size_t(T.kv);   // nodes per leaf, group-V K
+    if ((e = dev_upload<double>(al, &s.Pnear, nullptr, size_t(nn) * NP)) != cudaSuccess ||
         (e = dev_upload<double>(al, &s.PX, nullptr, size_t(nx) * kSplitKE)) != cudaSuccess ||
-        (e = dev_upload<double>(al, &s.PE, nullptr, size_t(h.nleaf) * 256)) != cudaSuccess ||
-        (e = dev_upload<double>(al, &s.PW, nullptr, size_t(nw) * 256)) != cudaSuccess ||
-        (e = dev_upload<uint16_t>(al, &s.vdig, nullptr, size_t(h.nleaf) * kSplitSlices * 256)) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.PE, nullptr, size_t(h.nleaf) * NP)) != cudaSuccess ||
+        (e = dev_upload<double>(al, &s.PW, nullptr, size_t(nw) * NP)) != cudaSuccess ||
+        (e = dev_upload<uint16_t>(al, &s.vdig, nullptr, size_t(h.nleaf) * kSplitSlices * KV)) != cudaSuccess ||
         (e = dev_upload<int32_t>(al, &s.vexp, nullptr, size_t(h.nleaf))) != cudaSuccess ||
         (e = dev_upload<uint16_t>(al, &s.edig, nullptr, size_t(2 * nbox) * kSplitSlices * kSplitKE)) != cudaSuccess ||
         (e = dev_upload<int32_t>(al, &s.eexp, nullptr, size_t(2 * nbox))) != cudaSuccess)
@@ -777,7 +782,7 @@ bc_status build_split_tree(bc_tree *t)
             SplitCol c;
             c.vec = src;
             c.ctl = col_ctl(-2 * (adj ? h.leaf_level[own] : h.leaf_level[src]), false);
-            c.out = s.Pnear + size_t(k) * 256;
+            c.out = s.Pnear + size_t(k) * NP;
             by_tab[h.near_tab[k]].push_back(c);
         }
         for (int tab = 0; tab < kNumNear; tab++)
@@ -812,7 +817,7 @@ bc_status build_split_tree(bc_tree *t)
             SplitCol c;
             c.vec = int32_t(second_which * nbox + h.leaf_box[o]);
             c.ctl = col_ctl(adj ? -2 * h.leaf_level[o] : 0, false);
-            c.out = s.PE + size_t(o) * 256;
+            c.out = s.PE + size_t(o) * NP;
             cl.push_back(c);
         }
         E.add(T.e_op[dir], cl);
@@ -822,7 +827,7 @@ bc_status build_split_tree(bc_tree *t)
             SplitCol c;
             c.vec = int32_t(first_which * nbox + h.w_src[k]);
             c.ctl = col_ctl(adj ? -2 * h.leaf_level[w_owner[k]] : 0, false);
-            c.out = s.PW + size_t(k) * 256;
+            c.out = s.PW + size_t(k) * NP;
             by_code[h.w_code[k]].push_back(c);
         }
         for (int c = 0; c < kNumWX; c++)
@@ -930,7 +935,7 @@ bc_status apply_impl(bc_ctx *ctx, const bc_tree *tree, const double *vin, double
     bc_tree *tw = const_cast<bc_tree *>(tree);
     if (is_split(prec)) {
         if (!ctx->split_ready) {
-            set_error("apply: split precision is provided for p = 16 with nterms <= 32 only");
+            set_error("apply: split precision is provided for p = 8, 12 and 16 with nterms <= 32 only");
             return BC_ERR_UNSUPPORTED;
         }
         s = build_split_tree(tw);
@@ -1542,7 +1547,7 @@ bc_status bc_batch_autotune(bc_ctx *ctx, bc_batch *b, bc_precision prec, void *s
 {
     if (!ctx || !b || b->ctx != ctx) { set_error("bc_batch_autotune: bad argument"); return BC_ERR_ARG; }
     if (prec != BC_FP64 && !is_split(prec)) { set_error("bc_batch_autotune: unknown precision"); return BC_ERR_ARG; }
-    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_autotune: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_autotune: split precision needs p = 8, 12 or 16"); return BC_ERR_UNSUPPORTED; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     static const int cand[][2] = {{16, 12}, {8, 8}, {4, 4}, {16, 16}, {8, 12}, {32, 12}, {16, 6}};
     cudaEvent_t e0, e1;
@@ -1593,7 +1598,7 @@ bc_status bc_batch_run(bc_ctx *ctx, bc_batch *b, const double *const *in, double
 {
     if (!ctx || !b || b->ctx != ctx || !in || !out) { set_error("bc_batch_run: bad argument"); return BC_ERR_ARG; }
     if (prec != BC_FP64 && !is_split(prec)) { set_error("bc_batch_run: unknown precision"); return BC_ERR_ARG; }
-    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_run: split precision needs p = 16"); return BC_ERR_UNSUPPORTED; }
+    if (is_split(prec) && !ctx->split_ready) { set_error("bc_batch_run: split precision needs p = 8, 12 or 16"); return BC_ERR_UNSUPPORTED; }
     const int n = int(b->trees.size());
     for (int k = 0; k < n; k++)
         if (!in[k] || !out[k] || !is_device_ptr(in[k]) || !is_device_ptr(out[k]) || in[k] == out[k]) {

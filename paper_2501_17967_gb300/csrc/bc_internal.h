@@ -230,6 +230,9 @@ struct SplitTables {
     // taken and column k of the operator is divided by s_k (exact rescaling
     // that balances the fixed-point rounding of operator and input).
     const double *escale[2] = {nullptr, nullptr};
+    // group V's inner dimension: the p^2 leaf nodes, zero-padded to one of
+    // the tensor kernel's K (64 for p = 8, 256 for p = 12 and 16)
+    int np = 256, kv = 256;
     long long wait_limit = 1ll << 26;            // polls of a bounded mbarrier wait
     int withhold_copy = 0;                       // diagnostics: never start the operator copies (forces a timeout)
 };
@@ -306,8 +309,9 @@ struct SplitLaunch {
 };
 // Digits of the leaf vectors (times scale), of the two expansion arrays
 // (times scale), and the tensor-core operator products of one group.
+// (np nodes per leaf, digits zero-padded to kv per slice)
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
-                                    cudaStream_t st, const uint8_t *active = nullptr);
+                                    cudaStream_t st, const uint8_t *active, int np, int kv);
 // Expansion digits of vectors [i0, i1) of the pair (expA: 0..nbox-1, expB:
 // nbox..2 nbox-1).
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,

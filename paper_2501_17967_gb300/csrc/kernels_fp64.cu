@@ -1468,12 +1468,13 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             return e;
         if (ev) cudaEventRecord(ev[8], sd->side);
         if (!leaf_tc) {
-            e = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side, d.leaf_active);
+            e = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, sd->side, d.leaf_active,
+                                            a.NP, sT->kv);
             if (e != cudaSuccess) return e;
         }
         SplitGemm g = gv;
         g.tiles = sp->tV[dir] + sp->ntA[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntV[dir] - sp->ntA[dir];
-        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
+        e = launch_split_gemm(g, sT->kv, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
         if (e != cudaSuccess) return e;
         if ((e = cudaEventRecord(sd->xdone, sd->side)) != cudaSuccess) return e;
         if (late) {
@@ -1494,7 +1495,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         }
         g.tiles = sp->tN[dir]; g.cols = sp->cN[dir]; g.ntiles = sp->ntN[dir];
         g.max_ctas = split->near_ctas;
-        e = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
+        e = launch_split_gemm(g, sT->kv, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, sd->side, late);
         if (e != cudaSuccess) return e;
         if (ev) cudaEventRecord(ev[9], sd->side);
         return cudaEventRecord(sd->join, sd->side);
@@ -1507,11 +1508,12 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
         if (!sd) {
             // one launch: the near-field tiles (two jobs each) first, then the
             // leaf-to-expansion and X-list tiles
-            ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active);
+            ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active, a.NP,
+                                             sT->kv);
             if (ce != cudaSuccess) return ce;
             SplitGemm g = gv;
             g.tiles = sp->tVN[dir]; g.cols = sp->cVN[dir]; g.ntiles = sp->ntVN[dir];
-            ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+            ce = launch_split_gemm(g, sT->kv, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
             if (ce != cudaSuccess) return ce;
             if (ev) {
                 cudaEventRecord(ev[8], st);
@@ -1523,14 +1525,15 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
             // double-float inside the upward pass, and then the digits run on
             // the internal stream too.
             if (leaf_tc) {
-                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active);
+                ce = launch_split_digits_vec(a.nleaf, vin, alpha0, sp->vdig, sp->vexp, st, d.leaf_active, a.NP,
+                                             sT->kv);
                 if (ce != cudaSuccess) return ce;
             }
             if (!late && (ce = side_launches()) != cudaSuccess) return ce;
             if (leaf_tc) {
                 SplitGemm g = gv;
                 g.tiles = sp->tV[dir]; g.cols = sp->cV[dir]; g.ntiles = sp->ntA[dir];
-                ce = launch_split_gemm(g, 256, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
+                ce = launch_split_gemm(g, sT->kv, 1.0 / alpha0, sp->err, sT->wait_limit, sT->withhold_copy, st);
                 if (ce != cudaSuccess) return ce;
             }
         }

@@ -313,29 +313,29 @@ __device__ __forceinline__ void digits_of(long long bits, int E, uint16_t *out, 
 
 // ---------------------------------------------------------------------------
 // Digits of scale * (leaf vectors): dig[leaf][a][k], dexp[leaf] = E with
-// max |scale v| < 2^(E-1).  One block of 256 threads per leaf.
-// ---------------------------------------------------------------------------
+// max |scale v| < 2^(E-1).  One block of kv threads (kv = 64 or 256) per
+// leaf; the np <= kv nodes of a leaf, then zero digits up to kv.
 __global__ void __launch_bounds__(256) k_split_vec(int64_t nleaf, const double *__restrict__ v, double scale,
                                                    uint16_t *__restrict__ dig, int32_t *__restrict__ dexp,
-                                                   const uint8_t *__restrict__ active)
+                                                   const uint8_t *__restrict__ active, int np)
 {
     griddep_wait();
     griddep_launch_dependents();
     __shared__ int wmax[8];
-    const int k = threadIdx.x;
+    const int k = threadIdx.x, kv = blockDim.x;
     for (int64_t leaf = blockIdx.x; leaf < nleaf; leaf += gridDim.x) {
         // a discarded leaf of a truncated tree is no source: zero digits
-        const double x = (active && !active[leaf]) ? 0.0 : v[leaf * 256 + k];
+        const double x = (k >= np || (active && !active[leaf])) ? 0.0 : v[leaf * np + k];
         const long long bits = __double_as_longlong(scale * x);
         int m = int((bits >> 52) & 0x7FF);
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if ((k & 31) == 0) wmax[k >> 5] = m;
         __syncthreads();
         int emax = wmax[0];
-        for (int w = 1; w < 8; w++) emax = max(emax, wmax[w]);
+        for (int w = 1; w < (kv >> 5); w++) emax = max(emax, wmax[w]);
         __syncthreads();
         const int E = emax ? emax - 1023 + 2 : 0;
-        digits_of(emax ? bits : 0ll, E, dig + leaf * (kS * 256) + k, 256);
+        digits_of(emax ? bits : 0ll, E, dig + leaf * (kS * kv) + k, kv);
         if (k == 0) dexp[leaf] = E;
     }
 }
@@ -796,11 +796,12 @@ cudaError_t split_prepare()
 int split_sm_count() { return g_sms > 0 ? g_sms : 152; }
 
 cudaError_t launch_split_digits_vec(int64_t nleaf, const double *v, double scale, uint16_t *dig, int32_t *dexp,
-                                    cudaStream_t st, const uint8_t *active)
+                                    cudaStream_t st, const uint8_t *active, int np, int kv)
 {
     if (nleaf <= 0) return cudaSuccess;
-    return launch_pdl(k_split_vec, int(std::min<int64_t>(nleaf, 152 * 16)), 256, 0, st, nleaf, v, scale, dig, dexp,
-                      active);
+    if ((kv != 64 && kv != 256) || np < 1 || np > kv) return cudaErrorInvalidValue;
+    return launch_pdl(k_split_vec, int(std::min<int64_t>(nleaf, 152 * 16)), kv, 0, st, nleaf, v, scale, dig, dexp,
+                      active, np);
 }
 
 cudaError_t launch_split_digits_exp(int64_t i0, int64_t i1, int64_t nbox, const double2 *ea, const double2 *eb,

@@ -93,3 +93,38 @@ def test_shifted_scaled_root(ctx):
     tree = bc.Tree(ctx, lv, ix, iy, x0=x0, y0=y0, L=L)
     err = _check(tree, lv, ix, iy, g, x0, y0, L)
     print(f"root [{x0},{x0 + L}] x [{y0},{y0 + L}]: {err:.2e}")
+
+
+@pytest.mark.parametrize("p", [8, 12])
+def test_split_orders_8_12(p):
+    """Split precision at p = 8 (64 nodes: the tensor kernel's K = 64 tiles)
+    and p = 12 (144 nodes, zero-padded to K = 256; near-field operators of 144
+    rows in two jobs) on an adaptive tree, forward and adjoint, against the
+    oracle at every node of sampled leaves (levels 2 and up) and by the
+    dot-product identity; the same bar as p = 16."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = bc.Context(p=p, nterms=24, device=0)
+    g = synth.config_density(1)
+    tree = bc.Tree.refine(c, g, eps=1e-10, max_level=10)
+    lv, ix, iy = (np.asarray(a) for a in tree.leaves())
+    geom = synth.leaf_geometry(lv, ix, iy)
+    nodes = oracle.leaf_nodes(geom, p)
+    fv = g(nodes.reshape(-1, 2)).reshape(-1, p * p)
+    f = torch.from_numpy(fv.reshape(-1)).cuda()
+    pick = synth.sample_leaves_per_level(lv, 1, seed=p)
+    ref = oracle.potential_at_nodes(p, geom, fv, leaf_ids=pick)
+    u = bc.apply(tree, f, precision=bc.SPLIT_BF16)
+    err = float(np.abs(u.cpu().numpy().reshape(-1, p * p)[pick] - ref).max() / np.abs(ref).max())
+    u64 = bc.apply(tree, f)
+    d64 = float(((u - u64).abs().max() / u64.abs().max()).item())
+    gr = torch.from_numpy(np.random.default_rng(p).standard_normal(fv.size)).cuda()
+    h = bc.apply_adjoint(tree, gr, precision=bc.SPLIT_BF16)
+    h64 = bc.apply_adjoint(tree, gr)
+    da = float(((h - h64).abs().max() / h64.abs().max()).item())
+    lhs, rhs = torch.dot(u, gr).item(), torch.dot(f, h).item()
+    scale = (u.abs() * gr.abs()).sum().item()
+    print(f"split p={p} ({tree.nleaf} leaves): oracle {err:.2e}, vs FP64 forward {d64:.2e} adjoint {da:.2e}")
+    assert err < TOL, err
+    assert d64 < 1e-10 and da < 1e-10, (d64, da)
+    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs)
