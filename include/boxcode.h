@@ -404,6 +404,12 @@ bc_status bc_debug_up_schedule(const bc_ctx *ctx, int adjoint, int32_t *T, int32
  * 8 blocks per SM, best of three timed runs).  The roofline denominator of
  * the FP64 passes (diagnostics; not in the paper). */
 bc_status bc_debug_fp64_peak(int device, double *tflops);
+/* The layer potential's near-sum logarithm and reciprocal (a table-driven
+ * logarithm after Tang, ACM TOMS 16, 1990, and the matching reciprocal
+ * series) applied to x[n] > 0 (normal, 1/x normal): lg[i] = log x[i],
+ * inv[i] = 1/x[i].  Device pointers, ordered on `stream`.  Diagnostics: the
+ * tests compare it with the CUDA math library's log and division. */
+bc_status bc_debug_log_inv(int device, const double *x, int64_t n, double *lg, double *inv, void *stream);
 
 /* FP64 apply (adjoint = 0: u = A f; adjoint != 0: the transpose) that
  * allocates no memory during the call.  The paper has no counterpart: this

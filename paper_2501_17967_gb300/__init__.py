@@ -87,6 +87,7 @@ SIGNATURES = [
     ("bc_layer_create", ctypes.c_int, [_VP, _DP, _I64, ctypes.POINTER(_VP)]),
     ("bc_layer_apply", ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int, _VP]),
     ("bc_layer_info", ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    ("bc_debug_log_inv", ctypes.c_int, [ctypes.c_int, _VP, _I64, _VP, _VP, _VP]),
     ("bc_layer_destroy", None, [_VP]),
     ("bc_strip_workspace", ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     ("bc_strip_solve", ctypes.c_int, [_I64, _I64, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP, _VP, _VP, _VP,

@@ -411,6 +411,10 @@ struct LayerDev {
 cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t stream,
                          const struct SplitLaunch *split = nullptr);
+// The near sums' logarithm and reciprocal: table upload (before the first
+// layer launch on a device) and a check launch (x, lg, inv device arrays).
+cudaError_t layer_log_init();
+cudaError_t launch_log_inv_check(const double *x, int64_t n, double *lg, double *inv, cudaStream_t st);
 // The split path's tiles of a tree (built on first use; api.cpp).
 bc_status prepare_split_tree(struct bc_tree *t);
 // Strip solve (kernels_strip.cu): nsys block-cyclic-tridiagonal systems,

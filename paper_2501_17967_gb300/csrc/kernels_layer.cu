@@ -24,6 +24,10 @@
 // target node contributes nothing.  FP64 throughout.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "bc_internal.h"
 
 namespace bc {
@@ -50,6 +54,60 @@ __device__ __forceinline__ double2 cpow(double2 a, int n)
         n >>= 1;
     }
     return r;
+}
+
+// ---------------------------------------------------------------------------
+// log x and 1/x for the direct near sums, written for this GPU's FP64 rate
+// (1/64 of FP32): a table-driven logarithm after Tang (ACM TOMS 16, 1990).
+// With x = 2^e m, m in [1, 2), and j the top kLogBits bits of m's fraction,
+// c_j is a short (9-bit) approximation of 1 / (1 + (j + 1/2) / 2^kLogBits)
+// (c_0 = 1), so that r = m c_j - 1 is one FMA with a single rounding and
+// |r| < 0.008; then
+//     log x = e ln 2 - log c_j + log1p(r),  log1p(r) = r - r^2/2 + ... + r^7/7,
+//     1/x   = 2^-e c_j / (1 + r),           1/(1 + r) = 1 - r + ... - r^7,
+// both series truncated below 2e-17 relative.  ln 2 is split so that e ln2_hi
+// is exact (42 bits); -log c_j is stored as a double-double.  About 13 FP64
+// operations for the logarithm and 8 for the reciprocal.  Valid for normal x
+// with 1/x normal (|e| <= 1021), which the near sums' squared distances meet.
+// Table: g_logtab[4 j + 0..2] = c_j, hi, lo of -log c_j; [4 kLogN + 0..1] =
+// ln2_hi, ln2_lo (set by layer_log_init).
+// ---------------------------------------------------------------------------
+constexpr int kLogBits = 7, kLogN = 1 << kLogBits, kLogTabLen = 4 * kLogN + 2;
+__device__ double g_logtab[kLogTabLen];
+
+__device__ __forceinline__ void log_inv(double x, const double *__restrict__ tab, double &lg, double &inv)
+{
+    const long long bits = __double_as_longlong(x);
+    const int e = int(bits >> 52) - 1023;   // x > 0
+    const int j = int((bits >> (52 - kLogBits)) & (kLogN - 1));
+    const double m = __longlong_as_double((bits & 0x000FFFFFFFFFFFFFll) | 0x3FF0000000000000ll);
+    const double c = tab[4 * j], Lh = tab[4 * j + 1], Ll = tab[4 * j + 2];
+    const double r = fma(m, c, -1.0);
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);   // log1p(r) = r + r^2 q(r)
+    q = fma(q, r, 0.2);
+    q = fma(q, r, -0.25);
+    q = fma(q, r, 1.0 / 3.0);
+    q = fma(q, r, -0.5);
+    const double ed = double(e);
+    lg = fma(ed, tab[4 * kLogN], Lh) + (fma(r * r, q, fma(ed, tab[4 * kLogN + 1], Ll)) + r);
+    double s = 1.0 - r;   // 1 / (1 + r)
+#pragma unroll
+    for (int k = 0; k < 6; k++) s = fma(s, -r, 1.0);
+    inv = __longlong_as_double(__double_as_longlong(c * s) - (static_cast<long long>(e) << 52));
+}
+
+__global__ void k_log_inv_check(const double *__restrict__ x, int64_t n, double *__restrict__ lg,
+                                double *__restrict__ inv)
+{
+    __shared__ double tab[kLogTabLen];
+    for (int i = threadIdx.x; i < kLogTabLen; i += blockDim.x) tab[i] = g_logtab[i];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+        double a, b;
+        log_inv(x[i], tab, a, b);
+        lg[i] = a;
+        inv[i] = b;
+    }
 }
 
 struct BoxGeom {
@@ -169,6 +227,8 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
     __shared__ double2 se[32];
     __shared__ double2 s_xy[kSrcChunk], s_m[kSrcChunk];
     __shared__ double s_q[kSrcChunk];
+    __shared__ double s_log[kLogTabLen];
+    for (int i = j; i < kLogTabLen; i += blockDim.x) s_log[i] = g_logtab[i];   // read after the first barrier below
     const double pi = 3.14159265358979323846;
     const double xj = -cos((2.0 * (j % p) + 1.0) * pi / (2.0 * p)), yj = -cos((2.0 * (j / p) + 1.0) * pi / (2.0 * p));
     for (int64_t li = blockIdx.x; li < nleaf; li += gridDim.x) {
@@ -219,7 +279,7 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                 __syncthreads();
                 for (int i = j; i < cnt; i += blockDim.x) {
                     s_xy[i] = sxy[c0 + i];
-                    s_q[i] = cq[c0 + i];
+                    s_q[i] = 0.5 * cq[c0 + i];   // c_q log|x - y| = (c_q / 2) log r^2
                     s_m[i] = cm[c0 + i];
                 }
                 __syncthreads();
@@ -227,8 +287,9 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
                     const double dx = zx - s_xy[i].x, dy = zy - s_xy[i].y;
                     const double r2 = fma(dx, dx, dy * dy);
                     if (r2 > 0.0) {
-                        const double ir2 = 1.0 / r2;
-                        near = fma(s_q[i], 0.5 * log(r2), near);
+                        double lg, ir2;
+                        log_inv(r2, s_log, lg, ir2);
+                        near = fma(s_q[i], lg, near);
                         near = fma(fma(s_m[i].x, dx, s_m[i].y * dy), ir2, near);
                     }
                 }
@@ -241,6 +302,39 @@ k_layer_out(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
 inline int grid_cap(int64_t n, int cap) { return int(n < cap ? (n > 0 ? n : 1) : cap); }
 
 }  // namespace
+
+cudaError_t layer_log_init()
+{
+    // c_j (9 bits), -log c_j as hi + lo from the host's extended-precision
+    // logarithm, and ln 2 split so that its high part has 42 bits
+    double t[kLogTabLen] = {};
+    for (int j = 0; j < kLogN; j++) {
+        const double F = 1.0 + (j + 0.5) / kLogN;
+        const double c = j == 0 ? 1.0 : std::nearbyint(512.0 / F) / 512.0;
+        const long double L = -logl(static_cast<long double>(c));
+        t[4 * j] = c;
+        t[4 * j + 1] = static_cast<double>(L);
+        t[4 * j + 2] = static_cast<double>(L - static_cast<long double>(t[4 * j + 1]));
+    }
+    const long double ln2 = logl(2.0L);
+    long long b;
+    const double l2 = static_cast<double>(ln2);
+    std::memcpy(&b, &l2, sizeof b);
+    b &= ~((1ll << 11) - 1);
+    double l2h;
+    std::memcpy(&l2h, &b, sizeof b);
+    t[4 * kLogN] = l2h;
+    t[4 * kLogN + 1] = static_cast<double>(ln2 - static_cast<long double>(l2h));
+    return cudaMemcpyToSymbol(g_logtab, t, sizeof t);
+}
+
+cudaError_t launch_log_inv_check(const double *x, int64_t n, double *lg, double *inv, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int grid = int(std::min<int64_t>((n + 255) / 256, 152 * 8));
+    k_log_inv_check<<<grid, 256, 0, st>>>(x, n, lg, inv);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                          const LayerDev &ly, const double *q, const double *m, double *u, cudaStream_t st,

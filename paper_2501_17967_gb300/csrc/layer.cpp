@@ -158,6 +158,7 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
     L->counts[4] = near_pairs;
     for (int64_t l = 0; l < nleaf; l++) L->counts[5] += src_ptr[l + 1] > src_ptr[l] ? 1 : 0;
     cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = layer_log_init();   // the near sums' log table
     LayerDev &d = L->d;
     d.n = n;
     d.nx = int64_t(x_src.size());
@@ -259,6 +260,19 @@ bc_status bc_layer_apply(bc_ctx *ctx, bc_layer *layer, const double *q, const do
     if (e == cudaSuccess) e = cudaMemcpyAsync(u, layer->stage_u, nu * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? BC_OK : fail(e, "bc_layer_apply");
+}
+
+bc_status bc_debug_log_inv(int device, const double *x, int64_t n, double *lg, double *inv, void *stream)
+{
+    if (n < 0 || (n > 0 && (!x || !lg || !inv))) { set_error("bc_debug_log_inv: bad argument"); return BC_ERR_ARG; }
+    if (n > 0 && (!on_device(x) || !on_device(lg) || !on_device(inv))) {
+        set_error("bc_debug_log_inv: x, lg and inv must be device pointers");
+        return BC_ERR_ARG;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = layer_log_init();
+    if (e == cudaSuccess) e = launch_log_inv_check(x, n, lg, inv, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? BC_OK : fail(e, "bc_debug_log_inv");
 }
 
 void bc_layer_destroy(bc_layer *layer)

@@ -17,6 +17,8 @@ default), a further 0.55^6 ~ 0.03.  The bar is 1e-10 of max |u| over the
 sample (Sec. 4's tolerance); the closed forms hold to the trapezoid rule's
 error (below 1e-14 at the selected nodes) plus the truncation, so the bar
 there is 1e-11 absolute."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -156,3 +158,31 @@ def test_layer_edge_cases(ctx):
     assert err < TOL and np.all(np.isfinite(u))
     with pytest.raises(bc.BoxCodeError):
         bc.Layer(tree, np.array([[1.5, 0.0]]))
+
+
+def test_near_sum_log_against_cuda():
+    """The near sums' table-driven logarithm (after Tang, 1990) and reciprocal
+    against the CUDA math library's log and IEEE division, on random squared
+    distances over 19 decades, on x = 1 +- small, and on both sides of every
+    table interval boundary over 41 binades.  Bars: |error| <= 2^-51
+    max(1, |log x|) for the logarithm (absolute near x = 1, where the near
+    sums need only absolute accuracy) and 2^-51 relative for 1/x."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rng = np.random.default_rng(3)
+    parts = [10.0 ** rng.uniform(-16, 3, 1 << 20)]
+    k = np.arange(1, 16)
+    parts += [1.0 + 10.0 ** -k, 1.0 - 10.0 ** -k, 1.0 + np.arange(1, 64) * 2.0 ** -52, 1.0 - np.arange(1, 64) * 2.0 ** -53]
+    e, j = np.meshgrid(np.arange(-20, 21), np.arange(128), indexing="ij")
+    b = np.ldexp(1.0 + j / 128.0, e).ravel()
+    parts += [b, np.nextafter(b, 0.0), np.nextafter(b, np.inf)]
+    x = torch.from_numpy(np.concatenate(parts)).cuda()
+    lg, inv = torch.empty_like(x), torch.empty_like(x)
+    bc._check(bc._load().bc_debug_log_inv(0, ctypes.c_void_p(x.data_ptr()), x.numel(), ctypes.c_void_p(lg.data_ptr()),
+                                         ctypes.c_void_p(inv.data_ptr()), None))
+    torch.cuda.synchronize()
+    ref_l, ref_i = torch.log(x), 1.0 / x
+    el = ((lg - ref_l).abs() / ref_l.abs().clamp(min=1.0)).max().item()
+    ei = ((inv - ref_i).abs() / ref_i.abs()).max().item()
+    print(f"table log: max error {el / 2.0 ** -53:.2f} units of 2^-53 (scaled); reciprocal {ei / 2.0 ** -53:.2f}")
+    assert el <= 2.0 ** -51 and ei <= 2.0 ** -51, (el, ei)
