@@ -382,6 +382,7 @@ struct FarLists {
     const int32_t *v_ptr = nullptr, *v_src = nullptr, *v_code = nullptr;   // per box
     const int32_t *x_ptr = nullptr, *x_src = nullptr;                        // per box
     const double2 *PX = nullptr;                                             // [n_x][P1]
+    const uint8_t *live = nullptr;   // [nbox] 1 where the subtree holds sources (null: every box)
 };
 cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTree &d, const DevTables &tb,
                               const FarLists &fl, cudaStream_t stream);
@@ -403,6 +404,7 @@ struct LayerDev {
     const int32_t *w_ptr = nullptr, *w_src = nullptr, *w_code = nullptr;
     const int32_t *n_ptr = nullptr, *n_src = nullptr;
     double2 *PX = nullptr;              // [nx][P1]
+    const uint8_t *live = nullptr;      // [nbox] 1 where the box's subtree holds sources
 };
 // u at every leaf node (device pointers: q [n], m [n][2] caller order, u [nleaf][NP]).
 // With split (tables and the tree's tiles), the L2P at every leaf runs as the

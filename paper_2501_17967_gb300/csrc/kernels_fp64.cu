@@ -165,7 +165,8 @@ inline size_t up_smem_bytes_f64(int NP, int P1, int T, int maxp)
 //           forward (P2M): OpA = Q^T, s = r^2;  adjoint (L2P^H): OpA = E^H, s = 1
 //           (OpA == nullptr: the leaf expansions are already in ex, split path)
 //   then level by level, deepest first, each parent once its children are
-//   published (per-box flags):
+//   published (per-box flags; a box whose subtree holds no point source, per
+//   the optional mask `live`, publishes a zero expansion at once):
 //   parent: ex[p][l] = sum_q sum_k Up_q[l][k] ex[child_q(p)][k]    (levels >= 2)
 //           forward: M2M; adjoint: L2L^H
 // Four warps per block: in the leaf step warp w sums over the w-th quarter of
@@ -187,7 +188,7 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
             const int32_t *__restrict__ box_child0, const double *__restrict__ vin,
             const double2 *__restrict__ OpA, const float4 *__restrict__ OpADF, DfSched us, ShiftFac uf, double2 *ex,
             float4 *exdf, int NP, int P1, const double *__restrict__ lvtab, bool climb, int32_t *flag,
-            const uint8_t *__restrict__ active, long long limit, int32_t *err)
+            const uint8_t *__restrict__ active, long long limit, int32_t *err, const uint8_t *__restrict__ live)
 {
     extern __shared__ double2 shu[];
     double2 *sc = shu;                                       // 4 * P1 children
@@ -300,6 +301,16 @@ k_up_levels(int64_t nleaf, const int32_t *__restrict__ order, const int32_t *__r
         for (int64_t p = level_start[lv] + blockIdx.x; p < level_start[lv + 1]; p += gridDim.x) {
             const int c0 = box_child0[p];
             if (c0 < 0) continue;   // a leaf (uniform over the block)
+            if (live && !live[p]) {
+                // no source below this box (point sources): its expansion is
+                // zero, with nothing to wait for
+                for (int i = threadIdx.x; i < P1; i += blockDim.x) {
+                    ex[int64_t(p) * P1 + i] = make_double2(0.0, 0.0);
+                    if (DF) exdf[int64_t(p) * P1 + i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                flag_publish(&flag[p], 1);
+                continue;
+            }
             // children computed in this launch: every child above the leaves,
             // and the leaves too when their expansions come from the leaf step
             if (threadIdx.x < 4) {
@@ -1565,7 +1576,7 @@ cudaError_t launch_apply(const PassArgs &a, const HostTree &h, const DevTree &d,
 #define BC_UP(A, D)                                                                                          \
     launch_pdl(k_up_levels<A, D>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box, d.leaf_level, \
                d.level_start, h.nlevels, d.box_child0, vin, opA, op.leafA_df, op.up_s, op.up_f, first, d.exdf, NP, \
-               P1, d.lvtab, climb, d.flag, d.leaf_active, glimit, a.err)
+               P1, d.lvtab, climb, d.flag, d.leaf_active, glimit, a.err, (const uint8_t *)nullptr)
         if (adj) ce = dfp ? BC_UP(true, true) : BC_UP(true, false);
         else ce = dfp ? BC_UP(false, true) : BC_UP(false, false);
 #undef BC_UP
@@ -1739,7 +1750,7 @@ cudaError_t launch_far_points(const PassArgs &a, const HostTree &h, const DevTre
         ce = launch_pdl(k_up_levels<false, false>, a.up_blocks, 128, shU, st, a.nleaf, d.leaf_order, d.leaf_box,
                         d.leaf_level, d.level_start, h.nlevels, d.box_child0, (const double *)nullptr,
                         (const double2 *)nullptr, op.leafA_df, op.up_s, op.up_f, d.expA, d.exdf, NP, P1, d.lvtab,
-                        true, d.flag, (const uint8_t *)nullptr, glimit, a.err);
+                        true, d.flag, (const uint8_t *)nullptr, glimit, a.err, fl.live);
         if (ce != cudaSuccess) return ce;
     }
     {

@@ -359,6 +359,7 @@ cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d,
     FarLists fl;
     fl.v_ptr = ly.v_ptr; fl.v_src = ly.v_src; fl.v_code = ly.v_code;
     fl.x_ptr = ly.x_ptr; fl.x_src = ly.x_src; fl.PX = ly.PX;
+    fl.live = ly.live;
     if ((e = launch_far_points(a, h, d, tb, fl, st)) != cudaSuccess) return e;
     const double *PE = nullptr;
     if (split) {

@@ -183,6 +183,11 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
     if (e == cudaSuccess) e = upload(L->allocs, &p_n_ptr, n_ptr.data(), n_ptr.size());
     if (e == cudaSuccess) e = upload(L->allocs, &p_n_src, n_src.data(), n_src.size());
     if (e == cudaSuccess) e = upload<double2>(L->allocs, &d.PX, nullptr, x_src.size() * size_t(ctx->P1));
+    // boxes whose subtree holds sources (the climb gives the others zero)
+    std::vector<uint8_t> live(nbox);
+    for (size_t b = 0; b < nbox; b++) live[b] = cnt[b] > 0 ? 1 : 0;
+    uint8_t *p_live = nullptr;
+    if (e == cudaSuccess) e = upload(L->allocs, &p_live, live.data(), live.size());
     if (e != cudaSuccess) {
         release(L->allocs);
         delete L;
@@ -193,6 +198,7 @@ bc_status bc_layer_create(bc_tree *tree, const double *xy, int64_t n, bc_layer *
     d.x_ptr = p_x_ptr; d.x_src = p_x_src; d.x_box = p_x_box;
     d.w_ptr = p_w_ptr; d.w_src = p_w_src; d.w_code = p_w_code;
     d.n_ptr = p_n_ptr; d.n_src = p_n_src;
+    d.live = p_live;
     *out = L;
     return BC_OK;
 }
