@@ -44,18 +44,6 @@ __device__ __forceinline__ double2 cinv(double2 a)
     const double d = 1.0 / fma(a.x, a.x, a.y * a.y);
     return make_double2(a.x * d, -a.y * d);
 }
-// a^n (n >= 0) by binary powering
-__device__ __forceinline__ double2 cpow(double2 a, int n)
-{
-    double2 r = make_double2(1.0, 0.0);
-    while (n > 0) {
-        if (n & 1) r = cmul(r, a);
-        a = cmul(a, a);
-        n >>= 1;
-    }
-    return r;
-}
-
 // ---------------------------------------------------------------------------
 // log x and 1/x for the direct near sums, written for this GPU's FP64 rate
 // (1/64 of FP32): a table-driven logarithm after Tang (ACM TOMS 16, 1990).
@@ -131,47 +119,82 @@ __global__ void k_layer_gather(int64_t n, const int32_t *__restrict__ perm, cons
     }
 }
 
-// P2M: one warp per leaf, lane k its coefficient; every leaf box is written
-// (zero without sources: the climb reads all children)
-__global__ void k_layer_p2m(int64_t nleaf, const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy,
-                            const double *__restrict__ cq, const double2 *__restrict__ cm,
-                            const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_level,
-                            const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy, double x0,
-                            double y0, double L, int P1, double2 *__restrict__ ex)
+// Sum over the warp of each coefficient k < P1 (butterfly, the same order on
+// every lane); lane k writes coefficient k to out[k].
+template <int PMAX>
+__device__ __forceinline__ void warp_sum_store(double2 (&acc)[PMAX], int P1, int lane, double2 *__restrict__ out)
+{
+#pragma unroll
+    for (int k = 0; k < PMAX; k++) {
+        if (k < P1) {   // uniform over the warp
+            double re = acc[k].x, im = acc[k].y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == k) out[k] = make_double2(re, im);
+        }
+    }
+}
+
+// P2M: one warp per leaf, lane s the sources s, s + 32, ... of the leaf; each
+// lane carries eta^k up the coefficients (one complex multiplication per
+// term), then the warp sums each coefficient.  Every leaf box is written
+// (zero without sources: the climb reads all children).  P1 <= PMAX.
+template <int PMAX>
+__global__ void __launch_bounds__(128)
+k_layer_p2m(int64_t nleaf, const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy,
+            const double *__restrict__ cq, const double2 *__restrict__ cm, const int32_t *__restrict__ leaf_box,
+            const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_ix,
+            const int32_t *__restrict__ box_iy, double x0, double y0, double L, int P1, double2 *__restrict__ ex)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
     for (int64_t leaf = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); leaf < nleaf; leaf += nw) {
         const int b = leaf_box[leaf];
+        const int j0 = src_ptr[leaf], j1 = src_ptr[leaf + 1];
+        if (j0 == j1) {   // most leaves: no source, no sums to form (uniform over the warp)
+            for (int k = lane; k < P1; k += 32) ex[int64_t(b) * P1 + k] = make_double2(0.0, 0.0);
+            continue;
+        }
         const BoxGeom g = box_geom(b, box_level, box_ix, box_iy, x0, y0, L);
         const double ir = 1.0 / g.r;
-        double2 acc = make_double2(0.0, 0.0);
-        const int k = lane;
-        const double ik = k > 0 ? 1.0 / k : 0.0;
-        for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
+        double2 acc[PMAX];
+#pragma unroll
+        for (int k = 0; k < PMAX; k++) acc[k] = make_double2(0.0, 0.0);
+        for (int j = j0 + lane; j < j1; j += 32) {
             const double2 y = sxy[j];
             const double2 eta = make_double2((y.x - g.cx) * ir, (y.y - g.cy) * ir);
             const double c = cq[j];
-            if (k == 0) {
-                acc.x += c;
-            } else if (k < P1) {
-                const double2 e1 = cpow(eta, k - 1), ek = cmul(e1, eta);
-                const double2 d = cmul(make_double2(cm[j].x * ir, cm[j].y * ir), e1);
-                acc.x += fma(-c * ik, ek.x, d.x);
-                acc.y += fma(-c * ik, ek.y, d.y);
+            const double2 cmr = make_double2(cm[j].x * ir, cm[j].y * ir);   // c_m / r
+            acc[0].x += c;
+            double2 pw = make_double2(1.0, 0.0);   // eta^(k-1)
+#pragma unroll
+            for (int k = 1; k < PMAX; k++) {
+                if (k < P1) {
+                    const double2 d = cmul(cmr, pw);
+                    pw = cmul(pw, eta);
+                    const double ck = -c * (1.0 / double(k));
+                    acc[k].x += fma(ck, pw.x, d.x);
+                    acc[k].y += fma(ck, pw.y, d.y);
+                }
             }
         }
-        if (k < P1) ex[int64_t(b) * P1 + k] = acc;
+        warp_sum_store(acc, P1, lane, ex + int64_t(b) * P1);
     }
 }
 
-// P2L of the X list: one warp per entry, lane l its coefficient
-__global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__restrict__ x_src,
-                            const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy,
-                            const double *__restrict__ cq, const double2 *__restrict__ cm,
-                            const int32_t *__restrict__ leaf_box, const int32_t *__restrict__ box_level,
-                            const int32_t *__restrict__ box_ix, const int32_t *__restrict__ box_iy, double x0,
-                            double y0, double L, int P1, double2 *__restrict__ PX)
+// P2L of the X list: one warp per entry, lane s the sources s, s + 32, ... of
+// the source leaf; each lane carries t^l = (-1/(2w))^l up the coefficients,
+// then the warp sums each coefficient.  P1 <= PMAX.
+template <int PMAX>
+__global__ void __launch_bounds__(128)
+k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const int32_t *__restrict__ x_src,
+            const int32_t *__restrict__ src_ptr, const double2 *__restrict__ sxy, const double *__restrict__ cq,
+            const double2 *__restrict__ cm, const int32_t *__restrict__ leaf_box,
+            const int32_t *__restrict__ box_level, const int32_t *__restrict__ box_ix,
+            const int32_t *__restrict__ box_iy, double x0, double y0, double L, int P1, double2 *__restrict__ PX)
 {
     const int lane = threadIdx.x & 31;
     const int64_t nw = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -181,28 +204,30 @@ __global__ void k_layer_p2l(int64_t nx, const int32_t *__restrict__ x_box, const
         const BoxGeom gb = box_geom(x_box[x], box_level, box_ix, box_iy, x0, y0, L);
         const double ir = 1.0 / gc.r;
         const double2 e = make_double2((gb.cx - gc.cx) * ir, (gb.cy - gc.cy) * ir);
-        const int l = lane;
-        const double il = l > 0 ? 1.0 / l : 0.0;
-        double2 acc = make_double2(0.0, 0.0);
-        for (int j = src_ptr[leaf]; j < src_ptr[leaf + 1]; j++) {
+        double2 acc[PMAX];
+#pragma unroll
+        for (int l = 0; l < PMAX; l++) acc[l] = make_double2(0.0, 0.0);
+        for (int j = src_ptr[leaf] + lane; j < src_ptr[leaf + 1]; j += 32) {
             const double2 y = sxy[j];
             const double2 w = make_double2(e.x - (y.x - gc.cx) * ir, e.y - (y.y - gc.cy) * ir);
             const double2 iw = cinv(w);
             const double2 dm = cmul(make_double2(cm[j].x * ir, cm[j].y * ir), iw);   // (c_m / r_c) / w
             const double c = cq[j];
-            if (l == 0) {
-                acc.x += fma(c, 0.5 * log(fma(w.x, w.x, w.y * w.y)), dm.x);
-                acc.y += dm.y;
-            } else if (l < P1) {
-                double2 t = cpow(make_double2(0.5 * iw.x, 0.5 * iw.y), l);   // (2w)^-l
-                if (l & 1) t = make_double2(-t.x, -t.y);
-                const double2 s = make_double2(dm.x - c * il, dm.y);
-                const double2 v = cmul(t, s);
-                acc.x += v.x;
-                acc.y += v.y;
+            acc[0].x += fma(c, 0.5 * log(fma(w.x, w.x, w.y * w.y)), dm.x);
+            acc[0].y += dm.y;
+            const double2 t = make_double2(-0.5 * iw.x, -0.5 * iw.y);   // -1 / (2w)
+            double2 pw = make_double2(1.0, 0.0);
+#pragma unroll
+            for (int l = 1; l < PMAX; l++) {
+                if (l < P1) {
+                    pw = cmul(pw, t);
+                    const double2 v = cmul(pw, make_double2(dm.x - c * (1.0 / double(l)), dm.y));
+                    acc[l].x += v.x;
+                    acc[l].y += v.y;
+                }
             }
         }
-        if (l < P1) PX[x * P1 + l] = acc;
+        warp_sum_store(acc, P1, lane, PX + x * P1);
     }
 }
 
@@ -346,12 +371,12 @@ cudaError_t launch_layer(const PassArgs &a, const HostTree &h, const DevTree &d,
         k_layer_gather<<<grid_cap((ly.n + 255) / 256, 152 * 8), 256, 0, st>>>(ly.n, ly.perm, q, m, ly.cq, ly.cm);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_layer_p2m<<<grid_cap((a.nleaf + 3) / 4, 152 * 8), 128, 0, st>>>(
+    k_layer_p2m<32><<<grid_cap((a.nleaf + 3) / 4, 152 * 8), 128, 0, st>>>(
         a.nleaf, ly.src_ptr, ly.sxy, ly.cq, ly.cm, d.leaf_box, d.box_level, d.box_ix, d.box_iy, h.x0, h.y0, h.L, P1,
         d.expA);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ly.nx > 0) {
-        k_layer_p2l<<<grid_cap((ly.nx + 3) / 4, 152 * 8), 128, 0, st>>>(
+        k_layer_p2l<32><<<grid_cap((ly.nx + 3) / 4, 152 * 8), 128, 0, st>>>(
             ly.nx, ly.x_box, ly.x_src, ly.src_ptr, ly.sxy, ly.cq, ly.cm, d.leaf_box, d.box_level, d.box_ix, d.box_iy,
             h.x0, h.y0, h.L, P1, ly.PX);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
