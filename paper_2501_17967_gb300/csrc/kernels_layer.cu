@@ -21,7 +21,8 @@
 //        L_l = sum (-1)^l (2w)^-l [ -c_q / l + (c_m / r_c) / w ]
 //   M2P  (W list) and L2P as for the volume potential, near field direct;
 // with c_q = -q / (2 pi), c_m = -m / (2 pi).  A source that coincides with a
-// target node contributes nothing.  FP64 throughout.
+// target node contributes nothing.  FP64 throughout, except the split option's
+// L2P (the volume apply's group-E tensor tiles over the same locals).
 #include <cuda_runtime.h>
 
 #include <algorithm>
